@@ -1,0 +1,422 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by
+mathematics (closed forms, invariants, library routines, brute force).
+
+Each pin is chosen so that a plausible slip in the oracle (a dropped term, a
+wrong sign, a transposed operand, a wrong node ordering) fails it."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import dg_oracle as O
+from paper_2605_29598_gb300 import inputs as I
+
+
+# ----------------------------------------------------------------------------
+# time integrator (Section 3, Butcher tableau)
+# ----------------------------------------------------------------------------
+
+def test_tableau_order_conditions():
+    a, at, b, c = O.ark2_tableau()
+    assert abs(O.CHI - (2 - math.sqrt(2))) < 1e-16
+    for A in (a, at):
+        assert np.allclose(A.sum(axis=1), c, atol=1e-15)       # row sums = c
+    assert abs(b.sum() - 1.0) < 1e-15                          # first order
+    assert abs(b @ c - 0.5) < 1e-15                            # second order (fixes chi)
+    assert np.allclose(at[2], b, atol=0)                       # stiffly accurate
+    assert abs(at[1, 1] - at[2, 2]) == 0                       # singly diagonal
+    # IMEX coupling conditions of order 2 with b = bt, c = ct
+    assert abs(b @ (a @ np.ones(3)) - 0.5) < 1e-15
+    assert abs(b @ (at @ np.ones(3)) - 0.5) < 1e-15
+
+
+def ark2_amplification(z):
+    """Stability function of the implicit tableau for y' = lambda y, z = lambda dt."""
+    _, at, b, _ = O.ark2_tableau()
+    y1 = 1.0
+    y2 = (1 + at[1, 0] * z * y1) / (1 - at[1, 1] * z)
+    y3 = (1 + at[2, 0] * z * y1 + at[2, 1] * z * y2) / (1 - at[2, 2] * z)
+    return 1 + z * (b[0] * y1 + b[1] * y2 + b[2] * y3)
+
+
+def test_tableau_l_stability_and_order():
+    # L-stable: R(z) -> 0 like 1/z as z -> -infinity
+    assert abs(ark2_amplification(-1e6)) < 1e-4
+    assert abs(ark2_amplification(-1e6)) < 0.2 * abs(ark2_amplification(-1e5))
+    for z in (1e-2, 1e-2j, -1e-2 + 5e-3j):
+        # error of the stability function vs exp(z) is O(z^3)
+        assert abs(ark2_amplification(z) - np.exp(z)) < 0.2 * abs(z) ** 3
+
+
+# ----------------------------------------------------------------------------
+# bases and quadrature
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [2, 3, 4, 5])
+def test_basis_and_quadrature(n):
+    x, w = O.gauss_legendre01(n)
+    for k in range(2 * n):                                     # exact to degree 2n-1
+        assert abs(w @ x ** k - 1.0 / (k + 1)) < 1e-14
+    for nodes in (x, O.gauss_lobatto01(n)):
+        assert np.allclose(O.lagrange(nodes, nodes), np.eye(n), atol=1e-14)
+        t = np.linspace(-0.2, 1.3, 7)
+        for k in range(n):                                     # reproduces P_{n-1}
+            assert np.allclose(O.lagrange(nodes, t) @ nodes ** k, t ** k, atol=1e-12)
+            dk = k * t ** (k - 1) if k else 0 * t
+            assert np.allclose(O.dlagrange(nodes, t) @ nodes ** k, dk, atol=1e-11)
+    gll = O.gauss_lobatto01(n)
+    assert gll[0] == 0.0 and gll[-1] == 1.0
+
+
+# ----------------------------------------------------------------------------
+# explicit operator
+# ----------------------------------------------------------------------------
+
+def _refine_corner(d):
+    return lambda c: 1 if all(ci < 1.6 for ci in c) else 0
+
+
+def _poly_state(disc, rng, u):
+    d = disc.d
+    X = disc.node_points()
+    coef = rng.uniform(-1, 1, (disc.r + 1,) * d) * 0.05
+
+    def val(X):
+        v = np.ones(X.shape[:-1])
+        for idx in np.ndindex(*coef.shape):
+            t = coef[idx] * np.ones(X.shape[:-1])
+            for a in range(d):
+                t = t * X[..., a] ** idx[a]
+            v = v + t
+        return v
+
+    def grad(X):
+        g = np.zeros(X.shape)
+        for idx in np.ndindex(*coef.shape):
+            for b in range(d):
+                if idx[b] == 0:
+                    continue
+                t = coef[idx] * idx[b] * np.ones(X.shape[:-1])
+                for a in range(d):
+                    t = t * X[..., a] ** (idx[a] - 1 if a == b else idx[a])
+                g[..., b] += t
+        return g
+
+    rho = val(X)
+    q = np.zeros((5,) + rho.shape)
+    q[0] = rho
+    for c in range(3):
+        q[1 + c] = rho * u[c]
+    q[4] = 2.0 / 0.4 + 0.5 * rho * (u @ u)
+    ugr = sum(u[c] * grad(X)[..., b] for b, c in enumerate(disc.comp))
+    return q, ugr
+
+
+@pytest.mark.parametrize("d,r,refine,nodes", [
+    (2, 1, False, "gl"), (2, 3, False, "gl"), (2, 2, True, "gl"), (2, 3, True, "gll"),
+    (3, 1, True, "gl"), (3, 2, False, "gll"), (3, 3, True, "gl")])
+def test_polynomial_exactness(d, r, refine, nodes):
+    """Affine cells, rho in Q_r continuous, constant u and p: the non-stiff
+    rates equal -(u.grad rho)(1, u, kappa) at the nodes and the stiff rates
+    vanish (g = f = 0), on every cell with no wall face.  Pins cell terms,
+    conforming and hanging face traces, normals and the lift."""
+    cells = (4,) * d
+    mesh = I.box_mesh(cells, (4.0,) * d, periodic=[False] * d,
+                      refine_level=_refine_corner(d) if refine else None)
+    if refine:
+        assert len(mesh.hang_faces) > 0
+    disc = O.Discretisation(mesh, r, nodes)
+    u = np.array([0.3, -0.2, 0.5])
+    q, ugr = _poly_state(disc, np.random.default_rng(3), u)
+    Fns, Fs = O.explicit_rates(disc, q, O.Phys(f=0.0, g=0.0))
+    inner = np.setdiff1d(np.arange(disc.E), mesh.bdry_faces[:, 0])
+    exp = np.stack([-ugr] + [-ugr * u[c] for c in range(3)] + [-ugr * 0.5 * (u @ u)])
+    assert np.abs(Fns[:, inner] - exp[:, inner]).max() < 1e-11
+    assert np.abs(Fs[:, inner]).max() < 1e-10
+
+
+def _random_state(disc, rng, wind=(5.0, 2.0, 1.0)):
+    X = disc.node_points()
+    q = I.stratified_state(X, wind=wind)
+    return I.perturb(q, rng, rel=1e-2)
+
+
+@pytest.mark.parametrize("d,refine,hill", [(2, False, False), (2, True, False),
+                                           (3, True, True)])
+def test_conservation(d, refine, hill):
+    """Periodic horizontally, walls in z: total mass is conserved by the
+    explicit operator, total energy too when g = 0 (Coriolis does no work)."""
+    cells = (6, 3) if d == 2 else (4, 4, 3)
+    ext = (6e3, 3e3) if d == 2 else (4e3, 4e3, 3e3)
+    hl = dict(h0=200.0, a_c=1e3, xc=2e3, yc=2e3) if hill else None
+    rl = (lambda c: 1 if c[0] < 2e3 else 0) if refine else None
+    mesh = I.box_mesh(cells, ext, hill=hl, refine_level=rl)
+    disc = O.Discretisation(mesh, 2)
+    q = _random_state(disc, np.random.default_rng(7))
+    r_ns, r_s = O.explicit_residuals(disc, q, O.Phys(f=1e-4, g=0.0))
+    scale = np.abs(r_ns[0]).sum()
+    assert abs(r_ns[0].sum()) < 1e-13 * scale
+    assert abs(r_s[0]).max() == 0.0
+    e_tot = (r_ns[4] + r_s[4]).sum()
+    assert abs(e_tot) < 1e-12 * (np.abs(r_ns[4]).sum() + np.abs(r_s[4]).sum())
+
+
+def test_free_stream_and_closed_cells():
+    """Uniform state with wind tangent to the walls gives zero rates on a
+    terrain-following mesh; the area-weighted normals of every cell sum to
+    zero (closed surfaces), including 2:1 faces."""
+    mesh = I.box_mesh((4, 4, 3), (4e3, 4e3, 3e3),
+                      hill=dict(h0=300.0, a_c=1e3, xc=2e3, yc=2e3),
+                      refine_level=lambda c: 1 if c[0] < 2e3 else 0)
+    disc = O.Discretisation(mesh, 2)
+    tot = np.zeros((disc.E, 3))
+    np.add.at(tot, disc.f_em, disc.f_nS.sum(axis=1))
+    inner = ~disc.f_wall
+    np.add.at(tot, disc.f_ep[inner], -disc.f_nS[inner].sum(axis=1))
+    assert np.abs(tot).max() < 1e-8 * np.abs(disc.f_nS).max()
+    q = np.zeros((5, disc.E, disc.Np))
+    q[0] = 1.2
+    q[1] = 1.2 * 10.0
+    q[2] = 1.2 * 4.0
+    q[4] = 1e5 / 0.4 + 0.5 * 1.2 * 116.0
+    # walls only at z; the hill makes the bottom wall tilt, so use a flat mesh
+    flat = I.box_mesh((4, 4, 3), (4e3, 4e3, 3e3),
+                      refine_level=lambda c: 1 if c[0] < 2e3 else 0)
+    dflat = O.Discretisation(flat, 2)
+    qf = q[:, :dflat.E]
+    Fns, Fs = O.explicit_rates(dflat, qf, O.Phys(f=0.0, g=0.0))
+    assert np.abs(Fns).max() < 1e-9 and np.abs(Fs).max() < 1e-9
+
+
+# ----------------------------------------------------------------------------
+# implicit operators (Section 3, Schur systems and the (A+R)^{-1} factorisation)
+# ----------------------------------------------------------------------------
+
+def _stage(disc, rng, adt=2.0):
+    q = _random_state(disc, rng)
+    u, p = O.nodal_primitives(q, 1.4)
+    return O.StageCoeffs(rho=q[0], p_lag=p, u_lag=u, adt=adt), q
+
+
+@pytest.mark.parametrize("nodes", ["gl", "gll"])
+def test_rotation_closed_form(nodes):
+    """R is energy-neutral, R = beta A J, and (A+R)^{-1} equals the
+    closed-form (I + beta J)^{-1} A^{-1} (the oracle itself uses a dense LU
+    of the full cell block)."""
+    mesh = I.box_mesh((3, 2, 2), (3e3, 2e3, 2e3))
+    disc = O.Discretisation(mesh, 2, nodes)
+    rng = np.random.default_rng(11)
+    cf, _ = _stage(disc, rng)
+    f = 1.3e-4
+    u = rng.standard_normal((3, disc.E, disc.Np))
+    Ru = O.op_R(disc, cf, u, f)
+    assert abs(np.sum(u * Ru)) < 1e-14 * np.sum(np.abs(u * O.op_A(disc, cf, u)))
+    beta = cf.adt * f
+    Jmat = np.array([[0, -1, 0], [1, 0, 0], [0, 0, 0]], float)
+    # R = beta A J
+    Ju = np.einsum("ab,bei->aei", Jmat, u)
+    assert np.allclose(Ru, beta * O.op_A(disc, cf, Ju), atol=1e-12 * np.abs(Ru).max())
+    rhs = rng.standard_normal((3, disc.E, disc.Np))
+    x = O.solve_AR(disc, cf, f, rhs, with_R=True)
+    Ainv = O.solve_AR(disc, cf, f, rhs, with_R=False)
+    inv = np.array([[1, beta, 0], [-beta, 1, 0], [0, 0, 1 + beta ** 2]]) / (1 + beta ** 2)
+    cf_form = np.einsum("ab,bei->aei", inv, Ainv)
+    assert np.allclose(x, cf_form, rtol=1e-12, atol=1e-14 * np.abs(x).max())
+
+
+def _dense(op, n_in, shape_in):
+    cols = []
+    for k in range(n_in):
+        e = np.zeros(n_in)
+        e[k] = 1.0
+        cols.append(op(e.reshape(shape_in)).reshape(-1))
+    return np.array(cols).T
+
+
+@pytest.mark.parametrize("d,refine", [(2, False), (2, True), (3, True)])
+def test_adjointness_and_spd(d, refine):
+    """With h rho = 1 on affine cells C = -B^T exactly (the quadrature is
+    exact for phi . grad psi), so the R1 Schur operator without the
+    penalty, D + B^T A^{-1} B, is symmetric positive definite."""
+    cells = (3, 2) if d == 2 else (2, 2, 2)
+    rl = (lambda c: 1 if c[0] < 1.0 else 0) if refine else None
+    mesh = I.box_mesh(cells, tuple(float(c) for c in cells), refine_level=rl)
+    disc = O.Discretisation(mesh, 1 if d == 3 else 2)
+    rng = np.random.default_rng(5)
+    gm = 1.4
+    cf = O.StageCoeffs(rho=1.0 + 0.1 * rng.uniform(size=(disc.E, disc.Np)),
+                       p_lag=np.full((disc.E, disc.Np), (gm - 1) / gm),
+                       u_lag=rng.standard_normal((3, disc.E, disc.Np)), adt=0.7)
+    n_p = disc.E * disc.Np
+    B = _dense(lambda x: O.op_B(disc, cf, x), n_p, (disc.E, disc.Np))
+    C = _dense(lambda u: O.op_C(disc, cf, u, gm), 3 * n_p, (3, disc.E, disc.Np))
+    assert np.abs(C + B.T).max() < 1e-13 * np.abs(B).max()
+    ph = O.Phys(variant="R1", penalty=False)
+    S = _dense(lambda x: O.schur_apply(disc, cf, ph, x), n_p, (disc.E, disc.Np))
+    Dm = _dense(lambda x: O.op_D(disc, x, gm), n_p, (disc.E, disc.Np))
+    Sw = Dm @ S                                  # unscaled S = D (D^{-1} S)
+    assert np.abs(Sw - Sw.T).max() < 1e-12 * np.abs(Sw).max()
+    assert np.linalg.eigvalsh(0.5 * (Sw + Sw.T)).min() > 0
+
+
+@pytest.mark.parametrize("variant", ["R1", "R2"])
+def test_schur_solution_solves_coupled_system(variant):
+    """The pressure from the Schur system and the recovered velocity satisfy
+    the undecomposed coupled system (eq. matrix_form) with the terms that
+    the variant lags held at the lagged iterate.  Pins the signs of every
+    term of the Schur operator, its right-hand side and the recovery."""
+    mesh = I.box_mesh((4, 3), (4e3, 3e3), refine_level=lambda c: 1 if c[0] < 1e3 else 0)
+    disc = O.Discretisation(mesh, 2)
+    rng = np.random.default_rng(21)
+    cf, q = _stage(disc, rng, adt=3.0)
+    ph = O.Phys(variant=variant, f=1.2e-4)
+    gm = ph.gamma
+    f_w = O.op_A(disc, cf, q[1:4] / q[0]) * (1 + 1e-3 * rng.standard_normal(q[1:4].shape))
+    g_w = disc.vol_weak(disc.at_quad(q[4])) * (1 + 1e-4 * rng.standard_normal(q[4].shape))
+    rhs = O.schur_rhs(disc, cf, ph, f_w, g_w)
+    p, its, rr, ok = O.gmres(lambda x: O.schur_apply(disc, cf, ph, x), rhs, cf.p_lag,
+                             rtol=1e-13, restart=40, maxit=400)
+    assert ok
+    u = O.recover_velocity(disc, cf, ph, f_w, p)
+    fg = O.vec_fg(disc, cf, ph.g)
+    kv = O.vec_k(disc, cf, cf.u_lag)
+    if variant == "R2":
+        mom = O.op_A(disc, cf, u) + O.op_R(disc, cf, u, ph.f) + O.op_B(disc, cf, p) + fg
+        ene = (O.op_C(disc, cf, u, gm) + O.op_Mg(disc, cf, u, ph.g) + O.op_D(disc, p, gm)
+               + O.op_P(disc, cf, p, gm) + kv)
+    else:
+        mom = (O.op_A(disc, cf, u) + O.op_R(disc, cf, cf.u_lag, ph.f)
+               + O.op_B(disc, cf, p) + fg)
+        ene = (O.op_C(disc, cf, u, gm) + O.op_Mg(disc, cf, cf.u_lag, ph.g)
+               + O.op_D(disc, p, gm) + O.op_P(disc, cf, p, gm) + kv)
+    assert np.abs(mom - f_w).max() < 1e-9 * np.abs(f_w).max()
+    assert np.abs(ene - g_w).max() < 1e-9 * np.abs(g_w).max()
+
+
+def test_gmres_matches_dense_solve():
+    rng = np.random.default_rng(2)
+    n = 60
+    A = np.eye(n) + 0.3 * rng.standard_normal((n, n)) / math.sqrt(n)
+    b = rng.standard_normal(n)
+    x, its, rr, ok = O.gmres(lambda v: A @ v, b, np.zeros(n), rtol=1e-13, restart=10,
+                             maxit=500)
+    assert ok and rr <= 1e-13
+    assert np.allclose(x, np.linalg.solve(A, b), rtol=1e-11, atol=1e-12)
+
+
+# ----------------------------------------------------------------------------
+# whole step
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("variant", ["R1", "R2"])
+def test_inertial_oscillation_closed_form(variant):
+    """Uniform state, g = 0, f != 0: every spatial term vanishes and
+    u + i v is multiplied by the ARK2 stability function at z = -i f dt per
+    step.  R2 holds the Coriolis term implicitly (one Picard iteration is
+    exact); R1 lags it and reaches the same value once Picard converges."""
+    # 100 km cells keep the acoustic Courant number (and so the conditioning
+    # of the Schur system) moderate at dt = 600 s
+    mesh = I.box_mesh((3, 2), (300e3, 200e3), periodic=[True, True])
+    disc = O.Discretisation(mesh, 2)
+    f, dt, U = 1e-4, 600.0, 10.0
+    q = np.zeros((5, disc.E, disc.Np))
+    q[0] = 1.1
+    q[1] = 1.1 * U
+    q[4] = 1e5 / 0.4 + 0.5 * 1.1 * U * U
+    ph = O.Phys(f=f, g=0.0, variant=variant)
+    opts = O.StepOpts(picard_rtol=1e-13, picard_maxit=30, gmres_rtol=1e-13,
+                      gmres_maxit=100)
+    steps = 4
+    for _ in range(steps):
+        q = O.imex_ark2_step(disc, ph, q, dt, opts)
+    amp = ark2_amplification(-1j * f * dt) ** steps
+    exact = U * amp
+    got = (q[1] + 1j * q[2]) / q[0]
+    # tolerance: GMRES stops at 1e-13 relative residual on p ~ 1e5 Pa
+    assert np.abs(got - exact).max() < 1e-10 * U
+
+
+def test_balanced_rest_state():
+    """Discretely balanced background (READING c11): rho = -(G_z p)/g from
+    the discrete weak vertical gradient of p.  With u = 0 and f != 0 the
+    scheme keeps u = 0 up to the GMRES tolerance (rtol 1e-12 on p ~ 1e5 Pa
+    bounds |u| near 1e-10 m/s; the continuous, non-balanced profile leaves
+    |u| ~ 1e-4 m/s), so the Schur right-hand side is consistent with p_bar."""
+    mesh = I.box_mesh((6, 4), (60e3, 8e3))
+    disc = O.Discretisation(mesh, 2)
+    X = disc.node_points()
+    _, pbar, _, _ = I.exner_background(X[..., -1], 300.0, 0.01)
+    gm, g = 1.4, 9.81
+    cf = O.StageCoeffs(rho=np.ones_like(pbar), p_lag=pbar, u_lag=np.zeros((3,) + pbar.shape),
+                       adt=1.0)
+    Gp = disc.mass_solve(O.op_B(disc, cf, pbar))                # = grad p (weak)
+    rho = -Gp[2] / g
+    assert np.abs(Gp[0]).max() < 1e-9 * np.abs(Gp[2]).max()
+    q = np.zeros((5,) + pbar.shape)
+    q[0] = rho
+    q[4] = pbar / (gm - 1)
+    ph = O.Phys(f=1e-4, g=g)
+    opts = O.StepOpts(picard_fixed=2, gmres_rtol=1e-12)
+    for _ in range(3):
+        q = O.imex_ark2_step(disc, ph, q, 10.0, opts)
+    u = q[1:4] / q[0]
+    assert np.abs(u).max() < 2e-9
+    assert np.abs(q[0] - rho).max() < 1e-11 * rho.max()
+
+
+def test_dof_counts_of_the_paper_meshes():
+    """4800 cells of degree 4 give 6e5 values per scalar field (Section 4.3)."""
+    mesh = I.box_mesh((30, 20, 8), (60e3, 40e3, 16e3))
+    assert mesh.n_elem * 5 ** 3 == 600_000
+    assert 1594 * 5 ** 3 == 199_250
+
+
+# ----------------------------------------------------------------------------
+# convergence orders on a linear rotating acoustic-inertia plane wave
+# ----------------------------------------------------------------------------
+
+def _plane_wave(X, t, k, m, f, rho0=1.2, p0=1e5, eps=1e-4, gm=1.4):
+    """Exact plane wave of the vertical-slice equations linearised about a
+    uniform rest state with g = 0 (eq. vertical_slice):
+    Omega^4 - Omega^2 (f^2 + c^2 (k^2 + m^2)) + c^2 m^2 f^2 = 0,
+    u = k Omega p' / (rho0 (Omega^2 - f^2)), v = -i f u / Omega,
+    w = m p' / (rho0 Omega), rho' = p' / c^2."""
+    c2 = gm * p0 / rho0
+    a = f * f + c2 * (k * k + m * m)
+    om = math.sqrt((a + math.sqrt(a * a - 4 * c2 * m * m * f * f)) / 2)
+    P = eps * p0 * np.exp(1j * (k * X[..., 0] + m * X[..., 1] - om * t))
+    uA = k * om / (rho0 * (om * om - f * f))
+    u = np.real(uA * P)
+    v = np.real(-1j * f * uA / om * P)
+    w = np.real(m / (rho0 * om) * P)
+    rho = rho0 + np.real(P) / c2
+    p = p0 + np.real(P)
+    return np.stack([rho, rho * u, rho * v, rho * w,
+                     p / (gm - 1) + 0.5 * rho * (u * u + v * v + w * w)])
+
+
+def _wave_error(n, r, dt, T, L=10e3, f=0.05):
+    mesh = I.box_mesh((n, n), (L, L), periodic=[True, True])
+    disc = O.Discretisation(mesh, r)
+    X = disc.node_points()
+    k = m = 2 * math.pi / L
+    q = _plane_wave(X, 0.0, k, m, f)
+    ph = O.Phys(f=f, g=0.0)
+    opts = O.StepOpts(picard_fixed=2, gmres_rtol=1e-12, gmres_maxit=200)
+    steps = int(round(T / dt))
+    for _ in range(steps):
+        q = O.imex_ark2_step(disc, ph, q, dt, opts)
+    _, pe = O.nodal_primitives(_plane_wave(X, steps * dt, k, m, f), 1.4)
+    _, pn = O.nodal_primitives(q, 1.4)
+    return np.sqrt(np.mean((pn - pe) ** 2))
+
+
+def test_convergence_orders():
+    """Spatial order r + 1 (r = 2, tiny dt) and temporal order 2 (r = 4 on a
+    fixed mesh, dt halved) of the whole IMEX-DG step."""
+    es = [_wave_error(n, 2, 0.01, 0.5) for n in (3, 6, 12)]
+    eoc_x = [math.log2(es[i] / es[i + 1]) for i in range(2)]
+    assert all(2.8 < e < 3.3 for e in eoc_x), eoc_x
+    et = [_wave_error(6, 4, dt, 8.0) for dt in (2.0, 1.0, 0.5)]
+    eoc_t = [math.log2(et[i] / et[i + 1]) for i in range(2)]
+    assert all(1.9 < e < 2.1 for e in eoc_t), eoc_t
