@@ -1,0 +1,212 @@
+/*
+ * dgimex.h -- C ABI of the GB300 (sm_103a) hot path of a rotating IMEX-DG
+ * solver for the compressible Euler equations on quad/hex meshes with 2:1
+ * hanging faces (Bottani, Benacchio, Orlando, Bonaventura, Engsig-Karup:
+ * "An IMEX-DG solver with non-conforming mesh refinement for atmospheric
+ * dynamics with rotation").
+ *
+ * Discretisation (Section 3): nodal DG on (r+1)^d Gauss-Legendre points per
+ * cell (collocated with the quadrature), Rusanov flux with
+ * lambda = max(|u-.n|, |u+.n|) for advection, centred fluxes for pressure
+ * and enthalpy, ARK2 IMEX stepping (TR-BDF2 implicit tableau,
+ * chi = 2 - sqrt 2, a32 = 1/2), Picard iteration over the Schur complement
+ * of the momentum/energy system (strategies R1 and R2), GMRES on the
+ * pressure system, (A+R)^{-1} = (I + beta J)^{-1} A^{-1} with the closed-form
+ * 3x3 inverse (Section 3.1).
+ *
+ * Conventions for every call:
+ *  - All functions return a dg_status; nothing throws across the ABI.
+ *  - Device arrays are caller-owned, contiguous, FP64, on the context's
+ *    device.  Field-major SoA: array[field][cell][node]; nodes of a cell in
+ *    tensor order with x fastest.  N = n_elem * (r+1)^d nodes.
+ *    State q has 5 fields (rho, rho u, rho v, rho w, rho E) -- in 2D (x-z
+ *    vertical slice, eq. vertical_slice) v is carried but has no derivative.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default).
+ *    apply_* calls are asynchronous on it; calls that fill an info struct
+ *    synchronise the stream before returning.
+ *  - Library-owned workspace (traces, face fluxes, Krylov basis) is
+ *    allocated lazily per mesh and released by dg_mesh_destroy.  A context
+ *    and its meshes are not thread-safe.
+ */
+#ifndef DGIMEX_H
+#define DGIMEX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DG_OK = 0,
+  DG_ERR_ARG = -1,           /* invalid argument or inconsistent mesh lists */
+  DG_ERR_UNSUPPORTED = -2,   /* valid but not implemented (e.g. GLL nodes) */
+  DG_ERR_CUDA = -3,          /* CUDA runtime error (message: dg_last_error) */
+  DG_ERR_NOT_CONVERGED = -4, /* iteration limit hit; best iterate returned */
+  DG_ERR_TIMEOUT = -5,       /* a bounded device wait gave up */
+  DG_ERR_NONFINITE = -6,     /* NaN/Inf met in a norm or reduction */
+  DG_ERR_OOM = -7            /* device allocation failed */
+} dg_status;
+
+enum { DG_NODES_GL = 0, DG_NODES_GLL = 1 };
+enum { DG_BC_WALL = 1 };
+enum { DG_R1 = 1, DG_R2 = 2 };
+enum { DG_FP64 = 0 };
+
+typedef struct dg_ctx dg_ctx;
+typedef struct dg_mesh dg_mesh;
+
+/* Human-readable name of a status code; message of the last failure. */
+const char* dg_status_string(int status);
+const char* dg_last_error(void);
+
+/* Create a context on CUDA device `device` (makes it current). */
+int dg_ctx_create(int device, dg_ctx** out);
+void dg_ctx_destroy(dg_ctx* ctx);
+
+/*
+ * Mesh description (host arrays, copied by dg_mesh_create).
+ *  dim        2 (x-z slice) or 3.
+ *  degree     r in 1..4; nodes per cell (r+1)^dim.
+ *  node_set   DG_NODES_GL (Section 3: Gauss-Legendre nodes); GLL -> UNSUPPORTED.
+ *  vertices   n_elem x 2^dim x dim doubles: corner v of a cell sits at
+ *             reference corner (v&1, (v>>1)&1[, (v>>2)&1]); the cell map is
+ *             multilinear (curved terrain-following cells included).
+ *  int_faces  n_int x 4: [eL, fL, eR, fR], face f = 2a+s is xi_a = s;
+ *             requires fL = 2a+1, fR = 2a (eL on the low side; periodic
+ *             pairs listed the same way); tangential axes aligned.
+ *  hang_faces n_hang x 5: [e_coarse, f_coarse, e_fine, f_fine, subface];
+ *             2:1 only; f_fine = f_coarse ^ 1; bit t of subface selects the
+ *             half along the t-th tangential axis.
+ *  bdry_faces n_bdry x 3: [e, f, DG_BC_WALL] (slip wall, mirror state).
+ * Every face of every cell must be covered exactly once (interior side,
+ * fine hanging side, one of the 2^(dim-1) coarse subfaces, or boundary);
+ * otherwise DG_ERR_ARG.
+ */
+typedef struct {
+  int dim, degree, node_set;
+  int64_t n_elem;
+  const double* vertices;
+  int64_t n_int;
+  const int64_t* int_faces;
+  int64_t n_hang;
+  const int64_t* hang_faces;
+  int64_t n_bdry;
+  const int64_t* bdry_faces;
+} dg_mesh_desc;
+
+int dg_mesh_create(dg_ctx* ctx, const dg_mesh_desc* desc, dg_mesh** out);
+void dg_mesh_destroy(dg_mesh* mesh);
+
+typedef struct {
+  int dim, degree, n1d, nodes_per_elem;
+  int64_t n_elem, n_nodes, n_face_points, n_hang_points;
+  int64_t workspace_bytes;   /* library-owned device memory held now */
+} dg_mesh_stats;
+int dg_mesh_info(const dg_mesh* mesh, dg_mesh_stats* out);
+
+/* Physical coordinates of all nodes: xyz[dim][cell][node] (device, FP64). */
+int dg_mesh_node_coords(dg_ctx* ctx, const dg_mesh* mesh, double* xyz, void* stream);
+
+/* Physics: gamma, g, f of eq. governing_equations_2 (f-plane, k = vertical
+ * unit vector = last coordinate); variant R1/R2 (Section 3); penalty = 1
+ * keeps the Rusanov term on rho e implicit at stage l (as a lagged-lambda
+ * jump term added to D). */
+typedef struct {
+  double gamma, g, f;
+  int variant;
+  int penalty;
+  int precision;             /* DG_FP64 */
+} dg_phys;
+
+/*
+ * Explicit operator (stage rates), Section 3: weak residuals of the
+ * non-stiff part f_NS (advection: rho u, rho u (x) u, kappa rho u with
+ * Rusanov) and of the stiff part f_S (pressure with centred {p}, enthalpy
+ * flux h rho u with centred flux and Rusanov on rho e, gravity -rho g k,
+ * Coriolis -f rho k x u, -g rho k.u), multiplied by the inverse mass matrix.
+ *  q     in : 5 x N
+ *  f_ns  out: 5 x N   (rho, rho u, rho v, rho w, rho E rates)
+ *  f_s   out: 4 x N   (rho u, rho v, rho w, rho E rates; the rho rate is 0)
+ */
+int dg_apply_explicit(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* phys,
+                      const double* q, double* f_ns, double* f_s, void* stream);
+
+/* Coefficients frozen during one Picard iteration of stage l (device,
+ * N each; u_lag 3 x N): rho^(n,l), p^(n,l,k), u^(n,l,k); a_dt = at_ll dt. */
+typedef struct {
+  const double* rho;
+  const double* p_lag;
+  const double* u_lag;
+  double a_dt;
+} dg_implicit_coeffs;
+
+/*
+ * Schur-complement vmult, Section 3 (R1 / R2 pressure systems), scaled by
+ * D^{-1} (D = M / (gamma-1), the diagonal mass term):
+ *   R2: y = D^{-1} [ D + P - (C^(k) + M_g)(A + R)^{-1} B ] x
+ *   R1: y = D^{-1} [ D + P - C^(k) A^{-1} B ] x
+ * B: centred weak gradient times a_dt; A: rho-weighted mass; R = beta A J,
+ * beta = a_dt f; C: weak divergence of h rho u with h rho = gamma p_lag /
+ * (gamma - 1); M_g = a_dt g rho k.; P: implicit Rusanov jump term
+ * a_dt/(2(gamma-1)) lambda^(k) [.][.] (zero when phys->penalty == 0).
+ *  x in: N, y out: N (must not alias x).
+ */
+int dg_apply_implicit(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* phys,
+                      const dg_implicit_coeffs* cf, const double* x, double* y,
+                      void* stream);
+
+/*
+ * Right-hand side of the scaled pressure system from the stage vectors
+ * m_hat (3 x N, nodal momentum predictor = M^{-1} f) and e_hat (N, nodal
+ * energy predictor = M^{-1} g):
+ *   R2: rhs = D^{-1} [ g - k^(k) - (C + M_g)(A + R)^{-1} (f - f_g) ]
+ *   R1: rhs = D^{-1} [ g - M_g u^(k) - k^(k) - C A^{-1} (f - R u^(k) - f_g) ]
+ */
+int dg_schur_rhs(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* phys,
+                 const dg_implicit_coeffs* cf, const double* m_hat,
+                 const double* e_hat, double* rhs, void* stream);
+
+/* Velocity recovery once p is known (u out: 3 x N):
+ *   R2: u = (A + R)^{-1} (f - f_g - B p)
+ *   R1: u = A^{-1} (f - f_g - R u^(k) - B p) */
+int dg_recover_velocity(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* phys,
+                        const dg_implicit_coeffs* cf, const double* m_hat,
+                        const double* p, double* u, void* stream);
+
+/* Restarted GMRES(restart) with classical Gram-Schmidt applied twice and
+ * FP64 device reductions on the scaled Schur system; stops when
+ * ||b - S x||_2 <= rtol ||b||_2.  x in: initial guess, out: solution (best
+ * iterate and DG_ERR_NOT_CONVERGED after maxit).  Synchronises `stream`. */
+typedef struct { double rtol; int restart, maxit; } dg_gmres_opts;
+typedef struct { int iters; double relres; } dg_gmres_info;
+int dg_gmres_solve(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* phys,
+                   const dg_implicit_coeffs* cf, const double* b, double* x,
+                   const dg_gmres_opts* opts, dg_gmres_info* info, void* stream);
+
+/*
+ * One ARK2 IMEX step (Section 3): stages 2 and 3 take rho explicitly, then
+ * the Picard loop (initial guess = previous stage; stop when
+ * max(||dp||/||p||, ||du||/||u||) < picard_rtol, or exactly picard_fixed
+ * iterations if > 0) around the Schur solve and the velocity recovery;
+ * final update y^{n+1} = y^n + dt sum_l b_l (F_NS,l + F_S,l).
+ *  q in/out: 5 x N (device).  Synchronises `stream` to fill info.
+ */
+typedef struct {
+  double picard_rtol;
+  int picard_maxit, picard_fixed;
+  dg_gmres_opts gmres;
+} dg_step_opts;
+typedef struct {
+  int picard_iters[3];
+  int gmres_iters_total;
+  double max_relres;
+} dg_step_info;
+int imex_ark2_step(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* phys,
+                   double* q, double dt, const dg_step_opts* opts,
+                   dg_step_info* info, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DGIMEX_H */

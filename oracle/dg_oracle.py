@@ -331,11 +331,13 @@ class Discretisation:
         return np.einsum("...beq,eq,eqbi->...ei", flux, self.wJ, self.G)
 
     def mass_solve(self, res):
-        """Apply the inverse (unweighted) mass matrix cell by cell (dense LU)."""
+        """Apply the inverse (unweighted) mass matrix cell by cell (dense
+        LU, factorised once per mesh)."""
+        if not hasattr(self, "_Minv"):
+            self._Minv = np.linalg.inv(self.M)
         lead = res.shape[:-2]
         r = res.reshape((-1,) + res.shape[-2:])
-        out = np.stack([np.linalg.solve(self.M, r[k][..., None])[..., 0]
-                        for k in range(r.shape[0])])
+        out = np.einsum("eij,kej->kei", self._Minv, r)
         return out.reshape(lead + res.shape[-2:])
 
     def node_points(self):
@@ -455,6 +457,7 @@ class StageCoeffs:
     p_lag: np.ndarray
     u_lag: np.ndarray
     adt: float
+    cache: dict = None
 
 
 def op_B(disc, cf, x):
@@ -506,10 +509,16 @@ def _cell_block_AR(disc, cf, f, with_R):
 
 
 def solve_AR(disc, cf, f, rhs, with_R=True):
-    """(A + R)^{-1} rhs (or A^{-1} rhs) by a dense LU per cell."""
-    blk = _cell_block_AR(disc, cf, f, with_R)
+    """(A + R)^{-1} rhs (or A^{-1} rhs) by a dense inverse per cell (the
+    cell blocks are factorised once per set of frozen coefficients)."""
+    if cf.cache is None:
+        cf.cache = {}
+    key = ("AR", f, with_R)
+    if key not in cf.cache:
+        cf.cache[key] = np.linalg.inv(_cell_block_AR(disc, cf, f, with_R))
+    inv = cf.cache[key]
     r = np.concatenate([rhs[0], rhs[1], rhs[2]], axis=-1)          # (E, 3Np)
-    s = np.linalg.solve(blk, r[..., None])[..., 0]
+    s = np.einsum("eij,ej->ei", inv, r)
     Np = disc.Np
     return np.stack([s[:, :Np], s[:, Np:2 * Np], s[:, 2 * Np:]])
 

@@ -1,0 +1,129 @@
+// Shared internals of libdgimex: context / mesh objects, 1D tables, error
+// plumbing and the compile-time (dim, degree) dispatch.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "../../include/dgimex.h"
+
+namespace dg {
+
+constexpr int MAX_N = 5;          // degree r <= 4
+constexpr int MAX_NFP = 25;       // face points per face (r = 4, 3D)
+
+__host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
+
+void set_error(const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define DG_CUDA(call)                                              \
+  do {                                                             \
+    cudaError_t e_ = (call);                                       \
+    if (e_ != cudaSuccess) return ::dg::cuda_fail(e_, #call);      \
+  } while (0)
+
+#define DG_LAUNCH_CHECK(what)                                      \
+  do {                                                             \
+    cudaError_t e_ = cudaGetLastError();                           \
+    if (e_ != cudaSuccess) return ::dg::cuda_fail(e_, what);       \
+  } while (0)
+
+// 1D tables of the Gauss-Legendre nodal basis on [0, 1], passed to kernels
+// by value (they land in the constant bank).
+template <typename T>
+struct Tables {
+  T D[MAX_N][MAX_N];         // D[k][j] = l_j'(xi_k)        (derivative at nodes)
+  T L[2][MAX_N];             // L[s][j] = l_j(s)             (trace to face s)
+  T P[2][MAX_N][MAX_N];      // P[b][q][j] = l_j((xi_q + b)/2)  (2:1 prolongation)
+};
+
+struct HostTables {
+  int n;
+  double x[MAX_N], w[MAX_N];
+  Tables<double> t;
+};
+void make_tables(int n, HostTables* out);   // Newton on Legendre P_n
+
+template <typename T>
+inline Tables<T> cast_tables(const Tables<double>& t) {
+  Tables<T> o;
+  for (int a = 0; a < MAX_N; ++a)
+    for (int b = 0; b < MAX_N; ++b) {
+      o.D[a][b] = (T)t.D[a][b];
+      o.P[0][a][b] = (T)t.P[0][a][b];
+      o.P[1][a][b] = (T)t.P[1][a][b];
+    }
+  for (int s = 0; s < 2; ++s)
+    for (int b = 0; b < MAX_N; ++b) o.L[s][b] = (T)t.L[s][b];
+  return o;
+}
+
+// Lazily grown device buffer owned by a mesh.
+struct DBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  int ensure(size_t nbytes);
+  void release();
+  template <typename T> T* as() const { return static_cast<T*>(p); }
+};
+
+}  // namespace dg
+
+struct dg_ctx {
+  int device = 0;
+};
+
+struct dg_mesh {
+  dg_ctx* ctx = nullptr;
+  int dim = 0, degree = 0, n = 0, Np = 0, nfp = 0, nfaces = 0;
+  int64_t E = 0, N = 0;
+  int64_t S = 0;         // face slots = E * 2d * nfp
+  int64_t nF = 0;        // unified face points
+  int64_t nH = 0;        // hanging fine points
+  int64_t nHC = 0;       // coarse hanging faces
+  dg::HostTables tab;
+  // geometry (device, FP64)
+  double* verts = nullptr;   // E x 2^d x d
+  double* K = nullptr;       // d*d x N : w det(J) (J^{-1})_{ab}
+  double* invM = nullptr;    // N       : 1 / (w det J)
+  double* fgeo = nullptr;    // (d+1) x nF : n dS (d comps), dS
+  // face-point topology (device, int32)
+  int* fp_minus = nullptr;   // nF: minus slot
+  int* fp_plus = nullptr;    // nF: plus slot, -1 wall, -2-hp hanging
+  int* hp_cslot = nullptr;   // nH: coarse slot base (e_c*2d+f_c)*nfp
+  int* hp_code = nullptr;    // nH: sub | (fine point index << 8)
+  int* hc_slot = nullptr;    // nHC: coarse slot base
+  // workspace
+  dg::DBuf trc, slot, hbuf, trh, pcoef, wv, gm_V, gm_work, red, st, fns, fs;
+  std::vector<double> host_h;
+  int64_t workspace_bytes() const;
+};
+
+namespace dg {
+
+// Arguments shared by the face kernels.
+struct FaceTopo {
+  const int* fp_minus;
+  const int* fp_plus;
+  const double* fgeo;
+  const int* hp_cslot;
+  const int* hp_code;
+  const int* hc_slot;
+  int64_t nF, nH, nHC, S;
+};
+
+inline FaceTopo topo(const dg_mesh* m) {
+  return FaceTopo{m->fp_minus, m->fp_plus, m->fgeo, m->hp_cslot, m->hp_code,
+                  m->hc_slot, m->nF, m->nH, m->nHC, m->S};
+}
+
+inline unsigned grid_for(int64_t n, int threads) {
+  int64_t g = (n + threads - 1) / threads;
+  return (unsigned)(g < 1 ? 1 : g);
+}
+
+}  // namespace dg

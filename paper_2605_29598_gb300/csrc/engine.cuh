@@ -1,0 +1,37 @@
+// Per-(T, DIM, N) operator engine and the runtime (dim, degree) dispatch.
+#pragma once
+
+#include "ops.cuh"
+
+namespace dg {
+
+template <typename T, int DIM, int N>
+struct Engine {
+  static int explicit_rates(dg_mesh* m, const PhysK& ph, const T* q, T* fns, T* fs, cudaStream_t st);
+  static int prepare(dg_mesh* m, const ImplK& ph, const T* plag, const T* ulag, int penalty, cudaStream_t st);
+  static int vmult(dg_mesh* m, const ImplK& ph, const T* rho, const T* plag, int penalty, const T* x, T* y,
+                   cudaStream_t st);
+  static int schur_rhs(dg_mesh* m, const ImplK& ph, const T* rho, const T* plag, const T* ulag, const T* mhat,
+                       const T* ehat, T* rhs, cudaStream_t st);
+  static int recover(dg_mesh* m, const ImplK& ph, const T* rho, const T* ulag, const T* mhat, const T* p, T* u,
+                     cudaStream_t st);
+};
+
+ImplK impl_consts(const dg_phys* ph, double a_dt);
+
+// Run the statement list for the mesh's compile-time (dim, n): D_ and N_ are
+// constexpr inside it.
+#define DG_DISPATCH(m, ...)                                  \
+  switch ((m)->dim * 10 + (m)->n) {                          \
+    case 22: { constexpr int D_ = 2, N_ = 2; __VA_ARGS__; } break; \
+    case 23: { constexpr int D_ = 2, N_ = 3; __VA_ARGS__; } break; \
+    case 24: { constexpr int D_ = 2, N_ = 4; __VA_ARGS__; } break; \
+    case 25: { constexpr int D_ = 2, N_ = 5; __VA_ARGS__; } break; \
+    case 32: { constexpr int D_ = 3, N_ = 2; __VA_ARGS__; } break; \
+    case 33: { constexpr int D_ = 3, N_ = 3; __VA_ARGS__; } break; \
+    case 34: { constexpr int D_ = 3, N_ = 4; __VA_ARGS__; } break; \
+    case 35: { constexpr int D_ = 3, N_ = 5; __VA_ARGS__; } break; \
+    default: break;                                          \
+  }
+
+}  // namespace dg

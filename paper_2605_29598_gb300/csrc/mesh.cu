@@ -1,0 +1,530 @@
+// Context, error plumbing, 1D tables and mesh creation (validation, face
+// lists, geometry) of libdgimex.
+#include <cmath>
+#include <cstdarg>
+#include <cstring>
+#include <mutex>
+
+#include "common.cuh"
+
+namespace dg {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  set_error("%s: %s", what, cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? DG_ERR_OOM : DG_ERR_CUDA;
+}
+
+int DBuf::ensure(size_t nbytes) {
+  if (nbytes <= bytes && p) return DG_OK;
+  release();
+  cudaError_t e = cudaMalloc(&p, nbytes ? nbytes : 16);
+  if (e != cudaSuccess) {
+    p = nullptr;
+    bytes = 0;
+    return cuda_fail(e, "cudaMalloc(workspace)");
+  }
+  bytes = nbytes;
+  return DG_OK;
+}
+
+void DBuf::release() {
+  if (p) cudaFree(p);
+  p = nullptr;
+  bytes = 0;
+}
+
+// Gauss-Legendre nodes on [-1, 1] by Newton iteration on P_n (three-term
+// recurrence), mapped to [0, 1]; Lagrange values and derivatives by the
+// product rule.
+void make_tables(int n, HostTables* out) {
+  out->n = n;
+  for (int i = 0; i < n; ++i) {
+    double t = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = t;
+      for (int k = 2; k <= n; ++k) {
+        double p2 = ((2.0 * k - 1.0) * t * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      double pn = n == 0 ? 1.0 : (n == 1 ? t : p1);
+      double pm = n == 1 ? 1.0 : p0;
+      dp = n * (t * pn - pm) / (t * t - 1.0);
+      double dt = pn / dp;
+      t -= dt;
+      if (std::fabs(dt) < 1e-17) break;
+    }
+    // node i counted from the right end; store ascending
+    out->x[n - 1 - i] = 0.5 * (t + 1.0);
+    out->w[n - 1 - i] = 1.0 / ((1.0 - t * t) * dp * dp);   // 2/((1-t^2)P'^2) / 2
+  }
+  const double* x = out->x;
+  auto lag = [&](int j, double s) {
+    double v = 1.0;
+    for (int k = 0; k < n; ++k)
+      if (k != j) v *= (s - x[k]) / (x[j] - x[k]);
+    return v;
+  };
+  auto dlag = [&](int j, double s) {
+    double acc = 0.0;
+    for (int m = 0; m < n; ++m) {
+      if (m == j) continue;
+      double v = 1.0 / (x[j] - x[m]);
+      for (int k = 0; k < n; ++k)
+        if (k != j && k != m) v *= (s - x[k]) / (x[j] - x[k]);
+      acc += v;
+    }
+    return acc;
+  };
+  std::memset(&out->t, 0, sizeof(out->t));
+  for (int k = 0; k < n; ++k)
+    for (int j = 0; j < n; ++j) {
+      out->t.D[k][j] = dlag(j, x[k]);
+      out->t.P[0][k][j] = lag(j, 0.5 * x[k]);
+      out->t.P[1][k][j] = lag(j, 0.5 * (x[k] + 1.0));
+    }
+  for (int j = 0; j < n; ++j) {
+    out->t.L[0][j] = lag(j, 0.0);
+    out->t.L[1][j] = lag(j, 1.0);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// geometry kernels
+// ---------------------------------------------------------------------------
+
+struct GeoArgs {
+  const double* verts;
+  int dim, n, Np, nfp;
+  int64_t E;
+  double x[MAX_N], w[MAX_N];
+};
+
+// Jacobian columns t_c = dx/dxi_c of the multilinear map at reference point xi.
+__device__ void jac(const double* V, int dim, const double* xi, double J[3][3]) {
+  for (int b = 0; b < 3; ++b)
+    for (int c = 0; c < 3; ++c) J[b][c] = 0.0;
+  int nv = 1 << dim;
+  for (int v = 0; v < nv; ++v) {
+    for (int c = 0; c < dim; ++c) {
+      double wgt = 1.0;
+      for (int a = 0; a < dim; ++a) {
+        int bit = (v >> a) & 1;
+        if (a == c) wgt *= bit ? 1.0 : -1.0;
+        else wgt *= bit ? xi[a] : 1.0 - xi[a];
+      }
+      for (int b = 0; b < dim; ++b) J[b][c] += wgt * V[v * dim + b];
+    }
+  }
+}
+
+// adj[a][b] = det(J) * (J^{-1})[a][b]
+__device__ double adjugate(int dim, const double J[3][3], double adj[3][3]) {
+  if (dim == 2) {
+    adj[0][0] = J[1][1];
+    adj[0][1] = -J[0][1];
+    adj[1][0] = -J[1][0];
+    adj[1][1] = J[0][0];
+    return J[0][0] * J[1][1] - J[0][1] * J[1][0];
+  }
+  // rows of adj are cross products of the Jacobian columns
+  for (int a = 0; a < 3; ++a) {
+    int c1 = (a + 1) % 3, c2 = (a + 2) % 3;
+    adj[a][0] = J[1][c1] * J[2][c2] - J[2][c1] * J[1][c2];
+    adj[a][1] = J[2][c1] * J[0][c2] - J[0][c1] * J[2][c2];
+    adj[a][2] = J[0][c1] * J[1][c2] - J[1][c1] * J[0][c2];
+  }
+  return J[0][0] * adj[0][0] + J[1][0] * adj[0][1] + J[2][0] * adj[0][2];
+}
+
+__global__ void k_volume_geometry(GeoArgs g, double* K, double* invM, int* bad) {
+  int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t N = g.E * g.Np;
+  if (node >= N) return;
+  int64_t e = node / g.Np;
+  int i = (int)(node % g.Np);
+  double xi[3] = {0, 0, 0};
+  double w = 1.0;
+  for (int a = 0, r = i; a < g.dim; ++a, r /= g.n) {
+    xi[a] = g.x[r % g.n];
+    w *= g.w[r % g.n];
+  }
+  double J[3][3], adj[3][3];
+  jac(g.verts + e * (int64_t)(g.dim << g.dim), g.dim, xi, J);
+  double det = adjugate(g.dim, J, adj);
+  if (!(det > 0.0)) atomicExch(bad, 1);
+  for (int a = 0; a < g.dim; ++a)
+    for (int b = 0; b < g.dim; ++b) K[(int64_t)(a * g.dim + b) * N + node] = w * adj[a][b];
+  invM[node] = 1.0 / (w * det);
+}
+
+// n dS at each face point of the minus side (Nanson: det(J) J^{-T} e_a).
+__global__ void k_face_geometry(GeoArgs g, const int* fp_minus, int64_t nF, double* fgeo) {
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= nF) return;
+  int slot = fp_minus[p];
+  int nfaces = 2 * g.dim;
+  int pt = slot % g.nfp;
+  int f = (slot / g.nfp) % nfaces;
+  int64_t e = slot / (g.nfp * nfaces);
+  int a = f / 2, s = f % 2;
+  double xi[3] = {0, 0, 0};
+  double w = 1.0;
+  xi[a] = (double)s;
+  for (int t = 0, r = pt; t < g.dim; ++t) {
+    if (t == a) continue;
+    xi[t] = g.x[r % g.n];
+    w *= g.w[r % g.n];
+    r /= g.n;
+  }
+  double J[3][3], adj[3][3];
+  jac(g.verts + e * (int64_t)(g.dim << g.dim), g.dim, xi, J);
+  adjugate(g.dim, J, adj);
+  double sg = s ? 1.0 : -1.0, nn = 0.0;
+  for (int b = 0; b < g.dim; ++b) {
+    double v = sg * w * adj[a][b];
+    fgeo[(int64_t)b * nF + p] = v;
+    nn += v * v;
+  }
+  fgeo[(int64_t)g.dim * nF + p] = sqrt(nn);
+}
+
+__global__ void k_node_coords(GeoArgs g, double* xyz) {
+  int64_t node = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t N = g.E * g.Np;
+  if (node >= N) return;
+  int64_t e = node / g.Np;
+  int i = (int)(node % g.Np);
+  double xi[3] = {0, 0, 0};
+  for (int a = 0, r = i; a < g.dim; ++a, r /= g.n) xi[a] = g.x[r % g.n];
+  const double* V = g.verts + e * (int64_t)(g.dim << g.dim);
+  for (int b = 0; b < g.dim; ++b) {
+    double acc = 0.0;
+    for (int v = 0; v < (1 << g.dim); ++v) {
+      double wgt = 1.0;
+      for (int a = 0; a < g.dim; ++a) wgt *= ((v >> a) & 1) ? xi[a] : 1.0 - xi[a];
+      acc += wgt * V[v * g.dim + b];
+    }
+    xyz[(int64_t)b * N + node] = acc;
+  }
+}
+
+static GeoArgs geo_args(const dg_mesh* m) {
+  GeoArgs g;
+  g.verts = m->verts;
+  g.dim = m->dim;
+  g.n = m->n;
+  g.Np = m->Np;
+  g.nfp = m->nfp;
+  g.E = m->E;
+  for (int k = 0; k < MAX_N; ++k) {
+    g.x[k] = m->tab.x[k];
+    g.w[k] = m->tab.w[k];
+  }
+  return g;
+}
+
+}  // namespace dg
+
+using namespace dg;
+
+int64_t dg_mesh::workspace_bytes() const {
+  const DBuf* b[] = {&trc, &slot, &hbuf, &trh, &pcoef, &wv, &gm_V, &gm_work, &red, &st, &fns, &fs};
+  int64_t s = 0;
+  for (auto* x : b) s += (int64_t)x->bytes;
+  return s;
+}
+
+extern "C" {
+
+const char* dg_status_string(int s) {
+  switch (s) {
+    case DG_OK: return "DG_OK";
+    case DG_ERR_ARG: return "DG_ERR_ARG";
+    case DG_ERR_UNSUPPORTED: return "DG_ERR_UNSUPPORTED";
+    case DG_ERR_CUDA: return "DG_ERR_CUDA";
+    case DG_ERR_NOT_CONVERGED: return "DG_ERR_NOT_CONVERGED";
+    case DG_ERR_TIMEOUT: return "DG_ERR_TIMEOUT";
+    case DG_ERR_NONFINITE: return "DG_ERR_NONFINITE";
+    case DG_ERR_OOM: return "DG_ERR_OOM";
+    default: return "DG_UNKNOWN";
+  }
+}
+
+const char* dg_last_error(void) { return g_err; }
+
+int dg_ctx_create(int device, dg_ctx** out) {
+  if (!out) {
+    set_error("dg_ctx_create: out is NULL");
+    return DG_ERR_ARG;
+  }
+  int count = 0;
+  DG_CUDA(cudaGetDeviceCount(&count));
+  if (device < 0 || device >= count) {
+    set_error("dg_ctx_create: device %d not in [0, %d)", device, count);
+    return DG_ERR_ARG;
+  }
+  DG_CUDA(cudaSetDevice(device));
+  dg_ctx* c = new dg_ctx;
+  c->device = device;
+  *out = c;
+  return DG_OK;
+}
+
+void dg_ctx_destroy(dg_ctx* ctx) { delete ctx; }
+
+void dg_mesh_destroy(dg_mesh* m) {
+  if (!m) return;
+  cudaFree(m->verts);
+  cudaFree(m->K);
+  cudaFree(m->invM);
+  cudaFree(m->fgeo);
+  cudaFree(m->fp_minus);
+  cudaFree(m->fp_plus);
+  cudaFree(m->hp_cslot);
+  cudaFree(m->hp_code);
+  cudaFree(m->hc_slot);
+  DBuf* b[] = {&m->trc, &m->slot, &m->hbuf, &m->trh, &m->pcoef, &m->wv, &m->gm_V,
+               &m->gm_work, &m->red, &m->st, &m->fns, &m->fs};
+  for (auto* x : b) x->release();
+  delete m;
+}
+
+int dg_mesh_create(dg_ctx* ctx, const dg_mesh_desc* d, dg_mesh** out) {
+  if (!ctx || !d || !out) {
+    set_error("dg_mesh_create: NULL argument");
+    return DG_ERR_ARG;
+  }
+  *out = nullptr;
+  if (d->dim != 2 && d->dim != 3) {
+    set_error("dg_mesh_create: dim %d not in {2, 3}", d->dim);
+    return DG_ERR_ARG;
+  }
+  if (d->degree < 1 || d->degree > 4) {
+    set_error("dg_mesh_create: degree %d not in 1..4", d->degree);
+    return d->degree > 4 ? DG_ERR_UNSUPPORTED : DG_ERR_ARG;
+  }
+  if (d->node_set == DG_NODES_GLL) {
+    set_error("dg_mesh_create: Gauss-Lobatto nodes are not implemented");
+    return DG_ERR_UNSUPPORTED;
+  }
+  if (d->node_set != DG_NODES_GL) {
+    set_error("dg_mesh_create: unknown node_set %d", d->node_set);
+    return DG_ERR_ARG;
+  }
+  if (d->n_elem <= 0 || !d->vertices || d->n_int < 0 || d->n_hang < 0 || d->n_bdry < 0 ||
+      (d->n_int && !d->int_faces) || (d->n_hang && !d->hang_faces) ||
+      (d->n_bdry && !d->bdry_faces)) {
+    set_error("dg_mesh_create: empty mesh or NULL list");
+    return DG_ERR_ARG;
+  }
+  const int dim = d->dim, n = d->degree + 1, nfaces = 2 * dim;
+  const int nfp = ipow(n, dim - 1), nsub = 1 << (dim - 1);
+  const int64_t E = d->n_elem;
+  if (E * nfaces * (int64_t)nfp >= (int64_t)1 << 31 || E * ipow(n, dim) >= (int64_t)1 << 31) {
+    set_error("dg_mesh_create: mesh too large for 32-bit slot indices");
+    return DG_ERR_UNSUPPORTED;
+  }
+  // ---- validation: every cell face covered exactly once
+  std::vector<uint8_t> cover((size_t)E * nfaces, 0);
+  auto bad = [&](const char* what, int64_t row) {
+    set_error("dg_mesh_create: %s (row %lld)", what, (long long)row);
+    return DG_ERR_ARG;
+  };
+  for (int64_t k = 0; k < d->n_int; ++k) {
+    const int64_t* r = d->int_faces + 4 * k;
+    if (r[0] < 0 || r[0] >= E || r[2] < 0 || r[2] >= E) return bad("interior face cell out of range", k);
+    if (r[1] < 0 || r[1] >= nfaces || r[3] < 0 || r[3] >= nfaces) return bad("interior face index out of range", k);
+    if (r[1] % 2 != 1 || r[3] != r[1] - 1) return bad("interior face needs fL = 2a+1, fR = 2a", k);
+    if (r[0] == r[2]) return bad("interior face joins a cell to itself", k);
+    cover[r[0] * nfaces + r[1]]++;
+    cover[r[2] * nfaces + r[3]]++;
+  }
+  for (int64_t k = 0; k < d->n_bdry; ++k) {
+    const int64_t* r = d->bdry_faces + 3 * k;
+    if (r[0] < 0 || r[0] >= E || r[1] < 0 || r[1] >= nfaces) return bad("boundary face out of range", k);
+    if (r[2] != DG_BC_WALL) return bad("unknown boundary condition", k);
+    cover[r[0] * nfaces + r[1]]++;
+  }
+  // group hanging rows by coarse face
+  std::vector<int64_t> hc_first((size_t)E * nfaces, -1);
+  std::vector<int64_t> hc_list;                 // coarse face keys in order of appearance
+  std::vector<int64_t> hc_rows;                 // nsub rows per coarse face
+  for (int64_t k = 0; k < d->n_hang; ++k) {
+    const int64_t* r = d->hang_faces + 5 * k;
+    if (r[0] < 0 || r[0] >= E || r[2] < 0 || r[2] >= E) return bad("hanging face cell out of range", k);
+    if (r[1] < 0 || r[1] >= nfaces || r[3] < 0 || r[3] >= nfaces) return bad("hanging face index out of range", k);
+    if (r[3] != (r[1] ^ 1)) return bad("hanging face needs f_fine = f_coarse ^ 1", k);
+    if (r[4] < 0 || r[4] >= nsub) return bad("subface index out of range", k);
+    if (r[0] == r[2]) return bad("hanging face joins a cell to itself", k);
+    cover[r[2] * nfaces + r[3]]++;
+    int64_t key = r[0] * nfaces + r[1];
+    if (hc_first[key] < 0) {
+      hc_first[key] = (int64_t)hc_list.size();
+      hc_list.push_back(key);
+      hc_rows.insert(hc_rows.end(), nsub, -1);
+      cover[key]++;
+    }
+    int64_t& slotrow = hc_rows[hc_first[key] * nsub + r[4]];
+    if (slotrow >= 0) return bad("subface listed twice", k);
+    slotrow = k;
+  }
+  for (size_t k = 0; k < hc_rows.size(); ++k)
+    if (hc_rows[k] < 0) {
+      set_error("dg_mesh_create: coarse face %lld misses a subface", (long long)(k / nsub));
+      return DG_ERR_ARG;
+    }
+  for (int64_t k = 0; k < E * nfaces; ++k)
+    if (cover[k] != 1) {
+      set_error("dg_mesh_create: face %d of cell %lld covered %d times", (int)(k % nfaces),
+                (long long)(k / nfaces), (int)cover[k]);
+      return DG_ERR_ARG;
+    }
+  for (int64_t k = 0; k < E * (dim << dim); ++k)
+    if (!std::isfinite(d->vertices[k])) return bad("non-finite vertex coordinate", k / (dim << dim));
+
+  // ---- unified face-point list
+  const int64_t nHC = (int64_t)hc_list.size();
+  const int64_t nH = nHC * nsub * nfp;
+  const int64_t nF = (d->n_int + d->n_bdry) * nfp + nH;
+  std::vector<int> fpm(nF), fpp(nF), hpc(nH), hpcode(nH), hcs(nHC);
+  int64_t p = 0;
+  for (int64_t k = 0; k < d->n_int; ++k) {
+    const int64_t* r = d->int_faces + 4 * k;
+    for (int t = 0; t < nfp; ++t, ++p) {
+      fpm[p] = (int)((r[0] * nfaces + r[1]) * nfp + t);
+      fpp[p] = (int)((r[2] * nfaces + r[3]) * nfp + t);
+    }
+  }
+  for (int64_t k = 0; k < d->n_bdry; ++k) {
+    const int64_t* r = d->bdry_faces + 3 * k;
+    for (int t = 0; t < nfp; ++t, ++p) {
+      fpm[p] = (int)((r[0] * nfaces + r[1]) * nfp + t);
+      fpp[p] = -1;
+    }
+  }
+  for (int64_t c = 0; c < nHC; ++c) {
+    hcs[c] = (int)(hc_list[c] * nfp);
+    for (int s = 0; s < nsub; ++s) {
+      const int64_t* r = d->hang_faces + 5 * hc_rows[c * nsub + s];
+      for (int t = 0; t < nfp; ++t, ++p) {
+        int64_t hp = (c * nsub + s) * nfp + t;
+        fpm[p] = (int)((r[2] * nfaces + r[3]) * nfp + t);
+        fpp[p] = (int)(-2 - hp);
+        hpc[hp] = hcs[c];
+        hpcode[hp] = s | (t << 8);
+      }
+    }
+  }
+
+  dg_mesh* m = new dg_mesh;
+  m->ctx = ctx;
+  m->dim = dim;
+  m->degree = d->degree;
+  m->n = n;
+  m->Np = ipow(n, dim);
+  m->nfp = nfp;
+  m->nfaces = nfaces;
+  m->E = E;
+  m->N = E * m->Np;
+  m->S = E * nfaces * nfp;
+  m->nF = nF;
+  m->nH = nH;
+  m->nHC = nHC;
+  make_tables(n, &m->tab);
+  auto fail = [&](int st) {
+    dg_mesh_destroy(m);
+    return st;
+  };
+#define ALLOC(ptr, count)                                                      \
+  do {                                                                         \
+    cudaError_t e_ = cudaMalloc(&(ptr), sizeof(*(ptr)) * (size_t)((count) > 0 ? (count) : 1)); \
+    if (e_ != cudaSuccess) return fail(cuda_fail(e_, "cudaMalloc(mesh)"));     \
+  } while (0)
+#define UPLOAD(dst, src, count)                                                \
+  do {                                                                         \
+    if ((count) > 0) {                                                         \
+      cudaError_t e_ = cudaMemcpy(dst, src, sizeof(*(dst)) * (size_t)(count),  \
+                                  cudaMemcpyHostToDevice);                     \
+      if (e_ != cudaSuccess) return fail(cuda_fail(e_, "cudaMemcpy(mesh)"));   \
+    }                                                                          \
+  } while (0)
+  ALLOC(m->verts, E * (dim << dim));
+  ALLOC(m->K, (int64_t)dim * dim * m->N);
+  ALLOC(m->invM, m->N);
+  ALLOC(m->fgeo, (int64_t)(dim + 1) * nF);
+  ALLOC(m->fp_minus, nF);
+  ALLOC(m->fp_plus, nF);
+  ALLOC(m->hp_cslot, nH);
+  ALLOC(m->hp_code, nH);
+  ALLOC(m->hc_slot, nHC);
+  UPLOAD(m->verts, d->vertices, E * (dim << dim));
+  UPLOAD(m->fp_minus, fpm.data(), nF);
+  UPLOAD(m->fp_plus, fpp.data(), nF);
+  UPLOAD(m->hp_cslot, hpc.data(), nH);
+  UPLOAD(m->hp_code, hpcode.data(), nH);
+  UPLOAD(m->hc_slot, hcs.data(), nHC);
+#undef ALLOC
+#undef UPLOAD
+  GeoArgs g = geo_args(m);
+  int* dbad = nullptr;
+  {
+    cudaError_t e = cudaMalloc(&dbad, sizeof(int));
+    if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMalloc(flag)"));
+  }
+  cudaMemset(dbad, 0, sizeof(int));
+  k_volume_geometry<<<grid_for(m->N, 256), 256>>>(g, m->K, m->invM, dbad);
+  if (nF > 0) k_face_geometry<<<grid_for(nF, 256), 256>>>(g, m->fp_minus, nF, m->fgeo);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  int hbad = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(&hbad, dbad, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(dbad);
+  if (e != cudaSuccess) return fail(cuda_fail(e, "mesh geometry"));
+  if (hbad) {
+    set_error("dg_mesh_create: a cell map has det(J) <= 0 at a node");
+    return fail(DG_ERR_ARG);
+  }
+  *out = m;
+  return DG_OK;
+}
+
+int dg_mesh_info(const dg_mesh* m, dg_mesh_stats* o) {
+  if (!m || !o) {
+    set_error("dg_mesh_info: NULL argument");
+    return DG_ERR_ARG;
+  }
+  o->dim = m->dim;
+  o->degree = m->degree;
+  o->n1d = m->n;
+  o->nodes_per_elem = m->Np;
+  o->n_elem = m->E;
+  o->n_nodes = m->N;
+  o->n_face_points = m->nF;
+  o->n_hang_points = m->nH;
+  o->workspace_bytes = m->workspace_bytes();
+  return DG_OK;
+}
+
+int dg_mesh_node_coords(dg_ctx* ctx, const dg_mesh* m, double* xyz, void* stream) {
+  if (!ctx || !m || !xyz) {
+    set_error("dg_mesh_node_coords: NULL argument");
+    return DG_ERR_ARG;
+  }
+  GeoArgs g = geo_args(m);
+  k_node_coords<<<grid_for(m->N, 256), 256, 0, (cudaStream_t)stream>>>(g, xyz);
+  DG_LAUNCH_CHECK("k_node_coords");
+  return DG_OK;
+}
+
+}  // extern "C"

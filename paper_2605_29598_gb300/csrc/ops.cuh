@@ -1,0 +1,562 @@
+// Operator kernels of libdgimex: face traces, numerical fluxes, 2:1 mortar
+// gather, sum-factorised cell kernels of the explicit operator and of the
+// Schur-complement vmult.  Templated on the scalar type T and on the
+// compile-time (DIM, N = r + 1).
+//
+// Face-slot convention.  Every cell owns 2*DIM faces x N^(DIM-1) face
+// points ("slots", slot = (e * 2 DIM + f) * NFP + pt, face f = 2a + s at
+// xi_a = s, face points in tangential tensor order).  A face kernel writes
+// into each slot the value v such that the cell's weak residual receives
+// -v * l_{i_a}(s) at node i (the lift).  Every slot is written exactly once
+// per pass (interior side, wall, fine hanging side, or the coarse gather),
+// so no slot buffer is ever cleared and no atomics are used.
+#pragma once
+
+#include "common.cuh"
+
+namespace dg {
+
+template <typename T> struct Fields {
+  const T* f[5];
+  T scale[5];
+};
+
+// tangential index of node i for faces normal to direction a
+template <int DIM, int N>
+__device__ __forceinline__ int tang_index(const int idx[3], int a) {
+  int t = 0, mul = 1;
+#pragma unroll
+  for (int b = 0; b < DIM; ++b) {
+    if (b == a) continue;
+    t += idx[b] * mul;
+    mul *= N;
+  }
+  return t;
+}
+
+template <int DIM, int N>
+__device__ __forceinline__ void node_index(int i, int idx[3]) {
+  idx[0] = i % N;
+  idx[1] = DIM > 1 ? (i / N) % N : 0;
+  idx[2] = DIM > 2 ? i / (N * N) : 0;
+}
+
+// Value of a coarse-face trace at fine point fp of subface `sub` (2:1).
+template <typename T, int DIM, int N>
+__device__ __forceinline__ T prolong(const Tables<T>& tb, const T* __restrict__ tr, int sub, int fp) {
+  if (DIM == 2) {
+    T acc = 0;
+#pragma unroll
+    for (int j = 0; j < N; ++j) acc += tb.P[sub][fp][j] * tr[j];
+    return acc;
+  } else {
+    int f0 = fp % N, f1 = fp / N, b0 = sub & 1, b1 = sub >> 1;
+    T acc = 0;
+#pragma unroll
+    for (int j1 = 0; j1 < N; ++j1) {
+      T row = 0;
+#pragma unroll
+      for (int j0 = 0; j0 < N; ++j0) row += tb.P[b0][f0][j0] * tr[j0 + N * j1];
+      acc += tb.P[b1][f1][j1] * row;
+    }
+    return acc;
+  }
+}
+
+template <typename T, int DIM, int N>
+__device__ __forceinline__ T prolong_weight(const Tables<T>& tb, int sub, int fp, int j) {
+  if (DIM == 2) return tb.P[sub][fp][j];
+  return tb.P[sub & 1][fp % N][j % N] * tb.P[sub >> 1][fp / N][j / N];
+}
+
+// ---------------------------------------------------------------------------
+// traces: slot values of up to 5 nodal fields (times a per-field scale)
+// ---------------------------------------------------------------------------
+template <typename T, int DIM, int N, int NFLD>
+__global__ void k_trace(Fields<T> in, int64_t E, int64_t Nn, T* __restrict__ trc, int64_t S,
+                        Tables<T> tb) {
+  constexpr int NP = ipow(N, DIM), NFP = ipow(N, DIM - 1), NF = 2 * DIM;
+  int64_t slot = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (slot >= S) return;
+  int pt = (int)(slot % NFP);
+  int f = (int)((slot / NFP) % NF);
+  int64_t e = slot / (NFP * NF);
+  int a = f >> 1, s = f & 1;
+  int idx[3] = {0, 0, 0};
+  for (int b = 0, r = pt; b < DIM; ++b) {
+    if (b == a) continue;
+    idx[b] = r % N;
+    r /= N;
+  }
+  int stride = a == 0 ? 1 : (a == 1 ? N : N * N);
+  int base = idx[0] + N * idx[1] + N * N * idx[2];
+  const int64_t off = e * NP + base;
+#pragma unroll
+  for (int q = 0; q < NFLD; ++q) {
+    const T* __restrict__ src = in.f[q] + off;
+    T acc = 0;
+#pragma unroll
+    for (int k = 0; k < N; ++k) acc += tb.L[s][k] * __ldg(src + k * stride);
+    trc[q * S + slot] = acc * in.scale[q];
+  }
+}
+
+// plus-side value of a traced field at face point p
+template <typename T, int DIM, int N>
+__device__ __forceinline__ T plus_value(const FaceTopo& ft, const Tables<T>& tb, const T* __restrict__ tr,
+                                        int code, T minus_val) {
+  if (code >= 0) return __ldg(tr + code);
+  if (code == -1) return minus_val;
+  int hp = -2 - code;
+  int cs = __ldg(ft.hp_cslot + hp), hc = __ldg(ft.hp_code + hp);
+  return prolong<T, DIM, N>(tb, tr + cs, hc & 0xff, hc >> 8);
+}
+
+// write an antisymmetric face value: minus slot v, plus slot -v, fine
+// hanging point -> mortar buffer
+template <typename T>
+__device__ __forceinline__ void put(T* __restrict__ slot, T* __restrict__ hbuf, int64_t S, int64_t nH,
+                                    int fld, int sm, int code, T v) {
+  slot[fld * S + sm] = v;
+  if (code >= 0) slot[fld * S + code] = -v;
+  else if (code <= -2) hbuf[fld * nH + (-2 - code)] = v;
+}
+
+// coarse side of 2:1 faces: slot(j) = -sum_sub sum_fp P_sub(fp, j) v(fp)
+template <typename T, int DIM, int N, int NFLD>
+__global__ void k_hang_gather(FaceTopo ft, const T* __restrict__ hbuf, T* __restrict__ slot,
+                              Tables<T> tb) {
+  constexpr int NFP = ipow(N, DIM - 1), NSUB = 1 << (DIM - 1);
+  int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= ft.nHC * NFP) return;
+  int64_t c = t / NFP;
+  int j = (int)(t % NFP);
+  int cs = ft.hc_slot[c];
+#pragma unroll
+  for (int q = 0; q < NFLD; ++q) {
+    T acc = 0;
+    const T* __restrict__ h = hbuf + q * ft.nH + c * NSUB * NFP;
+    for (int sub = 0; sub < NSUB; ++sub)
+#pragma unroll
+      for (int fp = 0; fp < NFP; ++fp) acc += prolong_weight<T, DIM, N>(tb, sub, fp, j) * h[sub * NFP + fp];
+    slot[q * ft.S + cs + j] = -acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// explicit operator: numerical fluxes at face points
+//   slot fields 0..4: non-stiff (rho, m_x, m_y, m_z, E), 5..8: stiff (m_x, m_y, m_z, E)
+// ---------------------------------------------------------------------------
+template <int DIM> __device__ __forceinline__ int comp_of(int b) { return DIM == 3 ? b : (b == 0 ? 0 : 2); }
+
+template <typename T, int DIM, int N>
+__global__ void k_face_explicit(FaceTopo ft, const T* __restrict__ trc, T* __restrict__ slot,
+                                T* __restrict__ hbuf, Tables<T> tb, T gamma) {
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= ft.nF) return;
+  const int64_t S = ft.S;
+  int sm = __ldg(ft.fp_minus + p), code = __ldg(ft.fp_plus + p);
+  T nS[DIM];
+  T n2 = 0;
+#pragma unroll
+  for (int b = 0; b < DIM; ++b) {
+    nS[b] = (T)__ldg(ft.fgeo + b * ft.nF + p);
+    n2 += nS[b] * nS[b];
+  }
+  T qm[5], qp[5];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) qm[q] = __ldg(trc + q * S + sm);
+  if (code == -1) {
+    // slip wall: mirror momentum, m+ = m- - 2 (m-.n) n
+    T mn = 0;
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) mn += qm[1 + comp_of<DIM>(b)] * nS[b];
+    mn /= n2;
+#pragma unroll
+    for (int q = 0; q < 5; ++q) qp[q] = qm[q];
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) qp[1 + comp_of<DIM>(b)] -= 2 * mn * nS[b];
+  } else {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) qp[q] = plus_value<T, DIM, N>(ft, tb, trc + q * S, code, qm[q]);
+  }
+  const T gm1 = gamma - 1;
+  T irm = 1 / qm[0], irp = 1 / qp[0];
+  T um[3] = {qm[1] * irm, qm[2] * irm, qm[3] * irm};
+  T up[3] = {qp[1] * irp, qp[2] * irp, qp[3] * irp};
+  T rkm = (T)0.5 * (qm[1] * um[0] + qm[2] * um[1] + qm[3] * um[2]);
+  T rkp = (T)0.5 * (qp[1] * up[0] + qp[2] * up[1] + qp[3] * up[2]);
+  T pm = gm1 * (qm[4] - rkm), pp = gm1 * (qp[4] - rkp);
+  T unm = 0, unp = 0;
+#pragma unroll
+  for (int b = 0; b < DIM; ++b) {
+    unm += um[comp_of<DIM>(b)] * nS[b];
+    unp += up[comp_of<DIM>(b)] * nS[b];
+  }
+  // lambda |n dS| / 2 with lambda = max(|u-.n|, |u+.n|)
+  T pen = (T)0.5 * fmax(fabs(unm), fabs(unp));
+  const int64_t nH = ft.nH;
+  put<T>(slot, hbuf, S, nH, 0, sm, code, (T)0.5 * (qm[0] * unm + qp[0] * unp) + pen * (qm[0] - qp[0]));
+#pragma unroll
+  for (int c = 0; c < 3; ++c)
+    put<T>(slot, hbuf, S, nH, 1 + c, sm, code,
+           (T)0.5 * (qm[1 + c] * unm + qp[1 + c] * unp) + pen * (qm[1 + c] - qp[1 + c]));
+  put<T>(slot, hbuf, S, nH, 4, sm, code, (T)0.5 * (rkm * unm + rkp * unp) + pen * (rkm - rkp));
+  T pav = (T)0.5 * (pm + pp);
+  put<T>(slot, hbuf, S, nH, 5, sm, code, pav * nS[0]);
+  put<T>(slot, hbuf, S, nH, 6, sm, code, DIM == 3 ? pav * nS[DIM == 3 ? 1 : 0] : (T)0);
+  put<T>(slot, hbuf, S, nH, 7, sm, code, pav * nS[DIM - 1]);
+  put<T>(slot, hbuf, S, nH, 8, sm, code,
+         (T)0.5 * gamma / gm1 * (pm * unm + pp * unp) + pen * (pm - pp) / gm1);
+}
+
+// ---------------------------------------------------------------------------
+// cell kernels (one thread per node, EPB cells per block)
+// ---------------------------------------------------------------------------
+template <int DIM, int N> struct CellShape {
+  static constexpr int NP = ipow(N, DIM);
+  static constexpr int EPB = NP >= 256 ? 1 : 256 / NP;
+  static constexpr int THREADS = EPB * NP;
+  static constexpr int NFP = ipow(N, DIM - 1);
+  static constexpr int NF = 2 * DIM;
+};
+
+// sum_a sum_k D[k][i_a] * sm[a][line(i, a, k)]  (test-gradient contraction)
+template <typename T, int DIM, int N>
+__device__ __forceinline__ T contract(const Tables<T>& tb, const T (*sm)[ipow(N, DIM)], int i,
+                                      const int idx[3]) {
+  T acc = 0;
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    const int stride = a == 0 ? 1 : (a == 1 ? N : N * N);
+    const int i0 = i - idx[a] * stride;
+#pragma unroll
+    for (int k = 0; k < N; ++k) acc += tb.D[k][idx[a]] * sm[a][i0 + k * stride];
+  }
+  return acc;
+}
+
+// lift of NFLD slot fields into the residuals of node i
+template <typename T, int DIM, int N, int NFLD>
+__device__ __forceinline__ void lift(const Tables<T>& tb, const T* __restrict__ slot, int64_t S,
+                                     int64_t e, const int idx[3], T* r) {
+  constexpr int NFP = ipow(N, DIM - 1), NF = 2 * DIM;
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    const int a = f >> 1, s = f & 1;
+    const T Lv = tb.L[s][idx[a]];
+    const int64_t sl = (e * NF + f) * NFP + tang_index<DIM, N>(idx, a);
+#pragma unroll
+    for (int q = 0; q < NFLD; ++q) r[q] -= __ldg(slot + q * S + sl) * Lv;
+  }
+}
+
+struct PhysK {
+  double gamma, g, f;
+};
+
+template <typename T, int DIM, int N>
+__global__ void __launch_bounds__(CellShape<DIM, N>::THREADS)
+k_volume_explicit(const T* __restrict__ q, const double* __restrict__ Kg, const double* __restrict__ invMg,
+                  const T* __restrict__ slot, int64_t E, int64_t S, Tables<T> tb, PhysK ph,
+                  T* __restrict__ fns, T* __restrict__ fs) {
+  using CS = CellShape<DIM, N>;
+  constexpr int NP = CS::NP, EPB = CS::EPB;
+  __shared__ T sm[EPB][DIM][NP];
+  const int le = threadIdx.x / NP, i = threadIdx.x % NP;
+  const int64_t e = (int64_t)blockIdx.x * EPB + le;
+  const bool active = e < E;
+  const int64_t Nn = E * NP;
+  const int64_t node = active ? e * NP + i : 0;
+  int idx[3];
+  node_index<DIM, N>(i, idx);
+  T rho = 1, m[3] = {0, 0, 0}, En = 1, K[DIM][DIM], iM = 0;
+  if (active) {
+    rho = __ldg(q + node);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) m[c] = __ldg(q + (1 + c) * Nn + node);
+    En = __ldg(q + 4 * Nn + node);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a)
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) K[a][b] = (T)__ldg(Kg + (a * DIM + b) * Nn + node);
+    iM = (T)__ldg(invMg + node);
+  } else {
+#pragma unroll
+    for (int a = 0; a < DIM; ++a)
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) K[a][b] = 0;
+  }
+  const T gm1 = (T)ph.gamma - 1;
+  const T ir = 1 / rho;
+  const T u[3] = {m[0] * ir, m[1] * ir, m[2] * ir};
+  const T rk = (T)0.5 * (m[0] * u[0] + m[1] * u[1] + m[2] * u[2]);
+  const T p = gm1 * (En - rk);
+  const T hr = (T)ph.gamma / gm1 * p;
+  T ut[DIM];   // contravariant velocity times w det J
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    ut[a] = 0;
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) ut[a] += K[a][b] * u[comp_of<DIM>(b)];
+  }
+  T r[9];
+  // flux fields: 0 rho, 1-3 m_c, 4 rho kappa (advective); 5-7 p e_c, 8 h rho (stiff)
+#pragma unroll
+  for (int fld = 0; fld < 9; ++fld) {
+    const bool skip = (DIM == 2 && fld == 6);   // no y-derivative in the x-z slice
+    if (skip) {
+      r[fld] = 0;
+      continue;
+    }
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      T v;
+      if (fld == 0) v = rho * ut[a];
+      else if (fld <= 3) v = m[fld - 1] * ut[a];
+      else if (fld == 4) v = rk * ut[a];
+      else if (fld <= 7) {
+        const int c = fld - 5;
+        const int b = DIM == 3 ? c : (c == 0 ? 0 : 1);
+        v = p * K[a][b];
+      } else v = hr * ut[a];
+      sm[le][a][i] = v;
+    }
+    __syncthreads();
+    r[fld] = contract<T, DIM, N>(tb, sm[le], i, idx);
+    __syncthreads();
+  }
+  if (!active) return;
+  lift<T, DIM, N, 9>(tb, slot, S, e, idx, r);
+#pragma unroll
+  for (int fld = 0; fld < 5; ++fld) fns[fld * Nn + node] = iM * r[fld];
+  const T f = (T)ph.f, g = (T)ph.g;
+  fs[0 * Nn + node] = iM * r[5] + f * m[1];
+  fs[1 * Nn + node] = iM * r[6] - f * m[0];
+  fs[2 * Nn + node] = iM * r[7] - g * rho;
+  fs[3 * Nn + node] = iM * r[8] - g * m[2];
+}
+
+// ---------------------------------------------------------------------------
+// implicit operator pieces
+// ---------------------------------------------------------------------------
+
+// centred weak-gradient flux {x} n dS (DIM fields) and the implicit Rusanov
+// jump pc * (x- - x+) (field DIM), pc = a_dt/2 max(|u-.n dS|, |u+.n dS|)
+template <typename T, int DIM, int N>
+__global__ void k_face_grad(FaceTopo ft, const T* __restrict__ trc, const T* __restrict__ pcoef,
+                            T* __restrict__ slot, T* __restrict__ hbuf, Tables<T> tb) {
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= ft.nF) return;
+  int sm = __ldg(ft.fp_minus + p), code = __ldg(ft.fp_plus + p);
+  T xm = __ldg(trc + sm);
+  T xp = plus_value<T, DIM, N>(ft, tb, trc, code, xm);
+  T avg = code == -1 ? xm : (T)0.5 * (xm + xp);
+#pragma unroll
+  for (int b = 0; b < DIM; ++b)
+    put<T>(slot, hbuf, ft.S, ft.nH, b, sm, code, -avg * (T)__ldg(ft.fgeo + b * ft.nF + p));
+  T pen = (code == -1 || pcoef == nullptr) ? (T)0 : __ldg(pcoef + p) * (xm - xp);
+  put<T>(slot, hbuf, ft.S, ft.nH, DIM, sm, code, -pen);
+}
+
+// central flux of h rho w:  -{h rho w}.n dS  (zero on walls)
+template <typename T, int DIM, int N>
+__global__ void k_face_div(FaceTopo ft, const T* __restrict__ trc, const T* __restrict__ trh,
+                           T* __restrict__ slot, T* __restrict__ hbuf, Tables<T> tb) {
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= ft.nF) return;
+  int sm = __ldg(ft.fp_minus + p), code = __ldg(ft.fp_plus + p);
+  T avg = 0;
+  if (code != -1) {
+    T hm = __ldg(trh + sm), hp = plus_value<T, DIM, N>(ft, tb, trh, code, hm);
+    T fm = 0, fp = 0;
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) {
+      T n = (T)__ldg(ft.fgeo + b * ft.nF + p);
+      T wm = __ldg(trc + b * ft.S + sm);
+      T wp = plus_value<T, DIM, N>(ft, tb, trc + b * ft.S, code, wm);
+      fm += wm * n;
+      fp += wp * n;
+    }
+    avg = (T)0.5 * (hm * fm + hp * fp);
+  }
+  put<T>(slot, hbuf, ft.S, ft.nH, 0, sm, code, -avg);
+}
+
+// lambda coefficient of the implicit Rusanov term from u_lag traces
+template <typename T, int DIM, int N>
+__global__ void k_face_lambda(FaceTopo ft, const T* __restrict__ tru, T a_dt_half, T* __restrict__ pcoef,
+                              Tables<T> tb) {
+  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (p >= ft.nF) return;
+  int sm = __ldg(ft.fp_minus + p), code = __ldg(ft.fp_plus + p);
+  T unm = 0, unp = 0;
+#pragma unroll
+  for (int b = 0; b < DIM; ++b) {
+    T n = (T)__ldg(ft.fgeo + b * ft.nF + p);
+    T um = __ldg(tru + comp_of<DIM>(b) * ft.S + sm);
+    T up = plus_value<T, DIM, N>(ft, tb, tru + comp_of<DIM>(b) * ft.S, code, um);
+    unm += um * n;
+    unp += up * n;
+  }
+  pcoef[p] = a_dt_half * fmax(fabs(unm), fabs(unp));
+}
+
+enum GradMode { GRAD_VMULT = 0, GRAD_RECOVER = 1 };
+
+struct ImplK {
+  double gamma, g, f, a_dt;
+  int r2;
+};
+
+// weak gradient G = M^{-1}[-int x grad(phi) + faces]; then
+//  VMULT  : w = rho^{-1} (I + beta J)^{-1} G (R2) or G / rho (R1) -> wv (DIM
+//           spatial comps); y = x + pen - (gamma-1) a_dt^2 g G_z (R2)
+//  RECOVER: u = ustar - a_dt * w  (3 comps)
+template <typename T, int DIM, int N, int MODE>
+__global__ void __launch_bounds__(CellShape<DIM, N>::THREADS)
+k_volume_grad(const T* __restrict__ x, const T* __restrict__ rho, const double* __restrict__ Kg,
+              const double* __restrict__ invMg, const T* __restrict__ slot, int64_t E, int64_t S,
+              Tables<T> tb, ImplK ph, T* __restrict__ wv, T* __restrict__ y,
+              const T* __restrict__ ustar, T* __restrict__ uout) {
+  using CS = CellShape<DIM, N>;
+  constexpr int NP = CS::NP, EPB = CS::EPB;
+  __shared__ T sm[EPB][DIM][NP];
+  const int le = threadIdx.x / NP, i = threadIdx.x % NP;
+  const int64_t e = (int64_t)blockIdx.x * EPB + le;
+  const bool active = e < E;
+  const int64_t Nn = E * NP;
+  const int64_t node = active ? e * NP + i : 0;
+  int idx[3];
+  node_index<DIM, N>(i, idx);
+  T xv = active ? __ldg(x + node) : (T)0;
+  T r[DIM + 1];
+#pragma unroll
+  for (int b = 0; b < DIM; ++b) {
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) sm[le][a][i] = active ? -xv * (T)__ldg(Kg + (a * DIM + b) * Nn + node) : (T)0;
+    __syncthreads();
+    r[b] = contract<T, DIM, N>(tb, sm[le], i, idx);
+    __syncthreads();
+  }
+  r[DIM] = 0;
+  if (!active) return;
+  lift<T, DIM, N, DIM + 1>(tb, slot, S, e, idx, r);
+  const T iM = (T)__ldg(invMg + node);
+  T G[3] = {0, 0, 0};
+#pragma unroll
+  for (int b = 0; b < DIM; ++b) G[comp_of<DIM>(b)] = iM * r[b];
+  const T ir = 1 / __ldg(rho + node);
+  T w[3];
+  if (ph.r2) {
+    const T beta = (T)(ph.a_dt * ph.f);
+    const T d = 1 / (1 + beta * beta);
+    w[0] = (G[0] + beta * G[1]) * d * ir;
+    w[1] = (G[1] - beta * G[0]) * d * ir;
+    w[2] = G[2] * ir;
+  } else {
+    w[0] = G[0] * ir;
+    w[1] = G[1] * ir;
+    w[2] = G[2] * ir;
+  }
+  if (MODE == GRAD_VMULT) {
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) wv[b * Nn + node] = w[comp_of<DIM>(b)];
+    const T gm1 = (T)ph.gamma - 1, adt = (T)ph.a_dt;
+    T yv = xv + iM * r[DIM];
+    if (ph.r2) yv -= gm1 * adt * adt * (T)ph.g * G[2];
+    y[node] = yv;
+  } else {
+    const T adt = (T)ph.a_dt;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) uout[c * Nn + node] = __ldg(ustar + c * Nn + node) - adt * w[c];
+  }
+}
+
+enum DivMode { DIV_VMULT = 0, DIV_RHS = 1 };
+
+// weak divergence Div = M^{-1}[-int h rho w . grad(psi) + faces], h rho =
+// gamma p_lag / (gamma - 1);
+//  VMULT: y -= (gamma-1) a_dt^2 Div
+//  RHS  : y = (gamma-1) [e_hat - rho |u_lag|^2 / 2 - a_dt (Div + g rho w3_z)],
+//         w3_z = ustar_z (R2) or u_lag_z (R1)
+template <typename T, int DIM, int N, int MODE>
+__global__ void __launch_bounds__(CellShape<DIM, N>::THREADS)
+k_volume_div(Fields<T> wv, const T* __restrict__ plag, const double* __restrict__ Kg,
+             const double* __restrict__ invMg, const T* __restrict__ slot, int64_t E, int64_t S,
+             Tables<T> tb, ImplK ph, T* __restrict__ y, const T* __restrict__ ehat,
+             const T* __restrict__ rho, const T* __restrict__ ulag, const T* __restrict__ ustar) {
+  using CS = CellShape<DIM, N>;
+  constexpr int NP = CS::NP, EPB = CS::EPB;
+  __shared__ T sm[EPB][DIM][NP];
+  const int le = threadIdx.x / NP, i = threadIdx.x % NP;
+  const int64_t e = (int64_t)blockIdx.x * EPB + le;
+  const bool active = e < E;
+  const int64_t Nn = E * NP;
+  const int64_t node = active ? e * NP + i : 0;
+  int idx[3];
+  node_index<DIM, N>(i, idx);
+  const T gm1 = (T)ph.gamma - 1;
+  if (active) {
+    T hr = (T)ph.gamma / gm1 * __ldg(plag + node);
+    T wl[DIM];
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) wl[b] = __ldg(wv.f[b] + node);
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      T v = 0;
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) v += (T)__ldg(Kg + (a * DIM + b) * Nn + node) * wl[b];
+      sm[le][a][i] = -hr * v;
+    }
+  } else {
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) sm[le][a][i] = 0;
+  }
+  __syncthreads();
+  T r[1];
+  r[0] = contract<T, DIM, N>(tb, sm[le], i, idx);
+  if (!active) return;
+  lift<T, DIM, N, 1>(tb, slot, S, e, idx, r);
+  const T div = (T)__ldg(invMg + node) * r[0];
+  const T adt = (T)ph.a_dt;
+  if (MODE == DIV_VMULT) {
+    y[node] -= gm1 * adt * adt * div;
+  } else {
+    const T rh = __ldg(rho + node);
+    T u2 = 0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      T uc = __ldg(ulag + c * Nn + node);
+      u2 += uc * uc;
+    }
+    const T wz = ph.r2 ? __ldg(ustar + 2 * Nn + node) : __ldg(ulag + 2 * Nn + node);
+    y[node] = gm1 * (__ldg(ehat + node) - (T)0.5 * rh * u2 - adt * (div + (T)ph.g * rh * wz));
+  }
+}
+
+// u* = rho^{-1} (I + beta J)^{-1} (m_hat - a_dt g rho k)           (R2)
+// u* = rho^{-1} (m_hat - a_dt f rho k x u_lag - a_dt g rho k)       (R1)
+template <typename T>
+__global__ void k_ustar(const T* __restrict__ mhat, const T* __restrict__ rho, const T* __restrict__ ulag,
+                        int64_t Nn, ImplK ph, T* __restrict__ ustar) {
+  int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (k >= Nn) return;
+  const T rh = rho[k], adt = (T)ph.a_dt;
+  T v0 = mhat[k], v1 = mhat[Nn + k], v2 = mhat[2 * Nn + k] - adt * (T)ph.g * rh;
+  const T ir = 1 / rh;
+  if (ph.r2) {
+    const T beta = (T)(ph.a_dt * ph.f), d = 1 / (1 + beta * beta);
+    ustar[k] = (v0 + beta * v1) * d * ir;
+    ustar[Nn + k] = (v1 - beta * v0) * d * ir;
+    ustar[2 * Nn + k] = v2 * ir;
+  } else {
+    const T fr = adt * (T)ph.f * rh;
+    // k x u = (-v, u, 0)
+    ustar[k] = (v0 + fr * ulag[Nn + k]) * ir;
+    ustar[Nn + k] = (v1 - fr * ulag[k]) * ir;
+    ustar[2 * Nn + k] = v2 * ir;
+  }
+}
+
+}  // namespace dg

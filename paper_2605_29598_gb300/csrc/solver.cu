@@ -1,0 +1,515 @@
+// GMRES on the scaled pressure Schur system, the Picard loop and the ARK2
+// IMEX step (Section 3), with FP64 device reductions.
+#include <cmath>
+#include <vector>
+
+#include "engine.cuh"
+
+namespace dg {
+
+constexpr int RED_BLOCKS = 1024;   // partial sums per reduction (fixed order)
+constexpr int MAX_RESTART = 64;
+
+// ---------------------------------------------------------------------------
+// vector kernels (FP64)
+// ---------------------------------------------------------------------------
+
+// partial[b * nvec + k] = sum over block b's chunk of V[k] . w
+__global__ void k_multidot(const double* __restrict__ V, int nvec, int64_t n, const double* __restrict__ w,
+                           double* __restrict__ partial) {
+  __shared__ double red[256];
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t lo = blockIdx.x * chunk;
+  const int64_t hi = lo + chunk < n ? lo + chunk : n;
+  for (int k = 0; k < nvec; ++k) {
+    const double* v = V + (int64_t)k * n;
+    double s = 0.0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) s += v[i] * w[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x * nvec + k] = red[0];
+    __syncthreads();
+  }
+}
+
+__global__ void k_reduce_partials(const double* __restrict__ partial, int nvec, int nblk, double* __restrict__ out) {
+  __shared__ double red[256];
+  const int k = blockIdx.x;
+  double s = 0.0;
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) s += partial[b * nvec + k];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[k] = red[0];
+}
+
+struct Coefs {
+  double c[MAX_RESTART + 1];
+};
+
+// w += sum_k c_k V_k
+__global__ void k_multiaxpy(const double* __restrict__ V, int nvec, int64_t n, Coefs c, double* __restrict__ w) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double acc = w[i];
+  for (int k = 0; k < nvec; ++k) acc += c.c[k] * V[(int64_t)k * n + i];
+  w[i] = acc;
+}
+
+__global__ void k_axpby(int64_t n, double a, const double* __restrict__ x, double b, const double* __restrict__ y,
+                        double* __restrict__ z) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) z[i] = a * x[i] + b * y[i];
+}
+
+__global__ void k_scale(int64_t n, double a, double* __restrict__ x) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) x[i] *= a;
+}
+
+// stage predictors: rho_l = rho^n + dt sum a F_NS,rho;
+// m_hat = m^n + dt sum (a F_NS,m + at F_S,m); e_hat likewise
+struct StageCoefs {
+  const double* fns[3];
+  const double* fs[3];
+  double a[3], at[3];
+  int nst;
+  double dt;
+};
+
+__global__ void k_stage_predict(const double* __restrict__ q, int64_t n, StageCoefs c, double* __restrict__ rho,
+                                double* __restrict__ mhat, double* __restrict__ ehat) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double r = 0, m0 = 0, m1 = 0, m2 = 0, e = 0;
+  for (int s = 0; s < c.nst; ++s) {
+    const double a = c.a[s], at = c.at[s];
+    const double* F = c.fns[s];
+    const double* G = c.fs[s];
+    r += a * F[i];
+    m0 += a * F[n + i] + at * G[i];
+    m1 += a * F[2 * n + i] + at * G[n + i];
+    m2 += a * F[3 * n + i] + at * G[2 * n + i];
+    e += a * F[4 * n + i] + at * G[3 * n + i];
+  }
+  rho[i] = q[i] + c.dt * r;
+  mhat[i] = q[n + i] + c.dt * m0;
+  mhat[n + i] = q[2 * n + i] + c.dt * m1;
+  mhat[2 * n + i] = q[3 * n + i] + c.dt * m2;
+  ehat[i] = q[4 * n + i] + c.dt * e;
+}
+
+// nodal u = m / rho, p = (gamma - 1)(E - m.u / 2)
+__global__ void k_primitives(const double* __restrict__ q, int64_t n, double gamma, double* __restrict__ u,
+                             double* __restrict__ p) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double ir = 1.0 / q[i];
+  const double u0 = q[n + i] * ir, u1 = q[2 * n + i] * ir, u2 = q[3 * n + i] * ir;
+  u[i] = u0;
+  u[n + i] = u1;
+  u[2 * n + i] = u2;
+  p[i] = (gamma - 1.0) * (q[4 * n + i] - 0.5 * (q[n + i] * u0 + q[2 * n + i] * u1 + q[3 * n + i] * u2));
+}
+
+// stage state: m = rho u, E = p / (gamma - 1) + rho |u|^2 / 2
+__global__ void k_stage_state(const double* __restrict__ rho, const double* __restrict__ u,
+                              const double* __restrict__ p, int64_t n, double gamma, double* __restrict__ y) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double r = rho[i], u0 = u[i], u1 = u[n + i], u2 = u[2 * n + i];
+  y[i] = r;
+  y[n + i] = r * u0;
+  y[2 * n + i] = r * u1;
+  y[3 * n + i] = r * u2;
+  y[4 * n + i] = p[i] / (gamma - 1.0) + 0.5 * r * (u0 * u0 + u1 * u1 + u2 * u2);
+}
+
+// q += dt sum_l b_l (F_NS,l + F_S,l)
+__global__ void k_final_update(double* __restrict__ q, int64_t n, StageCoefs c) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double acc[5] = {0, 0, 0, 0, 0};
+  for (int s = 0; s < c.nst; ++s) {
+    const double b = c.a[s];
+    const double* F = c.fns[s];
+    const double* G = c.fs[s];
+    acc[0] += b * F[i];
+    for (int k = 1; k < 5; ++k) acc[k] += b * (F[k * n + i] + G[(k - 1) * n + i]);
+  }
+  for (int k = 0; k < 5; ++k) q[k * n + i] += c.dt * acc[k];
+}
+
+// four sums for the Picard test: |p1-p0|^2, |p1|^2, |u1-u0|^2, |u1|^2
+__global__ void k_picard_norms(const double* __restrict__ p0, const double* __restrict__ p1,
+                               const double* __restrict__ u0, const double* __restrict__ u1, int64_t n,
+                               double* __restrict__ partial) {
+  __shared__ double red[4][256];
+  const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
+  const int64_t lo = blockIdx.x * chunk;
+  const int64_t hi = lo + chunk < n ? lo + chunk : n;
+  double s[4] = {0, 0, 0, 0};
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    const double dp = p1[i] - p0[i];
+    s[0] += dp * dp;
+    s[1] += p1[i] * p1[i];
+    for (int c = 0; c < 3; ++c) {
+      const double a = u1[c * n + i], du = a - u0[c * n + i];
+      s[2] += du * du;
+      s[3] += a * a;
+    }
+  }
+  for (int k = 0; k < 4; ++k) red[k][threadIdx.x] = s[k];
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o)
+      for (int k = 0; k < 4; ++k) red[k][threadIdx.x] += red[k][threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 4; ++k) partial[blockIdx.x * 4 + k] = red[k][0];
+}
+
+// ---------------------------------------------------------------------------
+// host helpers
+// ---------------------------------------------------------------------------
+
+struct Red {
+  double* partial;   // RED_BLOCKS * (MAX_RESTART + 1)
+  double* out;       // MAX_RESTART + 1
+};
+
+static int ensure_red(dg_mesh* m, Red* r) {
+  int rc = m->red.ensure(sizeof(double) * (RED_BLOCKS * (MAX_RESTART + 1) + (MAX_RESTART + 1)));
+  if (rc) return rc;
+  r->partial = m->red.as<double>();
+  r->out = r->partial + RED_BLOCKS * (MAX_RESTART + 1);
+  return DG_OK;
+}
+
+// host <- V[0..nvec)^T w  (synchronises the stream)
+static int dots(const Red& r, const double* V, int nvec, int64_t n, const double* w, double* host,
+                cudaStream_t st) {
+  k_multidot<<<RED_BLOCKS, 256, 0, st>>>(V, nvec, n, w, r.partial);
+  k_reduce_partials<<<nvec, 256, 0, st>>>(r.partial, nvec, RED_BLOCKS, r.out);
+  DG_LAUNCH_CHECK("reduction");
+  DG_CUDA(cudaMemcpyAsync(host, r.out, sizeof(double) * nvec, cudaMemcpyDeviceToHost, st));
+  DG_CUDA(cudaStreamSynchronize(st));
+  return DG_OK;
+}
+
+// generic vmult closure: the solver is written against y = S x
+struct Vmult {
+  int (*fn)(void* self, const double* x, double* y, cudaStream_t st);
+  void* self;
+  int operator()(const double* x, double* y, cudaStream_t st) const { return fn(self, x, y, st); }
+};
+
+// Restarted GMRES(m), classical Gram-Schmidt applied twice, Givens rotations.
+static int gmres(dg_mesh* m, const Vmult& A, const double* b, double* x, double rtol, int restart, int maxit,
+                 dg_gmres_info* info, cudaStream_t st) {
+  const int64_t n = m->N;
+  if (restart < 1 || restart > MAX_RESTART || maxit < 0 || !(rtol >= 0.0)) {
+    set_error("gmres: restart must be in 1..%d, maxit >= 0, rtol >= 0", MAX_RESTART);
+    return DG_ERR_ARG;
+  }
+  int rc;
+  if ((rc = m->gm_V.ensure(sizeof(double) * (size_t)(restart + 1) * n)) != DG_OK) return rc;
+  if ((rc = m->gm_work.ensure(sizeof(double) * (size_t)n)) != DG_OK) return rc;
+  Red red;
+  if ((rc = ensure_red(m, &red)) != DG_OK) return rc;
+  double* V = m->gm_V.as<double>();
+  double* tmp = m->gm_work.as<double>();
+  const unsigned gb = grid_for(n, 256);
+  double bn2;
+  if ((rc = dots(red, b, 1, n, b, &bn2, st)) != DG_OK) return rc;
+  const double bnorm = std::sqrt(bn2);
+  if (!std::isfinite(bnorm)) {
+    set_error("gmres: non-finite right-hand side");
+    return DG_ERR_NONFINITE;
+  }
+  if (bnorm == 0.0) {
+    DG_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
+    if (info) {
+      info->iters = 0;
+      info->relres = 0.0;
+    }
+    return DG_OK;
+  }
+  std::vector<double> H((restart + 1) * restart), cs(restart), sn(restart), g(restart + 1), h1(restart + 1),
+      h2(restart + 1), y(restart);
+  auto Hij = [&](int i, int j) -> double& { return H[i * restart + j]; };
+  int it = 0;
+  double relres = 0.0;
+  while (true) {
+    if ((rc = A(x, tmp, st)) != DG_OK) return rc;
+    k_axpby<<<gb, 256, 0, st>>>(n, 1.0, b, -1.0, tmp, V);
+    double b2;
+    if ((rc = dots(red, V, 1, n, V, &b2, st)) != DG_OK) return rc;
+    const double beta = std::sqrt(b2);
+    if (!std::isfinite(beta)) {
+      set_error("gmres: non-finite residual");
+      return DG_ERR_NONFINITE;
+    }
+    relres = beta / bnorm;
+    if (beta <= rtol * bnorm || it >= maxit) {
+      if (info) {
+        info->iters = it;
+        info->relres = relres;
+      }
+      if (beta <= rtol * bnorm) return DG_OK;
+      set_error("gmres: %d iterations, relative residual %.3e > %.3e", it, relres, rtol);
+      return DG_ERR_NOT_CONVERGED;
+    }
+    k_scale<<<gb, 256, 0, st>>>(n, 1.0 / beta, V);
+    std::fill(g.begin(), g.end(), 0.0);
+    g[0] = beta;
+    int jused = 0;
+    for (int j = 0; j < restart; ++j) {
+      double* vj = V + (int64_t)j * n;
+      double* w = V + (int64_t)(j + 1) * n;
+      if ((rc = A(vj, w, st)) != DG_OK) return rc;
+      Coefs c;
+      if ((rc = dots(red, V, j + 1, n, w, h1.data(), st)) != DG_OK) return rc;
+      for (int k = 0; k <= j; ++k) c.c[k] = -h1[k];
+      k_multiaxpy<<<gb, 256, 0, st>>>(V, j + 1, n, c, w);
+      if ((rc = dots(red, V, j + 1, n, w, h2.data(), st)) != DG_OK) return rc;
+      for (int k = 0; k <= j; ++k) c.c[k] = -h2[k];
+      k_multiaxpy<<<gb, 256, 0, st>>>(V, j + 1, n, c, w);
+      for (int k = 0; k <= j; ++k) Hij(k, j) = h1[k] + h2[k];
+      double w2;
+      if ((rc = dots(red, w, 1, n, w, &w2, st)) != DG_OK) return rc;
+      const double hn = std::sqrt(w2);
+      if (!std::isfinite(hn)) {
+        set_error("gmres: non-finite Krylov vector");
+        return DG_ERR_NONFINITE;
+      }
+      Hij(j + 1, j) = hn;
+      if (hn > 0.0) k_scale<<<gb, 256, 0, st>>>(n, 1.0 / hn, w);
+      for (int k = 0; k < j; ++k) {
+        const double t = cs[k] * Hij(k, j) + sn[k] * Hij(k + 1, j);
+        Hij(k + 1, j) = -sn[k] * Hij(k, j) + cs[k] * Hij(k + 1, j);
+        Hij(k, j) = t;
+      }
+      const double den = std::hypot(Hij(j, j), Hij(j + 1, j));
+      cs[j] = Hij(j, j) / den;
+      sn[j] = Hij(j + 1, j) / den;
+      Hij(j, j) = den;
+      Hij(j + 1, j) = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      ++it;
+      jused = j + 1;
+      if (std::fabs(g[j + 1]) <= rtol * bnorm || it >= maxit) break;
+    }
+    for (int i = jused - 1; i >= 0; --i) {
+      double s = g[i];
+      for (int k = i + 1; k < jused; ++k) s -= Hij(i, k) * y[k];
+      y[i] = s / Hij(i, i);
+    }
+    Coefs c;
+    for (int k = 0; k < jused; ++k) c.c[k] = y[k];
+    k_multiaxpy<<<gb, 256, 0, st>>>(V, jused, n, c, x);
+    DG_LAUNCH_CHECK("gmres update");
+  }
+}
+
+struct SchurCtx {
+  dg_mesh* m;
+  ImplK k;
+  const double* rho;
+  const double* plag;
+  int penalty;
+};
+
+template <int D, int NN>
+static int schur_vmult_fn(void* self, const double* x, double* y, cudaStream_t st) {
+  SchurCtx* s = static_cast<SchurCtx*>(self);
+  return Engine<double, D, NN>::vmult(s->m, s->k, s->rho, s->plag, s->penalty, x, y, st);
+}
+
+static Vmult make_vmult(SchurCtx* s) {
+  Vmult v{nullptr, s};
+  DG_DISPATCH(s->m, v.fn = &schur_vmult_fn<D_, N_>);
+  return v;
+}
+
+static int prepare_rt(dg_mesh* m, const ImplK& k, const double* plag, const double* ulag, int penalty,
+                      cudaStream_t st) {
+  DG_DISPATCH(m, return (Engine<double, D_, N_>::prepare(m, k, plag, ulag, penalty, st)));
+  return DG_ERR_UNSUPPORTED;
+}
+
+static int explicit_rt(dg_mesh* m, const dg_phys* ph, const double* q, double* fns, double* fs, cudaStream_t st) {
+  PhysK k{ph->gamma, ph->g, ph->f};
+  DG_DISPATCH(m, return (Engine<double, D_, N_>::explicit_rates(m, k, q, fns, fs, st)));
+  return DG_ERR_UNSUPPORTED;
+}
+
+static int rhs_rt(dg_mesh* m, const ImplK& k, const double* rho, const double* plag, const double* ulag,
+                  const double* mhat, const double* ehat, double* rhs, cudaStream_t st) {
+  DG_DISPATCH(m, return (Engine<double, D_, N_>::schur_rhs(m, k, rho, plag, ulag, mhat, ehat, rhs, st)));
+  return DG_ERR_UNSUPPORTED;
+}
+
+static int recover_rt(dg_mesh* m, const ImplK& k, const double* rho, const double* ulag, const double* mhat,
+                      const double* p, double* u, cudaStream_t st) {
+  DG_DISPATCH(m, return (Engine<double, D_, N_>::recover(m, k, rho, ulag, mhat, p, u, st)));
+  return DG_ERR_UNSUPPORTED;
+}
+
+static int check_phys(const dg_phys* ph, const char* who) {
+  if (!ph || !(ph->gamma > 1.0) || (ph->variant != DG_R1 && ph->variant != DG_R2)) {
+    set_error("%s: invalid physics (gamma > 1, variant R1/R2)", who);
+    return DG_ERR_ARG;
+  }
+  if (ph->precision != DG_FP64) {
+    set_error("%s: only DG_FP64 is implemented", who);
+    return DG_ERR_UNSUPPORTED;
+  }
+  return DG_OK;
+}
+
+}  // namespace dg
+
+using namespace dg;
+
+extern "C" {
+
+int dg_gmres_solve(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* ph, const dg_implicit_coeffs* cf,
+                   const double* b, double* x, const dg_gmres_opts* opts, dg_gmres_info* info, void* stream) {
+  if (!ctx || !mesh || !cf || !cf->rho || !cf->p_lag || !cf->u_lag || !b || !x || !opts) {
+    set_error("dg_gmres_solve: NULL argument");
+    return DG_ERR_ARG;
+  }
+  int rc = check_phys(ph, "dg_gmres_solve");
+  if (rc) return rc;
+  dg_mesh* m = const_cast<dg_mesh*>(mesh);
+  cudaStream_t st = (cudaStream_t)stream;
+  ImplK k = impl_consts(ph, cf->a_dt);
+  if ((rc = prepare_rt(m, k, cf->p_lag, cf->u_lag, ph->penalty, st)) != DG_OK) return rc;
+  SchurCtx sc{m, k, cf->rho, cf->p_lag, ph->penalty};
+  Vmult A = make_vmult(&sc);
+  if (!A.fn) return DG_ERR_UNSUPPORTED;
+  return gmres(m, A, b, x, opts->rtol, opts->restart, opts->maxit, info, st);
+}
+
+int imex_ark2_step(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* ph, double* q, double dt,
+                   const dg_step_opts* opts, dg_step_info* info, void* stream) {
+  if (!ctx || !mesh || !q || !opts) {
+    set_error("imex_ark2_step: NULL argument");
+    return DG_ERR_ARG;
+  }
+  int rc = check_phys(ph, "imex_ark2_step");
+  if (rc) return rc;
+  if (!(dt > 0.0) || opts->picard_maxit < 1 || opts->picard_fixed < 0) {
+    set_error("imex_ark2_step: dt > 0, picard_maxit >= 1, picard_fixed >= 0 required");
+    return DG_ERR_ARG;
+  }
+  dg_mesh* m = const_cast<dg_mesh*>(mesh);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = m->N;
+  // tableaux (Section 3): explicit a, implicit at, weights b
+  const double chi = 2.0 - std::sqrt(2.0), a32 = 0.5;
+  const double a[3][3] = {{0, 0, 0}, {chi, 0, 0}, {1.0 - a32, a32, 0}};
+  const double bw[3] = {0.5 - chi / 4.0, 0.5 - chi / 4.0, chi / 2.0};
+  const double at[3][3] = {{0, 0, 0}, {chi / 2.0, chi / 2.0, 0}, {bw[0], bw[1], bw[2]}};
+  // workspace: F_NS x3 (5n), F_S x3 (4n), y (5n), rho, mhat (3n), ehat, u, unew (3n each), p, pnew, rhs
+  if ((rc = m->fns.ensure(sizeof(double) * 15 * n)) != DG_OK) return rc;
+  if ((rc = m->fs.ensure(sizeof(double) * 12 * n)) != DG_OK) return rc;
+  if ((rc = m->st.ensure(sizeof(double) * 19 * n)) != DG_OK) return rc;
+  Red red;
+  if ((rc = ensure_red(m, &red)) != DG_OK) return rc;
+  double* Fns[3] = {m->fns.as<double>(), m->fns.as<double>() + 5 * n, m->fns.as<double>() + 10 * n};
+  double* Fs[3] = {m->fs.as<double>(), m->fs.as<double>() + 4 * n, m->fs.as<double>() + 8 * n};
+  double* w = m->st.as<double>();
+  double* y = w;
+  double* rho = w + 5 * n;
+  double* mhat = w + 6 * n;
+  double* ehat = w + 9 * n;
+  double* u = w + 10 * n;
+  double* unew = w + 13 * n;
+  double* p = w + 16 * n;
+  double* pnew = w + 17 * n;
+  double* rhs = w + 18 * n;
+  const unsigned gb = grid_for(n, 256);
+  dg_step_info inf{};
+  if ((rc = explicit_rt(m, ph, q, Fns[0], Fs[0], st)) != DG_OK) return rc;
+  const double* yprev = q;
+  for (int l = 1; l <= 2; ++l) {
+    const double adt = at[l][l] * dt;
+    StageCoefs sc{};
+    sc.nst = l;
+    sc.dt = dt;
+    for (int s = 0; s < l; ++s) {
+      sc.fns[s] = Fns[s];
+      sc.fs[s] = Fs[s];
+      sc.a[s] = a[l][s];
+      sc.at[s] = at[l][s];
+    }
+    k_stage_predict<<<gb, 256, 0, st>>>(q, n, sc, rho, mhat, ehat);
+    k_primitives<<<gb, 256, 0, st>>>(yprev, n, ph->gamma, u, p);
+    DG_LAUNCH_CHECK("stage predictors");
+    ImplK k = impl_consts(ph, adt);
+    const int kmax = opts->picard_fixed > 0 ? opts->picard_fixed : opts->picard_maxit;
+    int kk = 0;
+    for (; kk < kmax; ++kk) {
+      if ((rc = prepare_rt(m, k, p, u, ph->penalty, st)) != DG_OK) return rc;
+      if ((rc = rhs_rt(m, k, rho, p, u, mhat, ehat, rhs, st)) != DG_OK) return rc;
+      DG_CUDA(cudaMemcpyAsync(pnew, p, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+      SchurCtx schur{m, k, rho, p, ph->penalty};
+      Vmult A = make_vmult(&schur);
+      dg_gmres_info gi{};
+      rc = gmres(m, A, rhs, pnew, opts->gmres.rtol, opts->gmres.restart, opts->gmres.maxit, &gi, st);
+      if (rc != DG_OK && rc != DG_ERR_NOT_CONVERGED) return rc;
+      inf.gmres_iters_total += gi.iters;
+      if (gi.relres > inf.max_relres) inf.max_relres = gi.relres;
+      if ((rc = recover_rt(m, k, rho, u, mhat, pnew, unew, st)) != DG_OK) return rc;
+      k_picard_norms<<<RED_BLOCKS, 256, 0, st>>>(p, pnew, u, unew, n, red.partial);
+      k_reduce_partials<<<4, 256, 0, st>>>(red.partial, 4, RED_BLOCKS, red.out);
+      double s4[4];
+      DG_CUDA(cudaMemcpyAsync(s4, red.out, sizeof(s4), cudaMemcpyDeviceToHost, st));
+      DG_CUDA(cudaStreamSynchronize(st));
+      std::swap(p, pnew);
+      std::swap(u, unew);
+      if (!std::isfinite(s4[0] + s4[1] + s4[2] + s4[3])) {
+        set_error("imex_ark2_step: non-finite Picard iterate");
+        return DG_ERR_NONFINITE;
+      }
+      const double dp = std::sqrt(s4[0] / (s4[1] > 0 ? s4[1] : 1e-300));
+      const double du = s4[3] > 0 ? std::sqrt(s4[2] / s4[3]) : 0.0;
+      if (opts->picard_fixed <= 0 && std::max(dp, du) < opts->picard_rtol) {
+        ++kk;
+        break;
+      }
+    }
+    inf.picard_iters[l] = kk;
+    k_stage_state<<<gb, 256, 0, st>>>(rho, u, p, n, ph->gamma, y);
+    DG_LAUNCH_CHECK("stage state");
+    if ((rc = explicit_rt(m, ph, y, Fns[l], Fs[l], st)) != DG_OK) return rc;
+    yprev = y;
+    // the next stage reads y as its initial guess before overwriting it
+  }
+  StageCoefs fin{};
+  fin.nst = 3;
+  fin.dt = dt;
+  for (int s = 0; s < 3; ++s) {
+    fin.fns[s] = Fns[s];
+    fin.fs[s] = Fs[s];
+    fin.a[s] = bw[s];
+  }
+  k_final_update<<<gb, 256, 0, st>>>(q, n, fin);
+  DG_LAUNCH_CHECK("final update");
+  DG_CUDA(cudaStreamSynchronize(st));
+  if (info) *info = inf;
+  return DG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,284 @@
+"""ctypes binding of ``libdgimex.so`` (declared in ``include/dgimex.h``).
+
+Argument marshalling only: every step of the hot path runs in the library's
+CUDA kernels.  Device arrays are torch CUDA tensors (FP64, contiguous,
+field-major ``[field][cell][node]``); streams are taken from torch.
+
+The library is loaded on first use and must have been built
+(``paper_2605_29598_gb300.build.build()``); a missing library raises
+:class:`RuntimeError` -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+DG_OK = 0
+DG_NODES_GL, DG_NODES_GLL = 0, 1
+DG_R1, DG_R2 = 1, 2
+DG_FP64 = 0
+STATUS = {0: "DG_OK", -1: "DG_ERR_ARG", -2: "DG_ERR_UNSUPPORTED", -3: "DG_ERR_CUDA",
+          -4: "DG_ERR_NOT_CONVERGED", -5: "DG_ERR_TIMEOUT", -6: "DG_ERR_NONFINITE",
+          -7: "DG_ERR_OOM"}
+
+_I64P = C.POINTER(C.c_int64)
+_DP = C.POINTER(C.c_double)
+
+
+class MeshDesc(C.Structure):
+    _fields_ = [("dim", C.c_int), ("degree", C.c_int), ("node_set", C.c_int),
+                ("n_elem", C.c_int64), ("vertices", _DP),
+                ("n_int", C.c_int64), ("int_faces", _I64P),
+                ("n_hang", C.c_int64), ("hang_faces", _I64P),
+                ("n_bdry", C.c_int64), ("bdry_faces", _I64P)]
+
+
+class MeshStats(C.Structure):
+    _fields_ = [("dim", C.c_int), ("degree", C.c_int), ("n1d", C.c_int),
+                ("nodes_per_elem", C.c_int), ("n_elem", C.c_int64), ("n_nodes", C.c_int64),
+                ("n_face_points", C.c_int64), ("n_hang_points", C.c_int64),
+                ("workspace_bytes", C.c_int64)]
+
+
+class Phys(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("g", C.c_double), ("f", C.c_double),
+                ("variant", C.c_int), ("penalty", C.c_int), ("precision", C.c_int)]
+
+
+class ImplicitCoeffs(C.Structure):
+    _fields_ = [("rho", C.c_void_p), ("p_lag", C.c_void_p), ("u_lag", C.c_void_p),
+                ("a_dt", C.c_double)]
+
+
+class GmresOpts(C.Structure):
+    _fields_ = [("rtol", C.c_double), ("restart", C.c_int), ("maxit", C.c_int)]
+
+
+class GmresInfo(C.Structure):
+    _fields_ = [("iters", C.c_int), ("relres", C.c_double)]
+
+
+class StepOpts(C.Structure):
+    _fields_ = [("picard_rtol", C.c_double), ("picard_maxit", C.c_int),
+                ("picard_fixed", C.c_int), ("gmres", GmresOpts)]
+
+
+class StepInfo(C.Structure):
+    _fields_ = [("picard_iters", C.c_int * 3), ("gmres_iters_total", C.c_int),
+                ("max_relres", C.c_double)]
+
+
+EXPORTS = {
+    "dg_status_string": (C.c_char_p, [C.c_int]),
+    "dg_last_error": (C.c_char_p, []),
+    "dg_ctx_create": (C.c_int, [C.c_int, C.POINTER(C.c_void_p)]),
+    "dg_ctx_destroy": (None, [C.c_void_p]),
+    "dg_mesh_create": (C.c_int, [C.c_void_p, C.POINTER(MeshDesc), C.POINTER(C.c_void_p)]),
+    "dg_mesh_destroy": (None, [C.c_void_p]),
+    "dg_mesh_info": (C.c_int, [C.c_void_p, C.POINTER(MeshStats)]),
+    "dg_mesh_node_coords": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "dg_apply_explicit": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Phys), C.c_void_p,
+                                    C.c_void_p, C.c_void_p, C.c_void_p]),
+    "dg_apply_implicit": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Phys),
+                                    C.POINTER(ImplicitCoeffs), C.c_void_p, C.c_void_p,
+                                    C.c_void_p]),
+    "dg_schur_rhs": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Phys), C.POINTER(ImplicitCoeffs),
+                               C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "dg_recover_velocity": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Phys),
+                                      C.POINTER(ImplicitCoeffs), C.c_void_p, C.c_void_p,
+                                      C.c_void_p, C.c_void_p]),
+    "dg_gmres_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Phys),
+                                 C.POINTER(ImplicitCoeffs), C.c_void_p, C.c_void_p,
+                                 C.POINTER(GmresOpts), C.POINTER(GmresInfo), C.c_void_p]),
+    "imex_ark2_step": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Phys), C.c_void_p, C.c_double,
+                                 C.POINTER(StepOpts), C.POINTER(StepInfo), C.c_void_p]),
+}
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Open libdgimex.so (once) and declare every exported signature."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(
+            f"libdgimex.so not found at {path}: build it with "
+            "paper_2605_29598_gb300.build.build() (no CPU fallback exists)")
+    lib = C.CDLL(path)
+    for name, (res, args) in EXPORTS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class DGError(RuntimeError):
+    def __init__(self, status, where):
+        lib = load()
+        msg = lib.dg_last_error().decode()
+        super().__init__(f"{where}: {STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(status, where, allow=()):
+    if status != DG_OK and status not in allow:
+        raise DGError(status, where)
+    return status
+
+
+def _ptr(t):
+    """Device pointer of a contiguous FP64 CUDA tensor."""
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
+            and t.is_contiguous()):
+        raise TypeError("expected a contiguous float64 CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def make_phys(gamma=1.4, g=9.81, f=1e-4, variant="R2", penalty=True):
+    return Phys(gamma=gamma, g=g, f=f, variant=DG_R2 if variant == "R2" else DG_R1,
+                penalty=1 if penalty else 0, precision=DG_FP64)
+
+
+class Context:
+    def __init__(self, device=0):
+        self.lib = load()
+        h = C.c_void_p()
+        _check(self.lib.dg_ctx_create(device, C.byref(h)), "dg_ctx_create")
+        self.h = h
+        self.device = device
+
+    def close(self):
+        if self.h:
+            self.lib.dg_ctx_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Mesh:
+    """Device mesh built from host lists (see ``inputs.Mesh``)."""
+
+    def __init__(self, ctx: Context, mesh, degree: int, node_set: int = DG_NODES_GL):
+        self.ctx = ctx
+        self.lib = ctx.lib
+        self.dim = int(mesh.dim)
+        self.degree = int(degree)
+        self._verts = np.ascontiguousarray(mesh.vertices, dtype=np.float64)
+        self._int = np.ascontiguousarray(mesh.int_faces, dtype=np.int64).reshape(-1, 4)
+        self._hang = np.ascontiguousarray(mesh.hang_faces, dtype=np.int64).reshape(-1, 5)
+        self._bdry = np.ascontiguousarray(mesh.bdry_faces, dtype=np.int64).reshape(-1, 3)
+        d = MeshDesc(dim=self.dim, degree=self.degree, node_set=node_set,
+                     n_elem=self._verts.shape[0],
+                     vertices=self._verts.ctypes.data_as(_DP),
+                     n_int=self._int.shape[0], int_faces=self._int.ctypes.data_as(_I64P),
+                     n_hang=self._hang.shape[0], hang_faces=self._hang.ctypes.data_as(_I64P),
+                     n_bdry=self._bdry.shape[0], bdry_faces=self._bdry.ctypes.data_as(_I64P))
+        h = C.c_void_p()
+        _check(self.lib.dg_mesh_create(ctx.h, C.byref(d), C.byref(h)), "dg_mesh_create")
+        self.h = h
+        st = self.stats()
+        self.n_elem = st.n_elem
+        self.N = st.n_nodes
+        self.Np = st.nodes_per_elem
+
+    def stats(self) -> MeshStats:
+        s = MeshStats()
+        _check(self.lib.dg_mesh_info(self.h, C.byref(s)), "dg_mesh_info")
+        return s
+
+    def close(self):
+        if self.h:
+            self.lib.dg_mesh_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- operators -----------------------------------------------------------
+    def node_coords(self, stream=None):
+        import torch
+        xyz = torch.empty((self.dim, self.N), dtype=torch.float64, device="cuda")
+        _check(self.lib.dg_mesh_node_coords(self.ctx.h, self.h, _ptr(xyz), _stream(stream)),
+               "dg_mesh_node_coords")
+        return xyz
+
+    def apply_explicit(self, phys, q, f_ns=None, f_s=None, stream=None):
+        import torch
+        f_ns = torch.empty((5, self.N), dtype=torch.float64, device=q.device) if f_ns is None else f_ns
+        f_s = torch.empty((4, self.N), dtype=torch.float64, device=q.device) if f_s is None else f_s
+        _check(self.lib.dg_apply_explicit(self.ctx.h, self.h, C.byref(phys), _ptr(q), _ptr(f_ns),
+                                          _ptr(f_s), _stream(stream)), "dg_apply_explicit")
+        return f_ns, f_s
+
+    @staticmethod
+    def coeffs(rho, p_lag, u_lag, a_dt):
+        return ImplicitCoeffs(rho=_ptr(rho), p_lag=_ptr(p_lag), u_lag=_ptr(u_lag), a_dt=float(a_dt))
+
+    def apply_implicit(self, phys, cf, x, y=None, stream=None):
+        import torch
+        y = torch.empty_like(x) if y is None else y
+        _check(self.lib.dg_apply_implicit(self.ctx.h, self.h, C.byref(phys), C.byref(cf), _ptr(x),
+                                          _ptr(y), _stream(stream)), "dg_apply_implicit")
+        return y
+
+    def schur_rhs(self, phys, cf, m_hat, e_hat, rhs=None, stream=None):
+        import torch
+        rhs = torch.empty_like(e_hat) if rhs is None else rhs
+        _check(self.lib.dg_schur_rhs(self.ctx.h, self.h, C.byref(phys), C.byref(cf), _ptr(m_hat),
+                                     _ptr(e_hat), _ptr(rhs), _stream(stream)), "dg_schur_rhs")
+        return rhs
+
+    def recover_velocity(self, phys, cf, m_hat, p, u=None, stream=None):
+        import torch
+        u = torch.empty_like(m_hat) if u is None else u
+        _check(self.lib.dg_recover_velocity(self.ctx.h, self.h, C.byref(phys), C.byref(cf),
+                                            _ptr(m_hat), _ptr(p), _ptr(u), _stream(stream)),
+               "dg_recover_velocity")
+        return u
+
+    def gmres_solve(self, phys, cf, b, x, rtol=1e-12, restart=30, maxit=1000, stream=None,
+                    allow_not_converged=False):
+        opts = GmresOpts(rtol=rtol, restart=restart, maxit=maxit)
+        info = GmresInfo()
+        st = self.lib.dg_gmres_solve(self.ctx.h, self.h, C.byref(phys), C.byref(cf), _ptr(b),
+                                     _ptr(x), C.byref(opts), C.byref(info), _stream(stream))
+        _check(st, "dg_gmres_solve", allow=(-4,) if allow_not_converged else ())
+        return info
+
+    def step(self, phys, q, dt, picard_rtol=1e-10, picard_maxit=10, picard_fixed=0,
+             gmres_rtol=1e-10, gmres_restart=30, gmres_maxit=1000, stream=None):
+        opts = StepOpts(picard_rtol=picard_rtol, picard_maxit=picard_maxit,
+                        picard_fixed=picard_fixed,
+                        gmres=GmresOpts(rtol=gmres_rtol, restart=gmres_restart, maxit=gmres_maxit))
+        info = StepInfo()
+        _check(self.lib.imex_ark2_step(self.ctx.h, self.h, C.byref(phys), _ptr(q), float(dt),
+                                       C.byref(opts), C.byref(info), _stream(stream)),
+               "imex_ark2_step")
+        return info
