@@ -1,0 +1,404 @@
+"""Throughput benchmark of the IMEX-DG hot path on GB300.
+
+Workload (default): 3D stratified flow over a bell hill, 200 x 200 x 20 km,
+60 x 60 x 20 terrain-following hexes, degree 3 (4.608 M nodes x 5 fields,
+FP64), N = 0.01 1/s, theta_ref = 293.15 K, inflow 10 m/s, f = 1e-4 1/s,
+dt = 4 s, strategy R2, Picard to 1e-10 relative change, GMRES(30) to 1e-10
+relative residual.  One step = one full ARK2 IMEX step (3 explicit
+operators, 2 implicit stages with their Picard / Schur / GMRES work).
+
+Metric: GDoF-updates/s = 5 * nodes * steps / time / 1e9 (whole job over all
+ranks).  Multi-GPU runs are independent replicas (the solve has no data
+exchange in this build); the per-rank work is fixed, so scaling is weak.
+
+Printed JSON line: value (device time, inputs resident), e2e (host arrays
+copied in and out every step), roofline of the dominant kernel class (CUDA
+events around its launches inside the timed region), cpu_baseline (the FP64
+oracle on a bounded sample, host cores), clocks sampled during the timed
+region, and the number of library kernel launches in the timed region.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+PEAKS_FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}
+# FP64 FMA throughput (2 flops per FMA): GB300 nominal 1.25 TFLOP/s
+FP64_NOMINAL_TFLOPS = 1.25
+METRIC = "GDoF-updates/s per IMEX step"
+
+STEP_OPTS = dict(picard_rtol=1e-10, picard_maxit=10, gmres_rtol=1e-10, gmres_restart=30,
+                 gmres_maxit=3000)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return dict(PEAKS_FALLBACK), "fallback"
+
+
+# ----------------------------------------------------------------------------
+# algorithmic work per launch of each kernel class (FP64 flops, FMA = 2).
+# Per-node / per-face-point counts follow the kernels' arithmetic; they are
+# derived in the design notes (kernel table).
+# ----------------------------------------------------------------------------
+
+def work_model(dim, n, N, S, nF):
+    d = dim
+    return {
+        # sum_{b} sum_a (x K_ab) contraction + lift of d+1 fields + pointwise
+        "volume_grad": N * (d * d + 2 * d * d * n + 2 * 2 * d * (d + 1) + 20),
+        # h rho K w, d contractions, lift of 1 field, update
+        "volume_div": N * (d * (2 * d + 1) + 2 * d * n + 2 * 2 * d + 6),
+        # 9 flux fields x d contractions, contravariant velocity, lift of 9 fields
+        "volume_explicit": N * (2 * d * d + 9 * d + 2 * 9 * d * n + 2 * 2 * d * 9 + 30),
+        "face_explicit": nF * 90,
+        "face_grad": nF * (2 + d + 3),
+        "face_div": nF * (4 * d + 4),
+    }
+
+
+def bytes_model(dim, n, N, S, nF):
+    d = dim
+    return {
+        "volume_grad": N * 8 * (1 + d * d + 1 + 1 + d + 1) + S * 8 * (d + 1),
+        "volume_div": N * 8 * (d + 1 + d * d + 1 + 1 + 1) + S * 8,
+        "volume_explicit": N * 8 * (5 + d * d + 1 + 9) + S * 8 * 9,
+    }
+
+
+# ----------------------------------------------------------------------------
+# clocks
+# ----------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------
+# the oracle on a bounded sample (host cores)
+# ----------------------------------------------------------------------------
+
+SAMPLE = dict(nx=2, ny=2)
+
+
+def oracle_sample_main(steps, warmup, out_path):
+    """Child process: time the FP64 oracle's ARK2 step on a 2 x 2 x 20-cell
+    column of the hill workload (same cell size, degree, physics, dt and
+    solver settings; hill centred in the sample)."""
+    from oracle import dg_oracle as O
+    from paper_2605_29598_gb300 import inputs as I
+    nx, ny = SAMPLE["nx"], SAMPLE["ny"]
+    dx = 200e3 / 60
+    mesh = I.box_mesh((nx, ny, 20), (nx * dx, ny * dx, 20e3),
+                      hill=dict(h0=400.0, a_c=10e3, xc=nx * dx / 2, yc=ny * dx / 2))
+    disc = O.Discretisation(mesh, 3)
+    q = I.stratified_state(disc.node_points(), theta_ref=293.15, n_bv=0.01, wind=(10.0, 0, 0))
+    ph = O.Phys(f=1e-4)
+    opts = O.StepOpts(picard_rtol=STEP_OPTS["picard_rtol"], picard_maxit=STEP_OPTS["picard_maxit"],
+                      gmres_rtol=STEP_OPTS["gmres_rtol"], gmres_restart=STEP_OPTS["gmres_restart"],
+                      gmres_maxit=STEP_OPTS["gmres_maxit"])
+    for _ in range(warmup):
+        q = O.imex_ark2_step(disc, ph, q, 4.0, opts)
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        q = O.imex_ark2_step(disc, ph, q, 4.0, opts)
+        times.append(time.perf_counter() - t0)
+    nodes = disc.E * disc.Np
+    with open(out_path, "w") as f:
+        json.dump({"times": times, "nodes": nodes, "cells": disc.E}, f)
+
+
+def run_oracle_sample(steps, warmup):
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    fd, path = tempfile.mkstemp(suffix=".json")
+    os.close(fd)
+    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-child", path,
+           "--steps", str(steps), "--warmup", str(warmup)]
+    subprocess.run(cmd, check=True, env=env, cwd=ROOT)
+    with open(path) as f:
+        r = json.load(f)
+    os.unlink(path)
+    t = sum(r["times"]) / len(r["times"])
+    value = 5 * r["nodes"] / t / 1e9
+    sample = (f"ARK2 steps of the FP64 oracle on a {SAMPLE['nx']}x{SAMPLE['ny']}x20-cell "
+              f"column of the hill workload ({r['cells']} cells, degree 3, {r['nodes']} nodes, "
+              f"same dt/physics/solver), mean of {len(r['times'])} step(s)")
+    return {"value": value, "unit": "GDoF-updates/s", "cores": 1, "kind": "oracle",
+            "sample": sample, "seconds_per_step": t}
+
+
+# ----------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------
+
+def gpu_main(args):
+    import torch
+
+    from paper_2605_29598_gb300 import build as B
+    from paper_2605_29598_gb300 import dgimex as D
+    from paper_2605_29598_gb300 import inputs as I
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    if rank == 0:
+        B.build()
+    if dist:
+        dist.barrier()
+    B.build()
+
+    case = I.hill3d_case()
+    mesh_h = case["mesh"]
+    r = case["degree"]
+    ctx = D.Context(dev)
+    mesh = D.Mesh(ctx, mesh_h, r)
+    st = mesh.stats()
+    N = st.n_nodes
+    xyz = mesh.node_coords().cpu().numpy().T
+    q0 = I.stratified_state(xyz, **case["state_params"])
+    q = torch.tensor(q0, dtype=torch.float64, device="cuda").contiguous()
+    phys = D.make_phys(f=case["f"], variant="R2")
+    dt = case["dt"]
+    stream = torch.cuda.current_stream()
+
+    def step(qq):
+        return mesh.step(phys, qq, dt, **STEP_OPTS)
+
+    infos = []
+    for _ in range(args.warmup):
+        infos.append(step(q))
+    torch.cuda.synchronize()
+
+    # one profiled step with every class timed: breakdown and dominant class
+    D.profile_begin(mesh, timed=D.KERNEL_CLASSES)
+    step(q)
+    prof_all = D.profile_end(mesh)
+    dominant = max(prof_all, key=lambda k: prof_all[k][2])
+
+    # timed region: launches counted, dominant class bracketed by events
+    clocks = ClockSampler(dev)
+    clocks.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    D.profile_begin(mesh, timed=[dominant])
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    picard, gm_its, relres = [], 0, 0.0
+    for _ in range(args.steps):
+        inf = step(q)
+        picard.append(list(inf.picard_iters)[1:])
+        gm_its += inf.gmres_iters_total
+        relres = max(relres, inf.max_relres)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    prof = D.profile_end(mesh)
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    ms_max = ms
+    if dist:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_max = float(t.item())
+    value = 5.0 * N * args.steps * world / (ms_max / 1e3) / 1e9
+
+    # end to end: host state copied in and out around every step
+    qh = torch.empty_like(q, device="cpu").pin_memory()
+    qh.copy_(q)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    e2 = torch.cuda.Event(enable_timing=True)
+    e3 = torch.cuda.Event(enable_timing=True)
+    qd = torch.empty_like(q)
+    e2.record(stream)
+    for _ in range(args.steps):
+        qd.copy_(qh, non_blocking=True)
+        step(qd)
+        qh.copy_(qd, non_blocking=True)
+    e3.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = e2.elapsed_time(e3)
+    if dist:
+        t = torch.tensor([ms_e2e], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+    e2e_value = 5.0 * N * args.steps * world / (ms_e2e / 1e3) / 1e9
+    state_bytes = 5 * N * 8
+
+    # roofline of the dominant class
+    pk, src = peaks()
+    work = work_model(st.dim, st.n1d, N, N // st.nodes_per_elem * 2 * st.dim * st.n1d ** (st.dim - 1),
+                      st.n_face_points)
+    launches, timed_launches, tms = prof[dominant]
+    roof = None
+    if timed_launches and dominant in work:
+        per_launch_ms = tms / timed_launches
+        flops = work[dominant]
+        achieved = flops / (per_launch_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": dominant, "achieved": achieved,
+                "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_NOMINAL_TFLOPS,
+                "traffic": None, "peak_source": "GB300 nominal FP64 (recipe table); probe measured 1.20",
+                "launches": timed_launches, "ms_per_launch": per_launch_ms,
+                "algorithmic_flops_per_launch": flops}
+    elif timed_launches:
+        per_launch_ms = tms / timed_launches
+        roof = {"bound": "alu", "kernel": dominant, "achieved": None, "peak": FP64_NOMINAL_TFLOPS,
+                "unit": "TFLOP/s", "frac": None, "traffic": None, "launches": timed_launches,
+                "ms_per_launch": per_launch_ms}
+    total_launches = sum(v[0] for v in prof.values())
+    breakdown = {k: {"launches": v[0], "ms": round(v[2], 3)} for k, v in prof_all.items() if v[0]}
+
+    if dist and rank != 0:
+        dist.barrier()
+        dist.destroy_process_group()
+        return
+    cpu = None
+    if not args.no_cpu_baseline and world == 1:
+        try:
+            cpu = run_oracle_sample(steps=2, warmup=0)
+        except Exception as exc:  # report, do not fail the bench
+            cpu = {"error": str(exc)[:200]}
+    line = {
+        "metric": METRIC, "value": value, "unit": "GDoF-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": "hill3d_60x60x20_r3_fp64_R2", "cells": st.n_elem, "degree": r,
+                   "nodes": N, "dof": 5 * N, "dt": dt, "variant": "R2",
+                   "picard_rtol": STEP_OPTS["picard_rtol"], "gmres_rtol": STEP_OPTS["gmres_rtol"],
+                   "gmres_restart": STEP_OPTS["gmres_restart"],
+                   "l2": "state (%.0f MB) and Krylov basis exceed the 126 MB L2" % (state_bytes / 1e6),
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "e2e": {"value": e2e_value, "unit": "GDoF-updates/s", "h2d_bytes_per_step": state_bytes,
+                "d2h_bytes_per_step": state_bytes},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "clocks": clk,
+        "gpu_launches": total_launches,
+        "iterations": {"picard_per_stage": picard, "gmres_total": gm_its, "gmres_max_relres": relres},
+        "kernel_breakdown_one_step": breakdown,
+        "peaks_source": src,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def reference_main(args):
+    """The oracle as it stands, on host cores, on a bounded sample of the
+    same workload (rank 0 only)."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    res = run_oracle_sample(steps=args.steps, warmup=args.warmup)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": res["value"], "unit": "GDoF-updates/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": res["seconds_per_step"] * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "hill3d_60x60x20_r3_fp64_R2", "sample": res["sample"]},
+        "cpu_baseline": {"value": res["value"], "unit": res["unit"], "cores": res["cores"],
+                         "kind": "oracle", "sample": res["sample"]},
+        "e2e": {"value": res["value"], "unit": "GDoF-updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--oracle-child", default=None)
+    args = ap.parse_args()
+    if args.oracle_child:
+        oracle_sample_main(args.steps, args.warmup, args.oracle_child)
+        return
+    if args.warmup < 3 and args.oracle_child is None and args.impl == "ours":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        reference_main(args)
+    else:
+        gpu_main(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -206,6 +206,25 @@ int imex_ark2_step(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* phys,
                    double* q, double dt, const dg_step_opts* opts,
                    dg_step_info* info, void* stream);
 
+/*
+ * Launch accounting (no counterpart in the paper; used to measure the hot
+ * path).  Between begin and end every kernel launch of `mesh` is counted
+ * per kernel class; classes whose bit is set in time_mask are also
+ * bracketed by CUDA events on the launching stream.  dg_profile_end
+ * synchronises on the last event and fills out[k] for k < min(max_out,
+ * DG_KERNEL_CLASSES) with the class name, launch count, number of timed
+ * launches and their summed device time in ms.
+ */
+enum { DG_KERNEL_CLASSES = 16 };
+typedef struct {
+  char name[32];
+  int64_t launches;
+  int64_t timed_launches;
+  double total_ms;
+} dg_kernel_stat;
+int dg_profile_begin(dg_mesh* mesh, uint32_t time_mask);
+int dg_profile_end(dg_mesh* mesh, dg_kernel_stat* out, int max_out, int* n_out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -73,6 +73,31 @@ struct DBuf {
 
 }  // namespace dg
 
+namespace dg {
+
+// Kernel classes counted (and optionally timed with CUDA events) between
+// dg_profile_begin and dg_profile_end.
+enum KernelId {
+  K_TRACE = 0, K_FACE_EXPLICIT, K_HANG_GATHER, K_VOL_EXPLICIT, K_FACE_LAMBDA, K_FACE_GRAD,
+  K_VOL_GRAD, K_FACE_DIV, K_VOL_DIV, K_USTAR, K_MULTIDOT, K_REDUCE, K_MULTIAXPY, K_VEC,
+  K_STAGE, K_PICARD_NORMS, K_COUNT
+};
+extern const char* const kKernelNames[K_COUNT];
+
+struct Profiler {
+  bool on = false;
+  uint32_t time_mask = 0;
+  int64_t launches[K_COUNT] = {};
+  std::vector<cudaEvent_t> pool;
+  size_t used = 0;
+  std::vector<int> pending_kid;      // kernel class of event pair k (events 2k, 2k+1)
+  cudaEvent_t next_event();
+  void reset();
+  void release();
+};
+
+}  // namespace dg
+
 struct dg_ctx {
   int device = 0;
 };
@@ -100,6 +125,7 @@ struct dg_mesh {
   // workspace
   dg::DBuf trc, slot, hbuf, trh, pcoef, wv, gm_V, gm_work, red, st, fns, fs;
   std::vector<double> host_h;
+  dg::Profiler prof;
   int64_t workspace_bytes() const;
 };
 
@@ -120,6 +146,38 @@ inline FaceTopo topo(const dg_mesh* m) {
   return FaceTopo{m->fp_minus, m->fp_plus, m->fgeo, m->hp_cslot, m->hp_code,
                   m->hc_slot, m->nF, m->nH, m->nHC, m->S};
 }
+
+// Counts a launch of class `kid` and brackets it with CUDA events when that
+// class is being timed.
+struct ProfScope {
+  Profiler* p;
+  int kid;
+  cudaStream_t st;
+  cudaEvent_t stop = nullptr;
+  ProfScope(dg_mesh* m, int k, cudaStream_t s) : p(&m->prof), kid(k), st(s) {
+    if (!p->on) return;
+    p->launches[kid]++;
+    if (p->time_mask & (1u << kid)) {
+      cudaEvent_t start = p->next_event();
+      stop = p->next_event();
+      if (start && stop) {
+        cudaEventRecord(start, st);
+        p->pending_kid.push_back(kid);
+      } else {
+        stop = nullptr;
+      }
+    }
+  }
+  ~ProfScope() {
+    if (stop) cudaEventRecord(stop, st);
+  }
+};
+
+#define DG_RUN(m, kid, st, ...)                      \
+  do {                                               \
+    ::dg::ProfScope prof_scope_((m), (kid), (st));   \
+    __VA_ARGS__;                                     \
+  } while (0)
 
 inline unsigned grid_for(int64_t n, int threads) {
   int64_t g = (n + threads - 1) / threads;

@@ -42,6 +42,32 @@ void DBuf::release() {
   bytes = 0;
 }
 
+const char* const kKernelNames[K_COUNT] = {
+    "trace", "face_explicit", "hang_gather", "volume_explicit", "face_lambda", "face_grad",
+    "volume_grad", "face_div", "volume_div", "ustar", "multidot", "reduce", "multiaxpy", "vector",
+    "stage", "picard_norms"};
+
+cudaEvent_t Profiler::next_event() {
+  if (used == pool.size()) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    pool.push_back(e);
+  }
+  return pool[used++];
+}
+
+void Profiler::reset() {
+  for (int k = 0; k < K_COUNT; ++k) launches[k] = 0;
+  used = 0;
+  pending_kid.clear();
+}
+
+void Profiler::release() {
+  for (auto e : pool) cudaEventDestroy(e);
+  pool.clear();
+  reset();
+}
+
 // Gauss-Legendre nodes on [-1, 1] by Newton iteration on P_n (three-term
 // recurrence), mapped to [0, 1]; Lagrange values and derivatives by the
 // product rule.
@@ -297,6 +323,7 @@ void dg_mesh_destroy(dg_mesh* m) {
   DBuf* b[] = {&m->trc, &m->slot, &m->hbuf, &m->trh, &m->pcoef, &m->wv, &m->gm_V,
                &m->gm_work, &m->red, &m->st, &m->fns, &m->fs};
   for (auto* x : b) x->release();
+  m->prof.release();
   delete m;
 }
 
@@ -496,6 +523,46 @@ int dg_mesh_create(dg_ctx* ctx, const dg_mesh_desc* d, dg_mesh** out) {
     return fail(DG_ERR_ARG);
   }
   *out = m;
+  return DG_OK;
+}
+
+int dg_profile_begin(dg_mesh* m, uint32_t time_mask) {
+  if (!m) {
+    set_error("dg_profile_begin: NULL mesh");
+    return DG_ERR_ARG;
+  }
+  m->prof.reset();
+  m->prof.time_mask = time_mask;
+  m->prof.on = true;
+  return DG_OK;
+}
+
+int dg_profile_end(dg_mesh* m, dg_kernel_stat* out, int max_out, int* n_out) {
+  if (!m || (max_out > 0 && !out)) {
+    set_error("dg_profile_end: NULL argument");
+    return DG_ERR_ARG;
+  }
+  Profiler& p = m->prof;
+  p.on = false;
+  double ms[K_COUNT] = {};
+  int64_t timed[K_COUNT] = {};
+  if (!p.pending_kid.empty()) DG_CUDA(cudaEventSynchronize(p.pool[2 * p.pending_kid.size() - 1]));
+  for (size_t k = 0; k < p.pending_kid.size(); ++k) {
+    float t = 0.f;
+    DG_CUDA(cudaEventElapsedTime(&t, p.pool[2 * k], p.pool[2 * k + 1]));
+    ms[p.pending_kid[k]] += t;
+    timed[p.pending_kid[k]]++;
+  }
+  int n = max_out < K_COUNT ? max_out : K_COUNT;
+  for (int k = 0; k < n; ++k) {
+    std::memset(out[k].name, 0, sizeof(out[k].name));
+    std::strncpy(out[k].name, kKernelNames[k], sizeof(out[k].name) - 1);
+    out[k].launches = p.launches[k];
+    out[k].timed_launches = timed[k];
+    out[k].total_ms = ms[k];
+  }
+  if (n_out) *n_out = n;
+  p.reset();
   return DG_OK;
 }
 

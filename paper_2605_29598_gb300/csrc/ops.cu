@@ -23,12 +23,12 @@ int Engine<T, DIM, N>::explicit_rates(dg_mesh* m, const PhysK& ph, const T* q, T
     in.f[k] = q + k * m->N;
     in.scale[k] = 1;
   }
-  k_trace<T, DIM, N, 5><<<grid_for(m->S, 256), 256, 0, st>>>(in, m->E, m->N, trc, m->S, tb);
-  k_face_explicit<T, DIM, N><<<grid_for(m->nF, 128), 128, 0, st>>>(ft, trc, slot, hbuf, tb, (T)ph.gamma);
+  DG_RUN(m, K_TRACE, st, k_trace<T, DIM, N, 5><<<grid_for(m->S, 256), 256, 0, st>>>(in, m->E, m->N, trc, m->S, tb));
+  DG_RUN(m, K_FACE_EXPLICIT, st, k_face_explicit<T, DIM, N><<<grid_for(m->nF, 128), 128, 0, st>>>(ft, trc, slot, hbuf, tb, (T)ph.gamma));
   if (m->nHC > 0)
-    k_hang_gather<T, DIM, N, 9><<<grid_for(m->nHC * CS::NFP, 128), 128, 0, st>>>(ft, hbuf, slot, tb);
-  k_volume_explicit<T, DIM, N><<<grid_for(m->E, CS::EPB), CS::THREADS, 0, st>>>(
-      q, m->K, m->invM, slot, m->E, m->S, tb, ph, fns, fs);
+    DG_RUN(m, K_HANG_GATHER, st, k_hang_gather<T, DIM, N, 9><<<grid_for(m->nHC * CS::NFP, 128), 128, 0, st>>>(ft, hbuf, slot, tb));
+  DG_RUN(m, K_VOL_EXPLICIT, st, k_volume_explicit<T, DIM, N><<<grid_for(m->E, CS::EPB), CS::THREADS, 0, st>>>(
+      q, m->K, m->invM, slot, m->E, m->S, tb, ph, fns, fs));
   DG_LAUNCH_CHECK("explicit operator");
   return DG_OK;
 }
@@ -50,15 +50,15 @@ int Engine<T, DIM, N>::prepare(dg_mesh* m, const ImplK& ph, const T* plag, const
   Fields<T> in;
   in.f[0] = plag;
   in.scale[0] = (T)(ph.gamma / (ph.gamma - 1.0));
-  k_trace<T, DIM, N, 1><<<grid_for(m->S, 256), 256, 0, st>>>(in, m->E, m->N, m->trh.as<T>(), m->S, tb);
+  DG_RUN(m, K_TRACE, st, k_trace<T, DIM, N, 1><<<grid_for(m->S, 256), 256, 0, st>>>(in, m->E, m->N, m->trh.as<T>(), m->S, tb));
   if (penalty) {
     for (int c = 0; c < 3; ++c) {
       in.f[c] = ulag + c * m->N;
       in.scale[c] = 1;
     }
-    k_trace<T, DIM, N, 3><<<grid_for(m->S, 256), 256, 0, st>>>(in, m->E, m->N, m->trc.as<T>(), m->S, tb);
-    k_face_lambda<T, DIM, N><<<grid_for(m->nF, 128), 128, 0, st>>>(ft, m->trc.as<T>(), (T)(0.5 * ph.a_dt),
-                                                                    m->pcoef.as<T>(), tb);
+    DG_RUN(m, K_TRACE, st, k_trace<T, DIM, N, 3><<<grid_for(m->S, 256), 256, 0, st>>>(in, m->E, m->N, m->trc.as<T>(), m->S, tb));
+    DG_RUN(m, K_FACE_LAMBDA, st, k_face_lambda<T, DIM, N><<<grid_for(m->nF, 128), 128, 0, st>>>(ft, m->trc.as<T>(), (T)(0.5 * ph.a_dt),
+                                                                    m->pcoef.as<T>(), tb));
   }
   DG_LAUNCH_CHECK("implicit coefficients");
   return DG_OK;
@@ -78,24 +78,24 @@ int Engine<T, DIM, N>::vmult(dg_mesh* m, const ImplK& ph, const T* rho, const T*
   Fields<T> in;
   in.f[0] = x;
   in.scale[0] = 1;
-  k_trace<T, DIM, N, 1><<<grid_for(m->S, 256), 256, 0, st>>>(in, m->E, m->N, trc, m->S, tb);
-  k_face_grad<T, DIM, N><<<grid_for(m->nF, 128), 128, 0, st>>>(ft, trc, penalty ? m->pcoef.as<T>() : nullptr,
-                                                                slot, hbuf, tb);
+  DG_RUN(m, K_TRACE, st, k_trace<T, DIM, N, 1><<<grid_for(m->S, 256), 256, 0, st>>>(in, m->E, m->N, trc, m->S, tb));
+  DG_RUN(m, K_FACE_GRAD, st, k_face_grad<T, DIM, N><<<grid_for(m->nF, 128), 128, 0, st>>>(ft, trc, penalty ? m->pcoef.as<T>() : nullptr,
+                                                                slot, hbuf, tb));
   if (m->nHC > 0)
-    k_hang_gather<T, DIM, N, DIM + 1><<<grid_for(m->nHC * CS::NFP, 128), 128, 0, st>>>(ft, hbuf, slot, tb);
-  k_volume_grad<T, DIM, N, GRAD_VMULT><<<grid_for(m->E, CS::EPB), CS::THREADS, 0, st>>>(
-      x, rho, m->K, m->invM, slot, m->E, m->S, tb, ph, wv, y, nullptr, nullptr);
+    DG_RUN(m, K_HANG_GATHER, st, k_hang_gather<T, DIM, N, DIM + 1><<<grid_for(m->nHC * CS::NFP, 128), 128, 0, st>>>(ft, hbuf, slot, tb));
+  DG_RUN(m, K_VOL_GRAD, st, k_volume_grad<T, DIM, N, GRAD_VMULT><<<grid_for(m->E, CS::EPB), CS::THREADS, 0, st>>>(
+      x, rho, m->K, m->invM, slot, m->E, m->S, tb, ph, wv, y, nullptr, nullptr));
   Fields<T> w;
   for (int b = 0; b < DIM; ++b) {
     w.f[b] = wv + b * m->N;
     w.scale[b] = 1;
   }
-  k_trace<T, DIM, N, DIM><<<grid_for(m->S, 256), 256, 0, st>>>(w, m->E, m->N, trc, m->S, tb);
-  k_face_div<T, DIM, N><<<grid_for(m->nF, 128), 128, 0, st>>>(ft, trc, m->trh.as<T>(), slot, hbuf, tb);
+  DG_RUN(m, K_TRACE, st, k_trace<T, DIM, N, DIM><<<grid_for(m->S, 256), 256, 0, st>>>(w, m->E, m->N, trc, m->S, tb));
+  DG_RUN(m, K_FACE_DIV, st, k_face_div<T, DIM, N><<<grid_for(m->nF, 128), 128, 0, st>>>(ft, trc, m->trh.as<T>(), slot, hbuf, tb));
   if (m->nHC > 0)
-    k_hang_gather<T, DIM, N, 1><<<grid_for(m->nHC * CS::NFP, 128), 128, 0, st>>>(ft, hbuf, slot, tb);
-  k_volume_div<T, DIM, N, DIV_VMULT><<<grid_for(m->E, CS::EPB), CS::THREADS, 0, st>>>(
-      w, plag, m->K, m->invM, slot, m->E, m->S, tb, ph, y, nullptr, nullptr, nullptr, nullptr);
+    DG_RUN(m, K_HANG_GATHER, st, k_hang_gather<T, DIM, N, 1><<<grid_for(m->nHC * CS::NFP, 128), 128, 0, st>>>(ft, hbuf, slot, tb));
+  DG_RUN(m, K_VOL_DIV, st, k_volume_div<T, DIM, N, DIV_VMULT><<<grid_for(m->E, CS::EPB), CS::THREADS, 0, st>>>(
+      w, plag, m->K, m->invM, slot, m->E, m->S, tb, ph, y, nullptr, nullptr, nullptr, nullptr));
   DG_LAUNCH_CHECK("schur vmult");
   return DG_OK;
 }
@@ -111,19 +111,19 @@ int Engine<T, DIM, N>::schur_rhs(dg_mesh* m, const ImplK& ph, const T* rho, cons
   T* slot = m->slot.as<T>();
   T* hbuf = m->hbuf.as<T>();
   T* ustar = m->wv.as<T>() + 3 * m->N;
-  k_ustar<T><<<grid_for(m->N, 256), 256, 0, st>>>(mhat, rho, ulag, m->N, ph, ustar);
+  DG_RUN(m, K_USTAR, st, k_ustar<T><<<grid_for(m->N, 256), 256, 0, st>>>(mhat, rho, ulag, m->N, ph, ustar));
   Fields<T> w;
   for (int b = 0; b < DIM; ++b) {
     int c = DIM == 3 ? b : (b == 0 ? 0 : 2);
     w.f[b] = ustar + c * m->N;
     w.scale[b] = 1;
   }
-  k_trace<T, DIM, N, DIM><<<grid_for(m->S, 256), 256, 0, st>>>(w, m->E, m->N, trc, m->S, tb);
-  k_face_div<T, DIM, N><<<grid_for(m->nF, 128), 128, 0, st>>>(ft, trc, m->trh.as<T>(), slot, hbuf, tb);
+  DG_RUN(m, K_TRACE, st, k_trace<T, DIM, N, DIM><<<grid_for(m->S, 256), 256, 0, st>>>(w, m->E, m->N, trc, m->S, tb));
+  DG_RUN(m, K_FACE_DIV, st, k_face_div<T, DIM, N><<<grid_for(m->nF, 128), 128, 0, st>>>(ft, trc, m->trh.as<T>(), slot, hbuf, tb));
   if (m->nHC > 0)
-    k_hang_gather<T, DIM, N, 1><<<grid_for(m->nHC * CS::NFP, 128), 128, 0, st>>>(ft, hbuf, slot, tb);
-  k_volume_div<T, DIM, N, DIV_RHS><<<grid_for(m->E, CS::EPB), CS::THREADS, 0, st>>>(
-      w, plag, m->K, m->invM, slot, m->E, m->S, tb, ph, rhs, ehat, rho, ulag, ustar);
+    DG_RUN(m, K_HANG_GATHER, st, k_hang_gather<T, DIM, N, 1><<<grid_for(m->nHC * CS::NFP, 128), 128, 0, st>>>(ft, hbuf, slot, tb));
+  DG_RUN(m, K_VOL_DIV, st, k_volume_div<T, DIM, N, DIV_RHS><<<grid_for(m->E, CS::EPB), CS::THREADS, 0, st>>>(
+      w, plag, m->K, m->invM, slot, m->E, m->S, tb, ph, rhs, ehat, rho, ulag, ustar));
   DG_LAUNCH_CHECK("schur rhs");
   return DG_OK;
 }
@@ -139,16 +139,16 @@ int Engine<T, DIM, N>::recover(dg_mesh* m, const ImplK& ph, const T* rho, const 
   T* slot = m->slot.as<T>();
   T* hbuf = m->hbuf.as<T>();
   T* ustar = m->wv.as<T>() + 3 * m->N;
-  k_ustar<T><<<grid_for(m->N, 256), 256, 0, st>>>(mhat, rho, ulag, m->N, ph, ustar);
+  DG_RUN(m, K_USTAR, st, k_ustar<T><<<grid_for(m->N, 256), 256, 0, st>>>(mhat, rho, ulag, m->N, ph, ustar));
   Fields<T> in;
   in.f[0] = p;
   in.scale[0] = 1;
-  k_trace<T, DIM, N, 1><<<grid_for(m->S, 256), 256, 0, st>>>(in, m->E, m->N, trc, m->S, tb);
-  k_face_grad<T, DIM, N><<<grid_for(m->nF, 128), 128, 0, st>>>(ft, trc, nullptr, slot, hbuf, tb);
+  DG_RUN(m, K_TRACE, st, k_trace<T, DIM, N, 1><<<grid_for(m->S, 256), 256, 0, st>>>(in, m->E, m->N, trc, m->S, tb));
+  DG_RUN(m, K_FACE_GRAD, st, k_face_grad<T, DIM, N><<<grid_for(m->nF, 128), 128, 0, st>>>(ft, trc, nullptr, slot, hbuf, tb));
   if (m->nHC > 0)
-    k_hang_gather<T, DIM, N, DIM + 1><<<grid_for(m->nHC * CS::NFP, 128), 128, 0, st>>>(ft, hbuf, slot, tb);
-  k_volume_grad<T, DIM, N, GRAD_RECOVER><<<grid_for(m->E, CS::EPB), CS::THREADS, 0, st>>>(
-      p, rho, m->K, m->invM, slot, m->E, m->S, tb, ph, nullptr, nullptr, ustar, u);
+    DG_RUN(m, K_HANG_GATHER, st, k_hang_gather<T, DIM, N, DIM + 1><<<grid_for(m->nHC * CS::NFP, 128), 128, 0, st>>>(ft, hbuf, slot, tb));
+  DG_RUN(m, K_VOL_GRAD, st, k_volume_grad<T, DIM, N, GRAD_RECOVER><<<grid_for(m->E, CS::EPB), CS::THREADS, 0, st>>>(
+      p, rho, m->K, m->invM, slot, m->E, m->S, tb, ph, nullptr, nullptr, ustar, u));
   DG_LAUNCH_CHECK("velocity recovery");
   return DG_OK;
 }

@@ -195,10 +195,10 @@ static int ensure_red(dg_mesh* m, Red* r) {
 }
 
 // host <- V[0..nvec)^T w  (synchronises the stream)
-static int dots(const Red& r, const double* V, int nvec, int64_t n, const double* w, double* host,
-                cudaStream_t st) {
-  k_multidot<<<RED_BLOCKS, 256, 0, st>>>(V, nvec, n, w, r.partial);
-  k_reduce_partials<<<nvec, 256, 0, st>>>(r.partial, nvec, RED_BLOCKS, r.out);
+static int dots(dg_mesh* m, const Red& r, const double* V, int nvec, int64_t n, const double* w,
+                double* host, cudaStream_t st) {
+  DG_RUN(m, K_MULTIDOT, st, k_multidot<<<RED_BLOCKS, 256, 0, st>>>(V, nvec, n, w, r.partial));
+  DG_RUN(m, K_REDUCE, st, k_reduce_partials<<<nvec, 256, 0, st>>>(r.partial, nvec, RED_BLOCKS, r.out));
   DG_LAUNCH_CHECK("reduction");
   DG_CUDA(cudaMemcpyAsync(host, r.out, sizeof(double) * nvec, cudaMemcpyDeviceToHost, st));
   DG_CUDA(cudaStreamSynchronize(st));
@@ -229,7 +229,7 @@ static int gmres(dg_mesh* m, const Vmult& A, const double* b, double* x, double 
   double* tmp = m->gm_work.as<double>();
   const unsigned gb = grid_for(n, 256);
   double bn2;
-  if ((rc = dots(red, b, 1, n, b, &bn2, st)) != DG_OK) return rc;
+  if ((rc = dots(m, red, b, 1, n, b, &bn2, st)) != DG_OK) return rc;
   const double bnorm = std::sqrt(bn2);
   if (!std::isfinite(bnorm)) {
     set_error("gmres: non-finite right-hand side");
@@ -250,9 +250,9 @@ static int gmres(dg_mesh* m, const Vmult& A, const double* b, double* x, double 
   double relres = 0.0;
   while (true) {
     if ((rc = A(x, tmp, st)) != DG_OK) return rc;
-    k_axpby<<<gb, 256, 0, st>>>(n, 1.0, b, -1.0, tmp, V);
+    DG_RUN(m, K_VEC, st, k_axpby<<<gb, 256, 0, st>>>(n, 1.0, b, -1.0, tmp, V));
     double b2;
-    if ((rc = dots(red, V, 1, n, V, &b2, st)) != DG_OK) return rc;
+    if ((rc = dots(m, red, V, 1, n, V, &b2, st)) != DG_OK) return rc;
     const double beta = std::sqrt(b2);
     if (!std::isfinite(beta)) {
       set_error("gmres: non-finite residual");
@@ -268,7 +268,7 @@ static int gmres(dg_mesh* m, const Vmult& A, const double* b, double* x, double 
       set_error("gmres: %d iterations, relative residual %.3e > %.3e", it, relres, rtol);
       return DG_ERR_NOT_CONVERGED;
     }
-    k_scale<<<gb, 256, 0, st>>>(n, 1.0 / beta, V);
+    DG_RUN(m, K_VEC, st, k_scale<<<gb, 256, 0, st>>>(n, 1.0 / beta, V));
     std::fill(g.begin(), g.end(), 0.0);
     g[0] = beta;
     int jused = 0;
@@ -277,22 +277,22 @@ static int gmres(dg_mesh* m, const Vmult& A, const double* b, double* x, double 
       double* w = V + (int64_t)(j + 1) * n;
       if ((rc = A(vj, w, st)) != DG_OK) return rc;
       Coefs c;
-      if ((rc = dots(red, V, j + 1, n, w, h1.data(), st)) != DG_OK) return rc;
+      if ((rc = dots(m, red, V, j + 1, n, w, h1.data(), st)) != DG_OK) return rc;
       for (int k = 0; k <= j; ++k) c.c[k] = -h1[k];
-      k_multiaxpy<<<gb, 256, 0, st>>>(V, j + 1, n, c, w);
-      if ((rc = dots(red, V, j + 1, n, w, h2.data(), st)) != DG_OK) return rc;
+      DG_RUN(m, K_MULTIAXPY, st, k_multiaxpy<<<gb, 256, 0, st>>>(V, j + 1, n, c, w));
+      if ((rc = dots(m, red, V, j + 1, n, w, h2.data(), st)) != DG_OK) return rc;
       for (int k = 0; k <= j; ++k) c.c[k] = -h2[k];
-      k_multiaxpy<<<gb, 256, 0, st>>>(V, j + 1, n, c, w);
+      DG_RUN(m, K_MULTIAXPY, st, k_multiaxpy<<<gb, 256, 0, st>>>(V, j + 1, n, c, w));
       for (int k = 0; k <= j; ++k) Hij(k, j) = h1[k] + h2[k];
       double w2;
-      if ((rc = dots(red, w, 1, n, w, &w2, st)) != DG_OK) return rc;
+      if ((rc = dots(m, red, w, 1, n, w, &w2, st)) != DG_OK) return rc;
       const double hn = std::sqrt(w2);
       if (!std::isfinite(hn)) {
         set_error("gmres: non-finite Krylov vector");
         return DG_ERR_NONFINITE;
       }
       Hij(j + 1, j) = hn;
-      if (hn > 0.0) k_scale<<<gb, 256, 0, st>>>(n, 1.0 / hn, w);
+      if (hn > 0.0) DG_RUN(m, K_VEC, st, k_scale<<<gb, 256, 0, st>>>(n, 1.0 / hn, w));
       for (int k = 0; k < j; ++k) {
         const double t = cs[k] * Hij(k, j) + sn[k] * Hij(k + 1, j);
         Hij(k + 1, j) = -sn[k] * Hij(k, j) + cs[k] * Hij(k + 1, j);
@@ -316,7 +316,7 @@ static int gmres(dg_mesh* m, const Vmult& A, const double* b, double* x, double 
     }
     Coefs c;
     for (int k = 0; k < jused; ++k) c.c[k] = y[k];
-    k_multiaxpy<<<gb, 256, 0, st>>>(V, jused, n, c, x);
+    DG_RUN(m, K_MULTIAXPY, st, k_multiaxpy<<<gb, 256, 0, st>>>(V, jused, n, c, x));
     DG_LAUNCH_CHECK("gmres update");
   }
 }
@@ -454,8 +454,8 @@ int imex_ark2_step(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* ph, double* 
       sc.a[s] = a[l][s];
       sc.at[s] = at[l][s];
     }
-    k_stage_predict<<<gb, 256, 0, st>>>(q, n, sc, rho, mhat, ehat);
-    k_primitives<<<gb, 256, 0, st>>>(yprev, n, ph->gamma, u, p);
+    DG_RUN(m, K_STAGE, st, k_stage_predict<<<gb, 256, 0, st>>>(q, n, sc, rho, mhat, ehat));
+    DG_RUN(m, K_STAGE, st, k_primitives<<<gb, 256, 0, st>>>(yprev, n, ph->gamma, u, p));
     DG_LAUNCH_CHECK("stage predictors");
     ImplK k = impl_consts(ph, adt);
     const int kmax = opts->picard_fixed > 0 ? opts->picard_fixed : opts->picard_maxit;
@@ -472,8 +472,8 @@ int imex_ark2_step(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* ph, double* 
       inf.gmres_iters_total += gi.iters;
       if (gi.relres > inf.max_relres) inf.max_relres = gi.relres;
       if ((rc = recover_rt(m, k, rho, u, mhat, pnew, unew, st)) != DG_OK) return rc;
-      k_picard_norms<<<RED_BLOCKS, 256, 0, st>>>(p, pnew, u, unew, n, red.partial);
-      k_reduce_partials<<<4, 256, 0, st>>>(red.partial, 4, RED_BLOCKS, red.out);
+      DG_RUN(m, K_PICARD_NORMS, st, k_picard_norms<<<RED_BLOCKS, 256, 0, st>>>(p, pnew, u, unew, n, red.partial));
+      DG_RUN(m, K_REDUCE, st, k_reduce_partials<<<4, 256, 0, st>>>(red.partial, 4, RED_BLOCKS, red.out));
       double s4[4];
       DG_CUDA(cudaMemcpyAsync(s4, red.out, sizeof(s4), cudaMemcpyDeviceToHost, st));
       DG_CUDA(cudaStreamSynchronize(st));
@@ -491,7 +491,7 @@ int imex_ark2_step(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* ph, double* 
       }
     }
     inf.picard_iters[l] = kk;
-    k_stage_state<<<gb, 256, 0, st>>>(rho, u, p, n, ph->gamma, y);
+    DG_RUN(m, K_STAGE, st, k_stage_state<<<gb, 256, 0, st>>>(rho, u, p, n, ph->gamma, y));
     DG_LAUNCH_CHECK("stage state");
     if ((rc = explicit_rt(m, ph, y, Fns[l], Fs[l], st)) != DG_OK) return rc;
     yprev = y;
@@ -505,7 +505,7 @@ int imex_ark2_step(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* ph, double* 
     fin.fs[s] = Fs[s];
     fin.a[s] = bw[s];
   }
-  k_final_update<<<gb, 256, 0, st>>>(q, n, fin);
+  DG_RUN(m, K_STAGE, st, k_final_update<<<gb, 256, 0, st>>>(q, n, fin));
   DG_LAUNCH_CHECK("final update");
   DG_CUDA(cudaStreamSynchronize(st));
   if (info) *info = inf;

@@ -98,6 +98,16 @@ EXPORTS = {
                                  C.POINTER(StepOpts), C.POINTER(StepInfo), C.c_void_p]),
 }
 
+
+class KernelStat(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("timed_launches", C.c_int64),
+                ("total_ms", C.c_double)]
+
+
+EXPORTS["dg_profile_begin"] = (C.c_int, [C.c_void_p, C.c_uint32])
+EXPORTS["dg_profile_end"] = (C.c_int, [C.c_void_p, C.POINTER(KernelStat), C.c_int,
+                                       C.POINTER(C.c_int)])
+
 _lib = None
 
 
@@ -282,3 +292,31 @@ class Mesh:
                                        C.byref(opts), C.byref(info), _stream(stream)),
                "imex_ark2_step")
         return info
+
+
+# ----------------------------------------------------------------------------
+# launch accounting
+# ----------------------------------------------------------------------------
+
+KERNEL_CLASSES = ["trace", "face_explicit", "hang_gather", "volume_explicit", "face_lambda",
+                  "face_grad", "volume_grad", "face_div", "volume_div", "ustar", "multidot",
+                  "reduce", "multiaxpy", "vector", "stage", "picard_norms"]
+
+
+def profile_begin(mesh: "Mesh", timed=()):
+    """Count every launch on ``mesh``; bracket the classes in ``timed`` with
+    CUDA events."""
+    mask = 0
+    for name in timed:
+        mask |= 1 << KERNEL_CLASSES.index(name)
+    _check(mesh.lib.dg_profile_begin(mesh.h, mask), "dg_profile_begin")
+
+
+def profile_end(mesh: "Mesh"):
+    """Return {class: (launches, timed_launches, total_ms)}."""
+    out = (KernelStat * len(KERNEL_CLASSES))()
+    n = C.c_int()
+    _check(mesh.lib.dg_profile_end(mesh.h, out, len(KERNEL_CLASSES), C.byref(n)),
+           "dg_profile_end")
+    return {out[k].name.decode(): (out[k].launches, out[k].timed_launches, out[k].total_ms)
+            for k in range(n.value)}
