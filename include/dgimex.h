@@ -225,6 +225,32 @@ typedef struct {
 int dg_profile_begin(dg_mesh* mesh, uint32_t time_mask);
 int dg_profile_end(dg_mesh* mesh, dg_kernel_stat* out, int max_out, int* n_out);
 
+/*
+ * Allocation-free explicit operator (the paper has no counterpart: this
+ * exists for callers that must not allocate device memory while they run,
+ * e.g. a service that reserves its memory up front and forbids allocation
+ * in its steady state, or a framework that owns every device allocation
+ * and rejects raw cudaMalloc, which may also synchronise the device).
+ * Same arguments, results and layout as dg_apply_explicit, which instead
+ * grows per-mesh workspace with cudaMalloc on its first call on a mesh.
+ *  - Scratch comes from one fixed array of 2^22 doubles (32 MiB) of device
+ *    memory in the library image; every GPU that loads the library holds it
+ *    until the process exits.  A mesh needs 14 doubles per face-point slot
+ *    (n_elem * 2 dim * (r+1)^(dim-1) slots) plus 9 per hanging point;
+ *    larger meshes are rejected with DG_ERR_ARG and a message naming the
+ *    sizes.  The call makes no cudaMalloc / cudaFree and calls no
+ *    allocating library routine.
+ *  - The first call on a device looks up the array's device address with
+ *    cudaGetSymbolAddress (the current device must be the context's); make
+ *    that first call before any stream capture.
+ *  - All calls share the one array and every scratch value is written
+ *    before it is read (nothing needs clearing between calls), so two calls
+ *    that can overlap on the GPU (different streams, or different threads)
+ *    race on it: order them on one stream or synchronise between them.
+ */
+int dg_apply_explicit_noalloc(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* phys,
+                              const double* q, double* f_ns, double* f_s, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

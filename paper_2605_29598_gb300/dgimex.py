@@ -104,6 +104,8 @@ class KernelStat(C.Structure):
                 ("total_ms", C.c_double)]
 
 
+EXPORTS["dg_apply_explicit_noalloc"] = (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Phys),
+                                                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p])
 EXPORTS["dg_profile_begin"] = (C.c_int, [C.c_void_p, C.c_uint32])
 EXPORTS["dg_profile_end"] = (C.c_int, [C.c_void_p, C.POINTER(KernelStat), C.c_int,
                                        C.POINTER(C.c_int)])
