@@ -71,6 +71,12 @@ def work_model(dim, n, N, S, nF):
     }
 
 
+# DRAM bytes per node of one launch, from an ncu capture of the unchanged
+# kernel (profiles/volume_grad_hill3d_30x30x20_r3_fp64.md: 189.1 MB over
+# 1 152 000 nodes), scaled to a launch by the nodes it processes.
+NCU_TRAFFIC_B_PER_NODE = {"volume_grad": 189.1e6 / 1152000}
+
+
 def bytes_model(dim, n, N, S, nF):
     d = dim
     return {
@@ -244,6 +250,7 @@ def gpu_main(args):
     prof_all = D.profile_end(mesh)
     dominant = max(prof_all, key=lambda k: prof_all[k][2])
 
+    q_start = q.clone()
     # timed region: launches counted, dominant class bracketed by events
     clocks = ClockSampler(dev)
     clocks.start()
@@ -298,6 +305,52 @@ def gpu_main(args):
     e2e_value = 5.0 * N * args.steps * world / (ms_e2e / 1e3) / 1e9
     state_bytes = 5 * N * 8
 
+    # mixed precision (FP32 Schur vmults under FP64 refinement) from the same
+    # start state as the timed FP64 steps; error of its perturbation fields
+    # against the FP64 result
+    mixed = None
+    if not args.no_mixed:
+        q_fp64 = q
+        phys_mx = D.make_phys(f=case["f"], variant="R2", precision="mixed")
+        mx_opts = dict(STEP_OPTS, gmres_inner_rtol=1e-4)
+        qw = q_start.clone()
+        mesh.step(phys_mx, qw, dt, **mx_opts)               # allocates FP32 copies once
+        qm = q_start.clone()
+        torch.cuda.synchronize()
+        e4 = torch.cuda.Event(enable_timing=True)
+        e5 = torch.cuda.Event(enable_timing=True)
+        e4.record(stream)
+        mx_its, mx_ref = 0, 0
+        for _ in range(args.steps):
+            inf = mesh.step(phys_mx, qm, dt, **mx_opts)
+            mx_its += inf.gmres_iters_total
+            mx_ref += inf.refinements_total
+        e5.record(stream)
+        torch.cuda.synchronize()
+        ms_mx = e4.elapsed_time(e5)
+        if dist:
+            t = torch.tensor([ms_mx], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_mx = float(t.item())
+
+        def pert_fields(s):
+            u = s[1:4] / s[0]
+            p = 0.4 * (s[4] - 0.5 * (s[1:4] * u).sum(0))
+            theta = p / (287.0 * s[0]) * (1e5 / p) ** (0.4 / 1.4)
+            return {"rho": s[0], "theta": theta, "u": u[0], "v": u[1], "w": u[2]}
+
+        f0, f64, fmx = pert_fields(q_start), pert_fields(q_fp64), pert_fields(qm)
+        errs = {}
+        for k in f0:
+            den = torch.linalg.norm(f64[k] - f0[k]).item()
+            errs[k] = torch.linalg.norm(fmx[k] - f64[k]).item() / den if den > 0 else None
+        mixed = {"value": 5.0 * N * args.steps * world / (ms_mx / 1e3) / 1e9,
+                 "unit": "GDoF-updates/s", "ms_per_step": ms_mx / args.steps,
+                 "speedup_vs_fp64": ms_max / ms_mx, "gmres_inner_total": mx_its,
+                 "fp64_refinement_sweeps": mx_ref, "inner_rtol": 1e-4,
+                 "rel_l2_err_vs_fp64_gpu_perturbation": errs,
+                 "what_is_fp32": "Schur vmults inside the Krylov solves (FP32 accumulation)"}
+
     # roofline of the dominant class
     pk, src = peaks()
     work = work_model(st.dim, st.n1d, N, N // st.nodes_per_elem * 2 * st.dim * st.n1d ** (st.dim - 1),
@@ -310,7 +363,13 @@ def gpu_main(args):
         achieved = flops / (per_launch_ms / 1e3) / 1e12
         roof = {"bound": "alu", "kernel": dominant, "achieved": achieved,
                 "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_NOMINAL_TFLOPS,
-                "traffic": None, "peak_source": "GB300 nominal FP64 (recipe table); probe measured 1.20",
+                "traffic": (NCU_TRAFFIC_B_PER_NODE[dominant] * N
+                            if dominant in NCU_TRAFFIC_B_PER_NODE and st.dim == 3 and st.n1d == 4
+                            else None),
+                "algorithmic_bytes_per_launch": bytes_model(
+                    st.dim, st.n1d, N, st.n_elem * 2 * st.dim * st.n1d ** (st.dim - 1),
+                    st.n_face_points).get(dominant),
+                "peak_source": "GB300 nominal FP64 (recipe table); probe measured 1.20",
                 "launches": timed_launches, "ms_per_launch": per_launch_ms,
                 "algorithmic_flops_per_launch": flops}
     elif timed_launches:
@@ -346,6 +405,7 @@ def gpu_main(args):
                 "d2h_bytes_per_step": state_bytes},
         "roofline": roof,
         "cpu_baseline": cpu,
+        "mixed_precision": mixed,
         "clocks": clk,
         "gpu_launches": total_launches,
         "iterations": {"picard_per_stage": picard, "gmres_total": gm_its, "gmres_max_relres": relres},
@@ -387,6 +447,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--oracle-child", default=None)
     args = ap.parse_args()
     if args.oracle_child:

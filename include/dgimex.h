@@ -51,7 +51,7 @@ typedef enum {
 enum { DG_NODES_GL = 0, DG_NODES_GLL = 1 };
 enum { DG_BC_WALL = 1 };
 enum { DG_R1 = 1, DG_R2 = 2 };
-enum { DG_FP64 = 0 };
+enum { DG_FP64 = 0, DG_MIXED = 1 };
 
 typedef struct dg_ctx dg_ctx;
 typedef struct dg_mesh dg_mesh;
@@ -116,7 +116,12 @@ typedef struct {
   double gamma, g, f;
   int variant;
   int penalty;
-  int precision;             /* DG_FP64 */
+  int precision;             /* DG_FP64, or DG_MIXED: Schur vmults inside the
+                                Krylov solves run in FP32 (FP32 accumulation)
+                                under FP64 iterative refinement; the outer
+                                residual, orthogonalisation, reductions,
+                                Schur right-hand side, velocity recovery and
+                                explicit operator stay FP64 */
 } dg_phys;
 
 /*
@@ -177,9 +182,14 @@ int dg_recover_velocity(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* phys,
 /* Restarted GMRES(restart) with classical Gram-Schmidt applied twice and
  * FP64 device reductions on the scaled Schur system; stops when
  * ||b - S x||_2 <= rtol ||b||_2.  x in: initial guess, out: solution (best
- * iterate and DG_ERR_NOT_CONVERGED after maxit).  Synchronises `stream`. */
-typedef struct { double rtol; int restart, maxit; } dg_gmres_opts;
-typedef struct { int iters; double relres; } dg_gmres_info;
+ * iterate and DG_ERR_NOT_CONVERGED after maxit).  Synchronises `stream`.
+ * With phys->precision == DG_MIXED the solve is iterative refinement: the
+ * residual r = b - S x is formed with the FP64 vmult, a correction d with
+ * S d ~ r is found by GMRES whose vmults run in FP32 (to relative residual
+ * inner_rtol, default 1e-4 when 0), x += d, until the FP64 test above
+ * holds; maxit bounds the inner iterations in total. */
+typedef struct { double rtol; int restart, maxit; double inner_rtol; } dg_gmres_opts;
+typedef struct { int iters; double relres; int refinements; } dg_gmres_info;
 int dg_gmres_solve(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* phys,
                    const dg_implicit_coeffs* cf, const double* b, double* x,
                    const dg_gmres_opts* opts, dg_gmres_info* info, void* stream);
@@ -201,6 +211,7 @@ typedef struct {
   int picard_iters[3];
   int gmres_iters_total;
   double max_relres;
+  int refinements_total;   /* DG_MIXED: FP64 residual sweeps over all solves */
 } dg_step_info;
 int imex_ark2_step(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* phys,
                    double* q, double dt, const dg_step_opts* opts,

@@ -116,6 +116,9 @@ struct dg_mesh {
   double* K = nullptr;       // d*d x N : w det(J) (J^{-1})_{ab}
   double* invM = nullptr;    // N       : 1 / (w det J)
   double* fgeo = nullptr;    // (d+1) x nF : n dS (d comps), dS
+  float* K32 = nullptr;      // FP32 copies for the mixed-precision path
+  float* invM32 = nullptr;
+  float* fgeo32 = nullptr;
   // face-point topology (device, int32)
   int* fp_minus = nullptr;   // nF: minus slot
   int* fp_plus = nullptr;    // nF: plus slot, -1 wall, -2-hp hanging
@@ -124,6 +127,7 @@ struct dg_mesh {
   int* hc_slot = nullptr;    // nHC: coarse slot base
   // workspace
   dg::DBuf trc, slot, hbuf, trh, pcoef, wv, gm_V, gm_work, red, st, fns, fs;
+  dg::DBuf trh32, pcoef32, c32, ir32, irw;   // mixed precision: FP32 coefficients, IR vectors
   std::vector<double> host_h;
   dg::Profiler prof;
   int64_t workspace_bytes() const;
@@ -136,6 +140,7 @@ struct FaceTopo {
   const int* fp_minus;
   const int* fp_plus;
   const double* fgeo;
+  const float* fgeo32;
   const int* hp_cslot;
   const int* hp_code;
   const int* hc_slot;
@@ -143,7 +148,7 @@ struct FaceTopo {
 };
 
 inline FaceTopo topo(const dg_mesh* m) {
-  return FaceTopo{m->fp_minus, m->fp_plus, m->fgeo, m->hp_cslot, m->hp_code,
+  return FaceTopo{m->fp_minus, m->fp_plus, m->fgeo, m->fgeo32, m->hp_cslot, m->hp_code,
                   m->hc_slot, m->nF, m->nH, m->nHC, m->S};
 }
 

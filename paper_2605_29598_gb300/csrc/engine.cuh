@@ -19,6 +19,21 @@ struct Engine {
 
 ImplK impl_consts(const dg_phys* ph, double a_dt);
 
+// Per-precision views of the mesh geometry and of the per-Picard
+// coefficient buffers (FP32 copies are made by ensure_fp32_geometry).
+template <typename T> inline const T* met_K(const dg_mesh* m);
+template <> inline const double* met_K<double>(const dg_mesh* m) { return m->K; }
+template <> inline const float* met_K<float>(const dg_mesh* m) { return m->K32; }
+template <typename T> inline const T* met_invM(const dg_mesh* m);
+template <> inline const double* met_invM<double>(const dg_mesh* m) { return m->invM; }
+template <> inline const float* met_invM<float>(const dg_mesh* m) { return m->invM32; }
+template <typename T> inline DBuf& buf_trh(dg_mesh* m) { return sizeof(T) == 8 ? m->trh : m->trh32; }
+template <typename T> inline DBuf& buf_pcoef(dg_mesh* m) { return sizeof(T) == 8 ? m->pcoef : m->pcoef32; }
+int ensure_fp32_geometry(dg_mesh* m);
+// FP32 Schur vmult (coefficients and vectors cast from / to FP64)
+int schur_vmult_mixed(dg_mesh* m, const ImplK& k, const double* rho, const double* plag, const double* ulag,
+                      int penalty, const double* x, double* y, cudaStream_t st);
+
 // Run the statement list for the mesh's compile-time (dim, n): D_ and N_ are
 // constexpr inside it.
 #define DG_DISPATCH(m, ...)                                  \

@@ -245,6 +245,42 @@ __global__ void k_node_coords(GeoArgs g, double* xyz) {
   }
 }
 
+__global__ void k_cast_f64_f32(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+
+// FP32 copies of the geometry for the FP32 operator kernels (made once).
+int ensure_fp32_geometry(dg_mesh* m) {
+  if (m->K32) return DG_OK;
+  const int64_t nK = (int64_t)m->dim * m->dim * m->N, nG = (int64_t)(m->dim + 1) * (m->nF > 0 ? m->nF : 1);
+  float *K32 = nullptr, *iM32 = nullptr, *g32 = nullptr;
+  cudaError_t e = cudaMalloc(&K32, sizeof(float) * nK);
+  if (e == cudaSuccess) e = cudaMalloc(&iM32, sizeof(float) * m->N);
+  if (e == cudaSuccess) e = cudaMalloc(&g32, sizeof(float) * nG);
+  if (e != cudaSuccess) {
+    cudaFree(K32);
+    cudaFree(iM32);
+    cudaFree(g32);
+    return cuda_fail(e, "cudaMalloc(fp32 geometry)");
+  }
+  k_cast_f64_f32<<<grid_for(nK, 256), 256>>>(m->K, K32, nK);
+  k_cast_f64_f32<<<grid_for(m->N, 256), 256>>>(m->invM, iM32, m->N);
+  if (m->nF > 0) k_cast_f64_f32<<<grid_for(nG, 256), 256>>>(m->fgeo, g32, nG);
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    cudaFree(K32);
+    cudaFree(iM32);
+    cudaFree(g32);
+    return cuda_fail(e, "fp32 geometry");
+  }
+  m->K32 = K32;
+  m->invM32 = iM32;
+  m->fgeo32 = g32;
+  return DG_OK;
+}
+
 static GeoArgs geo_args(const dg_mesh* m) {
   GeoArgs g;
   g.verts = m->verts;
@@ -265,8 +301,10 @@ static GeoArgs geo_args(const dg_mesh* m) {
 using namespace dg;
 
 int64_t dg_mesh::workspace_bytes() const {
-  const DBuf* b[] = {&trc, &slot, &hbuf, &trh, &pcoef, &wv, &gm_V, &gm_work, &red, &st, &fns, &fs};
+  const DBuf* b[] = {&trc, &slot, &hbuf, &trh, &pcoef, &wv, &gm_V, &gm_work, &red, &st, &fns, &fs,
+                     &trh32, &pcoef32, &c32, &ir32, &irw};
   int64_t s = 0;
+  if (K32) s += (int64_t)sizeof(float) * ((int64_t)dim * dim * N + N + (int64_t)(dim + 1) * (nF > 0 ? nF : 1));
   for (auto* x : b) s += (int64_t)x->bytes;
   return s;
 }
@@ -320,8 +358,12 @@ void dg_mesh_destroy(dg_mesh* m) {
   cudaFree(m->hp_cslot);
   cudaFree(m->hp_code);
   cudaFree(m->hc_slot);
+  cudaFree(m->K32);
+  cudaFree(m->invM32);
+  cudaFree(m->fgeo32);
   DBuf* b[] = {&m->trc, &m->slot, &m->hbuf, &m->trh, &m->pcoef, &m->wv, &m->gm_V,
-               &m->gm_work, &m->red, &m->st, &m->fns, &m->fs};
+               &m->gm_work, &m->red, &m->st, &m->fns, &m->fs, &m->trh32, &m->pcoef32,
+               &m->c32, &m->ir32, &m->irw};
   for (auto* x : b) x->release();
   m->prof.release();
   delete m;

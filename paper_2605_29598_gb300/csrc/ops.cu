@@ -28,7 +28,7 @@ int Engine<T, DIM, N>::explicit_rates(dg_mesh* m, const PhysK& ph, const T* q, T
   if (m->nHC > 0)
     DG_RUN(m, K_HANG_GATHER, st, k_hang_gather<T, DIM, N, 9><<<grid_for(m->nHC * CS::NFP, 128), 128, 0, st>>>(ft, hbuf, slot, tb));
   DG_RUN(m, K_VOL_EXPLICIT, st, k_volume_explicit<T, DIM, N><<<grid_for(m->E, CS::EPB), CS::THREADS, 0, st>>>(
-      q, m->K, m->invM, slot, m->E, m->S, tb, ph, fns, fs));
+      q, met_K<T>(m), met_invM<T>(m), slot, m->E, m->S, tb, ph, fns, fs));
   DG_LAUNCH_CHECK("explicit operator");
   return DG_OK;
 }
@@ -42,15 +42,15 @@ int Engine<T, DIM, N>::prepare(dg_mesh* m, const ImplK& ph, const T* plag, const
   if ((rc = m->trc.ensure(sizeof(T) * 5 * m->S)) != DG_OK) return rc;
   if ((rc = m->slot.ensure(sizeof(T) * 9 * m->S)) != DG_OK) return rc;
   if ((rc = m->hbuf.ensure(sizeof(T) * 9 * (m->nH > 0 ? m->nH : 1))) != DG_OK) return rc;
-  if ((rc = m->trh.ensure(sizeof(T) * m->S)) != DG_OK) return rc;
-  if ((rc = m->pcoef.ensure(sizeof(T) * (m->nF > 0 ? m->nF : 1))) != DG_OK) return rc;
+  if ((rc = buf_trh<T>(m).ensure(sizeof(T) * m->S)) != DG_OK) return rc;
+  if ((rc = buf_pcoef<T>(m).ensure(sizeof(T) * (m->nF > 0 ? m->nF : 1))) != DG_OK) return rc;
   if ((rc = m->wv.ensure(sizeof(T) * 6 * m->N)) != DG_OK) return rc;
   Tables<T> tb = cast_tables<T>(m->tab.t);
   FaceTopo ft = topo(m);
   Fields<T> in;
   in.f[0] = plag;
   in.scale[0] = (T)(ph.gamma / (ph.gamma - 1.0));
-  DG_RUN(m, K_TRACE, st, k_trace<T, DIM, N, 1><<<grid_for(m->S, 256), 256, 0, st>>>(in, m->E, m->N, m->trh.as<T>(), m->S, tb));
+  DG_RUN(m, K_TRACE, st, k_trace<T, DIM, N, 1><<<grid_for(m->S, 256), 256, 0, st>>>(in, m->E, m->N, buf_trh<T>(m).template as<T>(), m->S, tb));
   if (penalty) {
     for (int c = 0; c < 3; ++c) {
       in.f[c] = ulag + c * m->N;
@@ -58,7 +58,7 @@ int Engine<T, DIM, N>::prepare(dg_mesh* m, const ImplK& ph, const T* plag, const
     }
     DG_RUN(m, K_TRACE, st, k_trace<T, DIM, N, 3><<<grid_for(m->S, 256), 256, 0, st>>>(in, m->E, m->N, m->trc.as<T>(), m->S, tb));
     DG_RUN(m, K_FACE_LAMBDA, st, k_face_lambda<T, DIM, N><<<grid_for(m->nF, 128), 128, 0, st>>>(ft, m->trc.as<T>(), (T)(0.5 * ph.a_dt),
-                                                                    m->pcoef.as<T>(), tb));
+                                                                    buf_pcoef<T>(m).template as<T>(), tb));
   }
   DG_LAUNCH_CHECK("implicit coefficients");
   return DG_OK;
@@ -79,23 +79,23 @@ int Engine<T, DIM, N>::vmult(dg_mesh* m, const ImplK& ph, const T* rho, const T*
   in.f[0] = x;
   in.scale[0] = 1;
   DG_RUN(m, K_TRACE, st, k_trace<T, DIM, N, 1><<<grid_for(m->S, 256), 256, 0, st>>>(in, m->E, m->N, trc, m->S, tb));
-  DG_RUN(m, K_FACE_GRAD, st, k_face_grad<T, DIM, N><<<grid_for(m->nF, 128), 128, 0, st>>>(ft, trc, penalty ? m->pcoef.as<T>() : nullptr,
+  DG_RUN(m, K_FACE_GRAD, st, k_face_grad<T, DIM, N><<<grid_for(m->nF, 128), 128, 0, st>>>(ft, trc, penalty ? buf_pcoef<T>(m).template as<T>() : nullptr,
                                                                 slot, hbuf, tb));
   if (m->nHC > 0)
     DG_RUN(m, K_HANG_GATHER, st, k_hang_gather<T, DIM, N, DIM + 1><<<grid_for(m->nHC * CS::NFP, 128), 128, 0, st>>>(ft, hbuf, slot, tb));
   DG_RUN(m, K_VOL_GRAD, st, k_volume_grad<T, DIM, N, GRAD_VMULT><<<grid_for(m->E, CS::EPB), CS::THREADS, 0, st>>>(
-      x, rho, m->K, m->invM, slot, m->E, m->S, tb, ph, wv, y, nullptr, nullptr));
+      x, rho, met_K<T>(m), met_invM<T>(m), slot, m->E, m->S, tb, ph, wv, y, nullptr, nullptr));
   Fields<T> w;
   for (int b = 0; b < DIM; ++b) {
     w.f[b] = wv + b * m->N;
     w.scale[b] = 1;
   }
   DG_RUN(m, K_TRACE, st, k_trace<T, DIM, N, DIM><<<grid_for(m->S, 256), 256, 0, st>>>(w, m->E, m->N, trc, m->S, tb));
-  DG_RUN(m, K_FACE_DIV, st, k_face_div<T, DIM, N><<<grid_for(m->nF, 128), 128, 0, st>>>(ft, trc, m->trh.as<T>(), slot, hbuf, tb));
+  DG_RUN(m, K_FACE_DIV, st, k_face_div<T, DIM, N><<<grid_for(m->nF, 128), 128, 0, st>>>(ft, trc, buf_trh<T>(m).template as<T>(), slot, hbuf, tb));
   if (m->nHC > 0)
     DG_RUN(m, K_HANG_GATHER, st, k_hang_gather<T, DIM, N, 1><<<grid_for(m->nHC * CS::NFP, 128), 128, 0, st>>>(ft, hbuf, slot, tb));
   DG_RUN(m, K_VOL_DIV, st, k_volume_div<T, DIM, N, DIV_VMULT><<<grid_for(m->E, CS::EPB), CS::THREADS, 0, st>>>(
-      w, plag, m->K, m->invM, slot, m->E, m->S, tb, ph, y, nullptr, nullptr, nullptr, nullptr));
+      w, plag, met_K<T>(m), met_invM<T>(m), slot, m->E, m->S, tb, ph, y, nullptr, nullptr, nullptr, nullptr));
   DG_LAUNCH_CHECK("schur vmult");
   return DG_OK;
 }
@@ -119,11 +119,11 @@ int Engine<T, DIM, N>::schur_rhs(dg_mesh* m, const ImplK& ph, const T* rho, cons
     w.scale[b] = 1;
   }
   DG_RUN(m, K_TRACE, st, k_trace<T, DIM, N, DIM><<<grid_for(m->S, 256), 256, 0, st>>>(w, m->E, m->N, trc, m->S, tb));
-  DG_RUN(m, K_FACE_DIV, st, k_face_div<T, DIM, N><<<grid_for(m->nF, 128), 128, 0, st>>>(ft, trc, m->trh.as<T>(), slot, hbuf, tb));
+  DG_RUN(m, K_FACE_DIV, st, k_face_div<T, DIM, N><<<grid_for(m->nF, 128), 128, 0, st>>>(ft, trc, buf_trh<T>(m).template as<T>(), slot, hbuf, tb));
   if (m->nHC > 0)
     DG_RUN(m, K_HANG_GATHER, st, k_hang_gather<T, DIM, N, 1><<<grid_for(m->nHC * CS::NFP, 128), 128, 0, st>>>(ft, hbuf, slot, tb));
   DG_RUN(m, K_VOL_DIV, st, k_volume_div<T, DIM, N, DIV_RHS><<<grid_for(m->E, CS::EPB), CS::THREADS, 0, st>>>(
-      w, plag, m->K, m->invM, slot, m->E, m->S, tb, ph, rhs, ehat, rho, ulag, ustar));
+      w, plag, met_K<T>(m), met_invM<T>(m), slot, m->E, m->S, tb, ph, rhs, ehat, rho, ulag, ustar));
   DG_LAUNCH_CHECK("schur rhs");
   return DG_OK;
 }
@@ -148,7 +148,7 @@ int Engine<T, DIM, N>::recover(dg_mesh* m, const ImplK& ph, const T* rho, const 
   if (m->nHC > 0)
     DG_RUN(m, K_HANG_GATHER, st, k_hang_gather<T, DIM, N, DIM + 1><<<grid_for(m->nHC * CS::NFP, 128), 128, 0, st>>>(ft, hbuf, slot, tb));
   DG_RUN(m, K_VOL_GRAD, st, k_volume_grad<T, DIM, N, GRAD_RECOVER><<<grid_for(m->E, CS::EPB), CS::THREADS, 0, st>>>(
-      p, rho, m->K, m->invM, slot, m->E, m->S, tb, ph, nullptr, nullptr, ustar, u));
+      p, rho, met_K<T>(m), met_invM<T>(m), slot, m->E, m->S, tb, ph, nullptr, nullptr, ustar, u));
   DG_LAUNCH_CHECK("velocity recovery");
   return DG_OK;
 }
@@ -161,6 +161,14 @@ template struct Engine<double, 3, 2>;
 template struct Engine<double, 3, 3>;
 template struct Engine<double, 3, 4>;
 template struct Engine<double, 3, 5>;
+template struct Engine<float, 2, 2>;
+template struct Engine<float, 2, 3>;
+template struct Engine<float, 2, 4>;
+template struct Engine<float, 2, 5>;
+template struct Engine<float, 3, 2>;
+template struct Engine<float, 3, 3>;
+template struct Engine<float, 3, 4>;
+template struct Engine<float, 3, 5>;
 
 }  // namespace dg
 
@@ -175,9 +183,9 @@ static int check_common(dg_ctx* ctx, const dg_mesh* m, const dg_phys* ph, const 
     set_error("%s: gamma must be > 1", who);
     return DG_ERR_ARG;
   }
-  if (ph->precision != DG_FP64) {
-    set_error("%s: only DG_FP64 is implemented", who);
-    return DG_ERR_UNSUPPORTED;
+  if (ph->precision != DG_FP64 && ph->precision != DG_MIXED) {
+    set_error("%s: precision must be DG_FP64 or DG_MIXED", who);
+    return DG_ERR_ARG;
   }
   if (ph->variant != DG_R1 && ph->variant != DG_R2) {
     set_error("%s: variant must be DG_R1 or DG_R2", who);
@@ -223,6 +231,8 @@ int dg_apply_implicit(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* ph, const
   dg_mesh* m = const_cast<dg_mesh*>(mesh);
   ImplK k = impl_consts(ph, cf->a_dt);
   cudaStream_t st = (cudaStream_t)stream;
+  if (ph->precision == DG_MIXED)
+    return schur_vmult_mixed(m, k, cf->rho, cf->p_lag, cf->u_lag, ph->penalty, x, y, st);
   DG_DISPATCH(m, {
     using EN = Engine<double, D_, N_>;
     if ((rc = EN::prepare(m, k, cf->p_lag, cf->u_lag, ph->penalty, st)) != DG_OK) return rc;

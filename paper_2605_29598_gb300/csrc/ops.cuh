@@ -16,6 +16,11 @@
 
 namespace dg {
 
+// face geometry (n dS) in the kernel's precision
+template <typename T> __device__ __forceinline__ const T* geo_ptr(const FaceTopo& ft);
+template <> __device__ __forceinline__ const double* geo_ptr<double>(const FaceTopo& ft) { return ft.fgeo; }
+template <> __device__ __forceinline__ const float* geo_ptr<float>(const FaceTopo& ft) { return ft.fgeo32; }
+
 template <typename T> struct Fields {
   const T* f[5];
   T scale[5];
@@ -160,7 +165,7 @@ __global__ void k_face_explicit(FaceTopo ft, const T* __restrict__ trc, T* __res
   T n2 = 0;
 #pragma unroll
   for (int b = 0; b < DIM; ++b) {
-    nS[b] = (T)__ldg(ft.fgeo + b * ft.nF + p);
+    nS[b] = __ldg(geo_ptr<T>(ft) + b * ft.nF + p);
     n2 += nS[b] * nS[b];
   }
   T qm[5], qp[5];
@@ -257,7 +262,7 @@ struct PhysK {
 
 template <typename T, int DIM, int N>
 __global__ void __launch_bounds__(CellShape<DIM, N>::THREADS)
-k_volume_explicit(const T* __restrict__ q, const double* __restrict__ Kg, const double* __restrict__ invMg,
+k_volume_explicit(const T* __restrict__ q, const T* __restrict__ Kg, const T* __restrict__ invMg,
                   const T* __restrict__ slot, int64_t E, int64_t S, Tables<T> tb, PhysK ph,
                   T* __restrict__ fns, T* __restrict__ fs) {
   using CS = CellShape<DIM, N>;
@@ -279,8 +284,8 @@ k_volume_explicit(const T* __restrict__ q, const double* __restrict__ Kg, const 
 #pragma unroll
     for (int a = 0; a < DIM; ++a)
 #pragma unroll
-      for (int b = 0; b < DIM; ++b) K[a][b] = (T)__ldg(Kg + (a * DIM + b) * Nn + node);
-    iM = (T)__ldg(invMg + node);
+      for (int b = 0; b < DIM; ++b) K[a][b] = __ldg(Kg + (a * DIM + b) * Nn + node);
+    iM = __ldg(invMg + node);
   } else {
 #pragma unroll
     for (int a = 0; a < DIM; ++a)
@@ -354,7 +359,7 @@ __global__ void k_face_grad(FaceTopo ft, const T* __restrict__ trc, const T* __r
   T avg = code == -1 ? xm : (T)0.5 * (xm + xp);
 #pragma unroll
   for (int b = 0; b < DIM; ++b)
-    put<T>(slot, hbuf, ft.S, ft.nH, b, sm, code, -avg * (T)__ldg(ft.fgeo + b * ft.nF + p));
+    put<T>(slot, hbuf, ft.S, ft.nH, b, sm, code, -avg * __ldg(geo_ptr<T>(ft) + b * ft.nF + p));
   T pen = (code == -1 || pcoef == nullptr) ? (T)0 : __ldg(pcoef + p) * (xm - xp);
   put<T>(slot, hbuf, ft.S, ft.nH, DIM, sm, code, -pen);
 }
@@ -372,7 +377,7 @@ __global__ void k_face_div(FaceTopo ft, const T* __restrict__ trc, const T* __re
     T fm = 0, fp = 0;
 #pragma unroll
     for (int b = 0; b < DIM; ++b) {
-      T n = (T)__ldg(ft.fgeo + b * ft.nF + p);
+      T n = __ldg(geo_ptr<T>(ft) + b * ft.nF + p);
       T wm = __ldg(trc + b * ft.S + sm);
       T wp = plus_value<T, DIM, N>(ft, tb, trc + b * ft.S, code, wm);
       fm += wm * n;
@@ -393,7 +398,7 @@ __global__ void k_face_lambda(FaceTopo ft, const T* __restrict__ tru, T a_dt_hal
   T unm = 0, unp = 0;
 #pragma unroll
   for (int b = 0; b < DIM; ++b) {
-    T n = (T)__ldg(ft.fgeo + b * ft.nF + p);
+    T n = __ldg(geo_ptr<T>(ft) + b * ft.nF + p);
     T um = __ldg(tru + comp_of<DIM>(b) * ft.S + sm);
     T up = plus_value<T, DIM, N>(ft, tb, tru + comp_of<DIM>(b) * ft.S, code, um);
     unm += um * n;
@@ -415,8 +420,8 @@ struct ImplK {
 //  RECOVER: u = ustar - a_dt * w  (3 comps)
 template <typename T, int DIM, int N, int MODE>
 __global__ void __launch_bounds__(CellShape<DIM, N>::THREADS)
-k_volume_grad(const T* __restrict__ x, const T* __restrict__ rho, const double* __restrict__ Kg,
-              const double* __restrict__ invMg, const T* __restrict__ slot, int64_t E, int64_t S,
+k_volume_grad(const T* __restrict__ x, const T* __restrict__ rho, const T* __restrict__ Kg,
+              const T* __restrict__ invMg, const T* __restrict__ slot, int64_t E, int64_t S,
               Tables<T> tb, ImplK ph, T* __restrict__ wv, T* __restrict__ y,
               const T* __restrict__ ustar, T* __restrict__ uout) {
   using CS = CellShape<DIM, N>;
@@ -434,7 +439,7 @@ k_volume_grad(const T* __restrict__ x, const T* __restrict__ rho, const double* 
 #pragma unroll
   for (int b = 0; b < DIM; ++b) {
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) sm[le][a][i] = active ? -xv * (T)__ldg(Kg + (a * DIM + b) * Nn + node) : (T)0;
+    for (int a = 0; a < DIM; ++a) sm[le][a][i] = active ? -xv * __ldg(Kg + (a * DIM + b) * Nn + node) : (T)0;
     __syncthreads();
     r[b] = contract<T, DIM, N>(tb, sm[le], i, idx);
     __syncthreads();
@@ -442,7 +447,7 @@ k_volume_grad(const T* __restrict__ x, const T* __restrict__ rho, const double* 
   r[DIM] = 0;
   if (!active) return;
   lift<T, DIM, N, DIM + 1>(tb, slot, S, e, idx, r);
-  const T iM = (T)__ldg(invMg + node);
+  const T iM = __ldg(invMg + node);
   T G[3] = {0, 0, 0};
 #pragma unroll
   for (int b = 0; b < DIM; ++b) G[comp_of<DIM>(b)] = iM * r[b];
@@ -482,8 +487,8 @@ enum DivMode { DIV_VMULT = 0, DIV_RHS = 1 };
 //         w3_z = ustar_z (R2) or u_lag_z (R1)
 template <typename T, int DIM, int N, int MODE>
 __global__ void __launch_bounds__(CellShape<DIM, N>::THREADS)
-k_volume_div(Fields<T> wv, const T* __restrict__ plag, const double* __restrict__ Kg,
-             const double* __restrict__ invMg, const T* __restrict__ slot, int64_t E, int64_t S,
+k_volume_div(Fields<T> wv, const T* __restrict__ plag, const T* __restrict__ Kg,
+             const T* __restrict__ invMg, const T* __restrict__ slot, int64_t E, int64_t S,
              Tables<T> tb, ImplK ph, T* __restrict__ y, const T* __restrict__ ehat,
              const T* __restrict__ rho, const T* __restrict__ ulag, const T* __restrict__ ustar) {
   using CS = CellShape<DIM, N>;
@@ -506,7 +511,7 @@ k_volume_div(Fields<T> wv, const T* __restrict__ plag, const double* __restrict_
     for (int a = 0; a < DIM; ++a) {
       T v = 0;
 #pragma unroll
-      for (int b = 0; b < DIM; ++b) v += (T)__ldg(Kg + (a * DIM + b) * Nn + node) * wl[b];
+      for (int b = 0; b < DIM; ++b) v += __ldg(Kg + (a * DIM + b) * Nn + node) * wl[b];
       sm[le][a][i] = -hr * v;
     }
   } else {
@@ -518,7 +523,7 @@ k_volume_div(Fields<T> wv, const T* __restrict__ plag, const double* __restrict_
   r[0] = contract<T, DIM, N>(tb, sm[le], i, idx);
   if (!active) return;
   lift<T, DIM, N, 1>(tb, slot, S, e, idx, r);
-  const T div = (T)__ldg(invMg + node) * r[0];
+  const T div = __ldg(invMg + node) * r[0];
   const T adt = (T)ph.a_dt;
   if (MODE == DIV_VMULT) {
     y[node] -= gm1 * adt * adt * div;

@@ -63,8 +63,7 @@ __global__ void k_multiaxpy(const double* __restrict__ V, int nvec, int64_t n, C
   w[i] = acc;
 }
 
-__global__ void k_axpby(int64_t n, double a, const double* __restrict__ x, double b, const double* __restrict__ y,
-                        double* __restrict__ z) {
+__global__ void k_axpby(int64_t n, double a, const double* x, double b, const double* y, double* z) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) z[i] = a * x[i] + b * y[i];
 }
@@ -214,7 +213,7 @@ struct Vmult {
 
 // Restarted GMRES(m), classical Gram-Schmidt applied twice, Givens rotations.
 static int gmres(dg_mesh* m, const Vmult& A, const double* b, double* x, double rtol, int restart, int maxit,
-                 dg_gmres_info* info, cudaStream_t st) {
+                 dg_gmres_info* info, cudaStream_t st, bool x_is_zero = false) {
   const int64_t n = m->N;
   if (restart < 1 || restart > MAX_RESTART || maxit < 0 || !(rtol >= 0.0)) {
     set_error("gmres: restart must be in 1..%d, maxit >= 0, rtol >= 0", MAX_RESTART);
@@ -249,8 +248,12 @@ static int gmres(dg_mesh* m, const Vmult& A, const double* b, double* x, double 
   int it = 0;
   double relres = 0.0;
   while (true) {
-    if ((rc = A(x, tmp, st)) != DG_OK) return rc;
-    DG_RUN(m, K_VEC, st, k_axpby<<<gb, 256, 0, st>>>(n, 1.0, b, -1.0, tmp, V));
+    if (x_is_zero && it == 0) {
+      DG_CUDA(cudaMemcpyAsync(V, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    } else {
+      if ((rc = A(x, tmp, st)) != DG_OK) return rc;
+      DG_RUN(m, K_VEC, st, k_axpby<<<gb, 256, 0, st>>>(n, 1.0, b, -1.0, tmp, V));
+    }
     double b2;
     if ((rc = dots(m, red, V, 1, n, V, &b2, st)) != DG_OK) return rc;
     const double beta = std::sqrt(b2);
@@ -341,6 +344,141 @@ static Vmult make_vmult(SchurCtx* s) {
   return v;
 }
 
+// ---------------------------------------------------------------------------
+// mixed precision: FP32 Schur vmult behind an FP64 interface
+// ---------------------------------------------------------------------------
+
+__global__ void k_d2f(const double* __restrict__ a, float* __restrict__ b, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+
+__global__ void k_f2d(const float* __restrict__ a, double* __restrict__ b, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (double)a[i];
+}
+
+struct Schur32Ctx {
+  dg_mesh* m;
+  ImplK k;
+  const float* rho;
+  const float* plag;
+  int penalty;
+  float* x32;
+  float* y32;
+};
+
+template <int D, int NN>
+static int schur32_vmult_fn(void* self, const double* x, double* y, cudaStream_t st) {
+  Schur32Ctx* s = static_cast<Schur32Ctx*>(self);
+  dg_mesh* m = s->m;
+  const unsigned gb = grid_for(m->N, 256);
+  DG_RUN(m, K_VEC, st, k_d2f<<<gb, 256, 0, st>>>(x, s->x32, m->N));
+  int rc = Engine<float, D, NN>::vmult(m, s->k, s->rho, s->plag, s->penalty, s->x32, s->y32, st);
+  if (rc != DG_OK) return rc;
+  DG_RUN(m, K_VEC, st, k_f2d<<<gb, 256, 0, st>>>(s->y32, y, m->N));
+  DG_LAUNCH_CHECK("fp32 vmult casts");
+  return DG_OK;
+}
+
+// FP32 copies of the frozen coefficients and their face data (h rho traces,
+// implicit Rusanov lambda) for the FP32 vmult.
+static int prepare32(dg_mesh* m, const ImplK& k, const double* rho, const double* plag, const double* ulag,
+                     int penalty, cudaStream_t st, Schur32Ctx* out) {
+  int rc;
+  if ((rc = ensure_fp32_geometry(m)) != DG_OK) return rc;
+  const int64_t n = m->N;
+  if ((rc = m->c32.ensure(sizeof(float) * 5 * n)) != DG_OK) return rc;
+  if ((rc = m->ir32.ensure(sizeof(float) * 2 * n)) != DG_OK) return rc;
+  float* c = m->c32.as<float>();
+  const unsigned gb = grid_for(n, 256), gb3 = grid_for(3 * n, 256);
+  DG_RUN(m, K_VEC, st, k_d2f<<<gb, 256, 0, st>>>(rho, c, n));
+  DG_RUN(m, K_VEC, st, k_d2f<<<gb, 256, 0, st>>>(plag, c + n, n));
+  DG_RUN(m, K_VEC, st, k_d2f<<<gb3, 256, 0, st>>>(ulag, c + 2 * n, 3 * n));
+  DG_LAUNCH_CHECK("fp32 coefficient casts");
+  rc = DG_ERR_UNSUPPORTED;
+  DG_DISPATCH(m, rc = (Engine<float, D_, N_>::prepare(m, k, c + n, c + 2 * n, penalty, st)));
+  if (rc != DG_OK) return rc;
+  *out = Schur32Ctx{m, k, c, c + n, penalty, m->ir32.as<float>(), m->ir32.as<float>() + n};
+  return DG_OK;
+}
+
+static Vmult make_vmult32(Schur32Ctx* s) {
+  Vmult v{nullptr, s};
+  DG_DISPATCH(s->m, v.fn = &schur32_vmult_fn<D_, N_>);
+  return v;
+}
+
+int schur_vmult_mixed(dg_mesh* m, const ImplK& k, const double* rho, const double* plag, const double* ulag,
+                      int penalty, const double* x, double* y, cudaStream_t st) {
+  Schur32Ctx sc;
+  int rc = prepare32(m, k, rho, plag, ulag, penalty, st, &sc);
+  if (rc != DG_OK) return rc;
+  Vmult A = make_vmult32(&sc);
+  if (!A.fn) return DG_ERR_UNSUPPORTED;
+  return A(x, y, st);
+}
+
+// Iterative refinement: FP64 residual r = b - A64 x, correction from GMRES
+// on the FP32 operator (FP64 basis, orthogonalisation and reductions) to
+// relative residual inner_rtol, x += d; until ||r|| <= rtol ||b||.
+static int gmres_ir(dg_mesh* m, const Vmult& A64, const Vmult& A32, const double* b, double* x, double rtol,
+                    int restart, int maxit, double inner_rtol, dg_gmres_info* info, cudaStream_t st) {
+  const int64_t n = m->N;
+  int rc;
+  if ((rc = m->irw.ensure(sizeof(double) * 2 * n)) != DG_OK) return rc;
+  Red red;
+  if ((rc = ensure_red(m, &red)) != DG_OK) return rc;
+  double* r = m->irw.as<double>();
+  double* d = r + n;
+  const unsigned gb = grid_for(n, 256);
+  if (!(inner_rtol > 0.0)) inner_rtol = 1e-4;
+  double bn2;
+  if ((rc = dots(m, red, b, 1, n, b, &bn2, st)) != DG_OK) return rc;
+  const double bnorm = std::sqrt(bn2);
+  if (!std::isfinite(bnorm)) {
+    set_error("gmres (mixed): non-finite right-hand side");
+    return DG_ERR_NONFINITE;
+  }
+  dg_gmres_info out{0, 0.0, 0};
+  if (bnorm == 0.0) {
+    DG_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
+    if (info) *info = out;
+    return DG_OK;
+  }
+  for (int sweep = 0;; ++sweep) {
+    if ((rc = A64(x, r, st)) != DG_OK) return rc;
+    DG_RUN(m, K_VEC, st, k_axpby<<<gb, 256, 0, st>>>(n, 1.0, b, -1.0, r, r));
+    double r2;
+    if ((rc = dots(m, red, r, 1, n, r, &r2, st)) != DG_OK) return rc;
+    const double rn = std::sqrt(r2);
+    if (!std::isfinite(rn)) {
+      set_error("gmres (mixed): non-finite residual");
+      return DG_ERR_NONFINITE;
+    }
+    out.relres = rn / bnorm;
+    out.refinements = sweep;
+    if (rn <= rtol * bnorm) break;
+    if (out.iters >= maxit || sweep >= 60) {
+      if (info) *info = out;
+      set_error("gmres (mixed): %d inner iterations, %d sweeps, relative residual %.3e > %.3e", out.iters,
+                sweep, out.relres, rtol);
+      return DG_ERR_NOT_CONVERGED;
+    }
+    // the inner solve only has to beat the FP32 operator's accuracy
+    const double tol_in = std::max(inner_rtol, 0.5 * rtol * bnorm / rn);
+    DG_CUDA(cudaMemsetAsync(d, 0, sizeof(double) * n, st));
+    dg_gmres_info gi{0, 0.0, 0};
+    rc = gmres(m, A32, r, d, tol_in, restart, maxit - out.iters, &gi, st, true);
+    if (rc != DG_OK && rc != DG_ERR_NOT_CONVERGED) return rc;
+    out.iters += gi.iters;
+    DG_RUN(m, K_VEC, st, k_axpby<<<gb, 256, 0, st>>>(n, 1.0, x, 1.0, d, x));
+    DG_LAUNCH_CHECK("refinement update");
+  }
+  if (info) *info = out;
+  return DG_OK;
+}
+
 static int prepare_rt(dg_mesh* m, const ImplK& k, const double* plag, const double* ulag, int penalty,
                       cudaStream_t st) {
   DG_DISPATCH(m, return (Engine<double, D_, N_>::prepare(m, k, plag, ulag, penalty, st)));
@@ -370,9 +508,9 @@ static int check_phys(const dg_phys* ph, const char* who) {
     set_error("%s: invalid physics (gamma > 1, variant R1/R2)", who);
     return DG_ERR_ARG;
   }
-  if (ph->precision != DG_FP64) {
-    set_error("%s: only DG_FP64 is implemented", who);
-    return DG_ERR_UNSUPPORTED;
+  if (ph->precision != DG_FP64 && ph->precision != DG_MIXED) {
+    set_error("%s: precision must be DG_FP64 or DG_MIXED", who);
+    return DG_ERR_ARG;
   }
   return DG_OK;
 }
@@ -398,6 +536,13 @@ int dg_gmres_solve(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* ph, const dg
   SchurCtx sc{m, k, cf->rho, cf->p_lag, ph->penalty};
   Vmult A = make_vmult(&sc);
   if (!A.fn) return DG_ERR_UNSUPPORTED;
+  if (ph->precision == DG_MIXED) {
+    Schur32Ctx sc32;
+    if ((rc = prepare32(m, k, cf->rho, cf->p_lag, cf->u_lag, ph->penalty, st, &sc32)) != DG_OK) return rc;
+    Vmult A32 = make_vmult32(&sc32);
+    return gmres_ir(m, A, A32, b, x, opts->rtol, opts->restart, opts->maxit, opts->inner_rtol, info, st);
+  }
+  if (info) info->refinements = 0;
   return gmres(m, A, b, x, opts->rtol, opts->restart, opts->maxit, info, st);
 }
 
@@ -467,9 +612,18 @@ int imex_ark2_step(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* ph, double* 
       SchurCtx schur{m, k, rho, p, ph->penalty};
       Vmult A = make_vmult(&schur);
       dg_gmres_info gi{};
-      rc = gmres(m, A, rhs, pnew, opts->gmres.rtol, opts->gmres.restart, opts->gmres.maxit, &gi, st);
+      if (ph->precision == DG_MIXED) {
+        Schur32Ctx sc32;
+        if ((rc = prepare32(m, k, rho, p, u, ph->penalty, st, &sc32)) != DG_OK) return rc;
+        Vmult A32 = make_vmult32(&sc32);
+        rc = gmres_ir(m, A, A32, rhs, pnew, opts->gmres.rtol, opts->gmres.restart, opts->gmres.maxit,
+                      opts->gmres.inner_rtol, &gi, st);
+      } else {
+        rc = gmres(m, A, rhs, pnew, opts->gmres.rtol, opts->gmres.restart, opts->gmres.maxit, &gi, st);
+      }
       if (rc != DG_OK && rc != DG_ERR_NOT_CONVERGED) return rc;
       inf.gmres_iters_total += gi.iters;
+      inf.refinements_total += gi.refinements;
       if (gi.relres > inf.max_relres) inf.max_relres = gi.relres;
       if ((rc = recover_rt(m, k, rho, u, mhat, pnew, unew, st)) != DG_OK) return rc;
       DG_RUN(m, K_PICARD_NORMS, st, k_picard_norms<<<RED_BLOCKS, 256, 0, st>>>(p, pnew, u, unew, n, red.partial));

@@ -20,7 +20,7 @@ from . import build as _build
 DG_OK = 0
 DG_NODES_GL, DG_NODES_GLL = 0, 1
 DG_R1, DG_R2 = 1, 2
-DG_FP64 = 0
+DG_FP64, DG_MIXED = 0, 1
 STATUS = {0: "DG_OK", -1: "DG_ERR_ARG", -2: "DG_ERR_UNSUPPORTED", -3: "DG_ERR_CUDA",
           -4: "DG_ERR_NOT_CONVERGED", -5: "DG_ERR_TIMEOUT", -6: "DG_ERR_NONFINITE",
           -7: "DG_ERR_OOM"}
@@ -55,11 +55,12 @@ class ImplicitCoeffs(C.Structure):
 
 
 class GmresOpts(C.Structure):
-    _fields_ = [("rtol", C.c_double), ("restart", C.c_int), ("maxit", C.c_int)]
+    _fields_ = [("rtol", C.c_double), ("restart", C.c_int), ("maxit", C.c_int),
+                ("inner_rtol", C.c_double)]
 
 
 class GmresInfo(C.Structure):
-    _fields_ = [("iters", C.c_int), ("relres", C.c_double)]
+    _fields_ = [("iters", C.c_int), ("relres", C.c_double), ("refinements", C.c_int)]
 
 
 class StepOpts(C.Structure):
@@ -69,7 +70,7 @@ class StepOpts(C.Structure):
 
 class StepInfo(C.Structure):
     _fields_ = [("picard_iters", C.c_int * 3), ("gmres_iters_total", C.c_int),
-                ("max_relres", C.c_double)]
+                ("max_relres", C.c_double), ("refinements_total", C.c_int)]
 
 
 EXPORTS = {
@@ -166,9 +167,10 @@ def _stream(stream):
     return C.c_void_p(stream.cuda_stream)
 
 
-def make_phys(gamma=1.4, g=9.81, f=1e-4, variant="R2", penalty=True):
+def make_phys(gamma=1.4, g=9.81, f=1e-4, variant="R2", penalty=True, precision="fp64"):
     return Phys(gamma=gamma, g=g, f=f, variant=DG_R2 if variant == "R2" else DG_R1,
-                penalty=1 if penalty else 0, precision=DG_FP64)
+                penalty=1 if penalty else 0,
+                precision=DG_MIXED if precision == "mixed" else DG_FP64)
 
 
 class Context:
@@ -276,8 +278,8 @@ class Mesh:
         return u
 
     def gmres_solve(self, phys, cf, b, x, rtol=1e-12, restart=30, maxit=1000, stream=None,
-                    allow_not_converged=False):
-        opts = GmresOpts(rtol=rtol, restart=restart, maxit=maxit)
+                    allow_not_converged=False, inner_rtol=0.0):
+        opts = GmresOpts(rtol=rtol, restart=restart, maxit=maxit, inner_rtol=inner_rtol)
         info = GmresInfo()
         st = self.lib.dg_gmres_solve(self.ctx.h, self.h, C.byref(phys), C.byref(cf), _ptr(b),
                                      _ptr(x), C.byref(opts), C.byref(info), _stream(stream))
@@ -285,10 +287,12 @@ class Mesh:
         return info
 
     def step(self, phys, q, dt, picard_rtol=1e-10, picard_maxit=10, picard_fixed=0,
-             gmres_rtol=1e-10, gmres_restart=30, gmres_maxit=1000, stream=None):
+             gmres_rtol=1e-10, gmres_restart=30, gmres_maxit=1000, stream=None,
+             gmres_inner_rtol=0.0):
         opts = StepOpts(picard_rtol=picard_rtol, picard_maxit=picard_maxit,
                         picard_fixed=picard_fixed,
-                        gmres=GmresOpts(rtol=gmres_rtol, restart=gmres_restart, maxit=gmres_maxit))
+                        gmres=GmresOpts(rtol=gmres_rtol, restart=gmres_restart, maxit=gmres_maxit,
+                                        inner_rtol=gmres_inner_rtol))
         info = StepInfo()
         _check(self.lib.imex_ark2_step(self.ctx.h, self.h, C.byref(phys), _ptr(q), float(dt),
                                        C.byref(opts), C.byref(info), _stream(stream)),
