@@ -198,6 +198,112 @@ def run_oracle_sample(steps, warmup):
 # GPU arm
 # ----------------------------------------------------------------------------
 
+def run_ensemble(D, I, ctx, steps, warmup):
+    """32 uneven instances: FP64 one instance at a time (one mesh each) vs
+    the batched ensemble (instances sharing (dim, degree) merged) in FP64
+    and mixed precision; whole-ensemble steps timed with CUDA events."""
+    import torch
+    cases = I.ensemble_cases()
+    stream = torch.cuda.current_stream()
+    states = []
+    out = {"instances": len(cases), "cells": sum(c["mesh"].n_elem for c in cases)}
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        its = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), its
+
+    # one at a time, FP64
+    meshes = []
+    for c in cases:
+        m = D.Mesh(ctx, c["mesh"], c["degree"])
+        xyz = m.node_coords().cpu().numpy().T
+        q0 = torch.tensor(I.stratified_state(xyz, **c["state_params"]), dtype=torch.float64,
+                          device="cuda").contiguous()
+        meshes.append(m)
+        states.append(q0)
+    nodes = sum(m.N for m in meshes)
+    out["nodes"] = nodes
+    phys = [D.make_phys(f=c["f"]) for c in cases]
+
+    def seq_steps(qs, n):
+        its = 0
+        for _ in range(n):
+            for m, ph, c, q in zip(meshes, phys, cases, qs):
+                its += m.step(ph, q, c["dt"], **STEP_OPTS).gmres_iters_total
+        return its
+
+    seq_steps([q.clone() for q in states], warmup)
+    ms, its = timed(lambda: seq_steps([q.clone() for q in states], steps))
+    out["fp64_one_at_a_time"] = {"value": 5.0 * nodes * steps / (ms / 1e3) / 1e9,
+                                 "ms_per_step": ms / steps, "gmres_iters": its}
+    for m in meshes:
+        m.close()
+    # batched
+    ens = D.Ensemble(ctx, [c["mesh"] for c in cases], [c["degree"] for c in cases],
+                     [c["f"] for c in cases])
+    out["groups"] = ens.n_groups
+    dts = [c["dt"] for c in cases]
+    for prec in ("fp64", "mixed"):
+        ph = D.make_phys(precision=prec)
+        opts = dict(STEP_OPTS, gmres_inner_rtol=1e-4) if prec == "mixed" else STEP_OPTS
+
+        def ens_steps(n):
+            for i, q in enumerate(states):
+                ens.set_state(i, q)
+            its = 0
+            for _ in range(n):
+                its += ens.step(ph, dts, **opts).gmres_iters_total
+            return its
+
+        ens_steps(warmup)
+        ms, its = timed(lambda: ens_steps(steps))
+        out["batched_" + prec] = {"value": 5.0 * nodes * steps / (ms / 1e3) / 1e9,
+                                  "ms_per_step": ms / steps, "gmres_iters": its}
+    ens.close()
+    out["unit"] = "GDoF-updates/s"
+    out["steps"] = steps
+    return out
+
+
+def run_variant(D, I, ctx, case, steps, warmup):
+    """FP64 and mixed steps of another workload (timed with CUDA events)."""
+    import torch
+    mesh = D.Mesh(ctx, case["mesh"], case["degree"])
+    st = mesh.stats()
+    xyz = mesh.node_coords().cpu().numpy().T
+    q0 = torch.tensor(I.stratified_state(xyz, **case["state_params"]), dtype=torch.float64,
+                      device="cuda").contiguous()
+    out = {"cells": st.n_elem, "nodes": st.n_nodes, "hanging_points": st.n_hang_points,
+           "degree": case["degree"], "dt": case["dt"]}
+    stream = torch.cuda.current_stream()
+    for prec in ("fp64", "mixed"):
+        phys = D.make_phys(f=case["f"], variant="R2", precision=prec)
+        opts = dict(STEP_OPTS, gmres_inner_rtol=1e-4) if prec == "mixed" else STEP_OPTS
+        q = q0.clone()
+        for _ in range(warmup):
+            mesh.step(phys, q, case["dt"], **opts)
+        q = q0.clone()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        its = 0
+        for _ in range(steps):
+            its += mesh.step(phys, q, case["dt"], **opts).gmres_iters_total
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[prec] = {"value": 5.0 * st.n_nodes * steps / (ms / 1e3) / 1e9, "unit": "GDoF-updates/s",
+                     "ms_per_step": ms / steps, "gmres_iters": its, "steps": steps}
+    mesh.close()
+    return out
+
 def gpu_main(args):
     import torch
 
@@ -344,7 +450,26 @@ def gpu_main(args):
         for k in f0:
             den = torch.linalg.norm(f64[k] - f0[k]).item()
             errs[k] = torch.linalg.norm(fmx[k] - f64[k]).item() / den if den > 0 else None
+        # error budget: both results against an FP64 run with tight solver
+        # tolerances from the same start state
+        qt = q_start.clone()
+        tight = dict(STEP_OPTS, picard_rtol=1e-13, gmres_rtol=1e-13)
+        for _ in range(args.steps):
+            mesh.step(phys, qt, dt, **tight)
+        ft = pert_fields(qt)
+        err_tight = {"fp64": {}, "mixed": {}}
+        for k in f0:
+            den = torch.linalg.norm(ft[k] - f0[k]).item()
+            err_tight["fp64"][k] = torch.linalg.norm(f64[k] - ft[k]).item() / den if den > 0 else None
+            err_tight["mixed"][k] = torch.linalg.norm(fmx[k] - ft[k]).item() / den if den > 0 else None
+        qp = q_start.clone()
+        D.profile_begin(mesh, timed=D.KERNEL_CLASSES)
+        mesh.step(phys_mx, qp, dt, **mx_opts)
+        prof_mx = D.profile_end(mesh)
         mixed = {"value": 5.0 * N * args.steps * world / (ms_mx / 1e3) / 1e9,
+                 "kernel_breakdown_one_step": {k: {"launches": v[0], "ms": round(v[2], 3)}
+                                               for k, v in prof_mx.items() if v[0]},
+                 "rel_l2_err_vs_tight_fp64_gpu": err_tight,
                  "unit": "GDoF-updates/s", "ms_per_step": ms_mx / args.steps,
                  "speedup_vs_fp64": ms_max / ms_mx, "gmres_inner_total": mx_its,
                  "fp64_refinement_sweeps": mx_ref, "inner_rtol": 1e-4,
@@ -380,6 +505,11 @@ def gpu_main(args):
     total_launches = sum(v[0] for v in prof.values())
     breakdown = {k: {"launches": v[0], "ms": round(v[2], 3)} for k, v in prof_all.items() if v[0]}
 
+    variants = {}
+    if not args.no_variants and world == 1:
+        variants["hill3d_nc"] = run_variant(D, I, ctx, I.hill3d_case(refine=True), steps=2, warmup=1)
+        variants["ensemble32"] = run_ensemble(D, I, ctx, steps=2, warmup=1)
+
     if dist and rank != 0:
         dist.barrier()
         dist.destroy_process_group()
@@ -406,6 +536,7 @@ def gpu_main(args):
         "roofline": roof,
         "cpu_baseline": cpu,
         "mixed_precision": mixed,
+        "variants": variants,
         "clocks": clk,
         "gpu_launches": total_launches,
         "iterations": {"picard_per_stage": picard, "gmres_total": gm_its, "gmres_max_relres": relres},
@@ -448,6 +579,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--oracle-child", default=None)
     args = ap.parse_args()
     if args.oracle_child:

@@ -122,6 +122,9 @@ typedef struct {
                                 residual, orthogonalisation, reductions,
                                 Schur right-hand side, velocity recovery and
                                 explicit operator stay FP64 */
+  const double* f_cell;      /* optional device array, one Coriolis parameter
+                                per cell (NULL: f everywhere); lets one mesh
+                                carry several independent instances */
 } dg_phys;
 
 /*
@@ -179,8 +182,9 @@ int dg_recover_velocity(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* phys,
                         const dg_implicit_coeffs* cf, const double* m_hat,
                         const double* p, double* u, void* stream);
 
-/* Restarted GMRES(restart) with classical Gram-Schmidt applied twice and
- * FP64 device reductions on the scaled Schur system; stops when
+/* Restarted GMRES(restart) with classical Gram-Schmidt (a second pass when
+ * the first cancels |w| by more than 1e3) and FP64 device reductions on the
+ * scaled Schur system; stops when
  * ||b - S x||_2 <= rtol ||b||_2.  x in: initial guess, out: solution (best
  * iterate and DG_ERR_NOT_CONVERGED after maxit).  Synchronises `stream`.
  * With phys->precision == DG_MIXED the solve is iterative refinement: the
@@ -216,6 +220,32 @@ typedef struct {
 int imex_ark2_step(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* phys,
                    double* q, double dt, const dg_step_opts* opts,
                    dg_step_info* info, void* stream);
+
+/*
+ * Ensembles: many independent instances (meshes of any size, dim 2 or 3,
+ * degree 1..4, each with its own Coriolis parameter) advanced together.
+ * Instances sharing (dim, degree) are merged into one device mesh (disjoint
+ * union of cells and faces) so that each kernel of a step covers all of
+ * them in one launch; the Coriolis parameter is carried per cell.  Within a
+ * group the Schur solves and Picard loops run jointly (norms over the
+ * group), and all instances of a group must share dt.
+ *  dg_ensemble_create: descs[n] as for dg_mesh_create (host, copied),
+ *    f_inst[n] host Coriolis parameters.  The ensemble owns device state.
+ *  dg_ensemble_set_state / get_state: copy instance i's state (device,
+ *    5 x N_i, same layout as for a single mesh) into / out of the ensemble.
+ *  dg_ensemble_step: one ARK2 step of every group (imex_ark2_step with the
+ *    per-cell f), dt_inst[n] host; info sums iterations over the groups.
+ */
+typedef struct dg_ensemble dg_ensemble;
+int dg_ensemble_create(dg_ctx* ctx, const dg_mesh_desc* descs, const double* f_inst, int n,
+                       dg_ensemble** out);
+void dg_ensemble_destroy(dg_ensemble* ens);
+int dg_ensemble_info(const dg_ensemble* ens, int* n_groups, int64_t* total_nodes);
+int dg_ensemble_instance_nodes(const dg_ensemble* ens, int i, int64_t* n_nodes);
+int dg_ensemble_set_state(dg_ensemble* ens, int i, const double* q, void* stream);
+int dg_ensemble_get_state(dg_ensemble* ens, int i, double* q, void* stream);
+int dg_ensemble_step(dg_ensemble* ens, const dg_phys* phys, const double* dt_inst,
+                     const dg_step_opts* opts, dg_step_info* info, void* stream);
 
 /*
  * Launch accounting (no counterpart in the paper; used to measure the hot

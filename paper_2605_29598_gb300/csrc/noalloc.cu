@@ -107,7 +107,7 @@ extern "C" int dg_apply_explicit_noalloc(dg_ctx* ctx, const dg_mesh* mesh, const
   int rc = noalloc_scratch(dev, &scratch);
   if (rc != DG_OK) return rc;
   dg_mesh* m = const_cast<dg_mesh*>(mesh);
-  PhysK k{ph->gamma, ph->g, ph->f};
+  PhysK k{ph->gamma, ph->g, ph->f, ph->f_cell};
   DG_DISPATCH(m, return explicit_with_scratch<D_, N_>(m, k, q, fns, fs, scratch, (cudaStream_t)stream));
   set_error("dg_apply_explicit_noalloc: unsupported (dim, degree)");
   return DG_ERR_UNSUPPORTED;

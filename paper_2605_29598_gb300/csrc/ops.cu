@@ -111,7 +111,9 @@ int Engine<T, DIM, N>::schur_rhs(dg_mesh* m, const ImplK& ph, const T* rho, cons
   T* slot = m->slot.as<T>();
   T* hbuf = m->hbuf.as<T>();
   T* ustar = m->wv.as<T>() + 3 * m->N;
-  DG_RUN(m, K_USTAR, st, k_ustar<T><<<grid_for(m->N, 256), 256, 0, st>>>(mhat, rho, ulag, m->N, ph, ustar));
+  ImplK pk = ph;
+  pk.np = CS::NP;
+  DG_RUN(m, K_USTAR, st, k_ustar<T><<<grid_for(m->N, 256), 256, 0, st>>>(mhat, rho, ulag, m->N, pk, ustar));
   Fields<T> w;
   for (int b = 0; b < DIM; ++b) {
     int c = DIM == 3 ? b : (b == 0 ? 0 : 2);
@@ -139,7 +141,9 @@ int Engine<T, DIM, N>::recover(dg_mesh* m, const ImplK& ph, const T* rho, const 
   T* slot = m->slot.as<T>();
   T* hbuf = m->hbuf.as<T>();
   T* ustar = m->wv.as<T>() + 3 * m->N;
-  DG_RUN(m, K_USTAR, st, k_ustar<T><<<grid_for(m->N, 256), 256, 0, st>>>(mhat, rho, ulag, m->N, ph, ustar));
+  ImplK pk = ph;
+  pk.np = CS::NP;
+  DG_RUN(m, K_USTAR, st, k_ustar<T><<<grid_for(m->N, 256), 256, 0, st>>>(mhat, rho, ulag, m->N, pk, ustar));
   Fields<T> in;
   in.f[0] = p;
   in.scale[0] = 1;
@@ -201,6 +205,8 @@ ImplK dg::impl_consts(const dg_phys* ph, double a_dt) {
   k.f = ph->f;
   k.a_dt = a_dt;
   k.r2 = ph->variant == DG_R2;
+  k.fcell = ph->f_cell;
+  k.np = 1;
   return k;
 }
 
@@ -214,7 +220,7 @@ int dg_apply_explicit(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* ph, const
     set_error("dg_apply_explicit: NULL array");
     return DG_ERR_ARG;
   }
-  PhysK k{ph->gamma, ph->g, ph->f};
+  PhysK k{ph->gamma, ph->g, ph->f, ph->f_cell};
   dg_mesh* m = const_cast<dg_mesh*>(mesh);
   DG_DISPATCH(m, return (Engine<double, D_, N_>::explicit_rates(m, k, q, fns, fs, (cudaStream_t)stream)));
   return DG_ERR_UNSUPPORTED;

@@ -256,8 +256,14 @@ __device__ __forceinline__ void lift(const Tables<T>& tb, const T* __restrict__ 
   }
 }
 
+// Coriolis parameter of a cell: per-cell array if given, else uniform.
+__device__ __forceinline__ double coriolis(const double* fcell, double f, int64_t cell) {
+  return fcell ? __ldg(fcell + cell) : f;
+}
+
 struct PhysK {
   double gamma, g, f;
+  const double* fcell = nullptr;   // per-cell Coriolis parameter, or null
 };
 
 template <typename T, int DIM, int N>
@@ -335,7 +341,7 @@ k_volume_explicit(const T* __restrict__ q, const T* __restrict__ Kg, const T* __
   lift<T, DIM, N, 9>(tb, slot, S, e, idx, r);
 #pragma unroll
   for (int fld = 0; fld < 5; ++fld) fns[fld * Nn + node] = iM * r[fld];
-  const T f = (T)ph.f, g = (T)ph.g;
+  const T f = (T)coriolis(ph.fcell, ph.f, e), g = (T)ph.g;
   fs[0 * Nn + node] = iM * r[5] + f * m[1];
   fs[1 * Nn + node] = iM * r[6] - f * m[0];
   fs[2 * Nn + node] = iM * r[7] - g * rho;
@@ -412,6 +418,8 @@ enum GradMode { GRAD_VMULT = 0, GRAD_RECOVER = 1 };
 struct ImplK {
   double gamma, g, f, a_dt;
   int r2;
+  const double* fcell;   // per-cell Coriolis parameter, or null for the uniform f
+  int np;                // nodes per cell (to map a node to its cell)
 };
 
 // weak gradient G = M^{-1}[-int x grad(phi) + faces]; then
@@ -454,7 +462,7 @@ k_volume_grad(const T* __restrict__ x, const T* __restrict__ rho, const T* __res
   const T ir = 1 / __ldg(rho + node);
   T w[3];
   if (ph.r2) {
-    const T beta = (T)(ph.a_dt * ph.f);
+    const T beta = (T)(ph.a_dt * coriolis(ph.fcell, ph.f, e));
     const T d = 1 / (1 + beta * beta);
     w[0] = (G[0] + beta * G[1]) * d * ir;
     w[1] = (G[1] - beta * G[0]) * d * ir;
@@ -550,13 +558,14 @@ __global__ void k_ustar(const T* __restrict__ mhat, const T* __restrict__ rho, c
   const T rh = rho[k], adt = (T)ph.a_dt;
   T v0 = mhat[k], v1 = mhat[Nn + k], v2 = mhat[2 * Nn + k] - adt * (T)ph.g * rh;
   const T ir = 1 / rh;
+  const double fc = coriolis(ph.fcell, ph.f, k / ph.np);
   if (ph.r2) {
-    const T beta = (T)(ph.a_dt * ph.f), d = 1 / (1 + beta * beta);
+    const T beta = (T)(ph.a_dt * fc), d = 1 / (1 + beta * beta);
     ustar[k] = (v0 + beta * v1) * d * ir;
     ustar[Nn + k] = (v1 - beta * v0) * d * ir;
     ustar[2 * Nn + k] = v2 * ir;
   } else {
-    const T fr = adt * (T)ph.f * rh;
+    const T fr = adt * (T)fc * rh;
     // k x u = (-v, u, 0)
     ustar[k] = (v0 + fr * ulag[Nn + k]) * ir;
     ustar[Nn + k] = (v1 - fr * ulag[k]) * ir;

@@ -15,23 +15,48 @@ constexpr int MAX_RESTART = 64;
 // ---------------------------------------------------------------------------
 
 // partial[b * nvec + k] = sum over block b's chunk of V[k] . w
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Vectors are taken in groups of 8: w is read once per group, each thread
+// keeps 8 running sums, warps reduce by shuffles (fixed order, so the
+// result is deterministic).  Launch with 256 threads.
 __global__ void k_multidot(const double* __restrict__ V, int nvec, int64_t n, const double* __restrict__ w,
                            double* __restrict__ partial) {
-  __shared__ double red[256];
+  constexpr int G = 8;
+  __shared__ double red[G][8];
   const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
   const int64_t lo = blockIdx.x * chunk;
   const int64_t hi = lo + chunk < n ? lo + chunk : n;
-  for (int k = 0; k < nvec; ++k) {
-    const double* v = V + (int64_t)k * n;
-    double s = 0.0;
-    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) s += v[i] * w[i];
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-      if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
-      __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int k0 = 0; k0 < nvec; k0 += G) {
+    const int ng = nvec - k0 < G ? nvec - k0 : G;
+    double s[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) s[g] = 0.0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+      const double wi = w[i];
+#pragma unroll
+      for (int g = 0; g < G; ++g)
+        if (g < ng) s[g] += V[(int64_t)(k0 + g) * n + i] * wi;
     }
-    if (threadIdx.x == 0) partial[blockIdx.x * nvec + k] = red[0];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+      const double t = warp_sum(s[g]);
+      if (lane == 0) red[g][wid] = t;
+    }
+    __syncthreads();
+    if (wid == 0) {
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        double t = lane < 8 ? red[g][lane] : 0.0;
+        t = warp_sum(t);
+        if (lane == 0 && g < ng) partial[blockIdx.x * nvec + k0 + g] = t;
+      }
+    }
     __syncthreads();
   }
 }
@@ -279,16 +304,35 @@ static int gmres(dg_mesh* m, const Vmult& A, const double* b, double* x, double 
       double* vj = V + (int64_t)j * n;
       double* w = V + (int64_t)(j + 1) * n;
       if ((rc = A(vj, w, st)) != DG_OK) return rc;
+      // classical Gram-Schmidt with a re-orthogonalisation test: one pass
+      // gives V^T w and |w|^2 together (w is stored right after V_j); a
+      // second pass runs only when the projection cancelled w down to
+      // |w'| < 1e-3 |w|, where one pass would lose more than ~1e3 eps of
+      // orthogonality.  (The scaled Schur operator is close to the identity,
+      // so w is dominated by its V_j component and a stricter threshold
+      // would re-orthogonalise every step.)
       Coefs c;
-      if ((rc = dots(m, red, V, j + 1, n, w, h1.data(), st)) != DG_OK) return rc;
-      for (int k = 0; k <= j; ++k) c.c[k] = -h1[k];
+      if ((rc = dots(m, red, V, j + 2, n, w, h1.data(), st)) != DG_OK) return rc;
+      double proj = 0.0;
+      for (int k = 0; k <= j; ++k) {
+        c.c[k] = -h1[k];
+        proj += h1[k] * h1[k];
+        Hij(k, j) = h1[k];
+      }
       DG_RUN(m, K_MULTIAXPY, st, k_multiaxpy<<<gb, 256, 0, st>>>(V, j + 1, n, c, w));
-      if ((rc = dots(m, red, V, j + 1, n, w, h2.data(), st)) != DG_OK) return rc;
-      for (int k = 0; k <= j; ++k) c.c[k] = -h2[k];
-      DG_RUN(m, K_MULTIAXPY, st, k_multiaxpy<<<gb, 256, 0, st>>>(V, j + 1, n, c, w));
-      for (int k = 0; k <= j; ++k) Hij(k, j) = h1[k] + h2[k];
-      double w2;
-      if ((rc = dots(m, red, w, 1, n, w, &w2, st)) != DG_OK) return rc;
+      double w2 = h1[j + 1] - proj;
+      if (!(w2 > 1e-6 * h1[j + 1])) {
+        if ((rc = dots(m, red, V, j + 2, n, w, h2.data(), st)) != DG_OK) return rc;
+        proj = 0.0;
+        for (int k = 0; k <= j; ++k) {
+          c.c[k] = -h2[k];
+          proj += h2[k] * h2[k];
+          Hij(k, j) += h2[k];
+        }
+        DG_RUN(m, K_MULTIAXPY, st, k_multiaxpy<<<gb, 256, 0, st>>>(V, j + 1, n, c, w));
+        w2 = h2[j + 1] - proj;
+      }
+      if (w2 < 0.0) w2 = 0.0;
       const double hn = std::sqrt(w2);
       if (!std::isfinite(hn)) {
         set_error("gmres: non-finite Krylov vector");
@@ -486,7 +530,7 @@ static int prepare_rt(dg_mesh* m, const ImplK& k, const double* plag, const doub
 }
 
 static int explicit_rt(dg_mesh* m, const dg_phys* ph, const double* q, double* fns, double* fs, cudaStream_t st) {
-  PhysK k{ph->gamma, ph->g, ph->f};
+  PhysK k{ph->gamma, ph->g, ph->f, ph->f_cell};
   DG_DISPATCH(m, return (Engine<double, D_, N_>::explicit_rates(m, k, q, fns, fs, st)));
   return DG_ERR_UNSUPPORTED;
 }

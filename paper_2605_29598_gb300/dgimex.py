@@ -46,7 +46,8 @@ class MeshStats(C.Structure):
 
 class Phys(C.Structure):
     _fields_ = [("gamma", C.c_double), ("g", C.c_double), ("f", C.c_double),
-                ("variant", C.c_int), ("penalty", C.c_int), ("precision", C.c_int)]
+                ("variant", C.c_int), ("penalty", C.c_int), ("precision", C.c_int),
+                ("f_cell", C.c_void_p)]
 
 
 class ImplicitCoeffs(C.Structure):
@@ -107,6 +108,15 @@ class KernelStat(C.Structure):
 
 EXPORTS["dg_apply_explicit_noalloc"] = (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Phys),
                                                   C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p])
+EXPORTS["dg_ensemble_create"] = (C.c_int, [C.c_void_p, C.POINTER(MeshDesc), C.POINTER(C.c_double),
+                                           C.c_int, C.POINTER(C.c_void_p)])
+EXPORTS["dg_ensemble_destroy"] = (None, [C.c_void_p])
+EXPORTS["dg_ensemble_info"] = (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int64)])
+EXPORTS["dg_ensemble_instance_nodes"] = (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_int64)])
+EXPORTS["dg_ensemble_set_state"] = (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p])
+EXPORTS["dg_ensemble_get_state"] = (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p])
+EXPORTS["dg_ensemble_step"] = (C.c_int, [C.c_void_p, C.POINTER(Phys), C.POINTER(C.c_double),
+                                         C.POINTER(StepOpts), C.POINTER(StepInfo), C.c_void_p])
 EXPORTS["dg_profile_begin"] = (C.c_int, [C.c_void_p, C.c_uint32])
 EXPORTS["dg_profile_end"] = (C.c_int, [C.c_void_p, C.POINTER(KernelStat), C.c_int,
                                        C.POINTER(C.c_int)])
@@ -326,3 +336,73 @@ def profile_end(mesh: "Mesh"):
            "dg_profile_end")
     return {out[k].name.decode(): (out[k].launches, out[k].timed_launches, out[k].total_ms)
             for k in range(n.value)}
+
+
+class Ensemble:
+    """Independent instances advanced together (see dg_ensemble_create).
+
+    meshes: list of host meshes (``inputs.Mesh``); degrees: list of ints;
+    f: list of Coriolis parameters (one per instance)."""
+
+    def __init__(self, ctx: Context, meshes, degrees, f):
+        self.ctx = ctx
+        self.lib = ctx.lib
+        n = len(meshes)
+        keep = []
+        descs = (MeshDesc * n)()
+        for i, (m, r) in enumerate(zip(meshes, degrees)):
+            v = np.ascontiguousarray(m.vertices, dtype=np.float64)
+            a = np.ascontiguousarray(m.int_faces, dtype=np.int64).reshape(-1, 4)
+            h = np.ascontiguousarray(m.hang_faces, dtype=np.int64).reshape(-1, 5)
+            b = np.ascontiguousarray(m.bdry_faces, dtype=np.int64).reshape(-1, 3)
+            keep += [v, a, h, b]
+            descs[i] = MeshDesc(dim=int(m.dim), degree=int(r), node_set=DG_NODES_GL,
+                                n_elem=v.shape[0], vertices=v.ctypes.data_as(_DP),
+                                n_int=a.shape[0], int_faces=a.ctypes.data_as(_I64P),
+                                n_hang=h.shape[0], hang_faces=h.ctypes.data_as(_I64P),
+                                n_bdry=b.shape[0], bdry_faces=b.ctypes.data_as(_I64P))
+        fa = (C.c_double * n)(*[float(x) for x in f])
+        hnd = C.c_void_p()
+        _check(self.lib.dg_ensemble_create(ctx.h, descs, fa, n, C.byref(hnd)), "dg_ensemble_create")
+        self.h = hnd
+        self.n = n
+        self.nodes = []
+        for i in range(n):
+            k = C.c_int64()
+            _check(self.lib.dg_ensemble_instance_nodes(self.h, i, C.byref(k)), "instance_nodes")
+            self.nodes.append(k.value)
+        g = C.c_int()
+        t = C.c_int64()
+        _check(self.lib.dg_ensemble_info(self.h, C.byref(g), C.byref(t)), "dg_ensemble_info")
+        self.n_groups = g.value
+        self.total_nodes = t.value
+
+    def set_state(self, i, q, stream=None):
+        _check(self.lib.dg_ensemble_set_state(self.h, i, _ptr(q), _stream(stream)), "set_state")
+
+    def get_state(self, i, q, stream=None):
+        _check(self.lib.dg_ensemble_get_state(self.h, i, _ptr(q), _stream(stream)), "get_state")
+        return q
+
+    def step(self, phys, dt, picard_rtol=1e-10, picard_maxit=10, picard_fixed=0, gmres_rtol=1e-10,
+             gmres_restart=30, gmres_maxit=1000, gmres_inner_rtol=0.0, stream=None):
+        opts = StepOpts(picard_rtol=picard_rtol, picard_maxit=picard_maxit,
+                        picard_fixed=picard_fixed,
+                        gmres=GmresOpts(rtol=gmres_rtol, restart=gmres_restart, maxit=gmres_maxit,
+                                        inner_rtol=gmres_inner_rtol))
+        dts = (C.c_double * self.n)(*[float(x) for x in dt])
+        info = StepInfo()
+        _check(self.lib.dg_ensemble_step(self.h, C.byref(phys), dts, C.byref(opts), C.byref(info),
+                                         _stream(stream)), "dg_ensemble_step")
+        return info
+
+    def close(self):
+        if self.h:
+            self.lib.dg_ensemble_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -83,6 +83,40 @@ def _multilinear(verts, ref_pts):
     return np.einsum("mv,...vd->...md", w, verts)
 
 
+def _uniform_mesh(cells, periodic, verts, name):
+    """Face lists of an unrefined structured mesh (cell index x fastest),
+    built with array arithmetic."""
+    d = len(cells)
+    n = int(np.prod(cells))
+    e = np.arange(n, dtype=np.int64)
+    coords = [(e // int(np.prod(cells[:a]))) % cells[a] for a in range(d)]
+    int_faces, bdry_faces = [], []
+    for a in range(d):
+        stride = int(np.prod(cells[:a]))
+        ca = coords[a]
+        inner = ca < cells[a] - 1
+        eL = e[inner]
+        int_faces.append(np.stack([eL, np.full_like(eL, 2 * a + 1), eL + stride,
+                                   np.full_like(eL, 2 * a)], axis=1))
+        last = e[ca == cells[a] - 1]
+        first = e[ca == 0]
+        if periodic[a]:
+            if cells[a] > 1:
+                int_faces.append(np.stack([last, np.full_like(last, 2 * a + 1),
+                                           last - (cells[a] - 1) * stride,
+                                           np.full_like(last, 2 * a)], axis=1))
+        else:
+            bdry_faces.append(np.stack([first, np.full_like(first, 2 * a),
+                                        np.full_like(first, BC_WALL)], axis=1))
+            bdry_faces.append(np.stack([last, np.full_like(last, 2 * a + 1),
+                                        np.full_like(last, BC_WALL)], axis=1))
+    i64 = lambda lst, w: (np.concatenate(lst).astype(np.int64) if lst
+                          else np.zeros((0, w), dtype=np.int64))
+    return Mesh(dim=d, vertices=verts, int_faces=i64(int_faces, 4),
+                hang_faces=np.zeros((0, 5), dtype=np.int64), bdry_faces=i64(bdry_faces, 3),
+                level=np.zeros(n, dtype=np.int64), name=name)
+
+
 def box_mesh(cells, extent, periodic=None, hill=None, z_top=None,
              refine_level=None, name=""):
     """Structured box mesh, optionally terrain-following and locally refined.
@@ -127,6 +161,9 @@ def box_mesh(cells, extent, periodic=None, hill=None, z_top=None,
                          hill.get("yc", 0.0))
         zeta = base_verts[..., d - 1]
         base_verts[..., d - 1] = zeta + hh * (1.0 - zeta / z_top)
+
+    if refine_level is None:
+        return _uniform_mesh(cells, periodic, base_verts, name)
 
     # refinement levels per base cell, then 2:1 balance across faces
     lev = np.zeros(nb, dtype=np.int64)
@@ -315,3 +352,41 @@ def hill3d_case(nx=60, ny=60, nz=20, r=3, refine=False, refine_box=None):
                     name="hill3d_nc" if refine else "hill3d")
     params = dict(theta_ref=293.15, n_bv=0.01, wind=(10.0, 0.0, 0.0), bubble=None)
     return dict(mesh=mesh, degree=r, f=1e-4, dt=4.0, state_params=params)
+
+
+def ensemble_cases(n=32, seed0=1000):
+    """Ensemble of independent instances of uneven sizes and degrees.
+
+    Instance i draws from PCG64(seed0 + i): dim 2 when i % 4 == 0 else 3;
+    degree 2 + i % 3; cell count log-uniform in [2 000, 60 000]; f uniform in
+    [0, 1.4e-4] 1/s; theta' amplitude uniform in [0.005, 0.02] K.  2D: the
+    inertia-gravity-wave channel with 10 layers (3 km x 1 km cells, dt 12 s);
+    3D: the hill box with 10 layers and the hill workload's cell size
+    (3.33 km x 3.33 km x 2 km, dt 4 s), hill at the centre."""
+    out = []
+    for i in range(n):
+        rng = np.random.default_rng(seed0 + i)
+        dim = 2 if i % 4 == 0 else 3
+        r = 2 + i % 3
+        ne = float(np.exp(rng.uniform(np.log(2000.0), np.log(60000.0))))
+        f = float(rng.uniform(0.0, 1.4e-4))
+        amp = float(rng.uniform(0.005, 0.02))
+        if dim == 2:
+            nz = 10
+            nx = max(4, int(round(ne / nz)))
+            mesh = box_mesh((nx, nz), (nx * 3e3, 10e3), name=f"ens{i}")
+            params = dict(theta_ref=300.0, n_bv=0.01, wind=(20.0, 0.0, 0.0),
+                          bubble=dict(A=amp, xc=nx * 3e3 / 3, a=5e3, H=10e3))
+            dt = 12.0
+        else:
+            nz = 10
+            nxy = max(3, int(round(np.sqrt(ne / nz))))
+            dx = 200e3 / 60
+            L = nxy * dx
+            mesh = box_mesh((nxy, nxy, nz), (L, L, 20e3),
+                            hill=dict(h0=400.0, a_c=10e3, xc=L / 2, yc=L / 2), name=f"ens{i}")
+            params = dict(theta_ref=293.15, n_bv=0.01, wind=(10.0, 0.0, 0.0),
+                          bubble=dict(A=amp, xc=L / 3, a=5e3, H=20e3))
+            dt = 4.0
+        out.append(dict(mesh=mesh, degree=r, f=f, dt=dt, state_params=params))
+    return out
