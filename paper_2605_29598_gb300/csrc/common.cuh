@@ -119,6 +119,7 @@ struct dg_mesh {
   float* K32 = nullptr;      // FP32 copies for the mixed-precision path
   float* invM32 = nullptr;
   float* fgeo32 = nullptr;
+  float* lv32 = nullptr;     // cell corners minus corner 0 (E x 2^d x d)
   // face-point topology (device, int32)
   int* fp_minus = nullptr;   // nF: minus slot
   int* fp_plus = nullptr;    // nF: plus slot, -1 wall, -2-hp hanging

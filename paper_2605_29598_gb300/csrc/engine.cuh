@@ -30,6 +30,33 @@ template <> inline const float* met_invM<float>(const dg_mesh* m) { return m->in
 template <typename T> inline DBuf& buf_trh(dg_mesh* m) { return sizeof(T) == 8 ? m->trh : m->trh32; }
 template <typename T> inline DBuf& buf_pcoef(dg_mesh* m) { return sizeof(T) == 8 ? m->pcoef : m->pcoef32; }
 int ensure_fp32_geometry(dg_mesh* m);
+
+// Metric source of the implicit cell kernels: FP64 loads the stored
+// metric; FP32 recomputes it from the cell corner offsets.
+template <typename T>
+inline CellGeo<T> cell_geo(const dg_mesh* m) {
+  CellGeo<T> g;
+  g.K = met_K<T>(m);
+  g.invM = met_invM<T>(m);
+  g.lv = nullptr;
+  for (int k = 0; k < MAX_N; ++k) {
+    g.x[k] = (T)m->tab.x[k];
+    g.w[k] = (T)m->tab.w[k];
+  }
+  return g;
+}
+template <>
+inline CellGeo<float> cell_geo<float>(const dg_mesh* m) {
+  CellGeo<float> g;
+  g.K = m->K32;
+  g.invM = m->invM32;
+  g.lv = m->lv32;
+  for (int k = 0; k < MAX_N; ++k) {
+    g.x[k] = (float)m->tab.x[k];
+    g.w[k] = (float)m->tab.w[k];
+  }
+  return g;
+}
 // FP32 Schur vmult (coefficients and vectors cast from / to FP64)
 int schur_vmult_mixed(dg_mesh* m, const ImplK& k, const double* rho, const double* plag, const double* ulag,
                       int penalty, const double* x, double* y, cudaStream_t st);

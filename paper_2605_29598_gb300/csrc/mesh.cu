@@ -278,6 +278,26 @@ int ensure_fp32_geometry(dg_mesh* m) {
   m->K32 = K32;
   m->invM32 = iM32;
   m->fgeo32 = g32;
+  // corner offsets relative to corner 0, formed in FP64 and rounded: the
+  // FP32 metric built from them keeps FP32 relative accuracy however far the
+  // cell is from the origin
+  const int nv = m->dim << m->dim;
+  std::vector<double> hv((size_t)m->E * nv);
+  std::vector<float> lv((size_t)m->E * nv);
+  e = cudaMemcpy(hv.data(), m->verts, sizeof(double) * hv.size(), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "fp32 corner offsets");
+  for (int64_t c = 0; c < m->E; ++c)
+    for (int v = 0; v < (1 << m->dim); ++v)
+      for (int b = 0; b < m->dim; ++b)
+        lv[c * nv + v * m->dim + b] = (float)(hv[c * nv + v * m->dim + b] - hv[c * nv + b]);
+  float* lv32 = nullptr;
+  e = cudaMalloc(&lv32, sizeof(float) * lv.size());
+  if (e == cudaSuccess) e = cudaMemcpy(lv32, lv.data(), sizeof(float) * lv.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(lv32);
+    return cuda_fail(e, "fp32 corner offsets");
+  }
+  m->lv32 = lv32;
   return DG_OK;
 }
 
@@ -361,6 +381,7 @@ void dg_mesh_destroy(dg_mesh* m) {
   cudaFree(m->K32);
   cudaFree(m->invM32);
   cudaFree(m->fgeo32);
+  cudaFree(m->lv32);
   DBuf* b[] = {&m->trc, &m->slot, &m->hbuf, &m->trh, &m->pcoef, &m->wv, &m->gm_V,
                &m->gm_work, &m->red, &m->st, &m->fns, &m->fs, &m->trh32, &m->pcoef32,
                &m->c32, &m->ir32, &m->irw};

@@ -84,7 +84,7 @@ int Engine<T, DIM, N>::vmult(dg_mesh* m, const ImplK& ph, const T* rho, const T*
   if (m->nHC > 0)
     DG_RUN(m, K_HANG_GATHER, st, k_hang_gather<T, DIM, N, DIM + 1><<<grid_for(m->nHC * CS::NFP, 128), 128, 0, st>>>(ft, hbuf, slot, tb));
   DG_RUN(m, K_VOL_GRAD, st, k_volume_grad<T, DIM, N, GRAD_VMULT><<<grid_for(m->E, CS::EPB), CS::THREADS, 0, st>>>(
-      x, rho, met_K<T>(m), met_invM<T>(m), slot, m->E, m->S, tb, ph, wv, y, nullptr, nullptr));
+      x, rho, cell_geo<T>(m), slot, m->E, m->S, tb, ph, wv, y, nullptr, nullptr));
   Fields<T> w;
   for (int b = 0; b < DIM; ++b) {
     w.f[b] = wv + b * m->N;
@@ -95,7 +95,7 @@ int Engine<T, DIM, N>::vmult(dg_mesh* m, const ImplK& ph, const T* rho, const T*
   if (m->nHC > 0)
     DG_RUN(m, K_HANG_GATHER, st, k_hang_gather<T, DIM, N, 1><<<grid_for(m->nHC * CS::NFP, 128), 128, 0, st>>>(ft, hbuf, slot, tb));
   DG_RUN(m, K_VOL_DIV, st, k_volume_div<T, DIM, N, DIV_VMULT><<<grid_for(m->E, CS::EPB), CS::THREADS, 0, st>>>(
-      w, plag, met_K<T>(m), met_invM<T>(m), slot, m->E, m->S, tb, ph, y, nullptr, nullptr, nullptr, nullptr));
+      w, plag, cell_geo<T>(m), slot, m->E, m->S, tb, ph, y, nullptr, nullptr, nullptr, nullptr));
   DG_LAUNCH_CHECK("schur vmult");
   return DG_OK;
 }
@@ -125,7 +125,7 @@ int Engine<T, DIM, N>::schur_rhs(dg_mesh* m, const ImplK& ph, const T* rho, cons
   if (m->nHC > 0)
     DG_RUN(m, K_HANG_GATHER, st, k_hang_gather<T, DIM, N, 1><<<grid_for(m->nHC * CS::NFP, 128), 128, 0, st>>>(ft, hbuf, slot, tb));
   DG_RUN(m, K_VOL_DIV, st, k_volume_div<T, DIM, N, DIV_RHS><<<grid_for(m->E, CS::EPB), CS::THREADS, 0, st>>>(
-      w, plag, met_K<T>(m), met_invM<T>(m), slot, m->E, m->S, tb, ph, rhs, ehat, rho, ulag, ustar));
+      w, plag, cell_geo<T>(m), slot, m->E, m->S, tb, ph, rhs, ehat, rho, ulag, ustar));
   DG_LAUNCH_CHECK("schur rhs");
   return DG_OK;
 }
@@ -152,7 +152,7 @@ int Engine<T, DIM, N>::recover(dg_mesh* m, const ImplK& ph, const T* rho, const 
   if (m->nHC > 0)
     DG_RUN(m, K_HANG_GATHER, st, k_hang_gather<T, DIM, N, DIM + 1><<<grid_for(m->nHC * CS::NFP, 128), 128, 0, st>>>(ft, hbuf, slot, tb));
   DG_RUN(m, K_VOL_GRAD, st, k_volume_grad<T, DIM, N, GRAD_RECOVER><<<grid_for(m->E, CS::EPB), CS::THREADS, 0, st>>>(
-      p, rho, met_K<T>(m), met_invM<T>(m), slot, m->E, m->S, tb, ph, nullptr, nullptr, ustar, u));
+      p, rho, cell_geo<T>(m), slot, m->E, m->S, tb, ph, nullptr, nullptr, ustar, u));
   DG_LAUNCH_CHECK("velocity recovery");
   return DG_OK;
 }
@@ -207,6 +207,11 @@ ImplK dg::impl_consts(const dg_phys* ph, double a_dt) {
   k.r2 = ph->variant == DG_R2;
   k.fcell = ph->f_cell;
   k.np = 1;
+  k.gamma_f = (float)ph->gamma;
+  k.g_f = (float)ph->g;
+  k.adt_f = (float)a_dt;
+  k.f_f = (float)ph->f;
+  k.fcell32 = nullptr;
   return k;
 }
 

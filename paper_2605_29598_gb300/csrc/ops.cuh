@@ -420,7 +420,100 @@ struct ImplK {
   int r2;
   const double* fcell;   // per-cell Coriolis parameter, or null for the uniform f
   int np;                // nodes per cell (to map a node to its cell)
+  // FP32 copies: FP32 kernels must issue no FP64 instruction (GB300 runs
+  // FP64 at 1/64 of the FP32 rate, so even a cast per node shows)
+  float gamma_f, g_f, adt_f, f_f;
+  const float* fcell32;
 };
+
+// kernel parameter in the kernel's precision
+template <typename T> __device__ __forceinline__ T kp(double d, float f);
+template <> __device__ __forceinline__ double kp<double>(double d, float) { return d; }
+template <> __device__ __forceinline__ float kp<float>(double, float f) { return f; }
+
+// beta = a_dt f of cell e (Section 3.1)
+template <typename T> __device__ __forceinline__ T beta_of(const ImplK& ph, int64_t e);
+template <> __device__ __forceinline__ double beta_of<double>(const ImplK& ph, int64_t e) {
+  return ph.a_dt * coriolis(ph.fcell, ph.f, e);
+}
+template <> __device__ __forceinline__ float beta_of<float>(const ImplK& ph, int64_t e) {
+  return ph.adt_f * (ph.fcell32 ? __ldg(ph.fcell32 + e) : ph.f_f);
+}
+
+// Per-node metric K_ab = w det(J) (J^{-1})_ab and 1/(w det J) of the
+// implicit-operator cell kernels: loaded from stored arrays, or (when `lv`
+// is set) recomputed from the cell's corner offsets relative to its first
+// corner.  The FP32 engine recomputes: that trades 4 (d^2 + 1) bytes per
+// node for about 30 d^2 FP32 flops, which GB300 has in excess.
+template <typename T>
+struct CellGeo {
+  const T* K;
+  const T* invM;
+  const T* lv;          // n_elem x 2^d x d corner offsets, or null
+  T x[MAX_N], w[MAX_N]; // Gauss-Legendre nodes and weights on [0, 1]
+};
+
+template <typename T, int DIM, int N>
+__device__ __forceinline__ void node_metric(const CellGeo<T>& g, int64_t e, int64_t node, int64_t Nn,
+                                            const int idx[3], T K[DIM][DIM], T& iM) {
+  if (g.lv == nullptr) {
+#pragma unroll
+    for (int a = 0; a < DIM; ++a)
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) K[a][b] = __ldg(g.K + (a * DIM + b) * Nn + node);
+    iM = __ldg(g.invM + node);
+    return;
+  }
+  const T* V = g.lv + e * (DIM << DIM);
+  T xi[3], wq = 1;
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    xi[a] = g.x[idx[a]];
+    wq *= g.w[idx[a]];
+  }
+  T J[DIM][DIM];   // J[b][c] = d x_b / d xi_c
+#pragma unroll
+  for (int b = 0; b < DIM; ++b)
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) J[b][c] = 0;
+#pragma unroll
+  for (int v = 1; v < (1 << DIM); ++v) {   // corner 0 is the origin
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) {
+      T wgt = 1;
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        const int bit = (v >> a) & 1;
+        if (a == c) wgt *= bit ? (T)1 : (T)-1;
+        else wgt *= bit ? xi[a] : (T)1 - xi[a];
+      }
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) J[b][c] += wgt * __ldg(V + v * DIM + b);
+    }
+  }
+  T det;
+  if (DIM == 2) {
+    K[0][0] = J[1][1];
+    K[0][1] = -J[0][1];
+    K[1][0] = -J[1][0];
+    K[1][1] = J[0][0];
+    det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+  } else {
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      const int c1 = (a + 1) % 3, c2 = (a + 2) % 3;
+      K[a][0] = J[1][c1] * J[2][c2] - J[2][c1] * J[1][c2];
+      K[a][1] = J[2][c1] * J[0][c2] - J[0][c1] * J[2][c2];
+      K[a][2] = J[0][c1] * J[1][c2] - J[1][c1] * J[0][c2];
+    }
+    det = J[0][0] * K[0][0] + J[1][0] * K[0][1] + J[2][0] * K[0][2];
+  }
+#pragma unroll
+  for (int a = 0; a < DIM; ++a)
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) K[a][b] *= wq;
+  iM = 1 / (wq * det);
+}
 
 // weak gradient G = M^{-1}[-int x grad(phi) + faces]; then
 //  VMULT  : w = rho^{-1} (I + beta J)^{-1} G (R2) or G / rho (R1) -> wv (DIM
@@ -428,8 +521,8 @@ struct ImplK {
 //  RECOVER: u = ustar - a_dt * w  (3 comps)
 template <typename T, int DIM, int N, int MODE>
 __global__ void __launch_bounds__(CellShape<DIM, N>::THREADS)
-k_volume_grad(const T* __restrict__ x, const T* __restrict__ rho, const T* __restrict__ Kg,
-              const T* __restrict__ invMg, const T* __restrict__ slot, int64_t E, int64_t S,
+k_volume_grad(const T* __restrict__ x, const T* __restrict__ rho, CellGeo<T> geo,
+              const T* __restrict__ slot, int64_t E, int64_t S,
               Tables<T> tb, ImplK ph, T* __restrict__ wv, T* __restrict__ y,
               const T* __restrict__ ustar, T* __restrict__ uout) {
   using CS = CellShape<DIM, N>;
@@ -443,11 +536,13 @@ k_volume_grad(const T* __restrict__ x, const T* __restrict__ rho, const T* __res
   int idx[3];
   node_index<DIM, N>(i, idx);
   T xv = active ? __ldg(x + node) : (T)0;
+  T K[DIM][DIM], iM = 0;
+  if (active) node_metric<T, DIM, N>(geo, e, node, Nn, idx, K, iM);
   T r[DIM + 1];
 #pragma unroll
   for (int b = 0; b < DIM; ++b) {
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) sm[le][a][i] = active ? -xv * __ldg(Kg + (a * DIM + b) * Nn + node) : (T)0;
+    for (int a = 0; a < DIM; ++a) sm[le][a][i] = active ? -xv * K[a][b] : (T)0;
     __syncthreads();
     r[b] = contract<T, DIM, N>(tb, sm[le], i, idx);
     __syncthreads();
@@ -455,14 +550,13 @@ k_volume_grad(const T* __restrict__ x, const T* __restrict__ rho, const T* __res
   r[DIM] = 0;
   if (!active) return;
   lift<T, DIM, N, DIM + 1>(tb, slot, S, e, idx, r);
-  const T iM = __ldg(invMg + node);
   T G[3] = {0, 0, 0};
 #pragma unroll
   for (int b = 0; b < DIM; ++b) G[comp_of<DIM>(b)] = iM * r[b];
   const T ir = 1 / __ldg(rho + node);
   T w[3];
   if (ph.r2) {
-    const T beta = (T)(ph.a_dt * coriolis(ph.fcell, ph.f, e));
+    const T beta = beta_of<T>(ph, e);
     const T d = 1 / (1 + beta * beta);
     w[0] = (G[0] + beta * G[1]) * d * ir;
     w[1] = (G[1] - beta * G[0]) * d * ir;
@@ -475,12 +569,12 @@ k_volume_grad(const T* __restrict__ x, const T* __restrict__ rho, const T* __res
   if (MODE == GRAD_VMULT) {
 #pragma unroll
     for (int b = 0; b < DIM; ++b) wv[b * Nn + node] = w[comp_of<DIM>(b)];
-    const T gm1 = (T)ph.gamma - 1, adt = (T)ph.a_dt;
+    const T gm1 = kp<T>(ph.gamma, ph.gamma_f) - 1, adt = kp<T>(ph.a_dt, ph.adt_f);
     T yv = xv + iM * r[DIM];
-    if (ph.r2) yv -= gm1 * adt * adt * (T)ph.g * G[2];
+    if (ph.r2) yv -= gm1 * adt * adt * kp<T>(ph.g, ph.g_f) * G[2];
     y[node] = yv;
   } else {
-    const T adt = (T)ph.a_dt;
+    const T adt = kp<T>(ph.a_dt, ph.adt_f);
 #pragma unroll
     for (int c = 0; c < 3; ++c) uout[c * Nn + node] = __ldg(ustar + c * Nn + node) - adt * w[c];
   }
@@ -495,8 +589,8 @@ enum DivMode { DIV_VMULT = 0, DIV_RHS = 1 };
 //         w3_z = ustar_z (R2) or u_lag_z (R1)
 template <typename T, int DIM, int N, int MODE>
 __global__ void __launch_bounds__(CellShape<DIM, N>::THREADS)
-k_volume_div(Fields<T> wv, const T* __restrict__ plag, const T* __restrict__ Kg,
-             const T* __restrict__ invMg, const T* __restrict__ slot, int64_t E, int64_t S,
+k_volume_div(Fields<T> wv, const T* __restrict__ plag, CellGeo<T> geo,
+             const T* __restrict__ slot, int64_t E, int64_t S,
              Tables<T> tb, ImplK ph, T* __restrict__ y, const T* __restrict__ ehat,
              const T* __restrict__ rho, const T* __restrict__ ulag, const T* __restrict__ ustar) {
   using CS = CellShape<DIM, N>;
@@ -509,9 +603,13 @@ k_volume_div(Fields<T> wv, const T* __restrict__ plag, const T* __restrict__ Kg,
   const int64_t node = active ? e * NP + i : 0;
   int idx[3];
   node_index<DIM, N>(i, idx);
-  const T gm1 = (T)ph.gamma - 1;
+  const T gam = kp<T>(ph.gamma, ph.gamma_f);
+  const T gm1 = gam - 1;
+  T iM = 0;
   if (active) {
-    T hr = (T)ph.gamma / gm1 * __ldg(plag + node);
+    T K[DIM][DIM];
+    node_metric<T, DIM, N>(geo, e, node, Nn, idx, K, iM);
+    T hr = gam / gm1 * __ldg(plag + node);
     T wl[DIM];
 #pragma unroll
     for (int b = 0; b < DIM; ++b) wl[b] = __ldg(wv.f[b] + node);
@@ -519,7 +617,7 @@ k_volume_div(Fields<T> wv, const T* __restrict__ plag, const T* __restrict__ Kg,
     for (int a = 0; a < DIM; ++a) {
       T v = 0;
 #pragma unroll
-      for (int b = 0; b < DIM; ++b) v += __ldg(Kg + (a * DIM + b) * Nn + node) * wl[b];
+      for (int b = 0; b < DIM; ++b) v += K[a][b] * wl[b];
       sm[le][a][i] = -hr * v;
     }
   } else {
@@ -531,8 +629,8 @@ k_volume_div(Fields<T> wv, const T* __restrict__ plag, const T* __restrict__ Kg,
   r[0] = contract<T, DIM, N>(tb, sm[le], i, idx);
   if (!active) return;
   lift<T, DIM, N, 1>(tb, slot, S, e, idx, r);
-  const T div = __ldg(invMg + node) * r[0];
-  const T adt = (T)ph.a_dt;
+  const T div = iM * r[0];
+  const T adt = kp<T>(ph.a_dt, ph.adt_f);
   if (MODE == DIV_VMULT) {
     y[node] -= gm1 * adt * adt * div;
   } else {
@@ -544,7 +642,7 @@ k_volume_div(Fields<T> wv, const T* __restrict__ plag, const T* __restrict__ Kg,
       u2 += uc * uc;
     }
     const T wz = ph.r2 ? __ldg(ustar + 2 * Nn + node) : __ldg(ulag + 2 * Nn + node);
-    y[node] = gm1 * (__ldg(ehat + node) - (T)0.5 * rh * u2 - adt * (div + (T)ph.g * rh * wz));
+    y[node] = gm1 * (__ldg(ehat + node) - (T)0.5 * rh * u2 - adt * (div + kp<T>(ph.g, ph.g_f) * rh * wz));
   }
 }
 

@@ -432,7 +432,7 @@ static int prepare32(dg_mesh* m, const ImplK& k, const double* rho, const double
   int rc;
   if ((rc = ensure_fp32_geometry(m)) != DG_OK) return rc;
   const int64_t n = m->N;
-  if ((rc = m->c32.ensure(sizeof(float) * 5 * n)) != DG_OK) return rc;
+  if ((rc = m->c32.ensure(sizeof(float) * (5 * n + m->E))) != DG_OK) return rc;
   if ((rc = m->ir32.ensure(sizeof(float) * 2 * n)) != DG_OK) return rc;
   float* c = m->c32.as<float>();
   const unsigned gb = grid_for(n, 256), gb3 = grid_for(3 * n, 256);
@@ -444,6 +444,12 @@ static int prepare32(dg_mesh* m, const ImplK& k, const double* rho, const double
   DG_DISPATCH(m, rc = (Engine<float, D_, N_>::prepare(m, k, c + n, c + 2 * n, penalty, st)));
   if (rc != DG_OK) return rc;
   *out = Schur32Ctx{m, k, c, c + n, penalty, m->ir32.as<float>(), m->ir32.as<float>() + n};
+  if (k.fcell) {   // FP32 copy of the per-cell Coriolis parameter after the coefficients
+    float* fc = c + 5 * n;
+    DG_RUN(m, K_VEC, st, k_d2f<<<grid_for(m->E, 256), 256, 0, st>>>(k.fcell, fc, m->E));
+    DG_LAUNCH_CHECK("fp32 coriolis cast");
+    out->k.fcell32 = fc;
+  }
   return DG_OK;
 }
 

@@ -21,6 +21,7 @@ def main():
     ap.add_argument("--cells", type=int, nargs=3, default=[60, 60, 20])
     ap.add_argument("--degree", type=int, default=3)
     ap.add_argument("--refine", action="store_true")
+    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
     args = ap.parse_args()
 
     import torch
@@ -38,7 +39,7 @@ def main():
     xyz = mesh.node_coords().cpu().numpy().T
     q = torch.tensor(I.stratified_state(xyz, **case["state_params"]), dtype=torch.float64,
                      device="cuda").contiguous()
-    phys = D.make_phys(f=case["f"])
+    phys = D.make_phys(f=case["f"], precision=args.precision)
     rho = q[0].contiguous()
     u = (q[1:4] / q[0]).contiguous()
     p = (0.4 * (q[4] - 0.5 * (q[1:4] * u).sum(0))).contiguous()
