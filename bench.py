@@ -333,6 +333,7 @@ def gpu_main(args):
     r = case["degree"]
     ctx = D.Context(dev)
     mesh = D.Mesh(ctx, mesh_h, r)
+    tiles = mesh.autotune("mixed")
     st = mesh.stats()
     N = st.n_nodes
     xyz = mesh.node_coords().cpu().numpy().T
@@ -530,7 +531,8 @@ def gpu_main(args):
                    "picard_rtol": STEP_OPTS["picard_rtol"], "gmres_rtol": STEP_OPTS["gmres_rtol"],
                    "gmres_restart": STEP_OPTS["gmres_restart"],
                    "l2": "state (%.0f MB) and Krylov basis exceed the 126 MB L2" % (state_bytes / 1e6),
-                   "parallelism": "replicas" if world > 1 else "single"},
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "tiles_fp64_fp32": tiles},
         "e2e": {"value": e2e_value, "unit": "GDoF-updates/s", "h2d_bytes_per_step": state_bytes,
                 "d2h_bytes_per_step": state_bytes},
         "roofline": roof,

@@ -102,8 +102,18 @@ typedef struct {
   int dim, degree, n1d, nodes_per_elem;
   int64_t n_elem, n_nodes, n_face_points, n_hang_points;
   int64_t workspace_bytes;   /* library-owned device memory held now */
+  int tile_fp64[3];          /* cells-per-block multipliers (1, 2, 4) of the */
+  int tile_fp32[3];          /* explicit, gradient and divergence cell kernels */
 } dg_mesh_stats;
 int dg_mesh_info(const dg_mesh* mesh, dg_mesh_stats* out);
+
+/* Tile autotuner (not in the paper): times the cell kernels of the
+ * explicit operator and of the Schur vmult with 1, 2 and 4 times the base
+ * number of cells per thread block on this mesh (synthetic coefficients,
+ * CUDA events) and keeps the fastest per kernel class, for FP64 and, when
+ * precision == DG_MIXED, for the FP32 kernels too.  Allocates temporary
+ * device memory; synchronises `stream`.  Results in dg_mesh_stats. */
+int dg_mesh_autotune(dg_ctx* ctx, dg_mesh* mesh, int precision, void* stream);
 
 /* Physical coordinates of all nodes: xyz[dim][cell][node] (device, FP64). */
 int dg_mesh_node_coords(dg_ctx* ctx, const dg_mesh* mesh, double* xyz, void* stream);

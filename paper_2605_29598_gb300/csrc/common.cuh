@@ -131,6 +131,9 @@ struct dg_mesh {
   dg::DBuf trh32, pcoef32, c32, ir32, irw;   // mixed precision: FP32 coefficients, IR vectors
   std::vector<double> host_h;
   dg::Profiler prof;
+  // cells-per-block multiplier of the cell kernels, per class (FP64, FP32)
+  int tile[dg::K_COUNT] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};
+  int tile32[dg::K_COUNT] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};
   int64_t workspace_bytes() const;
 };
 

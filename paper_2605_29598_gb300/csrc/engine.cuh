@@ -61,6 +61,18 @@ inline CellGeo<float> cell_geo<float>(const dg_mesh* m) {
 int schur_vmult_mixed(dg_mesh* m, const ImplK& k, const double* rho, const double* plag, const double* ulag,
                       int penalty, const double* x, double* y, cudaStream_t st);
 
+// Run the statement list with the tile multiplier M_ (cells per block =
+// M_ x the base count) chosen for kernel class `kid` of the mesh.
+template <typename T> inline int tile_of(const dg_mesh* m, int kid) {
+  return sizeof(T) == 8 ? m->tile[kid] : m->tile32[kid];
+}
+#define DG_TILE(m, kid, ...)                                         \
+  switch (tile_of<T>((m), kid)) {                                    \
+    case 2: { constexpr int M_ = 2; __VA_ARGS__; } break;            \
+    case 4: { constexpr int M_ = 4; __VA_ARGS__; } break;            \
+    default: { constexpr int M_ = 1; __VA_ARGS__; } break;           \
+  }
+
 // Run the statement list for the mesh's compile-time (dim, n): D_ and N_ are
 // constexpr inside it.
 #define DG_DISPATCH(m, ...)                                  \

@@ -125,6 +125,12 @@ int dg_ensemble_create(dg_ctx* ctx, const dg_mesh_desc* descs, const double* f_i
       return cuda_fail(e, "dg_ensemble_create");
     }
     for (int i : g.members) ens->inst[i].n_nodes = ens->inst[i].n_elem * g.mesh->Np;
+    // degree-specialised tile schedule of this group, picked by timing
+    rc = dg_mesh_autotune(ctx, g.mesh, DG_MIXED, nullptr);
+    if (rc != DG_OK) {
+      dg_ensemble_destroy(ens);
+      return rc;
+    }
   }
   *out = ens;
   return DG_OK;

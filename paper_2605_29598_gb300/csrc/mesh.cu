@@ -643,6 +643,11 @@ int dg_mesh_info(const dg_mesh* m, dg_mesh_stats* o) {
   o->n_face_points = m->nF;
   o->n_hang_points = m->nH;
   o->workspace_bytes = m->workspace_bytes();
+  const int kinds[3] = {K_VOL_EXPLICIT, K_VOL_GRAD, K_VOL_DIV};
+  for (int k = 0; k < 3; ++k) {
+    o->tile_fp64[k] = m->tile[kinds[k]];
+    o->tile_fp32[k] = m->tile32[kinds[k]];
+  }
   return DG_OK;
 }
 

@@ -27,8 +27,11 @@ int Engine<T, DIM, N>::explicit_rates(dg_mesh* m, const PhysK& ph, const T* q, T
   DG_RUN(m, K_FACE_EXPLICIT, st, k_face_explicit<T, DIM, N><<<grid_for(m->nF, 128), 128, 0, st>>>(ft, trc, slot, hbuf, tb, (T)ph.gamma));
   if (m->nHC > 0)
     DG_RUN(m, K_HANG_GATHER, st, k_hang_gather<T, DIM, N, 9><<<grid_for(m->nHC * CS::NFP, 128), 128, 0, st>>>(ft, hbuf, slot, tb));
-  DG_RUN(m, K_VOL_EXPLICIT, st, k_volume_explicit<T, DIM, N><<<grid_for(m->E, CS::EPB), CS::THREADS, 0, st>>>(
-      q, met_K<T>(m), met_invM<T>(m), slot, m->E, m->S, tb, ph, fns, fs));
+  DG_TILE(m, K_VOL_EXPLICIT,
+          DG_RUN(m, K_VOL_EXPLICIT, st,
+                 k_volume_explicit<T, DIM, N, M_><<<grid_for(m->E, CellShape<DIM, N, M_>::EPB),
+                                                    CellShape<DIM, N, M_>::THREADS, 0, st>>>(
+                     q, met_K<T>(m), met_invM<T>(m), slot, m->E, m->S, tb, ph, fns, fs)));
   DG_LAUNCH_CHECK("explicit operator");
   return DG_OK;
 }
@@ -83,8 +86,11 @@ int Engine<T, DIM, N>::vmult(dg_mesh* m, const ImplK& ph, const T* rho, const T*
                                                                 slot, hbuf, tb));
   if (m->nHC > 0)
     DG_RUN(m, K_HANG_GATHER, st, k_hang_gather<T, DIM, N, DIM + 1><<<grid_for(m->nHC * CS::NFP, 128), 128, 0, st>>>(ft, hbuf, slot, tb));
-  DG_RUN(m, K_VOL_GRAD, st, k_volume_grad<T, DIM, N, GRAD_VMULT><<<grid_for(m->E, CS::EPB), CS::THREADS, 0, st>>>(
-      x, rho, cell_geo<T>(m), slot, m->E, m->S, tb, ph, wv, y, nullptr, nullptr));
+  DG_TILE(m, K_VOL_GRAD,
+          DG_RUN(m, K_VOL_GRAD, st,
+                 k_volume_grad<T, DIM, N, GRAD_VMULT, M_><<<grid_for(m->E, CellShape<DIM, N, M_>::EPB),
+                                                          CellShape<DIM, N, M_>::THREADS, 0, st>>>(
+                     x, rho, cell_geo<T>(m), slot, m->E, m->S, tb, ph, wv, y, nullptr, nullptr)));
   Fields<T> w;
   for (int b = 0; b < DIM; ++b) {
     w.f[b] = wv + b * m->N;
@@ -94,8 +100,12 @@ int Engine<T, DIM, N>::vmult(dg_mesh* m, const ImplK& ph, const T* rho, const T*
   DG_RUN(m, K_FACE_DIV, st, k_face_div<T, DIM, N><<<grid_for(m->nF, 128), 128, 0, st>>>(ft, trc, buf_trh<T>(m).template as<T>(), slot, hbuf, tb));
   if (m->nHC > 0)
     DG_RUN(m, K_HANG_GATHER, st, k_hang_gather<T, DIM, N, 1><<<grid_for(m->nHC * CS::NFP, 128), 128, 0, st>>>(ft, hbuf, slot, tb));
-  DG_RUN(m, K_VOL_DIV, st, k_volume_div<T, DIM, N, DIV_VMULT><<<grid_for(m->E, CS::EPB), CS::THREADS, 0, st>>>(
-      w, plag, cell_geo<T>(m), slot, m->E, m->S, tb, ph, y, nullptr, nullptr, nullptr, nullptr));
+  DG_TILE(m, K_VOL_DIV,
+          DG_RUN(m, K_VOL_DIV, st,
+                 k_volume_div<T, DIM, N, DIV_VMULT, M_><<<grid_for(m->E, CellShape<DIM, N, M_>::EPB),
+                                                         CellShape<DIM, N, M_>::THREADS, 0, st>>>(
+                     w, plag, cell_geo<T>(m), slot, m->E, m->S, tb, ph, y, nullptr, nullptr, nullptr,
+                     nullptr)));
   DG_LAUNCH_CHECK("schur vmult");
   return DG_OK;
 }
@@ -124,8 +134,11 @@ int Engine<T, DIM, N>::schur_rhs(dg_mesh* m, const ImplK& ph, const T* rho, cons
   DG_RUN(m, K_FACE_DIV, st, k_face_div<T, DIM, N><<<grid_for(m->nF, 128), 128, 0, st>>>(ft, trc, buf_trh<T>(m).template as<T>(), slot, hbuf, tb));
   if (m->nHC > 0)
     DG_RUN(m, K_HANG_GATHER, st, k_hang_gather<T, DIM, N, 1><<<grid_for(m->nHC * CS::NFP, 128), 128, 0, st>>>(ft, hbuf, slot, tb));
-  DG_RUN(m, K_VOL_DIV, st, k_volume_div<T, DIM, N, DIV_RHS><<<grid_for(m->E, CS::EPB), CS::THREADS, 0, st>>>(
-      w, plag, cell_geo<T>(m), slot, m->E, m->S, tb, ph, rhs, ehat, rho, ulag, ustar));
+  DG_TILE(m, K_VOL_DIV,
+          DG_RUN(m, K_VOL_DIV, st,
+                 k_volume_div<T, DIM, N, DIV_RHS, M_><<<grid_for(m->E, CellShape<DIM, N, M_>::EPB),
+                                                       CellShape<DIM, N, M_>::THREADS, 0, st>>>(
+                     w, plag, cell_geo<T>(m), slot, m->E, m->S, tb, ph, rhs, ehat, rho, ulag, ustar)));
   DG_LAUNCH_CHECK("schur rhs");
   return DG_OK;
 }
@@ -151,8 +164,11 @@ int Engine<T, DIM, N>::recover(dg_mesh* m, const ImplK& ph, const T* rho, const 
   DG_RUN(m, K_FACE_GRAD, st, k_face_grad<T, DIM, N><<<grid_for(m->nF, 128), 128, 0, st>>>(ft, trc, nullptr, slot, hbuf, tb));
   if (m->nHC > 0)
     DG_RUN(m, K_HANG_GATHER, st, k_hang_gather<T, DIM, N, DIM + 1><<<grid_for(m->nHC * CS::NFP, 128), 128, 0, st>>>(ft, hbuf, slot, tb));
-  DG_RUN(m, K_VOL_GRAD, st, k_volume_grad<T, DIM, N, GRAD_RECOVER><<<grid_for(m->E, CS::EPB), CS::THREADS, 0, st>>>(
-      p, rho, cell_geo<T>(m), slot, m->E, m->S, tb, ph, nullptr, nullptr, ustar, u));
+  DG_TILE(m, K_VOL_GRAD,
+          DG_RUN(m, K_VOL_GRAD, st,
+                 k_volume_grad<T, DIM, N, GRAD_RECOVER, M_><<<grid_for(m->E, CellShape<DIM, N, M_>::EPB),
+                                                            CellShape<DIM, N, M_>::THREADS, 0, st>>>(
+                     p, rho, cell_geo<T>(m), slot, m->E, m->S, tb, ph, nullptr, nullptr, ustar, u)));
   DG_LAUNCH_CHECK("velocity recovery");
   return DG_OK;
 }

@@ -218,9 +218,10 @@ __global__ void k_face_explicit(FaceTopo ft, const T* __restrict__ trc, T* __res
 // ---------------------------------------------------------------------------
 // cell kernels (one thread per node, EPB cells per block)
 // ---------------------------------------------------------------------------
-template <int DIM, int N> struct CellShape {
+// M multiplies the cells per block (tile size picked by the autotuner).
+template <int DIM, int N, int M = 1> struct CellShape {
   static constexpr int NP = ipow(N, DIM);
-  static constexpr int EPB = NP >= 256 ? 1 : 256 / NP;
+  static constexpr int EPB = M * (NP >= 256 ? 1 : 256 / NP);
   static constexpr int THREADS = EPB * NP;
   static constexpr int NFP = ipow(N, DIM - 1);
   static constexpr int NF = 2 * DIM;
@@ -266,12 +267,12 @@ struct PhysK {
   const double* fcell = nullptr;   // per-cell Coriolis parameter, or null
 };
 
-template <typename T, int DIM, int N>
-__global__ void __launch_bounds__(CellShape<DIM, N>::THREADS)
+template <typename T, int DIM, int N, int M = 1>
+__global__ void __launch_bounds__(CellShape<DIM, N, M>::THREADS)
 k_volume_explicit(const T* __restrict__ q, const T* __restrict__ Kg, const T* __restrict__ invMg,
                   const T* __restrict__ slot, int64_t E, int64_t S, Tables<T> tb, PhysK ph,
                   T* __restrict__ fns, T* __restrict__ fs) {
-  using CS = CellShape<DIM, N>;
+  using CS = CellShape<DIM, N, M>;
   constexpr int NP = CS::NP, EPB = CS::EPB;
   __shared__ T sm[EPB][DIM][NP];
   const int le = threadIdx.x / NP, i = threadIdx.x % NP;
@@ -519,13 +520,13 @@ __device__ __forceinline__ void node_metric(const CellGeo<T>& g, int64_t e, int6
 //  VMULT  : w = rho^{-1} (I + beta J)^{-1} G (R2) or G / rho (R1) -> wv (DIM
 //           spatial comps); y = x + pen - (gamma-1) a_dt^2 g G_z (R2)
 //  RECOVER: u = ustar - a_dt * w  (3 comps)
-template <typename T, int DIM, int N, int MODE>
-__global__ void __launch_bounds__(CellShape<DIM, N>::THREADS)
+template <typename T, int DIM, int N, int MODE, int M = 1>
+__global__ void __launch_bounds__(CellShape<DIM, N, M>::THREADS)
 k_volume_grad(const T* __restrict__ x, const T* __restrict__ rho, CellGeo<T> geo,
               const T* __restrict__ slot, int64_t E, int64_t S,
               Tables<T> tb, ImplK ph, T* __restrict__ wv, T* __restrict__ y,
               const T* __restrict__ ustar, T* __restrict__ uout) {
-  using CS = CellShape<DIM, N>;
+  using CS = CellShape<DIM, N, M>;
   constexpr int NP = CS::NP, EPB = CS::EPB;
   __shared__ T sm[EPB][DIM][NP];
   const int le = threadIdx.x / NP, i = threadIdx.x % NP;
@@ -587,13 +588,13 @@ enum DivMode { DIV_VMULT = 0, DIV_RHS = 1 };
 //  VMULT: y -= (gamma-1) a_dt^2 Div
 //  RHS  : y = (gamma-1) [e_hat - rho |u_lag|^2 / 2 - a_dt (Div + g rho w3_z)],
 //         w3_z = ustar_z (R2) or u_lag_z (R1)
-template <typename T, int DIM, int N, int MODE>
-__global__ void __launch_bounds__(CellShape<DIM, N>::THREADS)
+template <typename T, int DIM, int N, int MODE, int M = 1>
+__global__ void __launch_bounds__(CellShape<DIM, N, M>::THREADS)
 k_volume_div(Fields<T> wv, const T* __restrict__ plag, CellGeo<T> geo,
              const T* __restrict__ slot, int64_t E, int64_t S,
              Tables<T> tb, ImplK ph, T* __restrict__ y, const T* __restrict__ ehat,
              const T* __restrict__ rho, const T* __restrict__ ulag, const T* __restrict__ ustar) {
-  using CS = CellShape<DIM, N>;
+  using CS = CellShape<DIM, N, M>;
   constexpr int NP = CS::NP, EPB = CS::EPB;
   __shared__ T sm[EPB][DIM][NP];
   const int le = threadIdx.x / NP, i = threadIdx.x % NP;

@@ -717,3 +717,99 @@ int imex_ark2_step(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* ph, double* 
 }
 
 }  // extern "C"
+
+namespace dg {
+
+__global__ void k_fill(double* __restrict__ a, int64_t n, double v) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) a[i] = v;
+}
+
+// Time the cell-kernel classes of one precision for each tile multiplier
+// and keep the fastest per class.
+static int tune_precision(dg_mesh* m, bool fp32, const double* q, const double* rho, const double* p,
+                          const double* u, double* x, double* y, double* fns, double* fs, cudaStream_t st) {
+  const int cand[3] = {1, 2, 4};
+  const int kinds[3] = {K_VOL_EXPLICIT, K_VOL_GRAD, K_VOL_DIV};
+  double best[3] = {1e300, 1e300, 1e300};
+  int pick[3] = {1, 1, 1};
+  dg_phys ph{1.4, 9.81, 1e-4, DG_R2, 1, fp32 ? DG_MIXED : DG_FP64, nullptr};
+  ImplK k = impl_consts(&ph, 1.0);
+  int* tiles = fp32 ? m->tile32 : m->tile;
+  int rc;
+  for (int c : cand) {
+    for (int kk : kinds) tiles[kk] = c;
+    SchurCtx sc{m, k, rho, p, 1};
+    Schur32Ctx sc32;
+    Vmult A{nullptr, nullptr};
+    if (fp32) {
+      if ((rc = prepare32(m, k, rho, p, u, 1, st, &sc32)) != DG_OK) return rc;
+      A = make_vmult32(&sc32);
+    } else {
+      if ((rc = prepare_rt(m, k, p, u, 1, st)) != DG_OK) return rc;
+      A = make_vmult(&sc);
+    }
+    for (int w = 0; w < 2; ++w) {   // warm-up
+      if ((rc = A(x, y, st)) != DG_OK) return rc;
+      if (!fp32 && (rc = explicit_rt(m, &ph, q, fns, fs, st)) != DG_OK) return rc;
+    }
+    uint32_t mask = 0;
+    for (int kk : kinds) mask |= 1u << kk;
+    m->prof.reset();
+    m->prof.time_mask = mask;
+    m->prof.on = true;
+    for (int rep = 0; rep < 4; ++rep) {
+      if ((rc = A(x, y, st)) != DG_OK) return rc;
+      if (!fp32 && (rc = explicit_rt(m, &ph, q, fns, fs, st)) != DG_OK) return rc;
+    }
+    dg_kernel_stat stats[K_COUNT];
+    int nst = 0;
+    if ((rc = dg_profile_end(m, stats, K_COUNT, &nst)) != DG_OK) return rc;
+    for (int j = 0; j < 3; ++j) {
+      const dg_kernel_stat& s = stats[kinds[j]];
+      if (s.timed_launches == 0) continue;
+      const double t = s.total_ms / (double)s.timed_launches;
+      if (t < best[j]) {
+        best[j] = t;
+        pick[j] = c;
+      }
+    }
+  }
+  for (int j = 0; j < 3; ++j) tiles[kinds[j]] = pick[j];
+  return DG_OK;
+}
+
+}  // namespace dg
+
+extern "C" int dg_mesh_autotune(dg_ctx* ctx, dg_mesh* m, int precision, void* stream) {
+  if (!ctx || !m) {
+    set_error("dg_mesh_autotune: NULL argument");
+    return DG_ERR_ARG;
+  }
+  if (precision != DG_FP64 && precision != DG_MIXED) {
+    set_error("dg_mesh_autotune: precision must be DG_FP64 or DG_MIXED");
+    return DG_ERR_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = m->N;
+  double* buf = nullptr;
+  // q (5n), rho, p, u (3n), x, y, fns (5n), fs (4n)
+  DG_CUDA(cudaMalloc(&buf, sizeof(double) * 21 * n));
+  double *q = buf, *rho = q + 5 * n, *p = rho + n, *u = p + n, *x = u + 3 * n, *y = x + n, *fns = y + n,
+         *fs = fns + 5 * n;
+  const unsigned gb = grid_for(n, 256);
+  k_fill<<<gb, 256, 0, st>>>(q, n, 1.2);
+  k_fill<<<gb, 256, 0, st>>>(q + n, n, 12.0);
+  k_fill<<<gb, 256, 0, st>>>(q + 2 * n, 2 * n, 1.0);
+  k_fill<<<gb, 256, 0, st>>>(q + 4 * n, n, 2.5e5);
+  k_fill<<<gb, 256, 0, st>>>(rho, n, 1.2);
+  k_fill<<<gb, 256, 0, st>>>(p, n, 1.0e5);
+  k_fill<<<gb, 256, 0, st>>>(u, 3 * n, 10.0);
+  k_fill<<<gb, 256, 0, st>>>(x, n, 1.0);
+  int rc = cudaGetLastError() == cudaSuccess ? DG_OK : DG_ERR_CUDA;
+  if (rc == DG_OK) rc = tune_precision(m, false, q, rho, p, u, x, y, fns, fs, st);
+  if (rc == DG_OK && precision == DG_MIXED) rc = tune_precision(m, true, q, rho, p, u, x, y, fns, fs, st);
+  cudaStreamSynchronize(st);
+  cudaFree(buf);
+  return rc;
+}

@@ -41,7 +41,8 @@ class MeshStats(C.Structure):
     _fields_ = [("dim", C.c_int), ("degree", C.c_int), ("n1d", C.c_int),
                 ("nodes_per_elem", C.c_int), ("n_elem", C.c_int64), ("n_nodes", C.c_int64),
                 ("n_face_points", C.c_int64), ("n_hang_points", C.c_int64),
-                ("workspace_bytes", C.c_int64)]
+                ("workspace_bytes", C.c_int64), ("tile_fp64", C.c_int * 3),
+                ("tile_fp32", C.c_int * 3)]
 
 
 class Phys(C.Structure):
@@ -117,6 +118,7 @@ EXPORTS["dg_ensemble_set_state"] = (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C
 EXPORTS["dg_ensemble_get_state"] = (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p])
 EXPORTS["dg_ensemble_step"] = (C.c_int, [C.c_void_p, C.POINTER(Phys), C.POINTER(C.c_double),
                                          C.POINTER(StepOpts), C.POINTER(StepInfo), C.c_void_p])
+EXPORTS["dg_mesh_autotune"] = (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p])
 EXPORTS["dg_profile_begin"] = (C.c_int, [C.c_void_p, C.c_uint32])
 EXPORTS["dg_profile_end"] = (C.c_int, [C.c_void_p, C.POINTER(KernelStat), C.c_int,
                                        C.POINTER(C.c_int)])
@@ -228,6 +230,14 @@ class Mesh:
         self.n_elem = st.n_elem
         self.N = st.n_nodes
         self.Np = st.nodes_per_elem
+
+    def autotune(self, precision="mixed", stream=None):
+        """Pick the cells-per-block multiplier of each cell kernel by timing."""
+        prec = DG_MIXED if precision == "mixed" else DG_FP64
+        _check(self.lib.dg_mesh_autotune(self.ctx.h, self.h, prec, _stream(stream)),
+               "dg_mesh_autotune")
+        s = self.stats()
+        return list(s.tile_fp64), list(s.tile_fp32)
 
     def stats(self) -> MeshStats:
         s = MeshStats()

@@ -225,3 +225,20 @@ def test_mesh_validation_errors(D, ctx):
         D.Mesh(ctx, I.Mesh(dim=2, vertices=flipped, int_faces=mesh.int_faces,
                            hang_faces=mesh.hang_faces, bdry_faces=mesh.bdry_faces), 2)
     assert ei.value.status == -1
+
+
+@pytest.mark.parametrize("name", ["2d_r2_nc", "3d_r3_hill_nc"])
+def test_autotuned_tiles_keep_parity(D, ctx, name):
+    """Every tile multiplier the autotuner can pick gives the same results."""
+    mesh, disc, gm, q = make_case(D, ctx, name, seed=7)
+    t64, t32 = gm.autotune("mixed")
+    assert all(t in (1, 2, 4) for t in t64 + t32)
+    Fns, Fs = O.explicit_rates(disc, q, O.Phys(f=1e-4))
+    fns, fs = gm.apply_explicit(D.make_phys(f=1e-4), to_dev(q.reshape(5, -1)))
+    assert relerr(from_dev(fns, Fns.shape), Fns) < 1e-11
+    cf = stage(disc, q, adt=3.0)
+    ref = O.schur_apply(disc, cf, O.Phys(f=1e-4), cf.p_lag)
+    keep, dcf = dev_coeffs(D, cf)
+    y = from_dev(gm.apply_implicit(D.make_phys(f=1e-4), dcf, to_dev(cf.p_lag.reshape(-1))),
+                 ref.shape)
+    assert relerr(y, ref) < 1e-11
