@@ -129,6 +129,7 @@ struct dg_mesh {
   // workspace
   dg::DBuf trc, slot, hbuf, trh, pcoef, wv, gm_V, gm_work, red, st, fns, fs;
   dg::DBuf trh32, pcoef32, c32, ir32, irw;   // mixed precision: FP32 coefficients, IR vectors
+  dg::DBuf irho, irho32;                      // 1/rho of the frozen stage density
   std::vector<double> host_h;
   dg::Profiler prof;
   // cells-per-block multiplier of the cell kernels, per class (FP64, FP32)

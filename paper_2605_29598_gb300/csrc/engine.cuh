@@ -8,7 +8,8 @@ namespace dg {
 template <typename T, int DIM, int N>
 struct Engine {
   static int explicit_rates(dg_mesh* m, const PhysK& ph, const T* q, T* fns, T* fs, cudaStream_t st);
-  static int prepare(dg_mesh* m, const ImplK& ph, const T* plag, const T* ulag, int penalty, cudaStream_t st);
+  static int prepare(dg_mesh* m, const ImplK& ph, const T* rho, const T* plag, const T* ulag, int penalty,
+                     cudaStream_t st);
   static int vmult(dg_mesh* m, const ImplK& ph, const T* rho, const T* plag, int penalty, const T* x, T* y,
                    cudaStream_t st);
   static int schur_rhs(dg_mesh* m, const ImplK& ph, const T* rho, const T* plag, const T* ulag, const T* mhat,
@@ -29,6 +30,7 @@ template <> inline const double* met_invM<double>(const dg_mesh* m) { return m->
 template <> inline const float* met_invM<float>(const dg_mesh* m) { return m->invM32; }
 template <typename T> inline DBuf& buf_trh(dg_mesh* m) { return sizeof(T) == 8 ? m->trh : m->trh32; }
 template <typename T> inline DBuf& buf_pcoef(dg_mesh* m) { return sizeof(T) == 8 ? m->pcoef : m->pcoef32; }
+template <typename T> inline DBuf& buf_irho(dg_mesh* m) { return sizeof(T) == 8 ? m->irho : m->irho32; }
 int ensure_fp32_geometry(dg_mesh* m);
 
 // Metric source of the implicit cell kernels: FP64 loads the stored

@@ -39,7 +39,7 @@ int Engine<T, DIM, N>::explicit_rates(dg_mesh* m, const PhysK& ph, const T* q, T
 // per-Picard-iteration coefficients: h rho traces and the implicit Rusanov
 // lambda coefficient at face points
 template <typename T, int DIM, int N>
-int Engine<T, DIM, N>::prepare(dg_mesh* m, const ImplK& ph, const T* plag, const T* ulag, int penalty,
+int Engine<T, DIM, N>::prepare(dg_mesh* m, const ImplK& ph, const T* rho, const T* plag, const T* ulag, int penalty,
                                cudaStream_t st) {
   int rc;
   if ((rc = m->trc.ensure(sizeof(T) * 5 * m->S)) != DG_OK) return rc;
@@ -48,8 +48,10 @@ int Engine<T, DIM, N>::prepare(dg_mesh* m, const ImplK& ph, const T* plag, const
   if ((rc = buf_trh<T>(m).ensure(sizeof(T) * m->S)) != DG_OK) return rc;
   if ((rc = buf_pcoef<T>(m).ensure(sizeof(T) * (m->nF > 0 ? m->nF : 1))) != DG_OK) return rc;
   if ((rc = m->wv.ensure(sizeof(T) * 6 * m->N)) != DG_OK) return rc;
+  if ((rc = buf_irho<T>(m).ensure(sizeof(T) * m->N)) != DG_OK) return rc;
   Tables<T> tb = cast_tables<T>(m->tab.t);
   FaceTopo ft = topo(m);
+  DG_RUN(m, K_VEC, st, k_recip<T><<<grid_for(m->N, 256), 256, 0, st>>>(rho, buf_irho<T>(m).template as<T>(), m->N));
   Fields<T> in;
   in.f[0] = plag;
   in.scale[0] = (T)(ph.gamma / (ph.gamma - 1.0));
@@ -90,7 +92,7 @@ int Engine<T, DIM, N>::vmult(dg_mesh* m, const ImplK& ph, const T* rho, const T*
           DG_RUN(m, K_VOL_GRAD, st,
                  k_volume_grad<T, DIM, N, GRAD_VMULT, M_><<<grid_for(m->E, CellShape<DIM, N, M_>::EPB),
                                                           CellShape<DIM, N, M_>::THREADS, 0, st>>>(
-                     x, rho, cell_geo<T>(m), slot, m->E, m->S, tb, ph, wv, y, nullptr, nullptr)));
+                     x, buf_irho<T>(m).template as<T>(), cell_geo<T>(m), slot, m->E, m->S, tb, ph, wv, y, nullptr, nullptr)));
   Fields<T> w;
   for (int b = 0; b < DIM; ++b) {
     w.f[b] = wv + b * m->N;
@@ -168,7 +170,7 @@ int Engine<T, DIM, N>::recover(dg_mesh* m, const ImplK& ph, const T* rho, const 
           DG_RUN(m, K_VOL_GRAD, st,
                  k_volume_grad<T, DIM, N, GRAD_RECOVER, M_><<<grid_for(m->E, CellShape<DIM, N, M_>::EPB),
                                                             CellShape<DIM, N, M_>::THREADS, 0, st>>>(
-                     p, rho, cell_geo<T>(m), slot, m->E, m->S, tb, ph, nullptr, nullptr, ustar, u)));
+                     p, buf_irho<T>(m).template as<T>(), cell_geo<T>(m), slot, m->E, m->S, tb, ph, nullptr, nullptr, ustar, u)));
   DG_LAUNCH_CHECK("velocity recovery");
   return DG_OK;
 }
@@ -228,6 +230,11 @@ ImplK dg::impl_consts(const dg_phys* ph, double a_dt) {
   k.adt_f = (float)a_dt;
   k.f_f = (float)ph->f;
   k.fcell32 = nullptr;
+  const double beta = a_dt * ph->f;
+  k.dbeta = 1.0 / (1.0 + beta * beta);
+  k.cgrav = (ph->gamma - 1.0) * a_dt * a_dt * ph->g;
+  k.dbeta_f = (float)k.dbeta;
+  k.cgrav_f = (float)k.cgrav;
   return k;
 }
 
@@ -262,7 +269,7 @@ int dg_apply_implicit(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* ph, const
     return schur_vmult_mixed(m, k, cf->rho, cf->p_lag, cf->u_lag, ph->penalty, x, y, st);
   DG_DISPATCH(m, {
     using EN = Engine<double, D_, N_>;
-    if ((rc = EN::prepare(m, k, cf->p_lag, cf->u_lag, ph->penalty, st)) != DG_OK) return rc;
+    if ((rc = EN::prepare(m, k, cf->rho, cf->p_lag, cf->u_lag, ph->penalty, st)) != DG_OK) return rc;
     return EN::vmult(m, k, cf->rho, cf->p_lag, ph->penalty, x, y, st);
   });
   return DG_ERR_UNSUPPORTED;
@@ -281,7 +288,7 @@ int dg_schur_rhs(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* ph, const dg_i
   cudaStream_t st = (cudaStream_t)stream;
   DG_DISPATCH(m, {
     using EN = Engine<double, D_, N_>;
-    if ((rc = EN::prepare(m, k, cf->p_lag, cf->u_lag, 0, st)) != DG_OK) return rc;
+    if ((rc = EN::prepare(m, k, cf->rho, cf->p_lag, cf->u_lag, 0, st)) != DG_OK) return rc;
     return EN::schur_rhs(m, k, cf->rho, cf->p_lag, cf->u_lag, mhat, ehat, rhs, st);
   });
   return DG_ERR_UNSUPPORTED;
@@ -300,7 +307,7 @@ int dg_recover_velocity(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* ph, con
   cudaStream_t st = (cudaStream_t)stream;
   DG_DISPATCH(m, {
     using EN = Engine<double, D_, N_>;
-    if ((rc = EN::prepare(m, k, cf->p_lag ? cf->p_lag : p, cf->u_lag, 0, st)) != DG_OK) return rc;
+    if ((rc = EN::prepare(m, k, cf->rho, cf->p_lag ? cf->p_lag : p, cf->u_lag, 0, st)) != DG_OK) return rc;
     return EN::recover(m, k, cf->rho, cf->u_lag, mhat, p, u, st);
   });
   return DG_ERR_UNSUPPORTED;

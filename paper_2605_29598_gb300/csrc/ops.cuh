@@ -425,7 +425,17 @@ struct ImplK {
   // FP64 at 1/64 of the FP32 rate, so even a cast per node shows)
   float gamma_f, g_f, adt_f, f_f;
   const float* fcell32;
+  // host-folded constants: 1/(1 + beta^2) for a uniform f, (gamma-1) a_dt^2 g
+  double dbeta, cgrav;
+  float dbeta_f, cgrav_f;
 };
+
+// 1/rho of the frozen stage density (read by the gradient cell kernel)
+template <typename T>
+__global__ void k_recip(const T* __restrict__ a, T* __restrict__ b, int64_t n) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (T)1 / a[i];
+}
 
 // kernel parameter in the kernel's precision
 template <typename T> __device__ __forceinline__ T kp(double d, float f);
@@ -522,7 +532,7 @@ __device__ __forceinline__ void node_metric(const CellGeo<T>& g, int64_t e, int6
 //  RECOVER: u = ustar - a_dt * w  (3 comps)
 template <typename T, int DIM, int N, int MODE, int M = 1>
 __global__ void __launch_bounds__(CellShape<DIM, N, M>::THREADS)
-k_volume_grad(const T* __restrict__ x, const T* __restrict__ rho, CellGeo<T> geo,
+k_volume_grad(const T* __restrict__ x, const T* __restrict__ irho, CellGeo<T> geo,
               const T* __restrict__ slot, int64_t E, int64_t S,
               Tables<T> tb, ImplK ph, T* __restrict__ wv, T* __restrict__ y,
               const T* __restrict__ ustar, T* __restrict__ uout) {
@@ -554,11 +564,11 @@ k_volume_grad(const T* __restrict__ x, const T* __restrict__ rho, CellGeo<T> geo
   T G[3] = {0, 0, 0};
 #pragma unroll
   for (int b = 0; b < DIM; ++b) G[comp_of<DIM>(b)] = iM * r[b];
-  const T ir = 1 / __ldg(rho + node);
+  const T ir = __ldg(irho + node);
   T w[3];
   if (ph.r2) {
     const T beta = beta_of<T>(ph, e);
-    const T d = 1 / (1 + beta * beta);
+    const T d = (ph.fcell || ph.fcell32) ? (T)1 / (1 + beta * beta) : kp<T>(ph.dbeta, ph.dbeta_f);
     w[0] = (G[0] + beta * G[1]) * d * ir;
     w[1] = (G[1] - beta * G[0]) * d * ir;
     w[2] = G[2] * ir;
@@ -570,9 +580,8 @@ k_volume_grad(const T* __restrict__ x, const T* __restrict__ rho, CellGeo<T> geo
   if (MODE == GRAD_VMULT) {
 #pragma unroll
     for (int b = 0; b < DIM; ++b) wv[b * Nn + node] = w[comp_of<DIM>(b)];
-    const T gm1 = kp<T>(ph.gamma, ph.gamma_f) - 1, adt = kp<T>(ph.a_dt, ph.adt_f);
     T yv = xv + iM * r[DIM];
-    if (ph.r2) yv -= gm1 * adt * adt * kp<T>(ph.g, ph.g_f) * G[2];
+    if (ph.r2) yv -= kp<T>(ph.cgrav, ph.cgrav_f) * G[2];
     y[node] = yv;
   } else {
     const T adt = kp<T>(ph.a_dt, ph.adt_f);

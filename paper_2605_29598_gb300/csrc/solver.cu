@@ -441,7 +441,7 @@ static int prepare32(dg_mesh* m, const ImplK& k, const double* rho, const double
   DG_RUN(m, K_VEC, st, k_d2f<<<gb3, 256, 0, st>>>(ulag, c + 2 * n, 3 * n));
   DG_LAUNCH_CHECK("fp32 coefficient casts");
   rc = DG_ERR_UNSUPPORTED;
-  DG_DISPATCH(m, rc = (Engine<float, D_, N_>::prepare(m, k, c + n, c + 2 * n, penalty, st)));
+  DG_DISPATCH(m, rc = (Engine<float, D_, N_>::prepare(m, k, c, c + n, c + 2 * n, penalty, st)));
   if (rc != DG_OK) return rc;
   *out = Schur32Ctx{m, k, c, c + n, penalty, m->ir32.as<float>(), m->ir32.as<float>() + n};
   if (k.fcell) {   // FP32 copy of the per-cell Coriolis parameter after the coefficients
@@ -529,9 +529,10 @@ static int gmres_ir(dg_mesh* m, const Vmult& A64, const Vmult& A32, const double
   return DG_OK;
 }
 
-static int prepare_rt(dg_mesh* m, const ImplK& k, const double* plag, const double* ulag, int penalty,
+static int prepare_rt(dg_mesh* m, const ImplK& k, const double* rho, const double* plag, const double* ulag,
+                      int penalty,
                       cudaStream_t st) {
-  DG_DISPATCH(m, return (Engine<double, D_, N_>::prepare(m, k, plag, ulag, penalty, st)));
+  DG_DISPATCH(m, return (Engine<double, D_, N_>::prepare(m, k, rho, plag, ulag, penalty, st)));
   return DG_ERR_UNSUPPORTED;
 }
 
@@ -582,7 +583,7 @@ int dg_gmres_solve(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* ph, const dg
   dg_mesh* m = const_cast<dg_mesh*>(mesh);
   cudaStream_t st = (cudaStream_t)stream;
   ImplK k = impl_consts(ph, cf->a_dt);
-  if ((rc = prepare_rt(m, k, cf->p_lag, cf->u_lag, ph->penalty, st)) != DG_OK) return rc;
+  if ((rc = prepare_rt(m, k, cf->rho, cf->p_lag, cf->u_lag, ph->penalty, st)) != DG_OK) return rc;
   SchurCtx sc{m, k, cf->rho, cf->p_lag, ph->penalty};
   Vmult A = make_vmult(&sc);
   if (!A.fn) return DG_ERR_UNSUPPORTED;
@@ -656,7 +657,7 @@ int imex_ark2_step(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* ph, double* 
     const int kmax = opts->picard_fixed > 0 ? opts->picard_fixed : opts->picard_maxit;
     int kk = 0;
     for (; kk < kmax; ++kk) {
-      if ((rc = prepare_rt(m, k, p, u, ph->penalty, st)) != DG_OK) return rc;
+      if ((rc = prepare_rt(m, k, rho, p, u, ph->penalty, st)) != DG_OK) return rc;
       if ((rc = rhs_rt(m, k, rho, p, u, mhat, ehat, rhs, st)) != DG_OK) return rc;
       DG_CUDA(cudaMemcpyAsync(pnew, p, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
       SchurCtx schur{m, k, rho, p, ph->penalty};
@@ -746,7 +747,7 @@ static int tune_precision(dg_mesh* m, bool fp32, const double* q, const double* 
       if ((rc = prepare32(m, k, rho, p, u, 1, st, &sc32)) != DG_OK) return rc;
       A = make_vmult32(&sc32);
     } else {
-      if ((rc = prepare_rt(m, k, p, u, 1, st)) != DG_OK) return rc;
+      if ((rc = prepare_rt(m, k, rho, p, u, 1, st)) != DG_OK) return rc;
       A = make_vmult(&sc);
     }
     for (int w = 0; w < 2; ++w) {   // warm-up
