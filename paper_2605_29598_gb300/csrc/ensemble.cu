@@ -8,6 +8,8 @@
 // whose stopping tests use norms over the group).
 #include <cmath>
 #include <map>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "engine.cuh"
@@ -20,7 +22,10 @@ struct dg_ensemble {
     double* f_cell = nullptr;     // device, one per merged cell
     double* q = nullptr;          // device, 5 x N merged state
     std::vector<int> members;     // instance ids
+    cudaStream_t stream = nullptr;  // groups step concurrently, one stream each
+    cudaEvent_t done = nullptr;
   };
+  cudaEvent_t start = nullptr;
   std::vector<Group> groups;
   struct Inst {
     int group = -1;
@@ -39,7 +44,10 @@ void dg_ensemble_destroy(dg_ensemble* e) {
     dg_mesh_destroy(g.mesh);
     cudaFree(g.f_cell);
     cudaFree(g.q);
+    if (g.stream) cudaStreamDestroy(g.stream);
+    if (g.done) cudaEventDestroy(g.done);
   }
+  if (e->start) cudaEventDestroy(e->start);
   delete e;
 }
 
@@ -120,6 +128,8 @@ int dg_ensemble_create(dg_ctx* ctx, const dg_mesh_desc* descs, const double* f_i
     if (e == cudaSuccess) e = cudaMemcpy(g.f_cell, fc.data(), sizeof(double) * off, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&g.q, sizeof(double) * 5 * g.mesh->N);
     if (e == cudaSuccess) e = cudaMemset(g.q, 0, sizeof(double) * 5 * g.mesh->N);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming);
     if (e != cudaSuccess) {
       dg_ensemble_destroy(ens);
       return cuda_fail(e, "dg_ensemble_create");
@@ -130,6 +140,13 @@ int dg_ensemble_create(dg_ctx* ctx, const dg_mesh_desc* descs, const double* f_i
     if (rc != DG_OK) {
       dg_ensemble_destroy(ens);
       return rc;
+    }
+  }
+  {
+    cudaError_t e = cudaEventCreateWithFlags(&ens->start, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      dg_ensemble_destroy(ens);
+      return cuda_fail(e, "dg_ensemble_create");
     }
   }
   *out = ens;
@@ -189,19 +206,49 @@ int dg_ensemble_step(dg_ensemble* e, const dg_phys* ph, const double* dt_inst, c
     set_error("dg_ensemble_step: NULL argument");
     return DG_ERR_ARG;
   }
-  dg_step_info total{};
-  for (auto& g : e->groups) {
-    const double dt = dt_inst[g.members[0]];
+  for (auto& g : e->groups)
     for (int i : g.members)
-      if (dt_inst[i] != dt) {
+      if (dt_inst[i] != dt_inst[g.members[0]]) {
         set_error("dg_ensemble_step: instances %d and %d share (dim, degree) but not dt", g.members[0], i);
         return DG_ERR_ARG;
       }
-    dg_phys pg = *ph;
-    pg.f_cell = g.f_cell;
-    dg_step_info gi{};
-    int rc = imex_ark2_step(e->ctx, g.mesh, &pg, g.q, dt, opts, &gi, stream);
-    if (rc != DG_OK) return rc;
+  // Each group steps on its own stream from its own host thread, so groups
+  // overlap on the GPU (their GMRES loops synchronise only their stream).
+  // The caller's stream orders before and after all of them.
+  cudaStream_t caller = (cudaStream_t)stream;
+  DG_CUDA(cudaEventRecord(e->start, caller));
+  const size_t ng = e->groups.size();
+  std::vector<int> rcs(ng, DG_OK);
+  std::vector<dg_step_info> infos(ng);
+  std::vector<std::string> errs(ng);
+  std::vector<std::thread> workers;
+  const int device = e->ctx->device;
+  for (size_t k = 0; k < ng; ++k) {
+    workers.emplace_back([&, k] {
+      auto& g = e->groups[k];
+      cudaSetDevice(device);
+      cudaError_t ce = cudaStreamWaitEvent(g.stream, e->start, 0);
+      if (ce != cudaSuccess) {
+        rcs[k] = DG_ERR_CUDA;
+        errs[k] = cudaGetErrorString(ce);
+        return;
+      }
+      dg_phys pg = *ph;
+      pg.f_cell = g.f_cell;
+      rcs[k] = imex_ark2_step(e->ctx, g.mesh, &pg, g.q, dt_inst[g.members[0]], opts, &infos[k], g.stream);
+      if (rcs[k] != DG_OK) errs[k] = dg_last_error();
+      cudaEventRecord(g.done, g.stream);
+    });
+  }
+  for (auto& w : workers) w.join();
+  for (auto& g : e->groups) DG_CUDA(cudaStreamWaitEvent(caller, g.done, 0));
+  dg_step_info total{};
+  for (size_t k = 0; k < ng; ++k) {
+    if (rcs[k] != DG_OK) {
+      set_error("dg_ensemble_step: group %d: %s", (int)k, errs[k].c_str());
+      return rcs[k];
+    }
+    const dg_step_info& gi = infos[k];
     for (int l = 0; l < 3; ++l) total.picard_iters[l] = std::max(total.picard_iters[l], gi.picard_iters[l]);
     total.gmres_iters_total += gi.gmres_iters_total;
     total.max_relres = std::max(total.max_relres, gi.max_relres);
