@@ -242,3 +242,62 @@ def test_autotuned_tiles_keep_parity(D, ctx, name):
     y = from_dev(gm.apply_implicit(D.make_phys(f=1e-4), dcf, to_dev(cf.p_lag.reshape(-1))),
                  ref.shape)
     assert relerr(y, ref) < 1e-11
+
+
+@pytest.mark.parametrize("r", [1, 4])
+def test_degree_extremes_3d(D, ctx, r):
+    """Lowest and highest supported degree on a 3D 2:1 terrain mesh."""
+    mesh = I.box_mesh((3, 2, 2), (3e3, 2e3, 2e3), hill=dict(h0=150.0, a_c=1e3, xc=1.5e3, yc=1e3),
+                      refine_level=lambda c: 1 if c[0] < 1e3 else 0)
+    disc = O.Discretisation(mesh, r)
+    gm = D.Mesh(ctx, mesh, r)
+    q = I.perturb(I.stratified_state(disc.node_points(), wind=(5.0, 1.0, 0.0)),
+                  np.random.default_rng(r), rel=1e-2)
+    Fns, Fs = O.explicit_rates(disc, q, O.Phys(f=1e-4))
+    fns, fs = gm.apply_explicit(D.make_phys(f=1e-4), to_dev(q.reshape(5, -1)))
+    assert relerr(from_dev(fns, Fns.shape), Fns) < 1e-11
+    cf = stage(disc, q, adt=2.0)
+    ref = O.schur_apply(disc, cf, O.Phys(f=1e-4), cf.p_lag)
+    keep, dcf = dev_coeffs(D, cf)
+    y = from_dev(gm.apply_implicit(D.make_phys(f=1e-4), dcf, to_dev(cf.p_lag.reshape(-1))), ref.shape)
+    assert relerr(y, ref) < 1e-11
+
+
+def test_fluid_at_rest_degenerate_lambda(D, ctx):
+    """u = 0 everywhere: every Rusanov coefficient lambda is zero."""
+    mesh, disc, gm, q = make_case(D, ctx, "2d_r2_nc", seed=8)
+    q = q.copy()
+    q[4] -= 0.5 * np.sum(q[1:4] ** 2, axis=0) / q[0]
+    q[1:4] = 0.0
+    Fns, Fs = O.explicit_rates(disc, q, O.Phys(f=1e-4))
+    fns, fs = gm.apply_explicit(D.make_phys(f=1e-4), to_dev(q.reshape(5, -1)))
+    assert relerr(from_dev(fs, (4,) + Fns.shape[1:]), Fs[1:]) < 1e-11
+    assert np.abs(from_dev(fns, Fns.shape)).max() < 1e-12 * np.abs(Fs).max()
+    cf = stage(disc, q, adt=3.0)
+    ref = O.schur_apply(disc, cf, O.Phys(f=1e-4), cf.p_lag * 1.001)
+    keep, dcf = dev_coeffs(D, cf)
+    y = from_dev(gm.apply_implicit(D.make_phys(f=1e-4), dcf, to_dev(cf.p_lag.reshape(-1) * 1.001)),
+                 ref.shape)
+    assert relerr(y, ref) < 1e-11
+
+
+def test_mesh_edge_cases_rejected(D, ctx):
+    """Empty mesh, a missing subface of a 2:1 face, out-of-range indices."""
+    import ctypes as C
+    lib = D.load()
+    v = np.zeros((0, 4, 2))
+    d = D.MeshDesc(dim=2, degree=2, node_set=0, n_elem=0,
+                   vertices=v.ctypes.data_as(C.POINTER(C.c_double)))
+    h = C.c_void_p()
+    assert lib.dg_mesh_create(ctx.h, C.byref(d), C.byref(h)) == -1
+    mesh = I.box_mesh((4, 3), (4.0, 3.0), refine_level=lambda c: 1 if c[0] < 1 else 0)
+    assert len(mesh.hang_faces) >= 2
+    for bad in (
+        I.Mesh(dim=2, vertices=mesh.vertices, int_faces=mesh.int_faces,
+               hang_faces=mesh.hang_faces[1:], bdry_faces=mesh.bdry_faces),
+        I.Mesh(dim=2, vertices=mesh.vertices,
+               int_faces=np.vstack([mesh.int_faces[:-1], [[0, 1, mesh.n_elem, 0]]]),
+               hang_faces=mesh.hang_faces, bdry_faces=mesh.bdry_faces)):
+        with pytest.raises(D.DGError) as ei:
+            D.Mesh(ctx, bad, 2)
+        assert ei.value.status == -1
