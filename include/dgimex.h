@@ -51,7 +51,7 @@ typedef enum {
 enum { DG_NODES_GL = 0, DG_NODES_GLL = 1 };
 enum { DG_BC_WALL = 1 };
 enum { DG_R1 = 1, DG_R2 = 2 };
-enum { DG_FP64 = 0, DG_MIXED = 1 };
+enum { DG_FP64 = 0, DG_MIXED = 1, DG_MIXED_EXPLICIT = 2 };
 
 typedef struct dg_ctx dg_ctx;
 typedef struct dg_mesh dg_mesh;
@@ -111,7 +111,7 @@ int dg_mesh_info(const dg_mesh* mesh, dg_mesh_stats* out);
  * explicit operator and of the Schur vmult with 1, 2 and 4 times the base
  * number of cells per thread block on this mesh (synthetic coefficients,
  * CUDA events) and keeps the fastest per kernel class, for FP64 and, when
- * precision == DG_MIXED, for the FP32 kernels too.  Allocates temporary
+ * precision is DG_MIXED or DG_MIXED_EXPLICIT, for the FP32 kernels too.  Allocates temporary
  * device memory; synchronises `stream`.  Results in dg_mesh_stats. */
 int dg_mesh_autotune(dg_ctx* ctx, dg_mesh* mesh, int precision, void* stream);
 
@@ -126,12 +126,15 @@ typedef struct {
   double gamma, g, f;
   int variant;
   int penalty;
-  int precision;             /* DG_FP64, or DG_MIXED: Schur vmults inside the
+  int precision;             /* DG_FP64; DG_MIXED: Schur vmults inside the
                                 Krylov solves run in FP32 (FP32 accumulation)
                                 under FP64 iterative refinement; the outer
                                 residual, orthogonalisation, reductions,
                                 Schur right-hand side, velocity recovery and
-                                explicit operator stay FP64 */
+                                explicit operator stay FP64;
+                                DG_MIXED_EXPLICIT: DG_MIXED plus the explicit
+                                operator in FP32 on perturbations (see
+                                dg_mesh_set_background and imex_ark2_step) */
   const double* f_cell;      /* optional device array, one Coriolis parameter
                                 per cell (NULL: f everywhere); lets one mesh
                                 carry several independent instances */
@@ -149,6 +152,28 @@ typedef struct {
  */
 int dg_apply_explicit(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* phys,
                       const double* q, double* f_ns, double* f_s, void* stream);
+
+/*
+ * Background for the FP32 explicit operator (DG_MIXED_EXPLICIT).  q_bg
+ * (device, 5 x N, FP64, e.g. the balanced hydrostatic state) is copied; its
+ * rates F(q_bg) are computed once in FP64 (again whenever gamma, g, f or
+ * f_cell change).  Afterwards, with phys->precision == DG_MIXED_EXPLICIT,
+ * dg_apply_explicit and every stage of imex_ark2_step evaluate
+ * F(q) = F(q_bg) + [F(q) - F(q_bg)], the difference in FP32 from
+ * q' = q - q_bg (subtracted in FP64) with every nonlinear flux expanded
+ * about the background so that no background-sized term cancels, and the
+ * Rusanov term split as lambda/2 [q'] + (lambda - lambda_bg)/2 [q_bg] with
+ * the background jumps and lambda_bg taken from FP64.  The background stays
+ * until the mesh is destroyed.  Accuracy: F' to FP32 precision of F', but
+ * after whole steps the perturbation fields carry errors of 1e-6 to 1e-4
+ * relative L2 (the stiff explicit rates amplify the FP32 error of F').
+ * Without a background, imex_ark2_step under DG_MIXED_EXPLICIT computes the
+ * first-stage rates F(q^n) in FP64 and the later stages' rates as FP32
+ * increments about q^n, which keeps the FP32 error proportional to the
+ * change within one step; dg_apply_explicit then returns DG_ERR_ARG.
+ */
+int dg_mesh_set_background(dg_ctx* ctx, dg_mesh* mesh, const dg_phys* phys,
+                           const double* q_bg, void* stream);
 
 /* Coefficients frozen during one Picard iteration of stage l (device,
  * N each; u_lag 3 x N): rho^(n,l), p^(n,l,k), u^(n,l,k); a_dt = at_ll dt. */

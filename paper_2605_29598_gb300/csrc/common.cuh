@@ -130,6 +130,11 @@ struct dg_mesh {
   dg::DBuf trc, slot, hbuf, trh, pcoef, wv, gm_V, gm_work, red, st, fns, fs;
   dg::DBuf trh32, pcoef32, c32, ir32, irw;   // mixed precision: FP32 coefficients, IR vectors
   dg::DBuf irho, irho32;                      // 1/rho of the frozen stage density
+  // background of the perturbation-form explicit operator (mixed precision)
+  dg::DBuf bg, bg32, bgF, bgtr, bgjump, pert32;
+  bool bg_set = false;
+  double bg_gamma = 0, bg_g = 0, bg_f = 0;
+  const double* bg_fcell = nullptr;
   std::vector<double> host_h;
   dg::Profiler prof;
   // cells-per-block multiplier of the cell kernels, per class (FP64, FP32)

@@ -59,6 +59,14 @@ inline CellGeo<float> cell_geo<float>(const dg_mesh* m) {
   }
   return g;
 }
+// Explicit operator in perturbation form about the mesh's background (FP32
+// differences + FP64 background rates); requires m->bg_set.
+int explicit_mixed(dg_mesh* m, const PhysK& ph, const double* q, double* fns, double* fs, cudaStream_t st);
+// FP32 rates of q as increments about a reference state q0 whose FP64 rates
+// are f0: increment_begin prepares the face data of q0 (once per q0)
+int increment_begin(dg_mesh* m, double gamma, const double* q0, cudaStream_t st);
+int explicit_increment(dg_mesh* m, const PhysK& ph, const double* q, const double* q0, const double* f0_ns,
+                       const double* f0_s, double* fns, double* fs, cudaStream_t st);
 // FP32 Schur vmult (coefficients and vectors cast from / to FP64)
 int schur_vmult_mixed(dg_mesh* m, const ImplK& k, const double* rho, const double* plag, const double* ulag,
                       int penalty, const double* x, double* y, cudaStream_t st);

@@ -205,8 +205,8 @@ static int check_common(dg_ctx* ctx, const dg_mesh* m, const dg_phys* ph, const 
     set_error("%s: gamma must be > 1", who);
     return DG_ERR_ARG;
   }
-  if (ph->precision != DG_FP64 && ph->precision != DG_MIXED) {
-    set_error("%s: precision must be DG_FP64 or DG_MIXED", who);
+  if (ph->precision != DG_FP64 && ph->precision != DG_MIXED && ph->precision != DG_MIXED_EXPLICIT) {
+    set_error("%s: precision must be DG_FP64, DG_MIXED or DG_MIXED_EXPLICIT", who);
     return DG_ERR_ARG;
   }
   if (ph->variant != DG_R1 && ph->variant != DG_R2) {
@@ -250,6 +250,13 @@ int dg_apply_explicit(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* ph, const
   }
   PhysK k{ph->gamma, ph->g, ph->f, ph->f_cell};
   dg_mesh* m = const_cast<dg_mesh*>(mesh);
+  if (ph->precision == DG_MIXED_EXPLICIT) {
+    if (!m->bg_set) {
+      set_error("dg_apply_explicit: DG_MIXED_EXPLICIT needs a background (dg_mesh_set_background)");
+      return DG_ERR_ARG;
+    }
+    return explicit_mixed(m, k, q, fns, fs, (cudaStream_t)stream);
+  }
   DG_DISPATCH(m, return (Engine<double, D_, N_>::explicit_rates(m, k, q, fns, fs, (cudaStream_t)stream)));
   return DG_ERR_UNSUPPORTED;
 }
@@ -265,7 +272,7 @@ int dg_apply_implicit(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* ph, const
   dg_mesh* m = const_cast<dg_mesh*>(mesh);
   ImplK k = impl_consts(ph, cf->a_dt);
   cudaStream_t st = (cudaStream_t)stream;
-  if (ph->precision == DG_MIXED)
+  if (ph->precision != DG_FP64)
     return schur_vmult_mixed(m, k, cf->rho, cf->p_lag, cf->u_lag, ph->penalty, x, y, st);
   DG_DISPATCH(m, {
     using EN = Engine<double, D_, N_>;

@@ -538,6 +538,7 @@ static int prepare_rt(dg_mesh* m, const ImplK& k, const double* rho, const doubl
 
 static int explicit_rt(dg_mesh* m, const dg_phys* ph, const double* q, double* fns, double* fs, cudaStream_t st) {
   PhysK k{ph->gamma, ph->g, ph->f, ph->f_cell};
+  if (ph->precision == DG_MIXED_EXPLICIT && m->bg_set) return explicit_mixed(m, k, q, fns, fs, st);
   DG_DISPATCH(m, return (Engine<double, D_, N_>::explicit_rates(m, k, q, fns, fs, st)));
   return DG_ERR_UNSUPPORTED;
 }
@@ -559,8 +560,8 @@ static int check_phys(const dg_phys* ph, const char* who) {
     set_error("%s: invalid physics (gamma > 1, variant R1/R2)", who);
     return DG_ERR_ARG;
   }
-  if (ph->precision != DG_FP64 && ph->precision != DG_MIXED) {
-    set_error("%s: precision must be DG_FP64 or DG_MIXED", who);
+  if (ph->precision != DG_FP64 && ph->precision != DG_MIXED && ph->precision != DG_MIXED_EXPLICIT) {
+    set_error("%s: precision must be DG_FP64, DG_MIXED or DG_MIXED_EXPLICIT", who);
     return DG_ERR_ARG;
   }
   return DG_OK;
@@ -587,7 +588,7 @@ int dg_gmres_solve(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* ph, const dg
   SchurCtx sc{m, k, cf->rho, cf->p_lag, ph->penalty};
   Vmult A = make_vmult(&sc);
   if (!A.fn) return DG_ERR_UNSUPPORTED;
-  if (ph->precision == DG_MIXED) {
+  if (ph->precision != DG_FP64) {
     Schur32Ctx sc32;
     if ((rc = prepare32(m, k, cf->rho, cf->p_lag, cf->u_lag, ph->penalty, st, &sc32)) != DG_OK) return rc;
     Vmult A32 = make_vmult32(&sc32);
@@ -637,7 +638,13 @@ int imex_ark2_step(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* ph, double* 
   double* rhs = w + 18 * n;
   const unsigned gb = grid_for(n, 256);
   dg_step_info inf{};
+  // FP32 explicit operator without a background: the rates of the later
+  // stages are increments about the step's start state q, whose FP64 rates
+  // are those of the first stage
+  const bool incr = ph->precision == DG_MIXED_EXPLICIT && !m->bg_set;
+  const PhysK pk{ph->gamma, ph->g, ph->f, ph->f_cell};
   if ((rc = explicit_rt(m, ph, q, Fns[0], Fs[0], st)) != DG_OK) return rc;
+  if (incr && (rc = increment_begin(m, ph->gamma, q, st)) != DG_OK) return rc;
   const double* yprev = q;
   for (int l = 1; l <= 2; ++l) {
     const double adt = at[l][l] * dt;
@@ -663,7 +670,7 @@ int imex_ark2_step(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* ph, double* 
       SchurCtx schur{m, k, rho, p, ph->penalty};
       Vmult A = make_vmult(&schur);
       dg_gmres_info gi{};
-      if (ph->precision == DG_MIXED) {
+      if (ph->precision != DG_FP64) {
         Schur32Ctx sc32;
         if ((rc = prepare32(m, k, rho, p, u, ph->penalty, st, &sc32)) != DG_OK) return rc;
         Vmult A32 = make_vmult32(&sc32);
@@ -698,7 +705,11 @@ int imex_ark2_step(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* ph, double* 
     inf.picard_iters[l] = kk;
     DG_RUN(m, K_STAGE, st, k_stage_state<<<gb, 256, 0, st>>>(rho, u, p, n, ph->gamma, y));
     DG_LAUNCH_CHECK("stage state");
-    if ((rc = explicit_rt(m, ph, y, Fns[l], Fs[l], st)) != DG_OK) return rc;
+    if (incr)
+      rc = explicit_increment(m, pk, y, q, Fns[0], Fs[0], Fns[l], Fs[l], st);
+    else
+      rc = explicit_rt(m, ph, y, Fns[l], Fs[l], st);
+    if (rc != DG_OK) return rc;
     yprev = y;
     // the next stage reads y as its initial guess before overwriting it
   }
@@ -787,8 +798,8 @@ extern "C" int dg_mesh_autotune(dg_ctx* ctx, dg_mesh* m, int precision, void* st
     set_error("dg_mesh_autotune: NULL argument");
     return DG_ERR_ARG;
   }
-  if (precision != DG_FP64 && precision != DG_MIXED) {
-    set_error("dg_mesh_autotune: precision must be DG_FP64 or DG_MIXED");
+  if (precision != DG_FP64 && precision != DG_MIXED && precision != DG_MIXED_EXPLICIT) {
+    set_error("dg_mesh_autotune: precision must be DG_FP64, DG_MIXED or DG_MIXED_EXPLICIT");
     return DG_ERR_ARG;
   }
   cudaStream_t st = (cudaStream_t)stream;
@@ -809,7 +820,7 @@ extern "C" int dg_mesh_autotune(dg_ctx* ctx, dg_mesh* m, int precision, void* st
   k_fill<<<gb, 256, 0, st>>>(x, n, 1.0);
   int rc = cudaGetLastError() == cudaSuccess ? DG_OK : DG_ERR_CUDA;
   if (rc == DG_OK) rc = tune_precision(m, false, q, rho, p, u, x, y, fns, fs, st);
-  if (rc == DG_OK && precision == DG_MIXED) rc = tune_precision(m, true, q, rho, p, u, x, y, fns, fs, st);
+  if (rc == DG_OK && precision != DG_FP64) rc = tune_precision(m, true, q, rho, p, u, x, y, fns, fs, st);
   cudaStreamSynchronize(st);
   cudaFree(buf);
   return rc;

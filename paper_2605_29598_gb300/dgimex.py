@@ -20,7 +20,8 @@ from . import build as _build
 DG_OK = 0
 DG_NODES_GL, DG_NODES_GLL = 0, 1
 DG_R1, DG_R2 = 1, 2
-DG_FP64, DG_MIXED = 0, 1
+DG_FP64, DG_MIXED, DG_MIXED_EXPLICIT = 0, 1, 2
+PRECISIONS = {"fp64": DG_FP64, "mixed": DG_MIXED, "mixed_explicit": DG_MIXED_EXPLICIT}
 STATUS = {0: "DG_OK", -1: "DG_ERR_ARG", -2: "DG_ERR_UNSUPPORTED", -3: "DG_ERR_CUDA",
           -4: "DG_ERR_NOT_CONVERGED", -5: "DG_ERR_TIMEOUT", -6: "DG_ERR_NONFINITE",
           -7: "DG_ERR_OOM"}
@@ -119,6 +120,8 @@ EXPORTS["dg_ensemble_get_state"] = (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C
 EXPORTS["dg_ensemble_step"] = (C.c_int, [C.c_void_p, C.POINTER(Phys), C.POINTER(C.c_double),
                                          C.POINTER(StepOpts), C.POINTER(StepInfo), C.c_void_p])
 EXPORTS["dg_mesh_autotune"] = (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p])
+EXPORTS["dg_mesh_set_background"] = (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Phys), C.c_void_p,
+                                                C.c_void_p])
 EXPORTS["dg_profile_begin"] = (C.c_int, [C.c_void_p, C.c_uint32])
 EXPORTS["dg_profile_end"] = (C.c_int, [C.c_void_p, C.POINTER(KernelStat), C.c_int,
                                        C.POINTER(C.c_int)])
@@ -182,7 +185,7 @@ def _stream(stream):
 def make_phys(gamma=1.4, g=9.81, f=1e-4, variant="R2", penalty=True, precision="fp64"):
     return Phys(gamma=gamma, g=g, f=f, variant=DG_R2 if variant == "R2" else DG_R1,
                 penalty=1 if penalty else 0,
-                precision=DG_MIXED if precision == "mixed" else DG_FP64)
+                precision=PRECISIONS[precision])
 
 
 class Context:
@@ -231,9 +234,14 @@ class Mesh:
         self.N = st.n_nodes
         self.Np = st.nodes_per_elem
 
+    def set_background(self, phys, q_bg, stream=None):
+        """Background state for the perturbation-form (mixed) explicit operator."""
+        _check(self.lib.dg_mesh_set_background(self.ctx.h, self.h, C.byref(phys), _ptr(q_bg),
+                                               _stream(stream)), "dg_mesh_set_background")
+
     def autotune(self, precision="mixed", stream=None):
         """Pick the cells-per-block multiplier of each cell kernel by timing."""
-        prec = DG_MIXED if precision == "mixed" else DG_FP64
+        prec = PRECISIONS[precision]
         _check(self.lib.dg_mesh_autotune(self.ctx.h, self.h, prec, _stream(stream)),
                "dg_mesh_autotune")
         s = self.stats()
