@@ -245,6 +245,15 @@ typedef struct {
   double picard_rtol;
   int picard_maxit, picard_fixed;
   dg_gmres_opts gmres;
+  int graph;   /* 1: device-driven step (not in the paper): the Givens
+                  rotations and every stopping test run on the GPU, the loops
+                  are CUDA-graph while nodes, and the whole step is captured
+                  once per (mesh, q, dt, phys, opts) and replayed as one graph
+                  launch; the first call for a configuration also runs one
+                  host-driven step on a copy of q to size the workspace.  Same
+                  arithmetic as graph = 0 up to the rounding of the Givens
+                  updates.  Not available under dg_profile_begin
+                  (DG_ERR_UNSUPPORTED). */
 } dg_step_opts;
 typedef struct {
   int picard_iters[3];

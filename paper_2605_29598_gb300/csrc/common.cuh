@@ -132,6 +132,9 @@ struct dg_mesh {
   dg::DBuf irho, irho32;                      // 1/rho of the frozen stage density
   // background of the perturbation-form explicit operator (mixed precision)
   dg::DBuf bg, bg32, bgF, bgtr, bgjump, pert32;
+  // device-driven step (CUDA graph): solver state and fixed work vectors
+  dg::DBuf gstate, gwork;
+  struct StepGraph* graph = nullptr;   // cached executable graph of imex_ark2_step
   bool bg_set = false;
   double bg_gamma = 0, bg_g = 0, bg_f = 0;
   const double* bg_fcell = nullptr;
@@ -141,9 +144,20 @@ struct dg_mesh {
   int tile[dg::K_COUNT] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};
   int tile32[dg::K_COUNT] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};
   int64_t workspace_bytes() const;
+  // every workspace buffer, for accounting, release and graph capture checks
+  static constexpr int kBufs = 27;
+  void bufs(const dg::DBuf** out) const {
+    const dg::DBuf* b[kBufs] = {&trc, &slot, &hbuf, &trh, &pcoef, &wv, &gm_V, &gm_work, &red, &st,
+                                &fns, &fs, &trh32, &pcoef32, &c32, &ir32, &irw, &irho, &irho32,
+                                &bg, &bg32, &bgF, &bgtr, &bgjump, &pert32, &gstate, &gwork};
+    for (int i = 0; i < kBufs; ++i) out[i] = b[i];
+  }
 };
 
 namespace dg {
+
+// releases the cached step graph of a mesh (defined with the graph code)
+void graph_release(dg_mesh* m);
 
 // Arguments shared by the face kernels.
 struct FaceTopo {

@@ -321,9 +321,8 @@ static GeoArgs geo_args(const dg_mesh* m) {
 using namespace dg;
 
 int64_t dg_mesh::workspace_bytes() const {
-  const DBuf* b[] = {&trc, &slot, &hbuf, &trh, &pcoef, &wv, &gm_V, &gm_work, &red, &st, &fns, &fs,
-                     &trh32, &pcoef32, &c32, &ir32, &irw, &irho, &irho32,
-                     &bg, &bg32, &bgF, &bgtr, &bgjump, &pert32};
+  const DBuf* b[kBufs];
+  bufs(b);
   int64_t s = 0;
   if (K32) s += (int64_t)sizeof(float) * ((int64_t)dim * dim * N + N + (int64_t)(dim + 1) * (nF > 0 ? nF : 1));
   for (auto* x : b) s += (int64_t)x->bytes;
@@ -383,11 +382,10 @@ void dg_mesh_destroy(dg_mesh* m) {
   cudaFree(m->invM32);
   cudaFree(m->fgeo32);
   cudaFree(m->lv32);
-  DBuf* b[] = {&m->trc, &m->slot, &m->hbuf, &m->trh, &m->pcoef, &m->wv, &m->gm_V,
-               &m->gm_work, &m->red, &m->st, &m->fns, &m->fs, &m->trh32, &m->pcoef32,
-               &m->c32, &m->ir32, &m->irw, &m->irho, &m->irho32, &m->bg, &m->bg32,
-               &m->bgF, &m->bgtr, &m->bgjump, &m->pert32};
-  for (auto* x : b) x->release();
+  graph_release(m);
+  const DBuf* b[dg_mesh::kBufs];
+  m->bufs(b);
+  for (auto* x : b) const_cast<DBuf*>(x)->release();
   m->prof.release();
   delete m;
 }

@@ -3,12 +3,10 @@
 #include <cmath>
 #include <vector>
 
-#include "engine.cuh"
+#include "solver.cuh"
 
 namespace dg {
 
-constexpr int RED_BLOCKS = 1024;   // partial sums per reduction (fixed order)
-constexpr int MAX_RESTART = 64;
 
 // ---------------------------------------------------------------------------
 // vector kernels (FP64)
@@ -75,9 +73,6 @@ __global__ void k_reduce_partials(const double* __restrict__ partial, int nvec, 
   if (threadIdx.x == 0) out[k] = red[0];
 }
 
-struct Coefs {
-  double c[MAX_RESTART + 1];
-};
 
 // w += sum_k c_k V_k
 __global__ void k_multiaxpy(const double* __restrict__ V, int nvec, int64_t n, Coefs c, double* __restrict__ w) {
@@ -98,16 +93,9 @@ __global__ void k_scale(int64_t n, double a, double* __restrict__ x) {
   if (i < n) x[i] *= a;
 }
 
+
 // stage predictors: rho_l = rho^n + dt sum a F_NS,rho;
 // m_hat = m^n + dt sum (a F_NS,m + at F_S,m); e_hat likewise
-struct StageCoefs {
-  const double* fns[3];
-  const double* fs[3];
-  double a[3], at[3];
-  int nst;
-  double dt;
-};
-
 __global__ void k_stage_predict(const double* __restrict__ q, int64_t n, StageCoefs c, double* __restrict__ rho,
                                 double* __restrict__ mhat, double* __restrict__ ehat) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -157,9 +145,10 @@ __global__ void k_stage_state(const double* __restrict__ rho, const double* __re
 }
 
 // q += dt sum_l b_l (F_NS,l + F_S,l)
-__global__ void k_final_update(double* __restrict__ q, int64_t n, StageCoefs c) {
+// (skipped when *skip != 0: the device-driven step's error status)
+__global__ void k_final_update(double* __restrict__ q, int64_t n, StageCoefs c, const int* __restrict__ skip) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  if (i >= n || (skip && *skip)) return;
   double acc[5] = {0, 0, 0, 0, 0};
   for (int s = 0; s < c.nst; ++s) {
     const double b = c.a[s];
@@ -205,12 +194,8 @@ __global__ void k_picard_norms(const double* __restrict__ p0, const double* __re
 // host helpers
 // ---------------------------------------------------------------------------
 
-struct Red {
-  double* partial;   // RED_BLOCKS * (MAX_RESTART + 1)
-  double* out;       // MAX_RESTART + 1
-};
 
-static int ensure_red(dg_mesh* m, Red* r) {
+int ensure_red(dg_mesh* m, Red* r) {
   int rc = m->red.ensure(sizeof(double) * (RED_BLOCKS * (MAX_RESTART + 1) + (MAX_RESTART + 1)));
   if (rc) return rc;
   r->partial = m->red.as<double>();
@@ -229,12 +214,6 @@ static int dots(dg_mesh* m, const Red& r, const double* V, int nvec, int64_t n, 
   return DG_OK;
 }
 
-// generic vmult closure: the solver is written against y = S x
-struct Vmult {
-  int (*fn)(void* self, const double* x, double* y, cudaStream_t st);
-  void* self;
-  int operator()(const double* x, double* y, cudaStream_t st) const { return fn(self, x, y, st); }
-};
 
 // Restarted GMRES(m), classical Gram-Schmidt applied twice, Givens rotations.
 static int gmres(dg_mesh* m, const Vmult& A, const double* b, double* x, double rtol, int restart, int maxit,
@@ -368,13 +347,6 @@ static int gmres(dg_mesh* m, const Vmult& A, const double* b, double* x, double 
   }
 }
 
-struct SchurCtx {
-  dg_mesh* m;
-  ImplK k;
-  const double* rho;
-  const double* plag;
-  int penalty;
-};
 
 template <int D, int NN>
 static int schur_vmult_fn(void* self, const double* x, double* y, cudaStream_t st) {
@@ -382,7 +354,7 @@ static int schur_vmult_fn(void* self, const double* x, double* y, cudaStream_t s
   return Engine<double, D, NN>::vmult(s->m, s->k, s->rho, s->plag, s->penalty, x, y, st);
 }
 
-static Vmult make_vmult(SchurCtx* s) {
+Vmult make_vmult(SchurCtx* s) {
   Vmult v{nullptr, s};
   DG_DISPATCH(s->m, v.fn = &schur_vmult_fn<D_, N_>);
   return v;
@@ -402,15 +374,6 @@ __global__ void k_f2d(const float* __restrict__ a, double* __restrict__ b, int64
   if (i < n) b[i] = (double)a[i];
 }
 
-struct Schur32Ctx {
-  dg_mesh* m;
-  ImplK k;
-  const float* rho;
-  const float* plag;
-  int penalty;
-  float* x32;
-  float* y32;
-};
 
 template <int D, int NN>
 static int schur32_vmult_fn(void* self, const double* x, double* y, cudaStream_t st) {
@@ -427,7 +390,7 @@ static int schur32_vmult_fn(void* self, const double* x, double* y, cudaStream_t
 
 // FP32 copies of the frozen coefficients and their face data (h rho traces,
 // implicit Rusanov lambda) for the FP32 vmult.
-static int prepare32(dg_mesh* m, const ImplK& k, const double* rho, const double* plag, const double* ulag,
+int prepare32(dg_mesh* m, const ImplK& k, const double* rho, const double* plag, const double* ulag,
                      int penalty, cudaStream_t st, Schur32Ctx* out) {
   int rc;
   if ((rc = ensure_fp32_geometry(m)) != DG_OK) return rc;
@@ -453,7 +416,7 @@ static int prepare32(dg_mesh* m, const ImplK& k, const double* rho, const double
   return DG_OK;
 }
 
-static Vmult make_vmult32(Schur32Ctx* s) {
+Vmult make_vmult32(Schur32Ctx* s) {
   Vmult v{nullptr, s};
   DG_DISPATCH(s->m, v.fn = &schur32_vmult_fn<D_, N_>);
   return v;
@@ -529,27 +492,27 @@ static int gmres_ir(dg_mesh* m, const Vmult& A64, const Vmult& A32, const double
   return DG_OK;
 }
 
-static int prepare_rt(dg_mesh* m, const ImplK& k, const double* rho, const double* plag, const double* ulag,
+int prepare_rt(dg_mesh* m, const ImplK& k, const double* rho, const double* plag, const double* ulag,
                       int penalty,
                       cudaStream_t st) {
   DG_DISPATCH(m, return (Engine<double, D_, N_>::prepare(m, k, rho, plag, ulag, penalty, st)));
   return DG_ERR_UNSUPPORTED;
 }
 
-static int explicit_rt(dg_mesh* m, const dg_phys* ph, const double* q, double* fns, double* fs, cudaStream_t st) {
+int explicit_rt(dg_mesh* m, const dg_phys* ph, const double* q, double* fns, double* fs, cudaStream_t st) {
   PhysK k{ph->gamma, ph->g, ph->f, ph->f_cell};
   if (ph->precision == DG_MIXED_EXPLICIT && m->bg_set) return explicit_mixed(m, k, q, fns, fs, st);
   DG_DISPATCH(m, return (Engine<double, D_, N_>::explicit_rates(m, k, q, fns, fs, st)));
   return DG_ERR_UNSUPPORTED;
 }
 
-static int rhs_rt(dg_mesh* m, const ImplK& k, const double* rho, const double* plag, const double* ulag,
+int rhs_rt(dg_mesh* m, const ImplK& k, const double* rho, const double* plag, const double* ulag,
                   const double* mhat, const double* ehat, double* rhs, cudaStream_t st) {
   DG_DISPATCH(m, return (Engine<double, D_, N_>::schur_rhs(m, k, rho, plag, ulag, mhat, ehat, rhs, st)));
   return DG_ERR_UNSUPPORTED;
 }
 
-static int recover_rt(dg_mesh* m, const ImplK& k, const double* rho, const double* ulag, const double* mhat,
+int recover_rt(dg_mesh* m, const ImplK& k, const double* rho, const double* ulag, const double* mhat,
                       const double* p, double* u, cudaStream_t st) {
   DG_DISPATCH(m, return (Engine<double, D_, N_>::recover(m, k, rho, ulag, mhat, p, u, st)));
   return DG_ERR_UNSUPPORTED;
@@ -610,14 +573,29 @@ int imex_ark2_step(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* ph, double* 
     set_error("imex_ark2_step: dt > 0, picard_maxit >= 1, picard_fixed >= 0 required");
     return DG_ERR_ARG;
   }
+  if (opts->gmres.restart < 1 || opts->gmres.restart > MAX_RESTART || opts->gmres.maxit < 0 ||
+      !(opts->gmres.rtol >= 0.0)) {
+    set_error("imex_ark2_step: gmres restart must be in 1..%d, maxit >= 0, rtol >= 0", MAX_RESTART);
+    return DG_ERR_ARG;
+  }
   dg_mesh* m = const_cast<dg_mesh*>(mesh);
   cudaStream_t st = (cudaStream_t)stream;
+  if (opts->graph) return step_graph(m, ph, q, dt, opts, info, st);
+  return step_host(m, ph, q, dt, opts, info, st);
+}
+
+}  // extern "C"
+
+namespace dg {
+
+int step_host(dg_mesh* m, const dg_phys* ph, double* q, double dt, const dg_step_opts* opts,
+              dg_step_info* info, cudaStream_t st) {
+  int rc;
   const int64_t n = m->N;
-  // tableaux (Section 3): explicit a, implicit at, weights b
-  const double chi = 2.0 - std::sqrt(2.0), a32 = 0.5;
-  const double a[3][3] = {{0, 0, 0}, {chi, 0, 0}, {1.0 - a32, a32, 0}};
-  const double bw[3] = {0.5 - chi / 4.0, 0.5 - chi / 4.0, chi / 2.0};
-  const double at[3][3] = {{0, 0, 0}, {chi / 2.0, chi / 2.0, 0}, {bw[0], bw[1], bw[2]}};
+  const Ark2 tab;
+  const auto& a = tab.a;
+  const auto& at = tab.at;
+  const auto& bw = tab.b;
   // workspace: F_NS x3 (5n), F_S x3 (4n), y (5n), rho, mhat (3n), ehat, u, unew (3n each), p, pnew, rhs
   if ((rc = m->fns.ensure(sizeof(double) * 15 * n)) != DG_OK) return rc;
   if ((rc = m->fs.ensure(sizeof(double) * 12 * n)) != DG_OK) return rc;
@@ -721,16 +699,12 @@ int imex_ark2_step(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* ph, double* 
     fin.fs[s] = Fs[s];
     fin.a[s] = bw[s];
   }
-  DG_RUN(m, K_STAGE, st, k_final_update<<<gb, 256, 0, st>>>(q, n, fin));
+  DG_RUN(m, K_STAGE, st, k_final_update<<<gb, 256, 0, st>>>(q, n, fin, nullptr));
   DG_LAUNCH_CHECK("final update");
   DG_CUDA(cudaStreamSynchronize(st));
   if (info) *info = inf;
   return DG_OK;
 }
-
-}  // extern "C"
-
-namespace dg {
 
 __global__ void k_fill(double* __restrict__ a, int64_t n, double v) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;

@@ -68,7 +68,7 @@ class GmresInfo(C.Structure):
 
 class StepOpts(C.Structure):
     _fields_ = [("picard_rtol", C.c_double), ("picard_maxit", C.c_int),
-                ("picard_fixed", C.c_int), ("gmres", GmresOpts)]
+                ("picard_fixed", C.c_int), ("gmres", GmresOpts), ("graph", C.c_int)]
 
 
 class StepInfo(C.Structure):
@@ -316,11 +316,11 @@ class Mesh:
 
     def step(self, phys, q, dt, picard_rtol=1e-10, picard_maxit=10, picard_fixed=0,
              gmres_rtol=1e-10, gmres_restart=30, gmres_maxit=1000, stream=None,
-             gmres_inner_rtol=0.0):
+             gmres_inner_rtol=0.0, graph=False):
         opts = StepOpts(picard_rtol=picard_rtol, picard_maxit=picard_maxit,
                         picard_fixed=picard_fixed,
                         gmres=GmresOpts(rtol=gmres_rtol, restart=gmres_restart, maxit=gmres_maxit,
-                                        inner_rtol=gmres_inner_rtol))
+                                        inner_rtol=gmres_inner_rtol), graph=1 if graph else 0)
         info = StepInfo()
         _check(self.lib.imex_ark2_step(self.ctx.h, self.h, C.byref(phys), _ptr(q), float(dt),
                                        C.byref(opts), C.byref(info), _stream(stream)),
@@ -403,11 +403,11 @@ class Ensemble:
         return q
 
     def step(self, phys, dt, picard_rtol=1e-10, picard_maxit=10, picard_fixed=0, gmres_rtol=1e-10,
-             gmres_restart=30, gmres_maxit=1000, gmres_inner_rtol=0.0, stream=None):
+             gmres_restart=30, gmres_maxit=1000, gmres_inner_rtol=0.0, stream=None, graph=False):
         opts = StepOpts(picard_rtol=picard_rtol, picard_maxit=picard_maxit,
                         picard_fixed=picard_fixed,
                         gmres=GmresOpts(rtol=gmres_rtol, restart=gmres_restart, maxit=gmres_maxit,
-                                        inner_rtol=gmres_inner_rtol))
+                                        inner_rtol=gmres_inner_rtol), graph=1 if graph else 0)
         dts = (C.c_double * self.n)(*[float(x) for x in dt])
         info = StepInfo()
         _check(self.lib.dg_ensemble_step(self.h, C.byref(phys), dts, C.byref(opts), C.byref(info),
