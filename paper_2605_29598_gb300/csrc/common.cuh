@@ -159,6 +159,16 @@ namespace dg {
 // releases the cached step graph of a mesh (defined with the graph code)
 void graph_release(dg_mesh* m);
 
+}  // namespace dg
+
+struct MultiGraph;   // several meshes' steps captured as one graph
+
+namespace dg {
+
+void multi_graph_release(MultiGraph* g);
+int multi_step_graph(int ng, dg_mesh* const* meshes, const dg_phys* phs, double* const* qs, const double* dts,
+                     const dg_step_opts* o, dg_step_info* infos, MultiGraph** cache, cudaStream_t st);
+
 // Arguments shared by the face kernels.
 struct FaceTopo {
   const int* fp_minus;

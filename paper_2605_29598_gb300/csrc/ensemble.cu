@@ -27,6 +27,7 @@ struct dg_ensemble {
   };
   cudaEvent_t start = nullptr;
   std::vector<Group> groups;
+  MultiGraph* graph = nullptr;   // all groups' steps as one CUDA graph (opts.graph)
   struct Inst {
     int group = -1;
     int64_t cell_off = 0, n_elem = 0, n_nodes = 0;
@@ -48,6 +49,7 @@ void dg_ensemble_destroy(dg_ensemble* e) {
     if (g.done) cudaEventDestroy(g.done);
   }
   if (e->start) cudaEventDestroy(e->start);
+  multi_graph_release(e->graph);
   delete e;
 }
 
@@ -212,10 +214,37 @@ int dg_ensemble_step(dg_ensemble* e, const dg_phys* ph, const double* dt_inst, c
         set_error("dg_ensemble_step: instances %d and %d share (dim, degree) but not dt", g.members[0], i);
         return DG_ERR_ARG;
       }
+  cudaStream_t caller = (cudaStream_t)stream;
+  if (opts->graph) {
+    // every group's step as a parallel branch of one graph: one launch
+    const size_t ng = e->groups.size();
+    std::vector<dg_mesh*> meshes(ng);
+    std::vector<dg_phys> phs(ng, *ph);
+    std::vector<double*> qs(ng);
+    std::vector<double> dts(ng);
+    std::vector<dg_step_info> infos(ng);
+    for (size_t k = 0; k < ng; ++k) {
+      meshes[k] = e->groups[k].mesh;
+      phs[k].f_cell = e->groups[k].f_cell;
+      qs[k] = e->groups[k].q;
+      dts[k] = dt_inst[e->groups[k].members[0]];
+    }
+    int rc = multi_step_graph((int)ng, meshes.data(), phs.data(), qs.data(), dts.data(), opts, infos.data(),
+                              &e->graph, caller);
+    if (rc != DG_OK) return rc;
+    dg_step_info total{};
+    for (const auto& gi : infos) {
+      for (int l = 0; l < 3; ++l) total.picard_iters[l] = std::max(total.picard_iters[l], gi.picard_iters[l]);
+      total.gmres_iters_total += gi.gmres_iters_total;
+      total.max_relres = std::max(total.max_relres, gi.max_relres);
+      total.refinements_total += gi.refinements_total;
+    }
+    if (info) *info = total;
+    return DG_OK;
+  }
   // Each group steps on its own stream from its own host thread, so groups
   // overlap on the GPU (their GMRES loops synchronise only their stream).
   // The caller's stream orders before and after all of them.
-  cudaStream_t caller = (cudaStream_t)stream;
   DG_CUDA(cudaEventRecord(e->start, caller));
   const size_t ng = e->groups.size();
   std::vector<int> rcs(ng, DG_OK);

@@ -742,49 +742,33 @@ int capture(dg_mesh* m, const dg_phys* ph, double* q, double dt, const dg_step_o
   return DG_OK;
 }
 
-}  // namespace
-
-int step_graph(dg_mesh* m, const dg_phys* ph, double* q, double dt, const dg_step_opts* o, dg_step_info* info,
-               cudaStream_t st) {
-  if (m->prof.on) {
-    set_error("imex_ark2_step: graph mode does not run under dg_profile_begin");
-    return DG_ERR_UNSUPPORTED;
-  }
-  int rc;
+int graph_of(dg_mesh* m, StepGraph** out) {
   if (!m->graph) {
     StepGraph* G = new StepGraph();
     m->graph = G;
     for (auto& s : G->s) DG_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
     DG_CUDA(cudaMallocHost(&G->host, sizeof(StepState)));
   }
-  StepGraph* G = m->graph;
-  unsigned char key[sizeof(StepGraph::key)];
-  const size_t kl = make_key(m, ph, q, dt, o, key);
-  if (!G->valid || G->key_len != kl || std::memcmp(G->key, key, kl) != 0) {
-    // One host-driven step on a copy of q sizes every workspace and builds
-    // the one-time data (FP32 geometry, background rates), so that the
-    // capture allocates nothing; the capture is checked for that.
-    double* qs = nullptr;
-    DG_CUDA(cudaMalloc(&qs, sizeof(double) * 5 * m->N));
-    cudaError_t e = cudaMemcpyAsync(qs, q, sizeof(double) * 5 * m->N, cudaMemcpyDeviceToDevice, st);
-    rc = e == cudaSuccess ? step_host(m, ph, qs, dt, o, nullptr, st) : DG_OK;
-    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-    cudaFree(qs);
-    if (e != cudaSuccess) return cuda_fail(e, "step graph warm-up");
-    if (rc != DG_OK && rc != DG_ERR_NOT_CONVERGED) return rc;
-    bool stable = false;
-    if ((rc = capture(m, ph, q, dt, o, G, &stable)) != DG_OK) return rc;
-    if (!stable) {
-      set_error("imex_ark2_step: workspace moved during graph capture");
-      return DG_ERR_CUDA;
-    }
-  }
-  DG_CUDA(cudaGraphLaunch(G->exec, st));
-  Work wk;
-  if ((rc = ensure_work(m, &wk)) != DG_OK) return rc;
-  DG_CUDA(cudaMemcpyAsync(G->host, wk.ss, sizeof(StepState), cudaMemcpyDeviceToHost, st));
-  DG_CUDA(cudaStreamSynchronize(st));
-  const StepState& h = *G->host;
+  *out = m->graph;
+  return DG_OK;
+}
+
+// One host-driven step on a copy of q sizes every workspace and builds the
+// one-time data (FP32 geometry, background rates), so that a capture
+// allocates nothing; captures check that.
+int warm_up(dg_mesh* m, const dg_phys* ph, const double* q, double dt, const dg_step_opts* o, cudaStream_t st) {
+  double* qs = nullptr;
+  DG_CUDA(cudaMalloc(&qs, sizeof(double) * 5 * m->N));
+  cudaError_t e = cudaMemcpyAsync(qs, q, sizeof(double) * 5 * m->N, cudaMemcpyDeviceToDevice, st);
+  int rc = e == cudaSuccess ? step_host(m, ph, qs, dt, o, nullptr, st) : DG_OK;
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(qs);
+  if (e != cudaSuccess) return cuda_fail(e, "step graph warm-up");
+  if (rc != DG_OK && rc != DG_ERR_NOT_CONVERGED) return rc;
+  return DG_OK;
+}
+
+int fill_info(const StepState& h, dg_step_info* info) {
   if (info) {
     dg_step_info inf{};
     for (int l = 0; l < 3; ++l) inf.picard_iters[l] = h.picard_iters[l];
@@ -798,6 +782,172 @@ int step_graph(dg_mesh* m, const dg_phys* ph, double* q, double dt, const dg_ste
     return DG_ERR_NONFINITE;
   }
   return h.status;
+}
+
+}  // namespace
+
+int step_graph(dg_mesh* m, const dg_phys* ph, double* q, double dt, const dg_step_opts* o, dg_step_info* info,
+               cudaStream_t st) {
+  if (m->prof.on) {
+    set_error("imex_ark2_step: graph mode does not run under dg_profile_begin");
+    return DG_ERR_UNSUPPORTED;
+  }
+  int rc;
+  StepGraph* G;
+  if ((rc = graph_of(m, &G)) != DG_OK) return rc;
+  unsigned char key[sizeof(StepGraph::key)];
+  const size_t kl = make_key(m, ph, q, dt, o, key);
+  if (!G->valid || G->key_len != kl || std::memcmp(G->key, key, kl) != 0) {
+    if ((rc = warm_up(m, ph, q, dt, o, st)) != DG_OK) return rc;
+    bool stable = false;
+    if ((rc = capture(m, ph, q, dt, o, G, &stable)) != DG_OK) return rc;
+    if (!stable) {
+      set_error("imex_ark2_step: workspace moved during graph capture");
+      return DG_ERR_CUDA;
+    }
+  }
+  DG_CUDA(cudaGraphLaunch(G->exec, st));
+  Work wk;
+  if ((rc = ensure_work(m, &wk)) != DG_OK) return rc;
+  DG_CUDA(cudaMemcpyAsync(G->host, wk.ss, sizeof(StepState), cudaMemcpyDeviceToHost, st));
+  DG_CUDA(cudaStreamSynchronize(st));
+  return fill_info(*G->host, info);
+}
+
+}  // namespace dg
+
+// ---------------------------------------------------------------------------
+// several meshes in one graph (ensemble groups): the steps are captured as
+// parallel branches of one graph, so an ensemble step is one launch
+// ---------------------------------------------------------------------------
+
+struct MultiGraph {
+  cudaStream_t main = nullptr;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<unsigned char> key;
+  bool valid = false;
+};
+
+namespace dg {
+
+void multi_graph_release(MultiGraph* M) {
+  if (!M) return;
+  if (M->exec) cudaGraphExecDestroy(M->exec);
+  if (M->graph) cudaGraphDestroy(M->graph);
+  if (M->main) cudaStreamDestroy(M->main);
+  if (M->fork) cudaEventDestroy(M->fork);
+  for (auto ev : M->join) cudaEventDestroy(ev);
+  delete M;
+}
+
+int multi_step_graph(int ng, dg_mesh* const* meshes, const dg_phys* phs, double* const* qs, const double* dts,
+                     const dg_step_opts* o, dg_step_info* infos, MultiGraph** cache, cudaStream_t st) {
+  int rc;
+  if (!*cache) {
+    MultiGraph* M = new MultiGraph();
+    *cache = M;
+    DG_CUDA(cudaStreamCreateWithFlags(&M->main, cudaStreamNonBlocking));
+    DG_CUDA(cudaEventCreateWithFlags(&M->fork, cudaEventDisableTiming));
+  }
+  MultiGraph* M = *cache;
+  while ((int)M->join.size() < ng) {
+    cudaEvent_t ev;
+    DG_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    M->join.push_back(ev);
+  }
+  std::vector<StepGraph*> G(ng);
+  std::vector<unsigned char> key;
+  for (int k = 0; k < ng; ++k) {
+    if (meshes[k]->prof.on) {
+      set_error("dg_ensemble_step: graph mode does not run under dg_profile_begin");
+      return DG_ERR_UNSUPPORTED;
+    }
+    if ((rc = graph_of(meshes[k], &G[k])) != DG_OK) return rc;
+    unsigned char kk[sizeof(StepGraph::key)];
+    const size_t kl = make_key(meshes[k], &phs[k], qs[k], dts[k], o, kk);
+    key.insert(key.end(), kk, kk + kl);
+  }
+  if (!M->valid || M->key != key) {
+    for (int k = 0; k < ng; ++k)
+      if ((rc = warm_up(meshes[k], &phs[k], qs[k], dts[k], o, st)) != DG_OK) return rc;
+    if (M->exec) cudaGraphExecDestroy(M->exec);
+    if (M->graph) cudaGraphDestroy(M->graph);
+    M->exec = nullptr;
+    M->graph = nullptr;
+    M->valid = false;
+    std::vector<Work> wk(ng);
+    for (int k = 0; k < ng; ++k)
+      if ((rc = ensure_work(meshes[k], &wk[k])) != DG_OK) return rc;
+    std::vector<unsigned char> before;
+    for (int k = 0; k < ng; ++k) {
+      unsigned char kk[sizeof(StepGraph::key)];
+      const size_t kl = make_key(meshes[k], &phs[k], qs[k], dts[k], o, kk);
+      before.insert(before.end(), kk, kk + kl);
+    }
+    DG_CUDA(cudaStreamBeginCapture(M->main, cudaStreamCaptureModeRelaxed));
+    int crc = cudaEventRecord(M->fork, M->main) == cudaSuccess ? DG_OK : DG_ERR_CUDA;
+    for (int k = 0; k < ng && crc == DG_OK; ++k) {
+      StepGraph* g = G[k];
+      if (cudaStreamWaitEvent(g->s[0], M->fork, 0) != cudaSuccess) {
+        crc = DG_ERR_CUDA;
+        break;
+      }
+      crc = capture_step(meshes[k], &phs[k], qs[k], dts[k], o, wk[k], g->s);
+      if (crc == DG_OK && (cudaEventRecord(M->join[k], g->s[0]) != cudaSuccess ||
+                           cudaStreamWaitEvent(M->main, M->join[k], 0) != cudaSuccess))
+        crc = DG_ERR_CUDA;
+    }
+    if (crc != DG_OK) {
+      // close every capture still open (bodies first), then the main one
+      for (int k = 0; k < ng; ++k)
+        for (int i = StepGraph::kStreams - 1; i >= 0; --i) {
+          cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+          if (cudaStreamIsCapturing(G[k]->s[i], &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive &&
+              i > 0) {
+            cudaGraph_t gb = nullptr;
+            cudaStreamEndCapture(G[k]->s[i], &gb);
+          }
+        }
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(M->main, &g);
+    if (crc != DG_OK || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      if (crc != DG_OK) return crc;
+      return cuda_fail(e, "ensemble graph capture");
+    }
+    M->graph = g;
+    std::vector<unsigned char> after;
+    for (int k = 0; k < ng; ++k) {
+      unsigned char kk[sizeof(StepGraph::key)];
+      const size_t kl = make_key(meshes[k], &phs[k], qs[k], dts[k], o, kk);
+      after.insert(after.end(), kk, kk + kl);
+    }
+    if (after != before) {
+      set_error("dg_ensemble_step: workspace moved during graph capture");
+      return DG_ERR_CUDA;
+    }
+    DG_CUDA(cudaGraphInstantiate(&M->exec, M->graph, 0));
+    M->key = after;
+    M->valid = true;
+  }
+  DG_CUDA(cudaGraphLaunch(M->exec, st));
+  for (int k = 0; k < ng; ++k) {
+    Work wk;
+    if ((rc = ensure_work(meshes[k], &wk)) != DG_OK) return rc;
+    DG_CUDA(cudaMemcpyAsync(G[k]->host, wk.ss, sizeof(StepState), cudaMemcpyDeviceToHost, st));
+  }
+  DG_CUDA(cudaStreamSynchronize(st));
+  int out = DG_OK;
+  for (int k = 0; k < ng; ++k) {
+    const int r = fill_info(*G[k]->host, infos ? &infos[k] : nullptr);
+    if (r != DG_OK && out == DG_OK) out = r;
+  }
+  return out;
 }
 
 }  // namespace dg
