@@ -249,7 +249,7 @@ def run_ensemble(D, I, ctx, steps, warmup):
                      [c["f"] for c in cases])
     out["groups"] = ens.n_groups
     dts = [c["dt"] for c in cases]
-    for prec in ("fp64", "mixed"):
+    for prec, graph in (("fp64", False), ("mixed", False), ("mixed", True)):
         ph = D.make_phys(precision=prec)
         opts = dict(STEP_OPTS, gmres_inner_rtol=1e-4) if prec == "mixed" else STEP_OPTS
 
@@ -258,16 +258,52 @@ def run_ensemble(D, I, ctx, steps, warmup):
                 ens.set_state(i, q)
             its = 0
             for _ in range(n):
-                its += ens.step(ph, dts, **opts).gmres_iters_total
+                its += ens.step(ph, dts, graph=graph, **opts).gmres_iters_total
             return its
 
         ens_steps(warmup)
         ms, its = timed(lambda: ens_steps(steps))
-        out["batched_" + prec] = {"value": 5.0 * nodes * steps / (ms / 1e3) / 1e9,
-                                  "ms_per_step": ms / steps, "gmres_iters": its}
+        out["batched_" + prec + ("_one_graph_launch" if graph else "")] = {
+            "value": 5.0 * nodes * steps / (ms / 1e3) / 1e9, "ms_per_step": ms / steps, "gmres_iters": its}
     ens.close()
     out["unit"] = "GDoF-updates/s"
     out["steps"] = steps
+    return out
+
+
+def run_graph_modes(D, I, ctx, case, steps, warmup):
+    """Host-driven vs device-driven (one CUDA graph per step) steps of a
+    workload, FP64 and mixed, timed with CUDA events."""
+    import torch
+    mesh = D.Mesh(ctx, case["mesh"], case["degree"])
+    xyz = mesh.node_coords().cpu().numpy().T
+    q0 = torch.tensor(I.stratified_state(xyz, **case["state_params"]), dtype=torch.float64,
+                      device="cuda").contiguous()
+    stream = torch.cuda.current_stream()
+    out = {"cells": mesh.stats().n_elem, "nodes": mesh.N, "degree": case["degree"], "dt": case["dt"],
+           "steps": steps}
+    for prec in ("fp64", "mixed"):
+        phys = D.make_phys(f=case["f"], variant="R2", precision=prec)
+        opts = dict(STEP_OPTS, gmres_inner_rtol=1e-4) if prec == "mixed" else STEP_OPTS
+        res = {}
+        for graph in (False, True):
+            q = q0.clone()
+            for _ in range(warmup):
+                mesh.step(phys, q, case["dt"], graph=graph, **opts)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            its = 0
+            for _ in range(steps):
+                its += mesh.step(phys, q, case["dt"], graph=graph, **opts).gmres_iters_total
+            e1.record(stream)
+            torch.cuda.synchronize()
+            res["graph" if graph else "host"] = {"ms_per_step": e0.elapsed_time(e1) / steps,
+                                                 "gmres_iters": its}
+        res["graph_speedup"] = res["host"]["ms_per_step"] / res["graph"]["ms_per_step"]
+        out[prec] = res
+    mesh.close()
     return out
 
 
@@ -537,6 +573,8 @@ def gpu_main(args):
     if not args.no_variants and world == 1:
         variants["hill3d_nc"] = run_variant(D, I, ctx, I.hill3d_case(refine=True), steps=2, warmup=1)
         variants["ensemble32"] = run_ensemble(D, I, ctx, steps=2, warmup=1)
+        variants["graph_mode_hill3d"] = run_graph_modes(D, I, ctx, I.hill3d_case(), steps=3, warmup=2)
+        variants["graph_mode_igw2d"] = run_graph_modes(D, I, ctx, I.igw2d_case(), steps=10, warmup=2)
 
     if dist and rank != 0:
         dist.barrier()
