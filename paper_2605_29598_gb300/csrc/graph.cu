@@ -52,56 +52,21 @@ __device__ __forceinline__ void set_cond(cudaGraphConditionalHandle h, bool v) {
 // vector kernels with counts read from device memory
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ double warp_sum_d(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
 // partial[b * DSTRIDE + k] = block b's share of v_k . w, where v_k = V_k for
-// k < *np + add and the last vector is w itself.  Same blocking and
-// summation order as k_multidot.  Launch with 256 threads; returns at once
-// when gate != nullptr and *gate == 0.
+// k < *np + add and the last vector is w itself (same blocking and order as
+// k_multidot).  Launch grid (RED_BLOCKS, ceil((restart + 2) / 8)) of 256
+// threads (rows past the current count return); returns at once when gate
+// != nullptr and *gate == 0.
 __global__ void k_ddots(const double* __restrict__ V, const int* __restrict__ np, int add, int64_t n,
                         const double* __restrict__ w, double* __restrict__ partial, const int* __restrict__ gate) {
   if (gate && !*gate) return;
-  constexpr int G = 8;
-  __shared__ double red[G][8];
-  const int nV = *np + add, nvec = nV + 1;
+  const int nV = *np + add;
   const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
   const int64_t lo = blockIdx.x * chunk;
   const int64_t hi = lo + chunk < n ? lo + chunk : n;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int k0 = 0; k0 < nvec; k0 += G) {
-    const int ng = nvec - k0 < G ? nvec - k0 : G;
-    const double* vec[G];
-#pragma unroll
-    for (int g = 0; g < G; ++g) vec[g] = (k0 + g < nV) ? V + (int64_t)(k0 + g) * n : w;
-    double s[G];
-#pragma unroll
-    for (int g = 0; g < G; ++g) s[g] = 0.0;
-    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-      const double wi = w[i];
-#pragma unroll
-      for (int g = 0; g < G; ++g)
-        if (g < ng) s[g] += vec[g][i] * wi;
-    }
-#pragma unroll
-    for (int g = 0; g < G; ++g) {
-      const double t = warp_sum_d(s[g]);
-      if (lane == 0) red[g][wid] = t;
-    }
-    __syncthreads();
-    if (wid == 0) {
-#pragma unroll
-      for (int g = 0; g < G; ++g) {
-        double t = lane < 8 ? red[g][lane] : 0.0;
-        t = warp_sum_d(t);
-        if (lane == 0 && g < ng) partial[blockIdx.x * DSTRIDE + k0 + g] = t;
-      }
-    }
-    __syncthreads();
-  }
+  block_dots_group(
+      nV + 1, [&](int k) { return k < nV ? V + (int64_t)k * n : w; }, w, lo, hi,
+      [&](int k0) { return partial + (int64_t)blockIdx.x * DSTRIDE + k0; });
 }
 
 // out[k] = sum over blocks of partial[b * DSTRIDE + k], k < *np + add + 1
@@ -123,13 +88,19 @@ __global__ void k_dreduce(const double* __restrict__ partial, const int* __restr
   if (threadIdx.x == 0) out[k] = red[0];
 }
 
-// w += sum_{k < *np + add} c_k V_k
+// w += sum_{k < *np + add} c_k V_k; element pairs when `pairs` (n even, V
+// and w 16-byte aligned; launch n/2 threads then), single elements otherwise
 __global__ void k_dmultiaxpy(const double* __restrict__ V, const int* __restrict__ np, int add, int64_t n,
-                             const double* __restrict__ c, double* __restrict__ w, const int* __restrict__ gate) {
+                             const double* __restrict__ c, double* __restrict__ w, const int* __restrict__ gate,
+                             int pairs) {
   if (gate && !*gate) return;
-  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int nvec = *np + add;
+  if (pairs) {
+    if (2 * i < n) multiaxpy_pair(V, nvec, n, c, w, i);
+    return;
+  }
+  if (i >= n) return;
   double acc = w[i];
   for (int k = 0; k < nvec; ++k) acc += c[k] * V[(int64_t)k * n + i];
   w[i] = acc;
@@ -450,6 +421,11 @@ int capture_gmres(dg_mesh* m, const Work& wk, GmState* gs, const Vmult& A, const
   if ((rc = m->gm_V.ensure(sizeof(double) * (size_t)(restart + 1) * n)) != DG_OK) return rc;
   double* V = m->gm_V.as<double>();
   const unsigned gb = grid_for(n, 256);
+  // k_dmultiaxpy over element pairs when every target allows 16-byte access
+  const int pairs = n % 2 == 0 && ((uintptr_t)V & 15) == 0 && ((uintptr_t)wk.w & 15) == 0 &&
+                    ((uintptr_t)x & 15) == 0;
+  const unsigned gma = grid_for(pairs ? n / 2 : n, 256);
+  const dim3 dgrid(RED_BLOCKS, (restart + 2 + 7) / 8);   // k_ddots: up to restart + 1 vectors and w
   if ((rc = dot_self(m, wk, b, &gs->dot[0], s[0])) != DG_OK) return rc;
   k_gm_begin<<<1, 1, 0, s[0]>>>(gs, tol, maxit, restart, tol_dev, maxit_dev);
   k_zero_if<<<gb, 256, 0, s[0]>>>(x, n, &gs->bnorm);
@@ -472,21 +448,21 @@ int capture_gmres(dg_mesh* m, const Work& wk, GmState* gs, const Vmult& A, const
     {
       cudaStream_t sa = s[2];
       if ((rc = A(wk.xin, wk.w, sa)) != DG_OK) return rc;
-      k_ddots<<<RED_BLOCKS, 256, 0, sa>>>(V, &gs->j, 1, n, wk.w, wk.partial, nullptr);
+      k_ddots<<<dgrid, 256, 0, sa>>>(V, &gs->j, 1, n, wk.w, wk.partial, nullptr);
       k_dreduce<<<MAX_RESTART + 2, 256, 0, sa>>>(wk.partial, &gs->j, 1, gs->dot, nullptr);
       k_orth1<<<1, 1, 0, sa>>>(gs);
-      k_dmultiaxpy<<<gb, 256, 0, sa>>>(V, &gs->j, 1, n, gs->c, wk.w, nullptr);
-      k_ddots<<<RED_BLOCKS, 256, 0, sa>>>(V, &gs->j, 1, n, wk.w, wk.partial, &gs->reorth);
+      k_dmultiaxpy<<<gma, 256, 0, sa>>>(V, &gs->j, 1, n, gs->c, wk.w, nullptr, pairs);
+      k_ddots<<<dgrid, 256, 0, sa>>>(V, &gs->j, 1, n, wk.w, wk.partial, &gs->reorth);
       k_dreduce<<<MAX_RESTART + 2, 256, 0, sa>>>(wk.partial, &gs->j, 1, gs->dot, &gs->reorth);
       k_orth2<<<1, 1, 0, sa>>>(gs);
-      k_dmultiaxpy<<<gb, 256, 0, sa>>>(V, &gs->j, 1, n, gs->c, wk.w, &gs->reorth);
+      k_dmultiaxpy<<<gma, 256, 0, sa>>>(V, &gs->j, 1, n, gs->c, wk.w, &gs->reorth, pairs);
       k_arnoldi_end<<<1, 1, 0, sa>>>(gs, ha);
       k_dnormalize<<<gb, 256, 0, sa>>>(wk.w, V, gs, n, wk.xin);
       DG_LAUNCH_CHECK("graph arnoldi step");
     }
     if ((rc = while_close(s[2])) != DG_OK) return rc;
     k_solve_y<<<1, 1, 0, s[1]>>>(gs);
-    k_dmultiaxpy<<<gb, 256, 0, s[1]>>>(V, &gs->jused, 0, n, gs->y, x, nullptr);
+    k_dmultiaxpy<<<gma, 256, 0, s[1]>>>(V, &gs->jused, 0, n, gs->y, x, nullptr, pairs);
     if ((rc = A(x, wk.tmp, s[1])) != DG_OK) return rc;
     k_axpby<<<gb, 256, 0, s[1]>>>(n, 1.0, b, -1.0, wk.tmp, V);
     if ((rc = dot_self(m, wk, V, &gs->dot[0], s[1])) != DG_OK) return rc;

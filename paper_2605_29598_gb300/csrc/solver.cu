@@ -12,51 +12,17 @@ namespace dg {
 // vector kernels (FP64)
 // ---------------------------------------------------------------------------
 
-// partial[b * nvec + k] = sum over block b's chunk of V[k] . w
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// Vectors are taken in groups of 8: w is read once per group, each thread
-// keeps 8 running sums, warps reduce by shuffles (fixed order, so the
-// result is deterministic).  Launch with 256 threads.
+// partial[b * nvec + k] = block b's share of V_k . w (contiguous chunk of
+// elements per block column b, one group of 8 vectors per block row; launch
+// grid (RED_BLOCKS, ceil(nvec / 8)) of 256 threads)
 __global__ void k_multidot(const double* __restrict__ V, int nvec, int64_t n, const double* __restrict__ w,
                            double* __restrict__ partial) {
-  constexpr int G = 8;
-  __shared__ double red[G][8];
   const int64_t chunk = (n + gridDim.x - 1) / gridDim.x;
   const int64_t lo = blockIdx.x * chunk;
   const int64_t hi = lo + chunk < n ? lo + chunk : n;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int k0 = 0; k0 < nvec; k0 += G) {
-    const int ng = nvec - k0 < G ? nvec - k0 : G;
-    double s[G];
-#pragma unroll
-    for (int g = 0; g < G; ++g) s[g] = 0.0;
-    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-      const double wi = w[i];
-#pragma unroll
-      for (int g = 0; g < G; ++g)
-        if (g < ng) s[g] += V[(int64_t)(k0 + g) * n + i] * wi;
-    }
-#pragma unroll
-    for (int g = 0; g < G; ++g) {
-      const double t = warp_sum(s[g]);
-      if (lane == 0) red[g][wid] = t;
-    }
-    __syncthreads();
-    if (wid == 0) {
-#pragma unroll
-      for (int g = 0; g < G; ++g) {
-        double t = lane < 8 ? red[g][lane] : 0.0;
-        t = warp_sum(t);
-        if (lane == 0 && g < ng) partial[blockIdx.x * nvec + k0 + g] = t;
-      }
-    }
-    __syncthreads();
-  }
+  block_dots_group(
+      nvec, [&](int k) { return V + (int64_t)k * n; }, w, lo, hi,
+      [&](int k0) { return partial + (int64_t)blockIdx.x * nvec + k0; });
 }
 
 __global__ void k_reduce_partials(const double* __restrict__ partial, int nvec, int nblk, double* __restrict__ out) {
@@ -74,13 +40,28 @@ __global__ void k_reduce_partials(const double* __restrict__ partial, int nvec, 
 }
 
 
-// w += sum_k c_k V_k
+// w += sum_k c_k V_k (one element per thread; any n)
 __global__ void k_multiaxpy(const double* __restrict__ V, int nvec, int64_t n, Coefs c, double* __restrict__ w) {
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   double acc = w[i];
   for (int k = 0; k < nvec; ++k) acc += c.c[k] * V[(int64_t)k * n + i];
   w[i] = acc;
+}
+
+// the same over element pairs (n even, V and w 16-byte aligned): 16-byte loads
+__global__ void k_multiaxpy2(const double* __restrict__ V, int nvec, int64_t n, Coefs c, double* __restrict__ w) {
+  int64_t i2 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (2 * i2 >= n) return;
+  multiaxpy_pair(V, nvec, n, c.c, w, i2);
+}
+
+static void launch_multiaxpy(dg_mesh* m, const double* V, int nvec, int64_t n, const Coefs& c, double* w,
+                             cudaStream_t st) {
+  if (n % 2 == 0 && ((uintptr_t)w & 15) == 0 && ((uintptr_t)V & 15) == 0)
+    DG_RUN(m, K_MULTIAXPY, st, k_multiaxpy2<<<grid_for(n / 2, 256), 256, 0, st>>>(V, nvec, n, c, w));
+  else
+    DG_RUN(m, K_MULTIAXPY, st, k_multiaxpy<<<grid_for(n, 256), 256, 0, st>>>(V, nvec, n, c, w));
 }
 
 __global__ void k_axpby(int64_t n, double a, const double* x, double b, const double* y, double* z) {
@@ -206,7 +187,7 @@ int ensure_red(dg_mesh* m, Red* r) {
 // host <- V[0..nvec)^T w  (synchronises the stream)
 static int dots(dg_mesh* m, const Red& r, const double* V, int nvec, int64_t n, const double* w,
                 double* host, cudaStream_t st) {
-  DG_RUN(m, K_MULTIDOT, st, k_multidot<<<RED_BLOCKS, 256, 0, st>>>(V, nvec, n, w, r.partial));
+  DG_RUN(m, K_MULTIDOT, st, k_multidot<<<dim3(RED_BLOCKS, (nvec + 7) / 8), 256, 0, st>>>(V, nvec, n, w, r.partial));
   DG_RUN(m, K_REDUCE, st, k_reduce_partials<<<nvec, 256, 0, st>>>(r.partial, nvec, RED_BLOCKS, r.out));
   DG_LAUNCH_CHECK("reduction");
   DG_CUDA(cudaMemcpyAsync(host, r.out, sizeof(double) * nvec, cudaMemcpyDeviceToHost, st));
@@ -298,7 +279,7 @@ static int gmres(dg_mesh* m, const Vmult& A, const double* b, double* x, double 
         proj += h1[k] * h1[k];
         Hij(k, j) = h1[k];
       }
-      DG_RUN(m, K_MULTIAXPY, st, k_multiaxpy<<<gb, 256, 0, st>>>(V, j + 1, n, c, w));
+      launch_multiaxpy(m, V, j + 1, n, c, w, st);
       double w2 = h1[j + 1] - proj;
       if (!(w2 > 1e-6 * h1[j + 1])) {
         if ((rc = dots(m, red, V, j + 2, n, w, h2.data(), st)) != DG_OK) return rc;
@@ -308,7 +289,7 @@ static int gmres(dg_mesh* m, const Vmult& A, const double* b, double* x, double 
           proj += h2[k] * h2[k];
           Hij(k, j) += h2[k];
         }
-        DG_RUN(m, K_MULTIAXPY, st, k_multiaxpy<<<gb, 256, 0, st>>>(V, j + 1, n, c, w));
+        launch_multiaxpy(m, V, j + 1, n, c, w, st);
         w2 = h2[j + 1] - proj;
       }
       if (w2 < 0.0) w2 = 0.0;
@@ -342,7 +323,7 @@ static int gmres(dg_mesh* m, const Vmult& A, const double* b, double* x, double 
     }
     Coefs c;
     for (int k = 0; k < jused; ++k) c.c[k] = y[k];
-    DG_RUN(m, K_MULTIAXPY, st, k_multiaxpy<<<gb, 256, 0, st>>>(V, jused, n, c, x));
+    launch_multiaxpy(m, V, jused, n, c, x, st);
     DG_LAUNCH_CHECK("gmres update");
   }
 }

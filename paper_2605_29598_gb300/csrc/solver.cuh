@@ -9,7 +9,7 @@
 
 namespace dg {
 
-constexpr int RED_BLOCKS = 1024;   // partial sums per reduction (fixed order)
+constexpr int RED_BLOCKS = 608;    // partial sums per reduction (fixed order): 4 blocks per SM
 constexpr int MAX_RESTART = 64;
 
 struct Coefs {
@@ -72,6 +72,97 @@ struct Ark2 {
     }
   }
 };
+
+// Block-partial dot products v_k . w for the NG vectors vec[0..NG) over
+// the block's element range [lo, hi): each thread sums its elements in
+// order, warps reduce by shuffles, the first warp adds the 8 warp sums (a
+// fixed order, so results are deterministic).  Exactly NG FP64 FMAs per
+// element: on GB300 these dot products are bound by the FP64 pipe, not by
+// HBM, so no padded group slot is computed.  Block of 256 threads.
+template <int NG>
+__device__ __forceinline__ void block_dots(const double* const* vec, const double* __restrict__ w, int64_t lo,
+                                           int64_t hi, double (*red)[8], double* __restrict__ out) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const double* p[NG];
+#pragma unroll
+  for (int g = 0; g < NG; ++g) p[g] = vec[g];
+  double s[NG];
+#pragma unroll
+  for (int g = 0; g < NG; ++g) s[g] = 0.0;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+    const double wi = w[i];
+#pragma unroll
+    for (int g = 0; g < NG; ++g) s[g] += p[g][i] * wi;
+  }
+#pragma unroll
+  for (int g = 0; g < NG; ++g) {
+    double t = s[g];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) red[g][wid] = t;
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+      double t = lane < 8 ? red[g][lane] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) out[g] = t;
+    }
+  }
+  __syncthreads();
+}
+
+// the group of up to 8 vectors starting at k0 = 8 blockIdx.y (one group per
+// block row of the grid); vec(k) gives the k-th vector, out(k0) the slots
+template <typename VecOf, typename OutOf>
+__device__ __forceinline__ void block_dots_group(int nvec, VecOf vec_of, const double* __restrict__ w, int64_t lo,
+                                                 int64_t hi, OutOf out_of) {
+  __shared__ double red[8][8];
+  const int k0 = 8 * blockIdx.y;
+  if (k0 < nvec) {
+    const int ng = nvec - k0 < 8 ? nvec - k0 : 8;
+    const double* vec[8];
+#pragma unroll
+    for (int g = 0; g < 8; ++g) vec[g] = vec_of(k0 + (g < ng ? g : 0));
+    double* out = out_of(k0);
+    switch (ng) {
+      case 8: block_dots<8>(vec, w, lo, hi, red, out); break;
+      case 7: block_dots<7>(vec, w, lo, hi, red, out); break;
+      case 6: block_dots<6>(vec, w, lo, hi, red, out); break;
+      case 5: block_dots<5>(vec, w, lo, hi, red, out); break;
+      case 4: block_dots<4>(vec, w, lo, hi, red, out); break;
+      case 3: block_dots<3>(vec, w, lo, hi, red, out); break;
+      case 2: block_dots<2>(vec, w, lo, hi, red, out); break;
+      default: block_dots<1>(vec, w, lo, hi, red, out); break;
+    }
+  }
+}
+
+// w += sum_k c[k] V_k over element pairs (n even, V 16-byte aligned)
+__device__ __forceinline__ void multiaxpy_pair(const double* __restrict__ V, int nvec, int64_t n,
+                                               const double* __restrict__ c, double* __restrict__ w,
+                                               int64_t i2) {
+  double2 acc = reinterpret_cast<double2*>(w)[i2];
+  int k = 0;
+  for (; k + 4 <= nvec; k += 4) {
+    double2 v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) v[u] = reinterpret_cast<const double2*>(V + (int64_t)(k + u) * n)[i2];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      acc.x += c[k + u] * v[u].x;
+      acc.y += c[k + u] * v[u].y;
+    }
+  }
+  for (; k < nvec; ++k) {
+    const double2 v = reinterpret_cast<const double2*>(V + (int64_t)k * n)[i2];
+    acc.x += c[k] * v.x;
+    acc.y += c[k] * v.y;
+  }
+  reinterpret_cast<double2*>(w)[i2] = acc;
+}
 
 __global__ void k_multidot(const double* __restrict__ V, int nvec, int64_t n, const double* __restrict__ w,
                            double* __restrict__ partial);
