@@ -56,33 +56,40 @@ def peaks():
 # derived in the design notes (kernel table).
 # ----------------------------------------------------------------------------
 
-def work_model(dim, n, N, S, nF):
+def work_model(dim, n, N, S, nF, nnz=None):
+    """FP64 flops per launch.  nnz: nonzero metric terms K_ab per node (d^2,
+    or 5 in 3D / 3 in 2D on terrain-following meshes, where the kernels skip
+    the exact zeros); per pressure component b the number of directions a
+    with K_ab != 0 sums to nnz."""
     d = dim
+    nnz = d * d if nnz is None else nnz
     return {
-        # sum_{b} sum_a (x K_ab) contraction + lift of d+1 fields + pointwise
-        "volume_grad": N * (d * d + 2 * d * d * n + 2 * 2 * d * (d + 1) + 20),
+        # sum_b sum_{a: K_ab != 0} (x K_ab) contraction + lift of d+1 fields + pointwise
+        "volume_grad": N * (nnz + 2 * nnz * n + 2 * 2 * d * (d + 1) + 20),
         # h rho K w, d contractions, lift of 1 field, update
-        "volume_div": N * (d * (2 * d + 1) + 2 * d * n + 2 * 2 * d + 6),
-        # 9 flux fields x d contractions, contravariant velocity, lift of 9 fields
-        "volume_explicit": N * (2 * d * d + 9 * d + 2 * 9 * d * n + 2 * 2 * d * 9 + 30),
+        "volume_div": N * (2 * nnz + d + 2 * d * n + 2 * 2 * d + 6),
+        # K u, 6 flux fields x d contractions + 3 pressure fields x their
+        # nonzero directions, lift of 9 fields
+        "volume_explicit": N * (2 * nnz + 9 * d + 2 * (6 * d + nnz) * n + 2 * 2 * d * 9 + 30),
         "face_explicit": nF * 90,
         "face_grad": nF * (2 + d + 3),
         "face_div": nF * (4 * d + 4),
     }
 
 
-# DRAM bytes per node of one launch, from an ncu capture of the unchanged
-# kernel (profiles/volume_grad_hill3d_30x30x20_r3_fp64.md: 189.1 MB over
-# 1 152 000 nodes), scaled to a launch by the nodes it processes.
-NCU_TRAFFIC_B_PER_NODE = {"volume_grad": 189.1e6 / 1152000}
+# DRAM bytes per node of one launch, from an ncu capture of the current
+# kernel on the 30 x 30 x 20 hill (1 152 000 nodes), scaled to a launch by
+# the nodes it processes; empty until that capture is taken.
+NCU_TRAFFIC_B_PER_NODE = {}
 
 
-def bytes_model(dim, n, N, S, nF):
+def bytes_model(dim, n, N, S, nF, nnz=None):
     d = dim
+    nnz = d * d if nnz is None else nnz
     return {
-        "volume_grad": N * 8 * (1 + d * d + 1 + 1 + d + 1) + S * 8 * (d + 1),
-        "volume_div": N * 8 * (d + 1 + d * d + 1 + 1 + 1) + S * 8,
-        "volume_explicit": N * 8 * (5 + d * d + 1 + 9) + S * 8 * 9,
+        "volume_grad": N * 8 * (1 + nnz + 1 + 1 + d + 1) + S * 8 * (d + 1),
+        "volume_div": N * 8 * (d + 1 + nnz + 1 + 1 + 1) + S * 8,
+        "volume_explicit": N * 8 * (5 + nnz + 1 + 9) + S * 8 * 9,
     }
 
 
@@ -542,8 +549,9 @@ def gpu_main(args):
 
     # roofline of the dominant class
     pk, src = peaks()
+    nnz = (5 if st.dim == 3 else 3) if st.terrain_following else st.dim * st.dim
     work = work_model(st.dim, st.n1d, N, N // st.nodes_per_elem * 2 * st.dim * st.n1d ** (st.dim - 1),
-                      st.n_face_points)
+                      st.n_face_points, nnz)
     launches, timed_launches, tms = prof[dominant]
     roof = None
     if timed_launches and dominant in work:
@@ -557,7 +565,8 @@ def gpu_main(args):
                             else None),
                 "algorithmic_bytes_per_launch": bytes_model(
                     st.dim, st.n1d, N, st.n_elem * 2 * st.dim * st.n1d ** (st.dim - 1),
-                    st.n_face_points).get(dominant),
+                    st.n_face_points, nnz).get(dominant),
+                "nonzero_metric_terms_per_node": nnz,
                 "peak_source": "GB300 nominal FP64 (recipe table); probe measured 1.20",
                 "launches": timed_launches, "ms_per_launch": per_launch_ms,
                 "algorithmic_flops_per_launch": flops}

@@ -104,6 +104,9 @@ typedef struct {
   int64_t workspace_bytes;   /* library-owned device memory held now */
   int tile_fp64[3];          /* cells-per-block multipliers (1, 2, 4) of the */
   int tile_fp32[3];          /* explicit, gradient and divergence cell kernels */
+  int terrain_following;     /* 1: every cell has x = x(xi_1) (and y = y(xi_2)),
+                                so the cell kernels skip the metric terms that
+                                vanish exactly (not in the paper) */
 } dg_mesh_stats;
 int dg_mesh_info(const dg_mesh* mesh, dg_mesh_stats* out);
 

@@ -143,6 +143,11 @@ struct dg_mesh {
   // cells-per-block multiplier of the cell kernels, per class (FP64, FP32)
   int tile[dg::K_COUNT] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};
   int tile32[dg::K_COUNT] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};
+  // every cell terrain-following: x depends on xi_1 only and y on xi_2 only
+  // (rectangular footprints, any vertical map), so the metric terms
+  // K_ab = w det(J) (J^-1)_ab vanish exactly for (a, b) = (1, y), (1, z),
+  // (2, x), (2, z) (3D) or (1, z) (2D) and the cell kernels skip them
+  bool terrain = false;
   int64_t workspace_bytes() const;
   // every workspace buffer, for accounting, release and graph capture checks
   static constexpr int kBufs = 27;

@@ -45,6 +45,7 @@ inline CellGeo<T> cell_geo(const dg_mesh* m) {
     g.x[k] = (T)m->tab.x[k];
     g.w[k] = (T)m->tab.w[k];
   }
+  g.terrain = m->terrain ? 1 : 0;
   return g;
 }
 template <>
@@ -57,6 +58,7 @@ inline CellGeo<float> cell_geo<float>(const dg_mesh* m) {
     g.x[k] = (float)m->tab.x[k];
     g.w[k] = (float)m->tab.w[k];
   }
+  g.terrain = m->terrain ? 1 : 0;
   return g;
 }
 // Explicit operator in perturbation form about the mesh's background (FP32

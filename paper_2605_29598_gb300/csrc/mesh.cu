@@ -559,6 +559,19 @@ int dg_mesh_create(dg_ctx* ctx, const dg_mesh_desc* d, dg_mesh** out) {
   ALLOC(m->hp_code, nH);
   ALLOC(m->hc_slot, nHC);
   UPLOAD(m->verts, d->vertices, E * (dim << dim));
+  {
+    // terrain-following test: horizontal coordinate c of every corner equals
+    // that of the corner with only bit c kept (exact comparison)
+    bool tf = true;
+    const int nc = 1 << dim;
+    for (int64_t e = 0; e < E && tf; ++e) {
+      const double* v = d->vertices + e * nc * dim;
+      for (int c = 0; c < dim - 1 && tf; ++c)
+        for (int k = 0; k < nc && tf; ++k)
+          if (v[k * dim + c] != v[(k & (1 << c)) * dim + c]) tf = false;
+    }
+    m->terrain = tf;
+  }
   UPLOAD(m->fp_minus, fpm.data(), nF);
   UPLOAD(m->fp_plus, fpp.data(), nF);
   UPLOAD(m->hp_cslot, hpc.data(), nH);
@@ -648,6 +661,7 @@ int dg_mesh_info(const dg_mesh* m, dg_mesh_stats* o) {
     o->tile_fp64[k] = m->tile[kinds[k]];
     o->tile_fp32[k] = m->tile32[kinds[k]];
   }
+  o->terrain_following = m->terrain ? 1 : 0;
   return DG_OK;
 }
 

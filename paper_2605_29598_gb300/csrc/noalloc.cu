@@ -67,7 +67,7 @@ static int explicit_with_scratch(dg_mesh* m, const PhysK& ph, const double* q, d
            k_hang_gather<T, DIM, N, 9><<<grid_for(m->nHC * CS::NFP, 128), 128, 0, st>>>(ft, hbuf, slot, tb));
   DG_RUN(m, K_VOL_EXPLICIT, st,
          k_volume_explicit<T, DIM, N><<<grid_for(m->E, CS::EPB), CS::THREADS, 0, st>>>(
-             q, m->K, m->invM, slot, m->E, m->S, tb, ph, fns, fs));
+             q, m->K, m->invM, slot, m->E, m->S, tb, ph, fns, fs, 0));
   DG_LAUNCH_CHECK("explicit operator (no-alloc)");
   return DG_OK;
 }

@@ -31,7 +31,8 @@ int Engine<T, DIM, N>::explicit_rates(dg_mesh* m, const PhysK& ph, const T* q, T
           DG_RUN(m, K_VOL_EXPLICIT, st,
                  k_volume_explicit<T, DIM, N, M_><<<grid_for(m->E, CellShape<DIM, N, M_>::EPB),
                                                     CellShape<DIM, N, M_>::THREADS, 0, st>>>(
-                     q, met_K<T>(m), met_invM<T>(m), slot, m->E, m->S, tb, ph, fns, fs)));
+                     q, met_K<T>(m), met_invM<T>(m), slot, m->E, m->S, tb, ph, fns, fs,
+                     m->terrain ? 1 : 0)));
   DG_LAUNCH_CHECK("explicit operator");
   return DG_OK;
 }

@@ -227,13 +227,32 @@ template <int DIM, int N, int M = 1> struct CellShape {
   static constexpr int NF = 2 * DIM;
 };
 
+// metric terms that vanish on terrain-following cells (x = x(xi_1), y =
+// y(xi_2)): reference direction a, physical component b
+template <int DIM>
+__host__ __device__ constexpr bool kzero(int a, int b) {
+  return DIM == 3 ? ((a == 0 && b != 0) || (a == 1 && b != 1)) : (a == 0 && b == 1);
+}
+
+// reference directions a with K_ab != 0 (all of them unless terrain-following)
+template <int DIM>
+__device__ __forceinline__ int amask_of(int terrain, int b) {
+  int msk = 0;
+#pragma unroll
+  for (int a = 0; a < DIM; ++a)
+    if (!(terrain && kzero<DIM>(a, b))) msk |= 1 << a;
+  return msk;
+}
+
 // sum_a sum_k D[k][i_a] * sm[a][line(i, a, k)]  (test-gradient contraction)
+// (directions a outside amask are skipped: their fluxes are zero)
 template <typename T, int DIM, int N>
 __device__ __forceinline__ T contract(const Tables<T>& tb, const T (*sm)[ipow(N, DIM)], int i,
-                                      const int idx[3]) {
+                                      const int idx[3], int amask = (1 << DIM) - 1) {
   T acc = 0;
 #pragma unroll
   for (int a = 0; a < DIM; ++a) {
+    if (!((amask >> a) & 1)) continue;
     const int stride = a == 0 ? 1 : (a == 1 ? N : N * N);
     const int i0 = i - idx[a] * stride;
 #pragma unroll
@@ -271,7 +290,7 @@ template <typename T, int DIM, int N, int M = 1>
 __global__ void __launch_bounds__(CellShape<DIM, N, M>::THREADS)
 k_volume_explicit(const T* __restrict__ q, const T* __restrict__ Kg, const T* __restrict__ invMg,
                   const T* __restrict__ slot, int64_t E, int64_t S, Tables<T> tb, PhysK ph,
-                  T* __restrict__ fns, T* __restrict__ fs) {
+                  T* __restrict__ fns, T* __restrict__ fs, int terrain) {
   using CS = CellShape<DIM, N, M>;
   constexpr int NP = CS::NP, EPB = CS::EPB;
   __shared__ T sm[EPB][DIM][NP];
@@ -291,7 +310,8 @@ k_volume_explicit(const T* __restrict__ q, const T* __restrict__ Kg, const T* __
 #pragma unroll
     for (int a = 0; a < DIM; ++a)
 #pragma unroll
-      for (int b = 0; b < DIM; ++b) K[a][b] = __ldg(Kg + (a * DIM + b) * Nn + node);
+      for (int b = 0; b < DIM; ++b)
+        K[a][b] = (terrain && kzero<DIM>(a, b)) ? (T)0 : __ldg(Kg + (a * DIM + b) * Nn + node);
     iM = __ldg(invMg + node);
   } else {
 #pragma unroll
@@ -310,7 +330,8 @@ k_volume_explicit(const T* __restrict__ q, const T* __restrict__ Kg, const T* __
   for (int a = 0; a < DIM; ++a) {
     ut[a] = 0;
 #pragma unroll
-    for (int b = 0; b < DIM; ++b) ut[a] += K[a][b] * u[comp_of<DIM>(b)];
+    for (int b = 0; b < DIM; ++b)
+      if (!(terrain && kzero<DIM>(a, b))) ut[a] += K[a][b] * u[comp_of<DIM>(b)];
   }
   T r[9];
   // flux fields: 0 rho, 1-3 m_c, 4 rho kappa (advective); 5-7 p e_c, 8 h rho (stiff)
@@ -321,21 +342,22 @@ k_volume_explicit(const T* __restrict__ q, const T* __restrict__ Kg, const T* __
       r[fld] = 0;
       continue;
     }
+    // pressure fluxes p K_ab e_b: directions with K_ab = 0 drop out
+    const int pb = DIM == 3 ? fld - 5 : (fld == 5 ? 0 : 1);
+    const int msk = (fld >= 5 && fld <= 7) ? amask_of<DIM>(terrain, pb) : (1 << DIM) - 1;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
+      if (!((msk >> a) & 1)) continue;
       T v;
       if (fld == 0) v = rho * ut[a];
       else if (fld <= 3) v = m[fld - 1] * ut[a];
       else if (fld == 4) v = rk * ut[a];
-      else if (fld <= 7) {
-        const int c = fld - 5;
-        const int b = DIM == 3 ? c : (c == 0 ? 0 : 1);
-        v = p * K[a][b];
-      } else v = hr * ut[a];
+      else if (fld <= 7) v = p * K[a][pb];
+      else v = hr * ut[a];
       sm[le][a][i] = v;
     }
     __syncthreads();
-    r[fld] = contract<T, DIM, N>(tb, sm[le], i, idx);
+    r[fld] = contract<T, DIM, N>(tb, sm[le], i, idx, msk);
     __syncthreads();
   }
   if (!active) return;
@@ -462,7 +484,9 @@ struct CellGeo {
   const T* invM;
   const T* lv;          // n_elem x 2^d x d corner offsets, or null
   T x[MAX_N], w[MAX_N]; // Gauss-Legendre nodes and weights on [0, 1]
+  int terrain;          // every cell terrain-following: K_ab = 0 where kzero(a, b)
 };
+
 
 template <typename T, int DIM, int N>
 __device__ __forceinline__ void node_metric(const CellGeo<T>& g, int64_t e, int64_t node, int64_t Nn,
@@ -471,7 +495,8 @@ __device__ __forceinline__ void node_metric(const CellGeo<T>& g, int64_t e, int6
 #pragma unroll
     for (int a = 0; a < DIM; ++a)
 #pragma unroll
-      for (int b = 0; b < DIM; ++b) K[a][b] = __ldg(g.K + (a * DIM + b) * Nn + node);
+      for (int b = 0; b < DIM; ++b)
+        K[a][b] = (g.terrain && kzero<DIM>(a, b)) ? (T)0 : __ldg(g.K + (a * DIM + b) * Nn + node);
     iM = __ldg(g.invM + node);
     return;
   }
@@ -552,10 +577,12 @@ k_volume_grad(const T* __restrict__ x, const T* __restrict__ irho, CellGeo<T> ge
   T r[DIM + 1];
 #pragma unroll
   for (int b = 0; b < DIM; ++b) {
+    const int msk = amask_of<DIM>(geo.terrain, b);
 #pragma unroll
-    for (int a = 0; a < DIM; ++a) sm[le][a][i] = active ? -xv * K[a][b] : (T)0;
+    for (int a = 0; a < DIM; ++a)
+      if ((msk >> a) & 1) sm[le][a][i] = active ? -xv * K[a][b] : (T)0;
     __syncthreads();
-    r[b] = contract<T, DIM, N>(tb, sm[le], i, idx);
+    r[b] = contract<T, DIM, N>(tb, sm[le], i, idx, msk);
     __syncthreads();
   }
   r[DIM] = 0;
@@ -627,7 +654,8 @@ k_volume_div(Fields<T> wv, const T* __restrict__ plag, CellGeo<T> geo,
     for (int a = 0; a < DIM; ++a) {
       T v = 0;
 #pragma unroll
-      for (int b = 0; b < DIM; ++b) v += K[a][b] * wl[b];
+      for (int b = 0; b < DIM; ++b)
+        if (!(geo.terrain && kzero<DIM>(a, b))) v += K[a][b] * wl[b];
       sm[le][a][i] = -hr * v;
     }
   } else {

@@ -231,6 +231,7 @@ k_volume_explicit_pert(const float* __restrict__ qp, const float* __restrict__ q
     mtp[a] = 0.f;
 #pragma unroll
     for (int b = 0; b < DIM; ++b) {
+      if (geo.terrain && kzero<DIM>(a, b)) continue;
       const int c = comp_of<DIM>(b);
       utb[a] += K[a][b] * P.ub[c];
       utp[a] += K[a][b] * P.up[c];
@@ -244,21 +245,21 @@ k_volume_explicit_pert(const float* __restrict__ qp, const float* __restrict__ q
       r[fld] = 0.f;
       continue;
     }
+    const int pb = DIM == 3 ? fld - 5 : (fld == 5 ? 0 : 1);
+    const int msk = (fld >= 5 && fld <= 7) ? amask_of<DIM>(geo.terrain, pb) : (1 << DIM) - 1;
 #pragma unroll
     for (int a = 0; a < DIM; ++a) {
+      if (!((msk >> a) & 1)) continue;
       float v;
       if (fld == 0) v = mtp[a];
       else if (fld <= 3) v = b5[fld] * utp[a] + p5[fld] * (utb[a] + utp[a]);
       else if (fld == 4) v = P.rkb * utp[a] + P.rkp * (utb[a] + utp[a]);
-      else if (fld <= 7) {
-        const int c = fld - 5;
-        const int b = DIM == 3 ? c : (c == 0 ? 0 : 1);
-        v = P.pp * K[a][b];
-      } else v = hb * utp[a] + hp * (utb[a] + utp[a]);
+      else if (fld <= 7) v = P.pp * K[a][pb];
+      else v = hb * utp[a] + hp * (utb[a] + utp[a]);
       sm[le][a][i] = v;
     }
     __syncthreads();
-    r[fld] = contract<float, DIM, N>(tb, sm[le], i, idx);
+    r[fld] = contract<float, DIM, N>(tb, sm[le], i, idx, msk);
     __syncthreads();
   }
   if (!active) return;

@@ -43,7 +43,7 @@ class MeshStats(C.Structure):
                 ("nodes_per_elem", C.c_int), ("n_elem", C.c_int64), ("n_nodes", C.c_int64),
                 ("n_face_points", C.c_int64), ("n_hang_points", C.c_int64),
                 ("workspace_bytes", C.c_int64), ("tile_fp64", C.c_int * 3),
-                ("tile_fp32", C.c_int * 3)]
+                ("tile_fp32", C.c_int * 3), ("terrain_following", C.c_int)]
 
 
 class Phys(C.Structure):

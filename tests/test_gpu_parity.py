@@ -45,6 +45,19 @@ def from_dev(t, shape):
     return t.detach().cpu().numpy().reshape(shape)
 
 
+def sheared(mesh, sx, sy=0.0):
+    """The mesh with x += sx z (and y += sy z): cells are no longer
+    terrain-following (x depends on the vertical reference coordinate), so
+    the cell kernels take their general-metric path.  Periodic and wall
+    faces stay matched."""
+    v = mesh.vertices.copy()
+    v[..., 0] += sx * v[..., -1]
+    if mesh.dim == 3:
+        v[..., 1] += sy * v[..., -1]
+    return I.Mesh(dim=mesh.dim, vertices=v, int_faces=mesh.int_faces, hang_faces=mesh.hang_faces,
+                  bdry_faces=mesh.bdry_faces, level=mesh.level, name=mesh.name + "_sheared")
+
+
 CASES = {
     # name: (mesh builder, degree)
     "2d_r1": (lambda: I.box_mesh((7, 3), (7e3, 3e3)), 1),
@@ -56,7 +69,21 @@ CASES = {
                                          hill=dict(h0=300.0, a_c=1e3, xc=2.5e3, yc=2e3),
                                          refine_level=lambda c: 1 if c[0] < 2e3 and c[2] < 1e3 else 0), 3),
     "3d_r2": (lambda: I.box_mesh((3, 5, 2), (3e3, 5e3, 2e3)), 2),
+    "2d_r2_nc_sheared": (lambda: sheared(I.box_mesh((9, 4), (9e3, 4e3),
+                                                    refine_level=lambda c: 1 if 2e3 < c[0] < 5e3 else 0), 0.3), 2),
+    "3d_r3_hill_nc_sheared": (lambda: sheared(I.box_mesh((5, 4, 3), (5e3, 4e3, 3e3),
+                                                         hill=dict(h0=300.0, a_c=1e3, xc=2.5e3, yc=2e3),
+                                                         refine_level=lambda c: 1 if c[0] < 2e3 and c[2] < 1e3
+                                                         else 0), 0.2, -0.15), 3),
 }
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_terrain_following_detection(D, ctx, name):
+    """Box and Gal-Chen meshes take the terrain-following kernels (metric
+    terms that vanish exactly are skipped); sheared meshes the general ones."""
+    mesh, disc, gm, _ = make_case(D, ctx, name)
+    assert gm.stats().terrain_following == (0 if name.endswith("sheared") else 1)
 
 
 def make_case(D, ctx, name, seed=0):
