@@ -12,6 +12,8 @@
 // so no slot buffer is ever cleared and no atomics are used.
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace dg {
@@ -488,10 +490,25 @@ struct CellGeo {
 };
 
 
+// Shared copy of the Gauss-Legendre nodes and weights for the FP32 metric
+// recomputation (one thread writes, after the block's first barrier all read).
+template <typename T, int N>
+__device__ __forceinline__ void stage_nodes(const CellGeo<T>& g, T* sxw) {
+  if (std::is_same<T, float>::value && threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      sxw[k] = g.x[k];
+      sxw[N + k] = g.w[k];
+    }
+  }
+}
+
 template <typename T, int DIM, int N>
 __device__ __forceinline__ void node_metric(const CellGeo<T>& g, int64_t e, int64_t node, int64_t Nn,
-                                            const int idx[3], T K[DIM][DIM], T& iM) {
-  if (g.lv == nullptr) {
+                                            const int idx[3], T K[DIM][DIM], T& iM, const T* sxw = nullptr) {
+  // FP64 always loads the stored metric (the FP64 geometry has no corner
+  // offsets); only FP32 recomputes it
+  if (!std::is_same<T, float>::value || g.lv == nullptr) {
 #pragma unroll
     for (int a = 0; a < DIM; ++a)
 #pragma unroll
@@ -504,8 +521,10 @@ __device__ __forceinline__ void node_metric(const CellGeo<T>& g, int64_t e, int6
   T xi[3], wq = 1;
 #pragma unroll
   for (int a = 0; a < DIM; ++a) {
-    xi[a] = g.x[idx[a]];
-    wq *= g.w[idx[a]];
+    // nodes and weights from the block's shared copy (sxw[0..N), sxw[N..2N)):
+    // indexing the parameter arrays per thread would copy them to local memory
+    xi[a] = sxw[idx[a]];
+    wq *= sxw[N + idx[a]];
   }
   T J[DIM][DIM];   // J[b][c] = d x_b / d xi_c
 #pragma unroll
@@ -572,8 +591,11 @@ k_volume_grad(const T* __restrict__ x, const T* __restrict__ irho, CellGeo<T> ge
   int idx[3];
   node_index<DIM, N>(i, idx);
   T xv = active ? __ldg(x + node) : (T)0;
+  __shared__ T sxw[2 * N];
+  stage_nodes<T, N>(geo, sxw);
+  if (std::is_same<T, float>::value) __syncthreads();
   T K[DIM][DIM], iM = 0;
-  if (active) node_metric<T, DIM, N>(geo, e, node, Nn, idx, K, iM);
+  if (active) node_metric<T, DIM, N>(geo, e, node, Nn, idx, K, iM, sxw);
   T r[DIM + 1];
 #pragma unroll
   for (int b = 0; b < DIM; ++b) {
@@ -642,10 +664,13 @@ k_volume_div(Fields<T> wv, const T* __restrict__ plag, CellGeo<T> geo,
   node_index<DIM, N>(i, idx);
   const T gam = kp<T>(ph.gamma, ph.gamma_f);
   const T gm1 = gam - 1;
+  __shared__ T sxw[2 * N];
+  stage_nodes<T, N>(geo, sxw);
+  if (std::is_same<T, float>::value) __syncthreads();
   T iM = 0;
   if (active) {
     T K[DIM][DIM];
-    node_metric<T, DIM, N>(geo, e, node, Nn, idx, K, iM);
+    node_metric<T, DIM, N>(geo, e, node, Nn, idx, K, iM, sxw);
     T hr = gam / gm1 * __ldg(plag + node);
     T wl[DIM];
 #pragma unroll

@@ -207,13 +207,16 @@ k_volume_explicit_pert(const float* __restrict__ qp, const float* __restrict__ q
   node_index<DIM, N>(i, idx);
   float b5[5] = {1.f, 0.f, 0.f, 0.f, 1.f}, p5[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
   float K[DIM][DIM], iM = 0.f;
+  __shared__ float sxw[2 * N];
+  stage_nodes<float, N>(geo, sxw);
+  __syncthreads();
   if (active) {
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
       b5[q] = __ldg(qb + q * Nn + node);
       p5[q] = __ldg(qp + q * Nn + node);
     }
-    node_metric<float, DIM, N>(geo, e, node, Nn, idx, K, iM);
+    node_metric<float, DIM, N>(geo, e, node, Nn, idx, K, iM, sxw);
   } else {
 #pragma unroll
     for (int a = 0; a < DIM; ++a)

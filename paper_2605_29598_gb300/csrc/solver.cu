@@ -82,7 +82,9 @@ __global__ void k_stage_predict(const double* __restrict__ q, int64_t n, StageCo
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n) return;
   double r = 0, m0 = 0, m1 = 0, m2 = 0, e = 0;
-  for (int s = 0; s < c.nst; ++s) {
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {   // static indices into c (no local copy)
+    if (s >= c.nst) break;
     const double a = c.a[s], at = c.at[s];
     const double* F = c.fns[s];
     const double* G = c.fs[s];
@@ -131,7 +133,9 @@ __global__ void k_final_update(double* __restrict__ q, int64_t n, StageCoefs c, 
   int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n || (skip && *skip)) return;
   double acc[5] = {0, 0, 0, 0, 0};
-  for (int s = 0; s < c.nst; ++s) {
+#pragma unroll
+  for (int s = 0; s < 3; ++s) {   // static indices into c (no local copy)
+    if (s >= c.nst) break;
     const double b = c.a[s];
     const double* F = c.fns[s];
     const double* G = c.fs[s];
