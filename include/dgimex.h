@@ -157,6 +157,19 @@ int dg_apply_explicit(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* phys,
                       const double* q, double* f_ns, double* f_s, void* stream);
 
 /*
+ * Geostrophic imbalance (Section 4, planetary-scale inertia-gravity wave,
+ * eq. egeo): E_geo = domain mean of |(1/rho) dp/dx - f v|, with the
+ * scheme's own FP64 discrete pressure gradient and Coriolis term (the stiff
+ * x-momentum rate of dg_apply_explicit, divided by rho at each node) and
+ * the volume quadrature weights w det J; the domain measure is the sum of
+ * the weights (x_max z_max on a flat box).  In 3D the x-momentum balance is
+ * averaged over the volume.  q: device 5 x N; *e_geo: host.  Synchronises
+ * `stream`.  phys->precision is ignored (always FP64).
+ */
+int dg_geostrophic_error(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* phys,
+                         const double* q, double* e_geo, void* stream);
+
+/*
  * Background for the FP32 explicit operator (DG_MIXED_EXPLICIT).  q_bg
  * (device, 5 x N, FP64, e.g. the balanced hydrostatic state) is copied; its
  * rates F(q_bg) are computed once in FP64 (again whenever gamma, g, f or

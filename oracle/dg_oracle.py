@@ -443,6 +443,22 @@ def explicit_rates(disc, q, phys):
     return disc.mass_solve(r_ns), disc.mass_solve(r_s)
 
 
+def geostrophic_error(disc, q, phys):
+    """Geostrophic imbalance E_geo of Section 4 (planetary-scale wave, eq.
+    egeo): the domain mean of |(1/rho) dp/dx - f v|.
+
+    The pressure gradient and the Coriolis term are the scheme's own: the
+    stiff x-momentum rate F_S = -dp/dx + f rho v of the explicit operator
+    (weak DG gradient with centred face pressures, M^{-1} applied), so the
+    integrand is |F_S / rho|.  The integral is the volume quadrature
+    sum_q wJ_q |.| of the values interpolated to the quadrature points.
+    READING: the domain measure sum_q wJ_q replaces x_max z_max (equal on a
+    flat box); in 3D the same x-momentum balance is averaged over the volume."""
+    _, Fs = explicit_rates(disc, q, phys)
+    ratio = disc.at_quad(Fs[1]) / disc.at_quad(q[0])
+    return float(np.sum(disc.wJ * np.abs(ratio)) / np.sum(disc.wJ))
+
+
 # ----------------------------------------------------------------------------
 # Implicit (acoustic) operators of one stage: the paper's matrices
 # ----------------------------------------------------------------------------

@@ -526,6 +526,51 @@ __device__ __forceinline__ void node_metric(const CellGeo<T>& g, int64_t e, int6
     xi[a] = sxw[idx[a]];
     wq *= sxw[N + idx[a]];
   }
+  if (g.terrain) {
+    // x = x0 + dx xi_1 (and y = y0 + dy xi_2): only the vertical row of J
+    // varies; dx, dy are the offsets of corners 1 and 2
+    T Jz[DIM];
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) Jz[c] = 0;
+#pragma unroll
+    for (int v = 1; v < (1 << DIM); ++v) {
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) {
+        T wgt = 1;
+#pragma unroll
+        for (int a = 0; a < DIM; ++a) {
+          const int bit = (v >> a) & 1;
+          if (a == c) wgt *= bit ? (T)1 : (T)-1;
+          else wgt *= bit ? xi[a] : (T)1 - xi[a];
+        }
+        Jz[c] += wgt * __ldg(V + v * DIM + DIM - 1);
+      }
+    }
+    const T dx = __ldg(V + 1 * DIM + 0);
+    T det;
+    if (DIM == 2) {
+      K[0][0] = Jz[1];
+      K[0][1] = 0;
+      K[1][0] = -Jz[0];
+      K[1][1] = dx;
+      det = dx * Jz[1];
+    } else {
+      const T dy = __ldg(V + 2 * DIM + 1);
+      K[0][0] = dy * Jz[2];
+      K[1][1] = Jz[2] * dx;
+      K[2][0] = -(Jz[0] * dy);
+      K[2][1] = -(dx * Jz[1]);
+      K[2][2] = dx * dy;
+      K[0][1] = K[0][2] = K[1][0] = K[1][2] = 0;
+      det = dx * K[0][0];
+    }
+#pragma unroll
+    for (int a = 0; a < DIM; ++a)
+#pragma unroll
+      for (int b = 0; b < DIM; ++b) K[a][b] *= wq;
+    iM = 1 / (wq * det);
+    return;
+  }
   T J[DIM][DIM];   // J[b][c] = d x_b / d xi_c
 #pragma unroll
   for (int b = 0; b < DIM; ++b)

@@ -120,6 +120,8 @@ EXPORTS["dg_ensemble_get_state"] = (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C
 EXPORTS["dg_ensemble_step"] = (C.c_int, [C.c_void_p, C.POINTER(Phys), C.POINTER(C.c_double),
                                          C.POINTER(StepOpts), C.POINTER(StepInfo), C.c_void_p])
 EXPORTS["dg_mesh_autotune"] = (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p])
+EXPORTS["dg_geostrophic_error"] = (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Phys), C.c_void_p,
+                                              C.POINTER(C.c_double), C.c_void_p])
 EXPORTS["dg_mesh_set_background"] = (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Phys), C.c_void_p,
                                                 C.c_void_p])
 EXPORTS["dg_profile_begin"] = (C.c_int, [C.c_void_p, C.c_uint32])
@@ -233,6 +235,13 @@ class Mesh:
         self.n_elem = st.n_elem
         self.N = st.n_nodes
         self.Np = st.nodes_per_elem
+
+    def geostrophic_error(self, phys, q, stream=None):
+        """E_geo: domain mean of |(1/rho) dp/dx - f v| (scheme's own operators)."""
+        out = C.c_double()
+        _check(self.lib.dg_geostrophic_error(self.ctx.h, self.h, C.byref(phys), _ptr(q), C.byref(out),
+                                             _stream(stream)), "dg_geostrophic_error")
+        return out.value
 
     def set_background(self, phys, q_bg, stream=None):
         """Background state for the perturbation-form (mixed) explicit operator."""

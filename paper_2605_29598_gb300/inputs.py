@@ -301,6 +301,31 @@ def stratified_state(points, theta_ref=300.0, n_bv=0.01, wind=(0.0, 0.0, 0.0),
     return np.stack([rho, m[..., 0], m[..., 1], m[..., 2], E], axis=0)
 
 
+def isothermal_state(points, T0=250.0, ps=P_REF, bubble=None, g=GRAV, R=R_GAS, gamma=GAMMA):
+    """Isothermal hydrostatic atmosphere at rest (Section 4, inertia-gravity
+    wave): p0 = ps exp(-delta z), rho0 = rho_s exp(-delta z), delta = g/(R T0),
+    rho_s = ps/(R T0), u = 0.
+
+    bubble: dict(dT, xc, a, H): the Bretherton-transformed perturbation
+            T' = exp(delta z / 2) T_b, rho' = exp(-delta z / 2) rho_b, p' = 0,
+            T_b = dT exp(-(x - xc)^2 / a^2) sin(pi z / H),
+            rho_b = rho_s (-T_b / T0).
+    Returns (5, ...) conserved variables."""
+    pts = np.asarray(points, dtype=np.float64)
+    z = pts[..., -1]
+    x = pts[..., 0]
+    delta = g / (R * T0)
+    rho_s = ps / (R * T0)
+    p = ps * np.exp(-delta * z)
+    rho = rho_s * np.exp(-delta * z)
+    if bubble is not None:
+        tb = bubble["dT"] * np.exp(-((x - bubble["xc"]) / bubble["a"]) ** 2) * \
+            np.sin(math.pi * z / bubble["H"])
+        rho = rho + np.exp(-0.5 * delta * z) * rho_s * (-tb / T0)
+    zeros = np.zeros_like(rho)
+    return np.stack([rho, zeros, zeros, zeros, p / (gamma - 1.0)], axis=0)
+
+
 def perturb(state, rng, rel=1e-3):
     """Seeded multiplicative noise on every field (parity-test inputs).
 
@@ -316,6 +341,17 @@ def perturb(state, rng, rel=1e-3):
 # ----------------------------------------------------------------------------
 # Named workloads
 # ----------------------------------------------------------------------------
+
+def planetary_igw_case(nx=300, nz=20, r=4):
+    """Planetary-scale inertia-gravity wave (Section 4): 60 000 km x 10 km
+    x-z channel, periodic in x, walls in z, 300 x 20 cells, degree 4;
+    isothermal background at rest (T0 = 250 K, ps = 1e5 Pa), Bretherton
+    perturbation dT = 0.01 K, half-width a = 1000 km at x_c = 30 000 km,
+    H = 10 km; f = 1.03126e-4 1/s (45 degrees); dt = 10 s, 96 h."""
+    mesh = box_mesh((nx, nz), (60000e3, 10e3), name="planetary_igw")
+    params = dict(T0=250.0, ps=P_REF, bubble=dict(dT=0.01, xc=30000e3, a=1000e3, H=10e3))
+    return dict(mesh=mesh, degree=r, f=1.03126e-4, dt=10.0, hours=96.0, state_params=params)
+
 
 def igw2d_case(seed=0, nx=100, nz=5, r=2):
     """2D x-z rotating inertia-gravity wave: 300 km x 10 km periodic channel,

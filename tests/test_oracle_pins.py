@@ -420,3 +420,50 @@ def test_convergence_orders():
     et = [_wave_error(6, 4, dt, 8.0) for dt in (2.0, 1.0, 0.5)]
     eoc_t = [math.log2(et[i] / et[i + 1]) for i in range(2)]
     assert all(1.9 < e < 2.1 for e in eoc_t), eoc_t
+
+
+# ----------------------------------------------------------------------------
+# geostrophic imbalance E_geo (Section 4, planetary-scale wave)
+# ----------------------------------------------------------------------------
+
+def _linear_pressure_state(disc, a, rho0, v0, gamma=1.4):
+    pts = disc.node_points()
+    p = 9e4 + a * pts[..., 0]
+    q = np.zeros((5,) + pts.shape[:-1])
+    q[0] = rho0
+    q[2] = rho0 * v0
+    q[4] = p / (gamma - 1) + 0.5 * rho0 * v0 ** 2
+    return q
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_geostrophic_error_closed_form(d):
+    """Linear pressure p = p0 + a x with uniform rho and v on a flat box with
+    walls on every side (2D case with a 2:1 strip): the DG gradient of a
+    linear field is exact, so E_geo = |a / rho - f v| everywhere; with
+    f v = a / rho (geostrophic balance) it vanishes, which fixes the sign
+    of the Coriolis term and of the pressure gradient."""
+    if d == 2:
+        mesh = I.box_mesh((5, 3), (5e3, 3e3), periodic=(False, False),
+                          refine_level=lambda c: 1 if c[0] < 2e3 else 0)
+    else:
+        mesh = I.box_mesh((3, 2, 2), (3e3, 2e3, 2e3), periodic=(False, False, False))
+    disc = O.Discretisation(mesh, 2)
+    a, rho0, v0, f = 2e-3, 1.1, 7.0, 1.3e-4
+    # rounding scale: p0 = 9e4 Pa differentiated on 500 m cells
+    tol = 1e-14 * 9e4 / (rho0 * 500.0)
+    e = O.geostrophic_error(disc, _linear_pressure_state(disc, a, rho0, v0), O.Phys(f=f))
+    assert abs(e - abs(a / rho0 - f * v0)) <= tol
+    vb = a / (rho0 * f)
+    e_bal = O.geostrophic_error(disc, _linear_pressure_state(disc, a, rho0, vb), O.Phys(f=f))
+    assert e_bal <= tol
+
+
+def test_geostrophic_error_vanishes_for_layered_rest_state():
+    """p = p(z), v = 0 on a flat periodic box: no horizontal pressure
+    gradient and no Coriolis force, E_geo = 0 to round-off (relative to the
+    vertical gradient scale g)."""
+    mesh = I.box_mesh((6, 3), (6e3, 3e3))
+    disc = O.Discretisation(mesh, 3)
+    q = I.stratified_state(disc.node_points())
+    assert O.geostrophic_error(disc, q, O.Phys(f=1e-4)) <= 1e-12 * 9.81
