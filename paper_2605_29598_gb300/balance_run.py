@@ -19,6 +19,7 @@ def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     ap.add_argument("--hours", type=float, default=96.0)
     ap.add_argument("--every", type=float, default=6.0)
+    ap.add_argument("--dt", type=float, default=None, help="time step in s (default: the case's 10 s)")
     ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
     ap.add_argument("--host-loop", action="store_true", help="host-driven steps instead of the graph")
     ap.add_argument("--json", default=None, help="also write the table as JSON lines here")
@@ -39,7 +40,7 @@ def main(argv=None):
     opts = dict(picard_rtol=1e-10, picard_maxit=10, gmres_rtol=1e-10, gmres_restart=30,
                 gmres_maxit=1000, graph=not args.host_loop,
                 gmres_inner_rtol=1e-4 if args.precision == "mixed" else 0.0)
-    dt = case["dt"]
+    dt = case["dt"] if args.dt is None else args.dt
     steps_per_report = max(1, int(round(args.every * 3600.0 / dt)))
     n_reports = max(1, int(round(args.hours / args.every)))
     rows = []
@@ -48,7 +49,7 @@ def main(argv=None):
     def report(t_h, its, wall):
         e = mesh.geostrophic_error(phys, q)
         w = (q[3] / q[0]).abs().max().item()
-        row = {"hours": round(t_h, 3), "E_geo": e, "max_abs_w": w, "gmres_iters": its,
+        row = {"hours": round(t_h, 3), "dt": dt, "E_geo": e, "max_abs_w": w, "gmres_iters": its,
                "wall_s": round(wall, 2)}
         rows.append(row)
         print(json.dumps(row), flush=True)
@@ -59,8 +60,15 @@ def main(argv=None):
     t0 = time.time()
     for k in range(n_reports):
         its = 0
-        for _ in range(steps_per_report):
-            its += mesh.step(phys, q, dt, **opts).gmres_iters_total
+        try:
+            for _ in range(steps_per_report):
+                its += mesh.step(phys, q, dt, **opts).gmres_iters_total
+        except D.DGError as err:   # e.g. a non-finite state: report and stop
+            row = {"hours_reached_before": round(k * steps_per_report * dt / 3600.0, 3), "dt": dt,
+                   "error": str(err)[:160]}
+            rows.append(row)
+            print(json.dumps(row), flush=True)
+            break
         torch.cuda.synchronize()
         report((k + 1) * steps_per_report * dt / 3600.0, its, time.time() - t0)
     if out:
