@@ -242,8 +242,37 @@ int dg_recover_velocity(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* phys,
  * residual r = b - S x is formed with the FP64 vmult, a correction d with
  * S d ~ r is found by GMRES whose vmults run in FP32 (to relative residual
  * inner_rtol, default 1e-4 when 0), x += d, until the FP64 test above
- * holds; maxit bounds the inner iterations in total. */
-typedef struct { double rtol; int restart, maxit; double inner_rtol; } dg_gmres_opts;
+ * holds; maxit bounds the inner iterations in total.
+ *
+ * precond (not in the paper, whose GMRES is unpreconditioned):
+ *   DG_PRECOND_NONE  (0) plain GMRES as above;
+ *   DG_PRECOND_VLINE (1) right preconditioning by the vertical-line solve:
+ *     the part of S that couples the nodes of one vertical line of cells
+ *     (chains joined by conforming faces of the last reference direction
+ *     that end in walls at both ends) -- vertical gradient and divergence
+ *     through the K_dd metric entry and the z normals, the vertical faces'
+ *     penalty, gravity -- factored once per solve in FP32 (block Thomas,
+ *     2n x 2n blocks in the unknowns x and w_z of a cell line) and applied
+ *     once per Arnoldi step in flexible form (the vectors Z_j = P^{-1} V_j
+ *     are kept, restart x N more doubles, and x += Z y); lines of chains cut
+ *     by a 2:1 face or a periodic column are left as the identity.  The
+ *     stopping test is still on the unpreconditioned residual b - S x.
+ *     Host-driven solves and steps only (graph mode: DG_ERR_UNSUPPORTED).
+ *   other values: DG_ERR_ARG. */
+enum { DG_PRECOND_NONE = 0, DG_PRECOND_VLINE = 1 };
+
+/* z = P^{-1} r for the vertical-line preconditioner P of DG_PRECOND_VLINE
+ * built from the frozen coefficients cf (r, z: N, device, not aliased);
+ * the phys precision field is ignored (P is always factored in FP32 from
+ * the FP64 coefficients).  Exposed to test and inspect the preconditioner. */
+int dg_precond_apply(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* phys,
+                     const dg_implicit_coeffs* cf, const double* r, double* z, void* stream);
+typedef struct {
+  double rtol;
+  int restart, maxit;
+  double inner_rtol;
+  int precond;
+} dg_gmres_opts;
 typedef struct { int iters; double relres; int refinements; } dg_gmres_info;
 int dg_gmres_solve(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* phys,
                    const dg_implicit_coeffs* cf, const double* b, double* x,
@@ -316,7 +345,7 @@ int dg_ensemble_step(dg_ensemble* ens, const dg_phys* phys, const double* dt_ins
  * DG_KERNEL_CLASSES) with the class name, launch count, number of timed
  * launches and their summed device time in ms.
  */
-enum { DG_KERNEL_CLASSES = 16 };
+enum { DG_KERNEL_CLASSES = 17 };
 typedef struct {
   char name[32];
   int64_t launches;

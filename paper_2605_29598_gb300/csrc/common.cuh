@@ -80,7 +80,7 @@ namespace dg {
 enum KernelId {
   K_TRACE = 0, K_FACE_EXPLICIT, K_HANG_GATHER, K_VOL_EXPLICIT, K_FACE_LAMBDA, K_FACE_GRAD,
   K_VOL_GRAD, K_FACE_DIV, K_VOL_DIV, K_USTAR, K_MULTIDOT, K_REDUCE, K_MULTIAXPY, K_VEC,
-  K_STAGE, K_PICARD_NORMS, K_COUNT
+  K_STAGE, K_PICARD_NORMS, K_VLINE, K_COUNT
 };
 extern const char* const kKernelNames[K_COUNT];
 
@@ -134,6 +134,14 @@ struct dg_mesh {
   dg::DBuf bg, bg32, bgF, bgtr, bgjump, pert32;
   // device-driven step (CUDA graph): solver state and fixed work vectors
   dg::DBuf gstate, gwork;
+  // vertical-line preconditioner: chains of cells linked through conforming
+  // bottom/top faces (device int32: cell above / below, -1 at a chain end;
+  // first cell of each chain), FP32 block factors and work vectors
+  int64_t n_vchains = 0;
+  int* vl_above = nullptr;
+  int* vl_below = nullptr;
+  int* vl_heads = nullptr;
+  dg::DBuf vl_slots, vl_fac, vl_scr, gm_pc;
   struct StepGraph* graph = nullptr;   // cached executable graph of imex_ark2_step
   bool bg_set = false;
   double bg_gamma = 0, bg_g = 0, bg_f = 0;
@@ -141,8 +149,8 @@ struct dg_mesh {
   std::vector<double> host_h;
   dg::Profiler prof;
   // cells-per-block multiplier of the cell kernels, per class (FP64, FP32)
-  int tile[dg::K_COUNT] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};
-  int tile32[dg::K_COUNT] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};
+  int tile[dg::K_COUNT] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};
+  int tile32[dg::K_COUNT] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};
   // every cell terrain-following: x depends on xi_1 only and y on xi_2 only
   // (rectangular footprints, any vertical map), so the metric terms
   // K_ab = w det(J) (J^-1)_ab vanish exactly for (a, b) = (1, y), (1, z),
@@ -150,11 +158,12 @@ struct dg_mesh {
   bool terrain = false;
   int64_t workspace_bytes() const;
   // every workspace buffer, for accounting, release and graph capture checks
-  static constexpr int kBufs = 27;
+  static constexpr int kBufs = 31;
   void bufs(const dg::DBuf** out) const {
     const dg::DBuf* b[kBufs] = {&trc, &slot, &hbuf, &trh, &pcoef, &wv, &gm_V, &gm_work, &red, &st,
                                 &fns, &fs, &trh32, &pcoef32, &c32, &ir32, &irw, &irho, &irho32,
-                                &bg, &bg32, &bgF, &bgtr, &bgjump, &pert32, &gstate, &gwork};
+                                &bg, &bg32, &bgF, &bgtr, &bgjump, &pert32, &gstate, &gwork,
+                                &vl_slots, &vl_fac, &vl_scr, &gm_pc};
     for (int i = 0; i < kBufs; ++i) out[i] = b[i];
   }
 };

@@ -768,6 +768,10 @@ int step_graph(dg_mesh* m, const dg_phys* ph, double* q, double dt, const dg_ste
     set_error("imex_ark2_step: graph mode does not run under dg_profile_begin");
     return DG_ERR_UNSUPPORTED;
   }
+  if (o->gmres.precond != DG_PRECOND_NONE) {
+    set_error("imex_ark2_step: graph mode runs the unpreconditioned GMRES only");
+    return DG_ERR_UNSUPPORTED;
+  }
   int rc;
   StepGraph* G;
   if ((rc = graph_of(m, &G)) != DG_OK) return rc;
@@ -822,6 +826,10 @@ void multi_graph_release(MultiGraph* M) {
 int multi_step_graph(int ng, dg_mesh* const* meshes, const dg_phys* phs, double* const* qs, const double* dts,
                      const dg_step_opts* o, dg_step_info* infos, MultiGraph** cache, cudaStream_t st) {
   int rc;
+  if (o->gmres.precond != DG_PRECOND_NONE) {
+    set_error("dg_ensemble_step: graph mode runs the unpreconditioned GMRES only");
+    return DG_ERR_UNSUPPORTED;
+  }
   if (!*cache) {
     MultiGraph* M = new MultiGraph();
     *cache = M;

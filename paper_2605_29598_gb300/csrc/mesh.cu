@@ -45,7 +45,7 @@ void DBuf::release() {
 const char* const kKernelNames[K_COUNT] = {
     "trace", "face_explicit", "hang_gather", "volume_explicit", "face_lambda", "face_grad",
     "volume_grad", "face_div", "volume_div", "ustar", "multidot", "reduce", "multiaxpy", "vector",
-    "stage", "picard_norms"};
+    "stage", "picard_norms", "vline"};
 
 cudaEvent_t Profiler::next_event() {
   if (used == pool.size()) {
@@ -382,6 +382,9 @@ void dg_mesh_destroy(dg_mesh* m) {
   cudaFree(m->invM32);
   cudaFree(m->fgeo32);
   cudaFree(m->lv32);
+  cudaFree(m->vl_above);
+  cudaFree(m->vl_below);
+  cudaFree(m->vl_heads);
   graph_release(m);
   const DBuf* b[dg_mesh::kBufs];
   m->bufs(b);
@@ -517,6 +520,36 @@ int dg_mesh_create(dg_ctx* ctx, const dg_mesh_desc* d, dg_mesh** out) {
     }
   }
 
+  // ---- vertical chains: cells linked through conforming top (2a+1) /
+  // bottom (2a) faces of the last reference direction a = dim - 1; a
+  // vertically periodic column is cut at its first cell
+  std::vector<int> above((size_t)E, -1), below((size_t)E, -1), heads;
+  for (int64_t k = 0; k < d->n_int; ++k) {
+    const int64_t* r = d->int_faces + 4 * k;
+    if (r[1] == 2 * (dim - 1) + 1) {
+      above[r[0]] = (int)r[2];
+      below[r[2]] = (int)r[0];
+    }
+  }
+  {
+    std::vector<uint8_t> seen((size_t)E, 0);
+    auto walk = [&](int64_t c) {
+      for (int64_t e = c; e >= 0 && !seen[e]; e = above[e]) seen[e] = 1;
+    };
+    for (int64_t c = 0; c < E; ++c)
+      if (below[c] < 0) {
+        heads.push_back((int)c);
+        walk(c);
+      }
+    for (int64_t c = 0; c < E; ++c)
+      if (!seen[c]) {
+        above[below[c]] = -1;
+        below[c] = -1;
+        heads.push_back((int)c);
+        walk(c);
+      }
+  }
+
   dg_mesh* m = new dg_mesh;
   m->ctx = ctx;
   m->dim = dim;
@@ -577,6 +610,13 @@ int dg_mesh_create(dg_ctx* ctx, const dg_mesh_desc* d, dg_mesh** out) {
   UPLOAD(m->hp_cslot, hpc.data(), nH);
   UPLOAD(m->hp_code, hpcode.data(), nH);
   UPLOAD(m->hc_slot, hcs.data(), nHC);
+  m->n_vchains = (int64_t)heads.size();
+  ALLOC(m->vl_above, E);
+  ALLOC(m->vl_below, E);
+  ALLOC(m->vl_heads, m->n_vchains);
+  UPLOAD(m->vl_above, above.data(), E);
+  UPLOAD(m->vl_below, below.data(), E);
+  UPLOAD(m->vl_heads, heads.data(), m->n_vchains);
 #undef ALLOC
 #undef UPLOAD
   GeoArgs g = geo_args(m);

@@ -202,7 +202,7 @@ static int dots(dg_mesh* m, const Red& r, const double* V, int nvec, int64_t n, 
 
 // Restarted GMRES(m), classical Gram-Schmidt applied twice, Givens rotations.
 static int gmres(dg_mesh* m, const Vmult& A, const double* b, double* x, double rtol, int restart, int maxit,
-                 dg_gmres_info* info, cudaStream_t st, bool x_is_zero = false) {
+                 dg_gmres_info* info, cudaStream_t st, bool x_is_zero = false, bool pc = false) {
   const int64_t n = m->N;
   if (restart < 1 || restart > MAX_RESTART || maxit < 0 || !(rtol >= 0.0)) {
     set_error("gmres: restart must be in 1..%d, maxit >= 0, rtol >= 0", MAX_RESTART);
@@ -211,6 +211,12 @@ static int gmres(dg_mesh* m, const Vmult& A, const double* b, double* x, double 
   int rc;
   if ((rc = m->gm_V.ensure(sizeof(double) * (size_t)(restart + 1) * n)) != DG_OK) return rc;
   if ((rc = m->gm_work.ensure(sizeof(double) * (size_t)n)) != DG_OK) return rc;
+  // right preconditioning in flexible form: Z_j = P^{-1} V_j is kept and x
+  // gains Z y, so the update matches the Arnoldi relation A Z = V H even
+  // though P^{-1} (FP32 factors) is only accurate to rounding; residuals
+  // are those of A x = b itself
+  if (pc && (rc = m->gm_pc.ensure(sizeof(double) * (size_t)restart * n)) != DG_OK) return rc;
+  double* Z = pc ? m->gm_pc.as<double>() : nullptr;
   Red red;
   if ((rc = ensure_red(m, &red)) != DG_OK) return rc;
   double* V = m->gm_V.as<double>();
@@ -267,7 +273,13 @@ static int gmres(dg_mesh* m, const Vmult& A, const double* b, double* x, double 
     for (int j = 0; j < restart; ++j) {
       double* vj = V + (int64_t)j * n;
       double* w = V + (int64_t)(j + 1) * n;
-      if ((rc = A(vj, w, st)) != DG_OK) return rc;
+      if (pc) {
+        double* zj = Z + (int64_t)j * n;
+        if ((rc = vline_apply(m, vj, zj, st)) != DG_OK) return rc;
+        if ((rc = A(zj, w, st)) != DG_OK) return rc;
+      } else if ((rc = A(vj, w, st)) != DG_OK) {
+        return rc;
+      }
       // classical Gram-Schmidt with a re-orthogonalisation test: one pass
       // gives V^T w and |w|^2 together (w is stored right after V_j); a
       // second pass runs only when the projection cancelled w down to
@@ -327,7 +339,7 @@ static int gmres(dg_mesh* m, const Vmult& A, const double* b, double* x, double 
     }
     Coefs c;
     for (int k = 0; k < jused; ++k) c.c[k] = y[k];
-    launch_multiaxpy(m, V, jused, n, c, x, st);
+    launch_multiaxpy(m, pc ? Z : V, jused, n, c, x, st);
     DG_LAUNCH_CHECK("gmres update");
   }
 }
@@ -421,7 +433,8 @@ int schur_vmult_mixed(dg_mesh* m, const ImplK& k, const double* rho, const doubl
 // on the FP32 operator (FP64 basis, orthogonalisation and reductions) to
 // relative residual inner_rtol, x += d; until ||r|| <= rtol ||b||.
 static int gmres_ir(dg_mesh* m, const Vmult& A64, const Vmult& A32, const double* b, double* x, double rtol,
-                    int restart, int maxit, double inner_rtol, dg_gmres_info* info, cudaStream_t st) {
+                    int restart, int maxit, double inner_rtol, dg_gmres_info* info, cudaStream_t st,
+                    bool pc = false) {
   const int64_t n = m->N;
   int rc;
   if ((rc = m->irw.ensure(sizeof(double) * 2 * n)) != DG_OK) return rc;
@@ -467,7 +480,7 @@ static int gmres_ir(dg_mesh* m, const Vmult& A64, const Vmult& A32, const double
     const double tol_in = std::max(inner_rtol, 0.5 * rtol * bnorm / rn);
     DG_CUDA(cudaMemsetAsync(d, 0, sizeof(double) * n, st));
     dg_gmres_info gi{0, 0.0, 0};
-    rc = gmres(m, A32, r, d, tol_in, restart, maxit - out.iters, &gi, st, true);
+    rc = gmres(m, A32, r, d, tol_in, restart, maxit - out.iters, &gi, st, true, pc);
     if (rc != DG_OK && rc != DG_ERR_NOT_CONVERGED) return rc;
     out.iters += gi.iters;
     DG_RUN(m, K_VEC, st, k_axpby<<<gb, 256, 0, st>>>(n, 1.0, x, 1.0, d, x));
@@ -531,8 +544,14 @@ int dg_gmres_solve(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* ph, const dg
   if (rc) return rc;
   dg_mesh* m = const_cast<dg_mesh*>(mesh);
   cudaStream_t st = (cudaStream_t)stream;
+  if (opts->precond != DG_PRECOND_NONE && opts->precond != DG_PRECOND_VLINE) {
+    set_error("dg_gmres_solve: precond must be DG_PRECOND_NONE or DG_PRECOND_VLINE");
+    return DG_ERR_ARG;
+  }
+  const bool pc = opts->precond == DG_PRECOND_VLINE;
   ImplK k = impl_consts(ph, cf->a_dt);
   if ((rc = prepare_rt(m, k, cf->rho, cf->p_lag, cf->u_lag, ph->penalty, st)) != DG_OK) return rc;
+  if (pc && (rc = vline_setup(m, k, cf->p_lag, ph->penalty, st)) != DG_OK) return rc;
   SchurCtx sc{m, k, cf->rho, cf->p_lag, ph->penalty};
   Vmult A = make_vmult(&sc);
   if (!A.fn) return DG_ERR_UNSUPPORTED;
@@ -540,10 +559,10 @@ int dg_gmres_solve(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* ph, const dg
     Schur32Ctx sc32;
     if ((rc = prepare32(m, k, cf->rho, cf->p_lag, cf->u_lag, ph->penalty, st, &sc32)) != DG_OK) return rc;
     Vmult A32 = make_vmult32(&sc32);
-    return gmres_ir(m, A, A32, b, x, opts->rtol, opts->restart, opts->maxit, opts->inner_rtol, info, st);
+    return gmres_ir(m, A, A32, b, x, opts->rtol, opts->restart, opts->maxit, opts->inner_rtol, info, st, pc);
   }
   if (info) info->refinements = 0;
-  return gmres(m, A, b, x, opts->rtol, opts->restart, opts->maxit, info, st);
+  return gmres(m, A, b, x, opts->rtol, opts->restart, opts->maxit, info, st, false, pc);
 }
 
 int imex_ark2_step(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* ph, double* q, double dt,
@@ -561,6 +580,10 @@ int imex_ark2_step(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* ph, double* 
   if (opts->gmres.restart < 1 || opts->gmres.restart > MAX_RESTART || opts->gmres.maxit < 0 ||
       !(opts->gmres.rtol >= 0.0)) {
     set_error("imex_ark2_step: gmres restart must be in 1..%d, maxit >= 0, rtol >= 0", MAX_RESTART);
+    return DG_ERR_ARG;
+  }
+  if (opts->gmres.precond != DG_PRECOND_NONE && opts->gmres.precond != DG_PRECOND_VLINE) {
+    set_error("imex_ark2_step: gmres precond must be DG_PRECOND_NONE or DG_PRECOND_VLINE");
     return DG_ERR_ARG;
   }
   dg_mesh* m = const_cast<dg_mesh*>(mesh);
@@ -581,6 +604,7 @@ int step_host(dg_mesh* m, const dg_phys* ph, double* q, double dt, const dg_step
   const auto& a = tab.a;
   const auto& at = tab.at;
   const auto& bw = tab.b;
+  const bool pc = opts->gmres.precond == DG_PRECOND_VLINE;
   // workspace: F_NS x3 (5n), F_S x3 (4n), y (5n), rho, mhat (3n), ehat, u, unew (3n each), p, pnew, rhs
   if ((rc = m->fns.ensure(sizeof(double) * 15 * n)) != DG_OK) return rc;
   if ((rc = m->fs.ensure(sizeof(double) * 12 * n)) != DG_OK) return rc;
@@ -628,6 +652,7 @@ int step_host(dg_mesh* m, const dg_phys* ph, double* q, double dt, const dg_step
     int kk = 0;
     for (; kk < kmax; ++kk) {
       if ((rc = prepare_rt(m, k, rho, p, u, ph->penalty, st)) != DG_OK) return rc;
+      if (pc && (rc = vline_setup(m, k, p, ph->penalty, st)) != DG_OK) return rc;
       if ((rc = rhs_rt(m, k, rho, p, u, mhat, ehat, rhs, st)) != DG_OK) return rc;
       DG_CUDA(cudaMemcpyAsync(pnew, p, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
       SchurCtx schur{m, k, rho, p, ph->penalty};
@@ -638,9 +663,10 @@ int step_host(dg_mesh* m, const dg_phys* ph, double* q, double dt, const dg_step
         if ((rc = prepare32(m, k, rho, p, u, ph->penalty, st, &sc32)) != DG_OK) return rc;
         Vmult A32 = make_vmult32(&sc32);
         rc = gmres_ir(m, A, A32, rhs, pnew, opts->gmres.rtol, opts->gmres.restart, opts->gmres.maxit,
-                      opts->gmres.inner_rtol, &gi, st);
+                      opts->gmres.inner_rtol, &gi, st, pc);
       } else {
-        rc = gmres(m, A, rhs, pnew, opts->gmres.rtol, opts->gmres.restart, opts->gmres.maxit, &gi, st);
+        rc = gmres(m, A, rhs, pnew, opts->gmres.rtol, opts->gmres.restart, opts->gmres.maxit, &gi, st, false,
+                   pc);
       }
       if (rc != DG_OK && rc != DG_ERR_NOT_CONVERGED) return rc;
       inf.gmres_iters_total += gi.iters;

@@ -192,6 +192,12 @@ int rhs_rt(dg_mesh* m, const ImplK& k, const double* rho, const double* plag, co
 int recover_rt(dg_mesh* m, const ImplK& k, const double* rho, const double* ulag, const double* mhat,
                const double* p, double* u, cudaStream_t st);
 
+// vertical-line preconditioner (vline.cu): setup from the FP64 frozen
+// coefficients that prepare_rt leaves (1/rho, h rho traces, penalty), then
+// z = P^{-1} r as often as needed
+int vline_setup(dg_mesh* m, const ImplK& k, const double* plag, int penalty, cudaStream_t st);
+int vline_apply(dg_mesh* m, const double* r, double* z, cudaStream_t st);
+
 // host-driven ARK2 step (any options) and the device-driven one (graph.cu)
 int step_host(dg_mesh* m, const dg_phys* ph, double* q, double dt, const dg_step_opts* opts,
               dg_step_info* info, cudaStream_t st);

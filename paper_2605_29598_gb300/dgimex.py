@@ -57,9 +57,14 @@ class ImplicitCoeffs(C.Structure):
                 ("a_dt", C.c_double)]
 
 
+# GMRES preconditioner choice (dg_gmres_opts.precond)
+DG_PRECOND_NONE = 0
+DG_PRECOND_VLINE = 1
+
+
 class GmresOpts(C.Structure):
     _fields_ = [("rtol", C.c_double), ("restart", C.c_int), ("maxit", C.c_int),
-                ("inner_rtol", C.c_double)]
+                ("inner_rtol", C.c_double), ("precond", C.c_int)]
 
 
 class GmresInfo(C.Structure):
@@ -90,6 +95,8 @@ EXPORTS = {
     "dg_apply_implicit": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Phys),
                                     C.POINTER(ImplicitCoeffs), C.c_void_p, C.c_void_p,
                                     C.c_void_p]),
+    "dg_precond_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Phys),
+                                   C.POINTER(ImplicitCoeffs), C.c_void_p, C.c_void_p, C.c_void_p]),
     "dg_schur_rhs": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Phys), C.POINTER(ImplicitCoeffs),
                                C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "dg_recover_velocity": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Phys),
@@ -299,6 +306,14 @@ class Mesh:
                                           _ptr(y), _stream(stream)), "dg_apply_implicit")
         return y
 
+    def precond_apply(self, phys, cf, r, z=None, stream=None):
+        """z = P^{-1} r, P the vertical-line preconditioner of the Schur GMRES."""
+        import torch
+        z = torch.empty_like(r) if z is None else z
+        _check(self.lib.dg_precond_apply(self.ctx.h, self.h, C.byref(phys), C.byref(cf), _ptr(r),
+                                         _ptr(z), _stream(stream)), "dg_precond_apply")
+        return z
+
     def schur_rhs(self, phys, cf, m_hat, e_hat, rhs=None, stream=None):
         import torch
         rhs = torch.empty_like(e_hat) if rhs is None else rhs
@@ -315,8 +330,10 @@ class Mesh:
         return u
 
     def gmres_solve(self, phys, cf, b, x, rtol=1e-12, restart=30, maxit=1000, stream=None,
-                    allow_not_converged=False, inner_rtol=0.0):
-        opts = GmresOpts(rtol=rtol, restart=restart, maxit=maxit, inner_rtol=inner_rtol)
+                    allow_not_converged=False, inner_rtol=0.0, precond=False):
+        """precond=True: right preconditioning by the vertical-line solve."""
+        opts = GmresOpts(rtol=rtol, restart=restart, maxit=maxit, inner_rtol=inner_rtol,
+                         precond=DG_PRECOND_VLINE if precond else DG_PRECOND_NONE)
         info = GmresInfo()
         st = self.lib.dg_gmres_solve(self.ctx.h, self.h, C.byref(phys), C.byref(cf), _ptr(b),
                                      _ptr(x), C.byref(opts), C.byref(info), _stream(stream))
@@ -325,11 +342,13 @@ class Mesh:
 
     def step(self, phys, q, dt, picard_rtol=1e-10, picard_maxit=10, picard_fixed=0,
              gmres_rtol=1e-10, gmres_restart=30, gmres_maxit=1000, stream=None,
-             gmres_inner_rtol=0.0, graph=False):
+             gmres_inner_rtol=0.0, graph=False, gmres_precond=False):
         opts = StepOpts(picard_rtol=picard_rtol, picard_maxit=picard_maxit,
                         picard_fixed=picard_fixed,
                         gmres=GmresOpts(rtol=gmres_rtol, restart=gmres_restart, maxit=gmres_maxit,
-                                        inner_rtol=gmres_inner_rtol), graph=1 if graph else 0)
+                                        inner_rtol=gmres_inner_rtol,
+                                        precond=DG_PRECOND_VLINE if gmres_precond else DG_PRECOND_NONE),
+                        graph=1 if graph else 0)
         info = StepInfo()
         _check(self.lib.imex_ark2_step(self.ctx.h, self.h, C.byref(phys), _ptr(q), float(dt),
                                        C.byref(opts), C.byref(info), _stream(stream)),
@@ -343,7 +362,7 @@ class Mesh:
 
 KERNEL_CLASSES = ["trace", "face_explicit", "hang_gather", "volume_explicit", "face_lambda",
                   "face_grad", "volume_grad", "face_div", "volume_div", "ustar", "multidot",
-                  "reduce", "multiaxpy", "vector", "stage", "picard_norms"]
+                  "reduce", "multiaxpy", "vector", "stage", "picard_norms", "vline"]
 
 
 def profile_begin(mesh: "Mesh", timed=()):
@@ -412,11 +431,14 @@ class Ensemble:
         return q
 
     def step(self, phys, dt, picard_rtol=1e-10, picard_maxit=10, picard_fixed=0, gmres_rtol=1e-10,
-             gmres_restart=30, gmres_maxit=1000, gmres_inner_rtol=0.0, stream=None, graph=False):
+             gmres_restart=30, gmres_maxit=1000, gmres_inner_rtol=0.0, stream=None, graph=False,
+             gmres_precond=False):
         opts = StepOpts(picard_rtol=picard_rtol, picard_maxit=picard_maxit,
                         picard_fixed=picard_fixed,
                         gmres=GmresOpts(rtol=gmres_rtol, restart=gmres_restart, maxit=gmres_maxit,
-                                        inner_rtol=gmres_inner_rtol), graph=1 if graph else 0)
+                                        inner_rtol=gmres_inner_rtol,
+                                        precond=DG_PRECOND_VLINE if gmres_precond else DG_PRECOND_NONE),
+                        graph=1 if graph else 0)
         dts = (C.c_double * self.n)(*[float(x) for x in dt])
         info = StepInfo()
         _check(self.lib.dg_ensemble_step(self.h, C.byref(phys), dts, C.byref(opts), C.byref(info),
