@@ -314,20 +314,23 @@ def run_graph_modes(D, I, ctx, case, steps, warmup):
     return out
 
 
-def run_variant(D, I, ctx, case, steps, warmup):
-    """FP64 and mixed steps of another workload (timed with CUDA events)."""
+def run_variant(D, I, ctx, case, steps, warmup, precond=False, state=None):
+    """FP64 and mixed steps of another workload (timed with CUDA events);
+    precond=True runs the Schur GMRES with the vertical-line preconditioner."""
     import torch
     mesh = D.Mesh(ctx, case["mesh"], case["degree"])
     st = mesh.stats()
     xyz = mesh.node_coords().cpu().numpy().T
-    q0 = torch.tensor(I.stratified_state(xyz, **case["state_params"]), dtype=torch.float64,
+    state = state or I.stratified_state
+    q0 = torch.tensor(state(xyz, **case["state_params"]), dtype=torch.float64,
                       device="cuda").contiguous()
     out = {"cells": st.n_elem, "nodes": st.n_nodes, "hanging_points": st.n_hang_points,
-           "degree": case["degree"], "dt": case["dt"]}
+           "degree": case["degree"], "dt": case["dt"], "gmres_precond": "vline" if precond else "none"}
     stream = torch.cuda.current_stream()
     for prec in ("fp64", "mixed"):
         phys = D.make_phys(f=case["f"], variant="R2", precision=prec)
-        opts = dict(STEP_OPTS, gmres_inner_rtol=1e-4) if prec == "mixed" else STEP_OPTS
+        opts = dict(STEP_OPTS, gmres_inner_rtol=1e-4) if prec == "mixed" else dict(STEP_OPTS)
+        opts["gmres_precond"] = precond
         q = q0.clone()
         for _ in range(warmup):
             mesh.step(phys, q, case["dt"], **opts)
@@ -581,6 +584,12 @@ def gpu_main(args):
     variants = {}
     if not args.no_variants and world == 1:
         variants["hill3d_nc"] = run_variant(D, I, ctx, I.hill3d_case(refine=True), steps=2, warmup=1)
+        variants["hill3d_vline_precond"] = run_variant(D, I, ctx, I.hill3d_case(), steps=2, warmup=1,
+                                                       precond=True)
+        pw = I.planetary_igw_case()
+        variants["planetary_igw"] = run_variant(D, I, ctx, pw, steps=4, warmup=1, state=I.isothermal_state)
+        variants["planetary_igw_vline_precond"] = run_variant(D, I, ctx, pw, steps=4, warmup=1, precond=True,
+                                                              state=I.isothermal_state)
         variants["ensemble32"] = run_ensemble(D, I, ctx, steps=2, warmup=1)
         variants["graph_mode_hill3d"] = run_graph_modes(D, I, ctx, I.hill3d_case(), steps=3, warmup=2)
         variants["graph_mode_igw2d"] = run_graph_modes(D, I, ctx, I.igw2d_case(), steps=10, warmup=2)
