@@ -345,7 +345,7 @@ int dg_ensemble_step(dg_ensemble* ens, const dg_phys* phys, const double* dt_ins
  * DG_KERNEL_CLASSES) with the class name, launch count, number of timed
  * launches and their summed device time in ms.
  */
-enum { DG_KERNEL_CLASSES = 17 };
+enum { DG_KERNEL_CLASSES = 18 };
 typedef struct {
   char name[32];
   int64_t launches;

@@ -80,7 +80,7 @@ namespace dg {
 enum KernelId {
   K_TRACE = 0, K_FACE_EXPLICIT, K_HANG_GATHER, K_VOL_EXPLICIT, K_FACE_LAMBDA, K_FACE_GRAD,
   K_VOL_GRAD, K_FACE_DIV, K_VOL_DIV, K_USTAR, K_MULTIDOT, K_REDUCE, K_MULTIAXPY, K_VEC,
-  K_STAGE, K_PICARD_NORMS, K_VLINE, K_COUNT
+  K_STAGE, K_PICARD_NORMS, K_VLINE, K_VLINE_SETUP, K_COUNT
 };
 extern const char* const kKernelNames[K_COUNT];
 
@@ -149,8 +149,8 @@ struct dg_mesh {
   std::vector<double> host_h;
   dg::Profiler prof;
   // cells-per-block multiplier of the cell kernels, per class (FP64, FP32)
-  int tile[dg::K_COUNT] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};
-  int tile32[dg::K_COUNT] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};
+  int tile[dg::K_COUNT] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};
+  int tile32[dg::K_COUNT] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};
   // every cell terrain-following: x depends on xi_1 only and y on xi_2 only
   // (rectangular footprints, any vertical map), so the metric terms
   // K_ab = w det(J) (J^-1)_ab vanish exactly for (a, b) = (1, y), (1, z),

@@ -45,7 +45,7 @@ void DBuf::release() {
 const char* const kKernelNames[K_COUNT] = {
     "trace", "face_explicit", "hang_gather", "volume_explicit", "face_lambda", "face_grad",
     "volume_grad", "face_div", "volume_div", "ustar", "multidot", "reduce", "multiaxpy", "vector",
-    "stage", "picard_norms", "vline"};
+    "stage", "picard_norms", "vline", "vline_setup"};
 
 cudaEvent_t Profiler::next_event() {
   if (used == pool.size()) {

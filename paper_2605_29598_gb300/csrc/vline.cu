@@ -339,7 +339,7 @@ int vl_setup_impl(dg_mesh* m, const ImplK& k, const double* plag, int penalty, c
   DG_CUDA(cudaMemsetAsync(sb + 8 * S, 2, (size_t)S, st));
   VlArgs a = vl_args(m);
   if (m->nF > 0)
-    DG_RUN(m, K_VLINE, st,
+    DG_RUN(m, K_VLINE_SETUP, st,
            k_vl_slots<<<grid_for(m->nF, 256), 256, 0, st>>>(topo(m), m->dim,
                                                              penalty ? m->pcoef.as<double>() : nullptr,
                                                              reinterpret_cast<float*>(sb),
@@ -351,7 +351,7 @@ int vl_setup_impl(dg_mesh* m, const ImplK& k, const double* plag, int penalty, c
   a.cg = k.r2 ? (float)k.cgrav : 0.f;
   const int64_t nth = m->n_vchains * m->nfp;
   if (nth > 0)
-    DG_RUN(m, K_VLINE, st,
+    DG_RUN(m, K_VLINE_SETUP, st,
            (k_vl_setup<DIM, N><<<grid_for(nth, 128), 128, 0, st>>>(a, cast_tables<float>(m->tab.t))));
   DG_LAUNCH_CHECK("vertical-line setup");
   return DG_OK;

@@ -362,7 +362,7 @@ class Mesh:
 
 KERNEL_CLASSES = ["trace", "face_explicit", "hang_gather", "volume_explicit", "face_lambda",
                   "face_grad", "volume_grad", "face_div", "volume_div", "ustar", "multidot",
-                  "reduce", "multiaxpy", "vector", "stage", "picard_norms", "vline"]
+                  "reduce", "multiaxpy", "vector", "stage", "picard_norms", "vline", "vline_setup"]
 
 
 def profile_begin(mesh: "Mesh", timed=()):
