@@ -20,7 +20,9 @@ It restates the paper's discretisation in the plainest form available:
 * the weak operators are the paper's matrices: A (eq. A), B, R, f_g, f
   (momentum), C, D, k, M_g, g (energy), the Schur systems of R1 and R2, the
   Picard (fixed-point) loop, restarted GMRES with modified Gram-Schmidt and
-  Givens rotations, and the three-stage ARK2 step (Butcher tableau).
+  Givens rotations, and the three-stage ARK2 step (Butcher tableau);
+* the Rayleigh damping layers of the orography tests (Section 4, eq.
+  damping) as an extra non-stiff rate -lambda (q - q_bar), in weak form.
 
 Readings where the paper is silent or garbled (each also used by the CUDA
 path) are marked ``READING`` below.
@@ -352,6 +354,50 @@ class Phys:
     f: float = 1.0e-4
     variant: str = "R2"          # "R1" | "R2"
     penalty: bool = True         # implicit Rusanov term on rho e (READING c5)
+    sponge: "Sponge" = None      # Rayleigh damping layers (Section 4), or none
+
+
+@dataclass
+class Sponge:
+    """Rayleigh damping (sponge) layers of the orography tests (Section 4,
+    eq. damping).
+
+    lam_bar (1/s): the damping coefficient at the boundary.  Top layer:
+    lambda = 0 below z_b, lam_bar sin^2(pi/2 (z - z_b)/(z_t - z_b)) above.
+    Lateral layers, (lo, hi, width) for x and/or y: the same sin^2 ramp over
+    ``width`` from the layer's inner edge (lo + width, hi - width) out to the
+    boundary lo or hi.  q_bar (5, E, Np): the nodal state the layers relax.
+    READINGS (the paper gives the top profile and says the lateral layers are
+    analogous): the damping term -lambda (q - q_bar) acts on all five
+    conserved fields and belongs to the non-stiff (explicit) part; where
+    layers overlap the largest coefficient applies; the ramp argument is
+    clipped to [0, 1]."""
+    lam_bar: float
+    z_b: float
+    z_t: float
+    x_layers: tuple = None
+    y_layers: tuple = None
+    q_bar: np.ndarray = None
+
+
+def sponge_coefficient(points, s):
+    """lambda at physical points (..., d) for the layers ``s``."""
+    pts = np.asarray(points, dtype=np.float64)
+
+    def ramp(t):
+        t = np.clip(t, 0.0, 1.0)
+        return s.lam_bar * np.sin(0.5 * math.pi * t) ** 2
+
+    z = pts[..., -1]
+    lam = np.where(z >= s.z_b, ramp((z - s.z_b) / (s.z_t - s.z_b)), 0.0)
+    for axis, lay in ((0, s.x_layers), (1, s.y_layers)):
+        if lay is None or (axis == 1 and pts.shape[-1] < 3):
+            continue
+        lo, hi, w = lay
+        c = pts[..., axis]
+        lam = np.maximum(lam, np.where(c <= lo + w, ramp((lo + w - c) / w), 0.0))
+        lam = np.maximum(lam, np.where(c >= hi - w, ramp((c - (hi - w)) / w), 0.0))
+    return lam
 
 
 # ----------------------------------------------------------------------------
@@ -386,6 +432,10 @@ def explicit_residuals(disc, q, phys):
     for c in range(3):
         r_ns[1 + c] += disc.vol_grad(m[c] * uS)
     r_ns[4] += disc.vol_grad(rho * kin * uS)
+    if phys.sponge is not None:
+        # -lambda (q - q_bar) in weak form, lambda at the quadrature points
+        lam = sponge_coefficient(map_points(disc.mesh.vertices, disc.qpts), phys.sponge)
+        r_ns += disc.vol_weak(-lam[None] * (Q - disc.at_quad(phys.sponge.q_bar)))
     for b, c in enumerate(comp):
         pf = np.zeros((d,) + p.shape)
         pf[b] = p

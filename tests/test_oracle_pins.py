@@ -467,3 +467,79 @@ def test_geostrophic_error_vanishes_for_layered_rest_state():
     disc = O.Discretisation(mesh, 3)
     q = I.stratified_state(disc.node_points())
     assert O.geostrophic_error(disc, q, O.Phys(f=1e-4)) <= 1e-12 * 9.81
+
+
+# ----------------------------------------------------------------------------
+# Rayleigh damping layers (Section 4, eq. damping)
+# ----------------------------------------------------------------------------
+
+def test_sponge_coefficient_closed_form():
+    """lambda = 0 below z_b, lam_bar/2 half way up (sin^2(pi/4)), lam_bar at
+    z_t; lateral layers ramp the same way towards both ends; overlaps take
+    the larger value."""
+    s = O.Sponge(lam_bar=0.3, z_b=10e3, z_t=16e3, x_layers=(0.0, 60e3, 20e3), y_layers=(0.0, 40e3, 10e3))
+    pts = np.array([[30e3, 20e3, 5e3],      # interior: 0
+                    [30e3, 20e3, 13e3],     # top layer, half way: 0.15
+                    [30e3, 20e3, 16e3],     # top: 0.3
+                    [10e3, 20e3, 5e3],      # x layer, half way from x = 20 km to 0: 0.15
+                    [60e3, 20e3, 5e3],      # x boundary: 0.3
+                    [30e3, 32.5e3, 5e3],    # y layer, 1/4 of the way from 30 km: sin^2(pi/8) 0.3
+                    [55e3, 20e3, 13e3]])    # x layer 3/4 (sin^2(3pi/8) 0.3) over top layer 0.15
+    lam = O.sponge_coefficient(pts, s)
+    want = [0.0, 0.15, 0.3, 0.15, 0.3, 0.3 * math.sin(math.pi / 8) ** 2, 0.3 * math.sin(3 * math.pi / 8) ** 2]
+    assert np.allclose(lam, want, rtol=0, atol=1e-15)
+    # 2D: the second coordinate is z, no y layers
+    lam2 = O.sponge_coefficient(np.array([[10e3, 13e3]]), s)
+    assert np.allclose(lam2, [0.15], rtol=0, atol=1e-15)
+
+
+def explicit_stability_polynomial(z):
+    """R(z) = 1 + z b.1 + z^2 b.A.1 + z^3 b.A^2.1 of the explicit tableau (A
+    strictly lower triangular): the factor one explicit step applies to
+    y' = lambda y, z = lambda dt."""
+    a, _, b, _ = O.ark2_tableau()
+    one = np.ones(3)
+    return 1.0 + z * b @ one + z ** 2 * b @ a @ one + z ** 3 * b @ a @ a @ one
+
+
+@pytest.mark.parametrize("variant", ["R2", "R1"])
+@pytest.mark.parametrize("lam_dt", [0.6, 1.2, 2.4])
+def test_sponge_uniform_state_relaxes_by_explicit_polynomial(variant, lam_dt):
+    """A uniform state in one degree-0 cell with walls, g = 0 and f = 0 has
+    no dynamics (no gradient, the wall pressures cancel), so one ARK2 step
+    only relaxes each conserved field towards q_bar: q+ - q_bar =
+    R(-lambda dt) (q - q_bar), R the explicit stability polynomial, since the
+    damping is part of the explicit rates.  The node sits half way up the
+    layer (lambda = lam_bar / 2); R(-0.6) = 0.5615 by hand."""
+    mesh = I.box_mesh((1, 1), (1e3, 1e3), periodic=(False, False))
+    disc = O.Discretisation(mesh, 0)
+
+    def state(rho, v, p):
+        q = np.zeros((5, 1, 1))
+        q[0], q[2], q[4] = rho, rho * v, p / 0.4 + 0.5 * rho * v * v
+        return q
+
+    q, qb = state(1.1, 5.0, 9e4), state(1.0, 0.0, 1e5)
+    dt = 2.0
+    ph = O.Phys(g=0.0, f=0.0, variant=variant,
+                sponge=O.Sponge(lam_bar=2.0 * lam_dt / dt, z_b=0.0, z_t=1e3, q_bar=qb))
+    q1 = O.imex_ark2_step(disc, ph, q, dt, O.StepOpts(picard_rtol=1e-14, picard_maxit=50, gmres_rtol=1e-14))
+    R = explicit_stability_polynomial(-lam_dt)
+    if lam_dt == 0.6:
+        assert abs(R - 0.5614701) < 1e-7
+    for k in (0, 2, 4):
+        assert abs((q1[k] - qb[k]) / (q[k] - qb[k]) - R).max() < 1e-11, (k, R)
+    assert np.abs(q1[[1, 3]]).max() == 0.0
+
+
+def test_sponge_inactive_below_layers():
+    """Where lambda = 0 (every node below z_b, no lateral layers) the rates
+    are those without the sponge, whatever q_bar is."""
+    mesh = I.box_mesh((6, 3), (6e3, 3e3), refine_level=lambda c: 1 if c[0] < 2e3 else 0)
+    disc = O.Discretisation(mesh, 2)
+    q = I.perturb(I.stratified_state(disc.node_points(), wind=(5.0, 1.0, 0.0)), np.random.default_rng(0), 1e-2)
+    qb = I.stratified_state(disc.node_points())
+    a_ns, a_s = O.explicit_rates(disc, q, O.Phys())
+    b_ns, b_s = O.explicit_rates(disc, q, O.Phys(sponge=O.Sponge(lam_bar=0.5, z_b=5e3, z_t=8e3, q_bar=qb)))
+    assert np.array_equal(a_s, b_s)
+    assert np.abs(a_ns - b_ns).max() <= 1e-14 * np.abs(a_ns).max()
