@@ -191,6 +191,32 @@ int dg_geostrophic_error(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* phys,
 int dg_mesh_set_background(dg_ctx* ctx, dg_mesh* mesh, const dg_phys* phys,
                            const double* q_bg, void* stream);
 
+/*
+ * Rayleigh damping (sponge) layers of the orography tests (Section 4, eq.
+ * damping).  With layers set, every evaluation of the explicit operator on
+ * this mesh (dg_apply_explicit, each stage of imex_ark2_step, host-driven or
+ * graph) adds -lambda(x) (q - q_bar) to the non-stiff rates f_NS of all five
+ * conserved fields.  lambda = lambda_bar sin^2(pi/2 (z - z_b)/(z_t - z_b))
+ * for z >= z_b, 0 below; lateral layers (x_layers / y_layers = 1, y in 3D
+ * only) ramp the same way over their width from lo + width down to lo and
+ * from hi - width up to hi; where layers overlap the largest lambda
+ * applies; ramp arguments are clipped to [0, 1].  The damping is explicit:
+ * one ARK2 step multiplies a pure relaxation by the explicit stability
+ * polynomial R(-lambda dt), |R| < 1 up to lambda dt of about 2.5 (the
+ * paper uses lambda_bar dt = 1.2).
+ * q_bar: 5 x N device state, copied; s == NULL switches the layers off.
+ * Not applied by dg_apply_explicit_noalloc or by ensembles.
+ */
+typedef struct {
+  double lambda_bar;               /* 1/s */
+  double z_b, z_t;                 /* top layer: zero below z_b, lambda_bar at z_t */
+  int x_layers;                    /* 1: layers inside both ends of [x_lo, x_hi] */
+  double x_lo, x_hi, x_width;
+  int y_layers;                    /* 1: the same in y (3D) */
+  double y_lo, y_hi, y_width;
+} dg_sponge;
+int dg_mesh_set_sponge(dg_ctx* ctx, dg_mesh* mesh, const dg_sponge* s, const double* q_bar, void* stream);
+
 /* Coefficients frozen during one Picard iteration of stage l (device,
  * N each; u_lag 3 x N): rho^(n,l), p^(n,l,k), u^(n,l,k); a_dt = at_ll dt. */
 typedef struct {

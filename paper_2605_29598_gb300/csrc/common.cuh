@@ -142,6 +142,9 @@ struct dg_mesh {
   int* vl_below = nullptr;
   int* vl_heads = nullptr;
   dg::DBuf vl_slots, vl_fac, vl_scr, gm_pc;
+  // Rayleigh damping layers: lambda (N) then q_bar (5 x N)
+  dg::DBuf sponge;
+  bool sponge_set = false;
   struct StepGraph* graph = nullptr;   // cached executable graph of imex_ark2_step
   bool bg_set = false;
   double bg_gamma = 0, bg_g = 0, bg_f = 0;
@@ -158,12 +161,12 @@ struct dg_mesh {
   bool terrain = false;
   int64_t workspace_bytes() const;
   // every workspace buffer, for accounting, release and graph capture checks
-  static constexpr int kBufs = 31;
+  static constexpr int kBufs = 32;
   void bufs(const dg::DBuf** out) const {
     const dg::DBuf* b[kBufs] = {&trc, &slot, &hbuf, &trh, &pcoef, &wv, &gm_V, &gm_work, &red, &st,
                                 &fns, &fs, &trh32, &pcoef32, &c32, &ir32, &irw, &irho, &irho32,
                                 &bg, &bg32, &bgF, &bgtr, &bgjump, &pert32, &gstate, &gwork,
-                                &vl_slots, &vl_fac, &vl_scr, &gm_pc};
+                                &vl_slots, &vl_fac, &vl_scr, &gm_pc, &sponge};
     for (int i = 0; i < kBufs; ++i) out[i] = b[i];
   }
 };

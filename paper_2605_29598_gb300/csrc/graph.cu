@@ -595,6 +595,7 @@ int capture_step(dg_mesh* m, const dg_phys* ph, double* q, double dt, const dg_s
     DG_LAUNCH_CHECK("graph stage state");
     if (incr)
       rc = explicit_increment(m, pk, y, q, Fns[0], Fs[0], Fns[l], Fs[l], s[0]);
+      if (rc == DG_OK) rc = sponge_rt(m, y, Fns[l], s[0]);
     else
       rc = explicit_rt(m, ph, y, Fns[l], Fs[l], s[0]);
     if (rc != DG_OK) return rc;
@@ -620,7 +621,7 @@ size_t make_key(const dg_mesh* m, const dg_phys* ph, const double* q, double dt,
     const double* q;
     double dt, gamma, g, f;
     const double* fcell;
-    int variant, penalty, precision, bg_set;
+    int variant, penalty, precision, bg_set, sponge_set;
     double picard_rtol;
     int picard_maxit, picard_fixed;
     double rtol, inner_rtol;
@@ -641,6 +642,7 @@ size_t make_key(const dg_mesh* m, const dg_phys* ph, const double* q, double dt,
   k.penalty = ph->penalty;
   k.precision = ph->precision;
   k.bg_set = m->bg_set ? 1 : 0;
+  k.sponge_set = m->sponge_set ? 1 : 0;
   k.picard_rtol = o->picard_rtol;
   k.picard_maxit = o->picard_maxit;
   k.picard_fixed = o->picard_fixed;

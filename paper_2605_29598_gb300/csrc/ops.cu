@@ -256,10 +256,13 @@ int dg_apply_explicit(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* ph, const
       set_error("dg_apply_explicit: DG_MIXED_EXPLICIT needs a background (dg_mesh_set_background)");
       return DG_ERR_ARG;
     }
-    return explicit_mixed(m, k, q, fns, fs, (cudaStream_t)stream);
+    rc = explicit_mixed(m, k, q, fns, fs, (cudaStream_t)stream);
+  } else {
+    rc = DG_ERR_UNSUPPORTED;
+    DG_DISPATCH(m, rc = (Engine<double, D_, N_>::explicit_rates(m, k, q, fns, fs, (cudaStream_t)stream)));
   }
-  DG_DISPATCH(m, return (Engine<double, D_, N_>::explicit_rates(m, k, q, fns, fs, (cudaStream_t)stream)));
-  return DG_ERR_UNSUPPORTED;
+  if (rc != DG_OK) return rc;
+  return sponge_rt(m, q, fns, (cudaStream_t)stream);
 }
 
 int dg_apply_implicit(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* ph, const dg_implicit_coeffs* cf,

@@ -499,9 +499,13 @@ int prepare_rt(dg_mesh* m, const ImplK& k, const double* rho, const double* plag
 
 int explicit_rt(dg_mesh* m, const dg_phys* ph, const double* q, double* fns, double* fs, cudaStream_t st) {
   PhysK k{ph->gamma, ph->g, ph->f, ph->f_cell};
-  if (ph->precision == DG_MIXED_EXPLICIT && m->bg_set) return explicit_mixed(m, k, q, fns, fs, st);
-  DG_DISPATCH(m, return (Engine<double, D_, N_>::explicit_rates(m, k, q, fns, fs, st)));
-  return DG_ERR_UNSUPPORTED;
+  int rc = DG_ERR_UNSUPPORTED;
+  if (ph->precision == DG_MIXED_EXPLICIT && m->bg_set)
+    rc = explicit_mixed(m, k, q, fns, fs, st);
+  else
+    DG_DISPATCH(m, rc = (Engine<double, D_, N_>::explicit_rates(m, k, q, fns, fs, st)));
+  if (rc != DG_OK) return rc;
+  return sponge_rt(m, q, fns, st);
 }
 
 int rhs_rt(dg_mesh* m, const ImplK& k, const double* rho, const double* plag, const double* ulag,
@@ -696,6 +700,7 @@ int step_host(dg_mesh* m, const dg_phys* ph, double* q, double dt, const dg_step
     DG_LAUNCH_CHECK("stage state");
     if (incr)
       rc = explicit_increment(m, pk, y, q, Fns[0], Fs[0], Fns[l], Fs[l], st);
+      if (rc == DG_OK) rc = sponge_rt(m, y, Fns[l], st);
     else
       rc = explicit_rt(m, ph, y, Fns[l], Fs[l], st);
     if (rc != DG_OK) return rc;

@@ -46,6 +46,13 @@ class MeshStats(C.Structure):
                 ("tile_fp32", C.c_int * 3), ("terrain_following", C.c_int)]
 
 
+class Sponge(C.Structure):
+    _fields_ = [("lambda_bar", C.c_double), ("z_b", C.c_double), ("z_t", C.c_double),
+                ("x_layers", C.c_int), ("x_lo", C.c_double), ("x_hi", C.c_double),
+                ("x_width", C.c_double), ("y_layers", C.c_int), ("y_lo", C.c_double),
+                ("y_hi", C.c_double), ("y_width", C.c_double)]
+
+
 class Phys(C.Structure):
     _fields_ = [("gamma", C.c_double), ("g", C.c_double), ("f", C.c_double),
                 ("variant", C.c_int), ("penalty", C.c_int), ("precision", C.c_int),
@@ -131,6 +138,8 @@ EXPORTS["dg_geostrophic_error"] = (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(P
                                               C.POINTER(C.c_double), C.c_void_p])
 EXPORTS["dg_mesh_set_background"] = (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Phys), C.c_void_p,
                                                 C.c_void_p])
+EXPORTS["dg_mesh_set_sponge"] = (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Sponge), C.c_void_p,
+                                            C.c_void_p])
 EXPORTS["dg_profile_begin"] = (C.c_int, [C.c_void_p, C.c_uint32])
 EXPORTS["dg_profile_end"] = (C.c_int, [C.c_void_p, C.POINTER(KernelStat), C.c_int,
                                        C.POINTER(C.c_int)])
@@ -254,6 +263,22 @@ class Mesh:
         """Background state for the perturbation-form (mixed) explicit operator."""
         _check(self.lib.dg_mesh_set_background(self.ctx.h, self.h, C.byref(phys), _ptr(q_bg),
                                                _stream(stream)), "dg_mesh_set_background")
+
+    def set_sponge(self, q_bar=None, lambda_bar=0.0, z_b=0.0, z_t=1.0, x_layers=None, y_layers=None,
+                   stream=None):
+        """Rayleigh damping layers (see dg_mesh_set_sponge); x_layers / y_layers
+        are (lo, hi, width) or None; q_bar=None switches the layers off."""
+        if q_bar is None:
+            _check(self.lib.dg_mesh_set_sponge(self.ctx.h, self.h, None, None, _stream(stream)),
+                   "dg_mesh_set_sponge")
+            return
+        s = Sponge(lambda_bar=lambda_bar, z_b=z_b, z_t=z_t)
+        if x_layers is not None:
+            s.x_layers, (s.x_lo, s.x_hi, s.x_width) = 1, x_layers
+        if y_layers is not None:
+            s.y_layers, (s.y_lo, s.y_hi, s.y_width) = 1, y_layers
+        _check(self.lib.dg_mesh_set_sponge(self.ctx.h, self.h, C.byref(s), _ptr(q_bar), _stream(stream)),
+               "dg_mesh_set_sponge")
 
     def autotune(self, precision="mixed", stream=None):
         """Pick the cells-per-block multiplier of each cell kernel by timing."""
