@@ -593,11 +593,12 @@ int capture_step(dg_mesh* m, const dg_phys* ph, double* q, double dt, const dg_s
     if ((rc = while_close(s[1])) != DG_OK) return rc;
     k_stage_state<<<gb, 256, 0, s[0]>>>(rho, u, p, n, ph->gamma, y);
     DG_LAUNCH_CHECK("graph stage state");
-    if (incr)
+    if (incr) {
       rc = explicit_increment(m, pk, y, q, Fns[0], Fs[0], Fns[l], Fs[l], s[0]);
       if (rc == DG_OK) rc = sponge_rt(m, y, Fns[l], s[0]);
-    else
+    } else {
       rc = explicit_rt(m, ph, y, Fns[l], Fs[l], s[0]);
+    }
     if (rc != DG_OK) return rc;
     yprev = y;
   }

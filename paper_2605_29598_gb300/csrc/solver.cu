@@ -698,11 +698,12 @@ int step_host(dg_mesh* m, const dg_phys* ph, double* q, double dt, const dg_step
     inf.picard_iters[l] = kk;
     DG_RUN(m, K_STAGE, st, k_stage_state<<<gb, 256, 0, st>>>(rho, u, p, n, ph->gamma, y));
     DG_LAUNCH_CHECK("stage state");
-    if (incr)
+    if (incr) {
       rc = explicit_increment(m, pk, y, q, Fns[0], Fs[0], Fns[l], Fs[l], st);
       if (rc == DG_OK) rc = sponge_rt(m, y, Fns[l], st);
-    else
+    } else {
       rc = explicit_rt(m, ph, y, Fns[l], Fs[l], st);
+    }
     if (rc != DG_OK) return rc;
     yprev = y;
     // the next stage reads y as its initial guess before overwriting it
