@@ -314,9 +314,11 @@ def run_graph_modes(D, I, ctx, case, steps, warmup):
     return out
 
 
-def run_variant(D, I, ctx, case, steps, warmup, precond=False, state=None):
+def run_variant(D, I, ctx, case, steps, warmup, precond=False, state=None, sponge=None):
     """FP64 and mixed steps of another workload (timed with CUDA events);
-    precond=True runs the Schur GMRES with the vertical-line preconditioner."""
+    precond=True runs the Schur GMRES with the vertical-line preconditioner;
+    sponge: keyword arguments of Mesh.set_sponge (damping towards the start
+    state)."""
     import torch
     mesh = D.Mesh(ctx, case["mesh"], case["degree"])
     st = mesh.stats()
@@ -326,6 +328,9 @@ def run_variant(D, I, ctx, case, steps, warmup, precond=False, state=None):
                       device="cuda").contiguous()
     out = {"cells": st.n_elem, "nodes": st.n_nodes, "hanging_points": st.n_hang_points,
            "degree": case["degree"], "dt": case["dt"], "gmres_precond": "vline" if precond else "none"}
+    if sponge:
+        mesh.set_sponge(q0, **sponge)
+        out["sponge"] = {k: v for k, v in sponge.items()}
     stream = torch.cuda.current_stream()
     for prec in ("fp64", "mixed"):
         phys = D.make_phys(f=case["f"], variant="R2", precision=prec)
@@ -586,6 +591,11 @@ def gpu_main(args):
         variants["hill3d_nc"] = run_variant(D, I, ctx, I.hill3d_case(refine=True), steps=2, warmup=1)
         variants["hill3d_vline_precond"] = run_variant(D, I, ctx, I.hill3d_case(), steps=2, warmup=1,
                                                        precond=True)
+        h3 = I.hill3d_case()
+        variants["hill3d_damped"] = run_variant(
+            D, I, ctx, h3, steps=2, warmup=1,
+            sponge=dict(lambda_bar=1.2 / h3["dt"], z_b=14e3, z_t=20e3, x_layers=(0.0, 200e3, 20e3),
+                        y_layers=(0.0, 200e3, 20e3)))
         pw = I.planetary_igw_case()
         variants["planetary_igw"] = run_variant(D, I, ctx, pw, steps=4, warmup=1, state=I.isothermal_state)
         variants["planetary_igw_vline_precond"] = run_variant(D, I, ctx, pw, steps=4, warmup=1, precond=True,
