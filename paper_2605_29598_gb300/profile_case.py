@@ -2,6 +2,7 @@
 
     python -m paper_2605_29598_gb300.profile_case --op vmult --reps 3
     python -m paper_2605_29598_gb300.profile_case --op explicit --cells 30 30 20
+    python -m paper_2605_29598_gb300.profile_case --op precond --cells 30 30 20
 
 Builds the mesh and state of the hill workload (optionally with fewer
 cells), prepares one set of implicit coefficients from the state and runs
@@ -16,7 +17,7 @@ import numpy as np
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--op", choices=["vmult", "explicit", "rhs", "recover"], default="vmult")
+    ap.add_argument("--op", choices=["vmult", "explicit", "rhs", "recover", "precond"], default="vmult")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--cells", type=int, nargs=3, default=[60, 60, 20])
     ap.add_argument("--degree", type=int, default=3)
@@ -51,6 +52,8 @@ def main():
             mesh.apply_implicit(phys, cf, x, y)
         elif args.op == "explicit":
             mesh.apply_explicit(phys, q)
+        elif args.op == "precond":
+            mesh.precond_apply(phys, cf, x, y)        # vertical-line setup + one solve
         elif args.op == "rhs":
             mesh.schur_rhs(phys, cf, q[1:4].contiguous(), q[4].contiguous(), y)
         else:
