@@ -69,8 +69,11 @@ int explicit_mixed(dg_mesh* m, const PhysK& ph, const double* q, double* fns, do
 int increment_begin(dg_mesh* m, double gamma, const double* q0, cudaStream_t st);
 int explicit_increment(dg_mesh* m, const PhysK& ph, const double* q, const double* q0, const double* f0_ns,
                        const double* f0_s, double* fns, double* fs, cudaStream_t st);
-// fns -= lambda (q - q_bar) when the mesh has damping layers (sponge.cu)
-int sponge_rt(dg_mesh* m, const double* q, double* fns, cudaStream_t st);
+// fns -= lambda (q - q_bar) when the mesh has damping layers (sponge.cu);
+// with ref, fns -= lambda (q - ref): the damping increment for rates that
+// were formed as increments about ref from rates that already hold the
+// damping at ref
+int sponge_rt(dg_mesh* m, const double* q, double* fns, cudaStream_t st, const double* ref = nullptr);
 // FP32 Schur vmult (coefficients and vectors cast from / to FP64)
 int schur_vmult_mixed(dg_mesh* m, const ImplK& k, const double* rho, const double* plag, const double* ulag,
                       int penalty, const double* x, double* y, cudaStream_t st);

@@ -595,7 +595,8 @@ int capture_step(dg_mesh* m, const dg_phys* ph, double* q, double dt, const dg_s
     DG_LAUNCH_CHECK("graph stage state");
     if (incr) {
       rc = explicit_increment(m, pk, y, q, Fns[0], Fs[0], Fns[l], Fs[l], s[0]);
-      if (rc == DG_OK) rc = sponge_rt(m, y, Fns[l], s[0]);
+      // Fns[0] already holds the damping at q: add its increment only
+      if (rc == DG_OK) rc = sponge_rt(m, y, Fns[l], s[0], q);
     } else {
       rc = explicit_rt(m, ph, y, Fns[l], Fs[l], s[0]);
     }

@@ -700,7 +700,8 @@ int step_host(dg_mesh* m, const dg_phys* ph, double* q, double dt, const dg_step
     DG_LAUNCH_CHECK("stage state");
     if (incr) {
       rc = explicit_increment(m, pk, y, q, Fns[0], Fs[0], Fns[l], Fs[l], st);
-      if (rc == DG_OK) rc = sponge_rt(m, y, Fns[l], st);
+      // Fns[0] already holds the damping at q: add its increment only
+      if (rc == DG_OK) rc = sponge_rt(m, y, Fns[l], st, q);
     } else {
       rc = explicit_rt(m, ph, y, Fns[l], Fs[l], st);
     }

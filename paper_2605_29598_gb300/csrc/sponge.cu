@@ -36,7 +36,8 @@ __global__ void k_sponge_lambda(const double* __restrict__ xyz, int dim, int64_t
   lam[i] = l;
 }
 
-// fns -= lambda (q - q_bar) for the five fields of every damped node
+// fns -= lambda (q - qbar) for the five fields of every damped node (qbar:
+// the background, or the reference state of an increment)
 __global__ void k_sponge(double* __restrict__ fns, const double* __restrict__ q, const double* __restrict__ lam,
                          const double* __restrict__ qbar, int64_t N) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -52,10 +53,10 @@ __global__ void k_sponge(double* __restrict__ fns, const double* __restrict__ q,
 
 }  // namespace
 
-int sponge_rt(dg_mesh* m, const double* q, double* fns, cudaStream_t st) {
+int sponge_rt(dg_mesh* m, const double* q, double* fns, cudaStream_t st, const double* ref) {
   if (!m->sponge_set) return DG_OK;
   const double* lam = m->sponge.as<double>();
-  DG_RUN(m, K_STAGE, st, k_sponge<<<grid_for(m->N, 256), 256, 0, st>>>(fns, q, lam, lam + m->N, m->N));
+  DG_RUN(m, K_STAGE, st, k_sponge<<<grid_for(m->N, 256), 256, 0, st>>>(fns, q, lam, ref ? ref : lam + m->N, m->N));
   DG_LAUNCH_CHECK("sponge");
   return DG_OK;
 }

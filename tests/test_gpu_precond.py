@@ -205,3 +205,57 @@ def test_graph_mode_rejects_precond(D, ctx):
         gm.step(D.make_phys(), qd, 3.0, graph=True, gmres_precond=True)
     assert ei.value.status == -2
     assert relerr(host(qd, q.shape), q) == 0.0
+
+
+def test_inverse_without_horizontal_coupling_3d(D, ctx):
+    """The 3D column (flat 2 x 2 x 8 hexes, degree 2): P^{-1} (S x) = x for
+    x = x(z) against the oracle's S."""
+    mesh = I.box_mesh((2, 2, 8), (2e3, 2e3, 8e3))
+    disc = O.Discretisation(mesh, 2)
+    pts = disc.node_points()
+    q = I.stratified_state(pts, wind=(5.0, -2.0, 0.5))
+    u, p = O.nodal_primitives(q, 1.4)
+    cf = O.StageCoeffs(rho=q[0], p_lag=p, u_lag=u, adt=6.0)
+    gm = D.Mesh(ctx, mesh, 2)
+    z = pts[..., -1]
+    x = p * (1.0 + 0.2 * np.sin(np.pi * z / 8e3))
+    Sx = O.schur_apply(disc, cf, O.Phys(f=1e-4), x)
+    keep = (dev(cf.rho.reshape(-1)), dev(cf.p_lag.reshape(-1)), dev(cf.u_lag.reshape(3, -1)))
+    zg = gm.precond_apply(D.make_phys(f=1e-4), D.Mesh.coeffs(*keep, cf.adt), dev(Sx.reshape(-1)))
+    assert relerr(host(zg, x.shape), x) < 2e-5
+
+
+def test_ensemble_step_with_precond(D, ctx):
+    """Ensemble groups step with the preconditioner (host-driven path): same
+    states as without it, to the solver tolerance."""
+    inst = [
+        (I.box_mesh((6, 8), (60e3, 4e3)), 3, 1.2e-4, 20.0),
+        (I.box_mesh((3, 3, 6), (9e3, 9e3, 3e3)), 2, 0.8e-4, 6.0),
+    ]
+    args = ([m for m, _, _, _ in inst], [r for _, r, _, _ in inst], [f for _, _, f, _ in inst])
+    ea, eb = D.Ensemble(ctx, *args), D.Ensemble(ctx, *args)
+    qs = []
+    for i, (m, r, f, dt) in enumerate(inst):
+        disc = O.Discretisation(m, r)
+        q = I.perturb(I.stratified_state(disc.node_points(), wind=(8.0, -2.0, 0.5)),
+                      np.random.default_rng(40 + i), rel=1e-2)
+        qs.append(q)
+        ea.set_state(i, dev(q.reshape(5, -1)))
+        eb.set_state(i, dev(q.reshape(5, -1)))
+    ph = D.make_phys()
+    dts = [dt for _, _, _, dt in inst]
+    opts = dict(picard_fixed=2, gmres_rtol=1e-12, gmres_restart=40, gmres_maxit=2000)
+    na = nb = 0
+    for _ in range(2):
+        na += ea.step(ph, dts, gmres_precond=True, **opts).gmres_iters_total
+        nb += eb.step(ph, dts, **opts).gmres_iters_total
+    assert na < nb, (na, nb)
+    for i, q in enumerate(qs):
+        a = torch.empty((5, ea.nodes[i]), dtype=torch.float64, device="cuda")
+        b = torch.empty((5, eb.nodes[i]), dtype=torch.float64, device="cuda")
+        ea.get_state(i, a)
+        eb.get_state(i, b)
+        torch.cuda.synchronize()
+        a, b = a.cpu().numpy().reshape(q.shape), b.cpu().numpy().reshape(q.shape)
+        for k in range(5):
+            assert relerr(a[k] - q[k], b[k] - q[k]) < 1e-6, (i, k)

@@ -131,3 +131,23 @@ def test_sponge_rejects_bad_layers(D, ctx):
         gm.set_sponge(qbd, lambda_bar=0.1, z_b=3e3, z_t=2e3)
     with pytest.raises(D.DGError):
         gm.set_sponge(qbd, lambda_bar=0.1, z_b=1e3, z_t=2e3, x_layers=(0.0, 9e3, 0.0))
+
+
+def test_sponge_with_fp32_increments(D, ctx):
+    """DG_MIXED_EXPLICIT without a background evaluates the later stages'
+    rates as FP32 increments; the damping pass follows those too: 3 steps
+    stay within the FP32 error level (1e-4 relative to the change) of the
+    FP64 oracle with the layers."""
+    mesh, r, disc, gm, q, qb, sp = setup(D, ctx, "2d_nc")
+    ph = O.Phys(f=1e-4, sponge=sp)
+    opts = O.StepOpts(picard_fixed=2, gmres_rtol=1e-12, gmres_restart=50, gmres_maxit=400)
+    qd = dev(q.reshape(5, -1))
+    dph = D.make_phys(f=1e-4, precision="mixed_explicit")
+    qo = q
+    for _ in range(3):
+        qo = O.imex_ark2_step(disc, ph, qo, 6.0, opts)
+        gm.step(dph, qd, 6.0, picard_fixed=2, gmres_rtol=1e-12, gmres_restart=50, gmres_maxit=2000,
+                gmres_inner_rtol=1e-4)
+    qg = host(qd, qo.shape)
+    for k in range(5):
+        assert relerr(qg[k] - q[k], qo[k] - q[k]) < 1e-4, (k, relerr(qg[k] - q[k], qo[k] - q[k]))
