@@ -355,6 +355,8 @@ class Phys:
     variant: str = "R2"          # "R1" | "R2"
     penalty: bool = True         # implicit Rusanov term on rho e (READING c5)
     sponge: "Sponge" = None      # Rayleigh damping layers (Section 4), or none
+    lambda_min: float = 0.0      # floor (m/s) of the non-stiff Rusanov coefficient; 0: the paper's
+                                 # lambda = |u.n| (a floor is not in the paper: see rusanov_floor)
 
 
 @dataclass
@@ -416,7 +418,15 @@ def explicit_residuals(disc, q, phys):
       [rho E], duplicates this one and is dropped), gravity -rho g k and
       Coriolis -f rho k x u in momentum, -g rho k.u in energy.
     lambda = max(|u- . n|, |u+ . n|) pointwise at face points (READING c3).
-    Walls use the mirror state (READING c12)."""
+    Walls use the mirror state (READING c12).
+
+    Option not in the paper: phys.lambda_min > 0 floors lambda in the three
+    non-stiff Rusanov terms (the stiff rho e term keeps |u.n|, as does its
+    implicit counterpart).  With the flow at rest lambda = |u.n| vanishes,
+    and a cell-to-cell checkerboard of vertical momentum, which the centred
+    pressure flux does not see, oscillates at the buoyancy frequency and
+    grows through the explicit density (about 9 % per step on the planetary
+    wave's columns at dt = 10 s); a floor of 1 m/s damps it."""
     gm = phys.gamma
     d, comp = disc.d, disc.comp
     Q = disc.at_quad(q)                                   # (5, E, Nq)
@@ -472,12 +482,14 @@ def explicit_residuals(disc, q, phys):
     rp, mp, Ep, up, kp, pp, unp, unhp = prim(tp)
     lam = np.maximum(np.abs(unhm), np.abs(unhp))
     pen = 0.5 * lam * dS
+    # non-stiff fluxes: lambda floored at phys.lambda_min (0: the paper's)
+    pen_ns = 0.5 * np.maximum(lam, phys.lambda_min) * dS
     fl_ns = np.zeros((5,) + lam.shape)
     fl_s = np.zeros((5,) + lam.shape)
-    fl_ns[0] = 0.5 * (rm * unm + rp * unp) + pen * (rm - rp)
+    fl_ns[0] = 0.5 * (rm * unm + rp * unp) + pen_ns * (rm - rp)
     for c in range(3):
-        fl_ns[1 + c] = 0.5 * (mm[c] * unm + mp[c] * unp) + pen * (mm[c] - mp[c])
-    fl_ns[4] = 0.5 * (rm * km * unm + rp * kp * unp) + pen * (rm * km - rp * kp)
+        fl_ns[1 + c] = 0.5 * (mm[c] * unm + mp[c] * unp) + pen_ns * (mm[c] - mp[c])
+    fl_ns[4] = 0.5 * (rm * km * unm + rp * kp * unp) + pen_ns * (rm * km - rp * kp)
     for b, c in enumerate(comp):
         fl_s[1 + c] = 0.5 * (pm + pp) * nS[..., b]
     fl_s[4] = 0.5 * gm / (gm - 1.0) * (pm * unm + pp * unp) \

@@ -543,3 +543,56 @@ def test_sponge_inactive_below_layers():
     b_ns, b_s = O.explicit_rates(disc, q, O.Phys(sponge=O.Sponge(lam_bar=0.5, z_b=5e3, z_t=8e3, q_bar=qb)))
     assert np.array_equal(a_s, b_s)
     assert np.abs(a_ns - b_ns).max() <= 1e-14 * np.abs(a_ns).max()
+
+
+# ----------------------------------------------------------------------------
+# Non-stiff Rusanov floor (option, not in the paper)
+# ----------------------------------------------------------------------------
+
+def column_step_jacobian(lambda_min, dt=10.0):
+    """Spectral radius of the linearised ARK2 step about the isothermal rest
+    state (T0 = 250 K) on a 10-cell column (walls at 0 and 10 km, degree 2),
+    for horizontally uniform perturbations of rho, rho w and rho E; built
+    column by column from finite differences of whole oracle steps."""
+    mesh = I.box_mesh((2, 10), (1000e3, 10e3))
+    disc = O.Discretisation(mesh, 2)
+    pts = disc.node_points()
+    q0 = I.isothermal_state(pts.reshape(-1, 2)).reshape((5,) + pts.shape[:-1])
+    ph = O.Phys(f=0.0, lambda_min=lambda_min)
+    opts = O.StepOpts(picard_rtol=1e-13, picard_maxit=30, gmres_rtol=1e-13, gmres_restart=60, gmres_maxit=5000)
+    z, x = pts[..., -1], pts[..., 0]
+    cols = [np.where(x.mean(axis=1) < 500e3)[0], np.where(x.mean(axis=1) >= 500e3)[0]]
+    cols = [c[np.argsort(z[c].mean(axis=1))] for c in cols]
+    n = 3
+    idx = [(f, ci, k) for f in (0, 3, 4) for ci in range(10) for k in range(n)]
+    scale = {0: 1e-6, 3: 1e-6, 4: 1e-1}
+    base = O.imex_ark2_step(disc, ph, q0, dt, opts)
+    J = np.zeros((len(idx), len(idx)))
+    for j, (f, ci, k) in enumerate(idx):
+        dq = np.zeros_like(q0)
+        for col in cols:
+            dq[f, col[ci], np.arange(n) + n * k] = scale[f]
+        d = O.imex_ark2_step(disc, ph, q0 + dq, dt, opts) - base
+        J[:, j] = [d[g, cols[0][cj], n * kk] / scale[g] for (g, cj, kk) in idx]
+    return np.abs(np.linalg.eigvals(J)).max()
+
+
+def test_rest_state_checkerboard_needs_rusanov_floor():
+    """The paper's lambda = |u.n| leaves the column's linearised step with a
+    growing mode (spectral radius about 1.04 at dt = 10 s: a checkerboard of
+    vertical momentum at the buoyancy frequency); lambda floored at 1 m/s in
+    the non-stiff fluxes brings the radius to 1 (neutral modes of the
+    frozen-in quantities only)."""
+    assert column_step_jacobian(0.0) > 1.02
+    assert column_step_jacobian(1.0) < 1.001
+
+
+def test_rusanov_floor_inactive_when_flow_faster():
+    """Where |u.n| exceeds the floor everywhere the rates do not change."""
+    mesh = I.box_mesh((5, 3), (5e3, 3e3), periodic=(True, False))
+    disc = O.Discretisation(mesh, 2)
+    q = I.stratified_state(disc.node_points(), wind=(20.0, 0.0, 15.0))
+    a_ns, a_s = O.explicit_rates(disc, q, O.Phys())
+    b_ns, b_s = O.explicit_rates(disc, q, O.Phys(lambda_min=1.0))
+    assert np.array_equal(a_s, b_s)
+    assert np.abs(a_ns - b_ns).max() <= 1e-13 * np.abs(a_ns).max()
