@@ -141,6 +141,18 @@ typedef struct {
   const double* f_cell;      /* optional device array, one Coriolis parameter
                                 per cell (NULL: f everywhere); lets one mesh
                                 carry several independent instances */
+  double lambda_min;         /* not in the paper: floor (m/s, >= 0) of the
+                                Rusanov coefficient of the non-stiff fluxes
+                                (rho, rho u, rho kappa); 0 keeps the paper's
+                                lambda = max(|u-.n|, |u+.n|).  At rest that
+                                lambda vanishes and a cell-to-cell
+                                checkerboard of vertical momentum, invisible
+                                to the centred pressure flux, grows through
+                                the explicit density at the buoyancy
+                                frequency (about 9 % per step on the
+                                planetary wave at dt = 10 s); 1 m/s damps it.
+                                The stiff rho e Rusanov term and its implicit
+                                counterpart keep |u.n|. */
 } dg_phys;
 
 /*

@@ -147,7 +147,7 @@ struct dg_mesh {
   bool sponge_set = false;
   struct StepGraph* graph = nullptr;   // cached executable graph of imex_ark2_step
   bool bg_set = false;
-  double bg_gamma = 0, bg_g = 0, bg_f = 0;
+  double bg_gamma = 0, bg_g = 0, bg_f = 0, bg_lmin = 0;
   const double* bg_fcell = nullptr;
   std::vector<double> host_h;
   dg::Profiler prof;

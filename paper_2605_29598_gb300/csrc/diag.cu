@@ -60,7 +60,7 @@ extern "C" int dg_geostrophic_error(dg_ctx* ctx, const dg_mesh* mesh, const dg_p
   double* fs = m->fs.as<double>();
   // the scheme's own FP64 pressure gradient and Coriolis term: the stiff
   // x-momentum rate -dp/dx + f rho v
-  PhysK k{ph->gamma, ph->g, ph->f, ph->f_cell};
+  PhysK k{ph->gamma, ph->g, ph->f, ph->f_cell, ph->lambda_min};
   rc = DG_ERR_UNSUPPORTED;
   DG_DISPATCH(m, rc = (Engine<double, D_, N_>::explicit_rates(m, k, q, fns, fs, st)));
   if (rc != DG_OK) return rc;

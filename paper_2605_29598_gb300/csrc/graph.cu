@@ -536,7 +536,7 @@ int capture_step(dg_mesh* m, const dg_phys* ph, double* q, double dt, const dg_s
   const unsigned gb = grid_for(n, 256);
   const bool mixed = ph->precision != DG_FP64;
   const bool incr = ph->precision == DG_MIXED_EXPLICIT && !m->bg_set;
-  const PhysK pk{ph->gamma, ph->g, ph->f, ph->f_cell};
+  const PhysK pk{ph->gamma, ph->g, ph->f, ph->f_cell, ph->lambda_min};
   k_step_begin<<<1, 1, 0, s[0]>>>(wk.ss);
   if ((rc = explicit_rt(m, ph, q, Fns[0], Fs[0], s[0])) != DG_OK) return rc;
   if (incr && (rc = increment_begin(m, ph->gamma, q, s[0])) != DG_OK) return rc;
@@ -621,7 +621,7 @@ size_t make_key(const dg_mesh* m, const dg_phys* ph, const double* q, double dt,
                 unsigned char* out) {
   struct Key {
     const double* q;
-    double dt, gamma, g, f;
+    double dt, gamma, g, f, lambda_min;
     const double* fcell;
     int variant, penalty, precision, bg_set, sponge_set;
     double picard_rtol;
@@ -639,6 +639,7 @@ size_t make_key(const dg_mesh* m, const dg_phys* ph, const double* q, double dt,
   k.gamma = ph->gamma;
   k.g = ph->g;
   k.f = ph->f;
+  k.lambda_min = ph->lambda_min;
   k.fcell = ph->f_cell;
   k.variant = ph->variant;
   k.penalty = ph->penalty;

@@ -61,7 +61,8 @@ static int explicit_with_scratch(dg_mesh* m, const PhysK& ph, const double* q, d
   }
   DG_RUN(m, K_TRACE, st, k_trace<T, DIM, N, 5><<<grid_for(m->S, 256), 256, 0, st>>>(in, m->E, m->N, trc, m->S, tb));
   DG_RUN(m, K_FACE_EXPLICIT, st,
-         k_face_explicit<T, DIM, N><<<grid_for(m->nF, 128), 128, 0, st>>>(ft, trc, slot, hbuf, tb, (T)ph.gamma));
+         k_face_explicit<T, DIM, N><<<grid_for(m->nF, 128), 128, 0, st>>>(ft, trc, slot, hbuf, tb, (T)ph.gamma,
+                                                                       (T)ph.lambda_min));
   if (m->nHC > 0)
     DG_RUN(m, K_HANG_GATHER, st,
            k_hang_gather<T, DIM, N, 9><<<grid_for(m->nHC * CS::NFP, 128), 128, 0, st>>>(ft, hbuf, slot, tb));
@@ -107,7 +108,7 @@ extern "C" int dg_apply_explicit_noalloc(dg_ctx* ctx, const dg_mesh* mesh, const
   int rc = noalloc_scratch(dev, &scratch);
   if (rc != DG_OK) return rc;
   dg_mesh* m = const_cast<dg_mesh*>(mesh);
-  PhysK k{ph->gamma, ph->g, ph->f, ph->f_cell};
+  PhysK k{ph->gamma, ph->g, ph->f, ph->f_cell, ph->lambda_min};
   DG_DISPATCH(m, return explicit_with_scratch<D_, N_>(m, k, q, fns, fs, scratch, (cudaStream_t)stream));
   set_error("dg_apply_explicit_noalloc: unsupported (dim, degree)");
   return DG_ERR_UNSUPPORTED;

@@ -24,7 +24,8 @@ int Engine<T, DIM, N>::explicit_rates(dg_mesh* m, const PhysK& ph, const T* q, T
     in.scale[k] = 1;
   }
   DG_RUN(m, K_TRACE, st, k_trace<T, DIM, N, 5><<<grid_for(m->S, 256), 256, 0, st>>>(in, m->E, m->N, trc, m->S, tb));
-  DG_RUN(m, K_FACE_EXPLICIT, st, k_face_explicit<T, DIM, N><<<grid_for(m->nF, 128), 128, 0, st>>>(ft, trc, slot, hbuf, tb, (T)ph.gamma));
+  DG_RUN(m, K_FACE_EXPLICIT, st, k_face_explicit<T, DIM, N><<<grid_for(m->nF, 128), 128, 0, st>>>(ft, trc, slot, hbuf, tb, (T)ph.gamma,
+                                                                                    (T)ph.lambda_min));
   if (m->nHC > 0)
     DG_RUN(m, K_HANG_GATHER, st, k_hang_gather<T, DIM, N, 9><<<grid_for(m->nHC * CS::NFP, 128), 128, 0, st>>>(ft, hbuf, slot, tb));
   DG_TILE(m, K_VOL_EXPLICIT,
@@ -206,6 +207,10 @@ static int check_common(dg_ctx* ctx, const dg_mesh* m, const dg_phys* ph, const 
     set_error("%s: gamma must be > 1", who);
     return DG_ERR_ARG;
   }
+  if (!(ph->lambda_min >= 0.0)) {
+    set_error("%s: lambda_min must be >= 0", who);
+    return DG_ERR_ARG;
+  }
   if (ph->precision != DG_FP64 && ph->precision != DG_MIXED && ph->precision != DG_MIXED_EXPLICIT) {
     set_error("%s: precision must be DG_FP64, DG_MIXED or DG_MIXED_EXPLICIT", who);
     return DG_ERR_ARG;
@@ -249,7 +254,7 @@ int dg_apply_explicit(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* ph, const
     set_error("dg_apply_explicit: NULL array");
     return DG_ERR_ARG;
   }
-  PhysK k{ph->gamma, ph->g, ph->f, ph->f_cell};
+  PhysK k{ph->gamma, ph->g, ph->f, ph->f_cell, ph->lambda_min};
   dg_mesh* m = const_cast<dg_mesh*>(mesh);
   if (ph->precision == DG_MIXED_EXPLICIT) {
     if (!m->bg_set) {

@@ -158,7 +158,7 @@ template <int DIM> __device__ __forceinline__ int comp_of(int b) { return DIM ==
 
 template <typename T, int DIM, int N>
 __global__ void k_face_explicit(FaceTopo ft, const T* __restrict__ trc, T* __restrict__ slot,
-                                T* __restrict__ hbuf, Tables<T> tb, T gamma) {
+                                T* __restrict__ hbuf, Tables<T> tb, T gamma, T lambda_min) {
   int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= ft.nF) return;
   const int64_t S = ft.S;
@@ -200,15 +200,17 @@ __global__ void k_face_explicit(FaceTopo ft, const T* __restrict__ trc, T* __res
     unm += um[comp_of<DIM>(b)] * nS[b];
     unp += up[comp_of<DIM>(b)] * nS[b];
   }
-  // lambda |n dS| / 2 with lambda = max(|u-.n|, |u+.n|)
+  // lambda |n dS| / 2 with lambda = max(|u-.n|, |u+.n|); the non-stiff
+  // terms use it floored at lambda_min |n dS| (lambda_min = 0: unchanged)
   T pen = (T)0.5 * fmax(fabs(unm), fabs(unp));
+  const T pns = lambda_min > 0 ? fmax(pen, (T)0.5 * lambda_min * sqrt(n2)) : pen;
   const int64_t nH = ft.nH;
-  put<T>(slot, hbuf, S, nH, 0, sm, code, (T)0.5 * (qm[0] * unm + qp[0] * unp) + pen * (qm[0] - qp[0]));
+  put<T>(slot, hbuf, S, nH, 0, sm, code, (T)0.5 * (qm[0] * unm + qp[0] * unp) + pns * (qm[0] - qp[0]));
 #pragma unroll
   for (int c = 0; c < 3; ++c)
     put<T>(slot, hbuf, S, nH, 1 + c, sm, code,
-           (T)0.5 * (qm[1 + c] * unm + qp[1 + c] * unp) + pen * (qm[1 + c] - qp[1 + c]));
-  put<T>(slot, hbuf, S, nH, 4, sm, code, (T)0.5 * (rkm * unm + rkp * unp) + pen * (rkm - rkp));
+           (T)0.5 * (qm[1 + c] * unm + qp[1 + c] * unp) + pns * (qm[1 + c] - qp[1 + c]));
+  put<T>(slot, hbuf, S, nH, 4, sm, code, (T)0.5 * (rkm * unm + rkp * unp) + pns * (rkm - rkp));
   T pav = (T)0.5 * (pm + pp);
   put<T>(slot, hbuf, S, nH, 5, sm, code, pav * nS[0]);
   put<T>(slot, hbuf, S, nH, 6, sm, code, DIM == 3 ? pav * nS[DIM == 3 ? 1 : 0] : (T)0);
@@ -286,6 +288,7 @@ __device__ __forceinline__ double coriolis(const double* fcell, double f, int64_
 struct PhysK {
   double gamma, g, f;
   const double* fcell = nullptr;   // per-cell Coriolis parameter, or null
+  double lambda_min = 0;           // floor of the non-stiff Rusanov coefficient
 };
 
 template <typename T, int DIM, int N, int M = 1>

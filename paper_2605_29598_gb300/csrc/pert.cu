@@ -99,7 +99,8 @@ __device__ __forceinline__ PertPrim pert_prim(const float qb[5], const float qp[
 template <int DIM, int N>
 __global__ void k_face_explicit_pert(FaceTopo ft, const float* __restrict__ trp, const float* __restrict__ trb,
                                      const float* __restrict__ jump, float* __restrict__ slot,
-                                     float* __restrict__ hbuf, Tables<float> tb, float gamma) {
+                                     float* __restrict__ hbuf, Tables<float> tb, float gamma,
+                                     float lambda_min) {
   int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= ft.nF) return;
   const int64_t S = ft.S, nF = ft.nF, nH = ft.nH;
@@ -161,7 +162,12 @@ __global__ void k_face_explicit_pert(FaceTopo ft, const float* __restrict__ trp,
   float jb[6];
 #pragma unroll
   for (int k = 0; k < 6; ++k) jb[k] = __ldg(jump + k * nF + p);
-  const float dpen = pen - __ldg(jump + 6 * nF + p);
+  const float pbar = __ldg(jump + 6 * nF + p);
+  const float dpen = pen - pbar;
+  // non-stiff terms: both coefficients floored at lambda_min |n dS| / 2
+  const float pfl = 0.5f * lambda_min * sqrtf(n2);
+  const float pns = lambda_min > 0.f ? fmaxf(pen, pfl) : pen;
+  const float dpns = lambda_min > 0.f ? pns - fmaxf(pbar, pfl) : dpen;
   // products (a u.n)' = ab un' + a' unb + a' un'
   auto prod = [](float ab, float ap, float unb, float unp) { return ab * unp + ap * unb + ap * unp; };
   float mnA = 0.f, mnB = 0.f;   // m'.n dS on both sides (the mass flux is linear)
@@ -170,15 +176,15 @@ __global__ void k_face_explicit_pert(FaceTopo ft, const float* __restrict__ trp,
     mnA += pm_[1 + comp_of<DIM>(b)] * nS[b];
     mnB += pp_[1 + comp_of<DIM>(b)] * nS[b];
   }
-  put<float>(slot, hbuf, S, nH, 0, sm, code, 0.5f * (mnA + mnB) + pen * (pm_[0] - pp_[0]) + dpen * jb[0]);
+  put<float>(slot, hbuf, S, nH, 0, sm, code, 0.5f * (mnA + mnB) + pns * (pm_[0] - pp_[0]) + dpns * jb[0]);
 #pragma unroll
   for (int c = 0; c < 3; ++c)
     put<float>(slot, hbuf, S, nH, 1 + c, sm, code,
                0.5f * (prod(bm[1 + c], pm_[1 + c], unbA, unpA) + prod(bp[1 + c], pp_[1 + c], unbB, unpB)) +
-                   pen * (pm_[1 + c] - pp_[1 + c]) + dpen * jb[1 + c]);
+                   pns * (pm_[1 + c] - pp_[1 + c]) + dpns * jb[1 + c]);
   put<float>(slot, hbuf, S, nH, 4, sm, code,
              0.5f * (prod(A.rkb, A.rkp, unbA, unpA) + prod(B.rkb, B.rkp, unbB, unpB)) +
-                 pen * (A.rkp - B.rkp) + dpen * jb[4]);
+                 pns * (A.rkp - B.rkp) + dpns * jb[4]);
   const float pav = 0.5f * (A.pp + B.pp);
   put<float>(slot, hbuf, S, nH, 5, sm, code, pav * nS[0]);
   put<float>(slot, hbuf, S, nH, 6, sm, code, DIM == 3 ? pav * nS[DIM == 3 ? 1 : 0] : 0.f);
@@ -290,6 +296,7 @@ static int bg_rates(dg_mesh* m, const PhysK& ph, cudaStream_t st) {
   m->bg_gamma = ph.gamma;
   m->bg_g = ph.g;
   m->bg_f = ph.f;
+  m->bg_lmin = ph.lambda_min;
   m->bg_fcell = ph.fcell;
   return DG_OK;
 }
@@ -377,7 +384,8 @@ static int explicit_pert_impl(dg_mesh* m, const PhysK& ph, const double* q, cons
   DG_RUN(m, K_TRACE, st, k_trace<float, DIM, N, 5><<<grid_for(m->S, 256), 256, 0, st>>>(in, m->E, n, trp, m->S, tb));
   DG_RUN(m, K_FACE_EXPLICIT, st,
          k_face_explicit_pert<DIM, N><<<grid_for(m->nF, 128), 128, 0, st>>>(
-             ft, trp, m->bgtr.as<float>(), m->bgjump.as<float>(), slot, hbuf, tb, (float)ph.gamma));
+             ft, trp, m->bgtr.as<float>(), m->bgjump.as<float>(), slot, hbuf, tb, (float)ph.gamma,
+             (float)ph.lambda_min));
   if (m->nHC > 0)
     DG_RUN(m, K_HANG_GATHER, st, k_hang_gather<float, DIM, N, 9><<<grid_for(m->nHC * CS::NFP, 128), 128, 0, st>>>(ft, hbuf, slot, tb));
   DG_RUN(m, K_VOL_EXPLICIT, st,
@@ -392,7 +400,8 @@ static int explicit_pert_impl(dg_mesh* m, const PhysK& ph, const double* q, cons
 
 int explicit_mixed(dg_mesh* m, const PhysK& ph, const double* q, double* fns, double* fs, cudaStream_t st) {
   int rc;
-  if (ph.gamma != m->bg_gamma || ph.g != m->bg_g || ph.f != m->bg_f || ph.fcell != m->bg_fcell)
+  if (ph.gamma != m->bg_gamma || ph.g != m->bg_g || ph.f != m->bg_f || ph.fcell != m->bg_fcell ||
+      ph.lambda_min != m->bg_lmin)
     if ((rc = bg_rates(m, ph, st)) != DG_OK) return rc;   // background rates for these physics
   const double* Fb = m->bgF.as<double>();
   rc = DG_ERR_UNSUPPORTED;
@@ -429,6 +438,6 @@ extern "C" int dg_mesh_set_background(dg_ctx* ctx, dg_mesh* mesh, const dg_phys*
     set_error("dg_mesh_set_background: gamma must be > 1");
     return DG_ERR_ARG;
   }
-  PhysK k{ph->gamma, ph->g, ph->f, ph->f_cell};
+  PhysK k{ph->gamma, ph->g, ph->f, ph->f_cell, ph->lambda_min};
   return set_background(mesh, k, q_bg, (cudaStream_t)stream);
 }

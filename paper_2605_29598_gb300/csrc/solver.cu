@@ -498,7 +498,7 @@ int prepare_rt(dg_mesh* m, const ImplK& k, const double* rho, const double* plag
 }
 
 int explicit_rt(dg_mesh* m, const dg_phys* ph, const double* q, double* fns, double* fs, cudaStream_t st) {
-  PhysK k{ph->gamma, ph->g, ph->f, ph->f_cell};
+  PhysK k{ph->gamma, ph->g, ph->f, ph->f_cell, ph->lambda_min};
   int rc = DG_ERR_UNSUPPORTED;
   if (ph->precision == DG_MIXED_EXPLICIT && m->bg_set)
     rc = explicit_mixed(m, k, q, fns, fs, st);
@@ -521,8 +521,8 @@ int recover_rt(dg_mesh* m, const ImplK& k, const double* rho, const double* ulag
 }
 
 static int check_phys(const dg_phys* ph, const char* who) {
-  if (!ph || !(ph->gamma > 1.0) || (ph->variant != DG_R1 && ph->variant != DG_R2)) {
-    set_error("%s: invalid physics (gamma > 1, variant R1/R2)", who);
+  if (!ph || !(ph->gamma > 1.0) || (ph->variant != DG_R1 && ph->variant != DG_R2) || !(ph->lambda_min >= 0.0)) {
+    set_error("%s: invalid physics (gamma > 1, variant R1/R2, lambda_min >= 0)", who);
     return DG_ERR_ARG;
   }
   if (ph->precision != DG_FP64 && ph->precision != DG_MIXED && ph->precision != DG_MIXED_EXPLICIT) {
@@ -633,7 +633,7 @@ int step_host(dg_mesh* m, const dg_phys* ph, double* q, double dt, const dg_step
   // stages are increments about the step's start state q, whose FP64 rates
   // are those of the first stage
   const bool incr = ph->precision == DG_MIXED_EXPLICIT && !m->bg_set;
-  const PhysK pk{ph->gamma, ph->g, ph->f, ph->f_cell};
+  const PhysK pk{ph->gamma, ph->g, ph->f, ph->f_cell, ph->lambda_min};
   if ((rc = explicit_rt(m, ph, q, Fns[0], Fs[0], st)) != DG_OK) return rc;
   if (incr && (rc = increment_begin(m, ph->gamma, q, st)) != DG_OK) return rc;
   const double* yprev = q;
@@ -737,7 +737,7 @@ static int tune_precision(dg_mesh* m, bool fp32, const double* q, const double* 
   const int kinds[3] = {K_VOL_EXPLICIT, K_VOL_GRAD, K_VOL_DIV};
   double best[3] = {1e300, 1e300, 1e300};
   int pick[3] = {1, 1, 1};
-  dg_phys ph{1.4, 9.81, 1e-4, DG_R2, 1, fp32 ? DG_MIXED : DG_FP64, nullptr};
+  dg_phys ph{1.4, 9.81, 1e-4, DG_R2, 1, fp32 ? DG_MIXED : DG_FP64, nullptr, 0.0};
   ImplK k = impl_consts(&ph, 1.0);
   int* tiles = fp32 ? m->tile32 : m->tile;
   int rc;

@@ -56,7 +56,7 @@ class Sponge(C.Structure):
 class Phys(C.Structure):
     _fields_ = [("gamma", C.c_double), ("g", C.c_double), ("f", C.c_double),
                 ("variant", C.c_int), ("penalty", C.c_int), ("precision", C.c_int),
-                ("f_cell", C.c_void_p)]
+                ("f_cell", C.c_void_p), ("lambda_min", C.c_double)]
 
 
 class ImplicitCoeffs(C.Structure):
@@ -200,10 +200,11 @@ def _stream(stream):
     return C.c_void_p(stream.cuda_stream)
 
 
-def make_phys(gamma=1.4, g=9.81, f=1e-4, variant="R2", penalty=True, precision="fp64"):
+def make_phys(gamma=1.4, g=9.81, f=1e-4, variant="R2", penalty=True, precision="fp64", lambda_min=0.0):
+    """lambda_min > 0: floor of the non-stiff Rusanov coefficient (not in the paper)."""
     return Phys(gamma=gamma, g=g, f=f, variant=DG_R2 if variant == "R2" else DG_R1,
                 penalty=1 if penalty else 0,
-                precision=PRECISIONS[precision])
+                precision=PRECISIONS[precision], lambda_min=lambda_min)
 
 
 class Context:
