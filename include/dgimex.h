@@ -289,7 +289,8 @@ int dg_recover_velocity(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* phys,
  *     (chains joined by conforming faces of the last reference direction
  *     that end in walls at both ends) -- vertical gradient and divergence
  *     through the K_dd metric entry and the z normals, the vertical faces'
- *     penalty, gravity -- factored once per solve in FP32 (block Thomas,
+ *     penalty, gravity -- factored in FP32 once per dg_gmres_solve call and
+ *     once per stage of imex_ark2_step (from the first Picard iterate; block Thomas,
  *     2n x 2n blocks in the unknowns x and w_z of a cell line) and applied
  *     once per Arnoldi step in flexible form (the vectors Z_j = P^{-1} V_j
  *     are kept, restart x N more doubles, and x += Z y); lines of chains cut
