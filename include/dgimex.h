@@ -296,7 +296,7 @@ int dg_recover_velocity(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* phys,
  *     are kept, restart x N more doubles, and x += Z y); lines of chains cut
  *     by a 2:1 face or a periodic column are left as the identity.  The
  *     stopping test is still on the unpreconditioned residual b - S x.
- *     Host-driven solves and steps only (graph mode: DG_ERR_UNSUPPORTED).
+ *     Also in graph mode (the factorisation is captured once per stage).
  *   other values: DG_ERR_ARG. */
 enum { DG_PRECOND_NONE = 0, DG_PRECOND_VLINE = 1 };
 

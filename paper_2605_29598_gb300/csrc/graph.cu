@@ -106,6 +106,14 @@ __global__ void k_dmultiaxpy(const double* __restrict__ V, const int* __restrict
   w[i] = acc;
 }
 
+// Z_j = z (j from the state): the flexible GMRES keeps the preconditioned
+// vectors for the restart update
+__global__ void k_store_col(const double* __restrict__ z, double* __restrict__ Z, const int* __restrict__ j,
+                            int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) Z[(int64_t)*j * n + i] = z[i];
+}
+
 // V_j = w * inv and the next vmult input xin = V_j (j and inv from the state)
 __global__ void k_dnormalize(const double* w, double* V, const GmState* __restrict__ s, int64_t n,
                              double* __restrict__ xin) {
@@ -415,15 +423,21 @@ int dot_self(dg_mesh* m, const Work& wk, const double* v, double* out, cudaStrea
 // cycles, s[2] Arnoldi steps.
 int capture_gmres(dg_mesh* m, const Work& wk, GmState* gs, const Vmult& A, const double* b, double* x,
                   bool x_is_zero, double tol, int maxit, int restart, const double* tol_dev, const int* maxit_dev,
-                  const cudaStream_t* s) {
+                  const cudaStream_t* s, bool pc = false) {
   const int64_t n = m->N;
   int rc;
   if ((rc = m->gm_V.ensure(sizeof(double) * (size_t)(restart + 1) * n)) != DG_OK) return rc;
   double* V = m->gm_V.as<double>();
+  // flexible right preconditioning as in the host-driven solver: Z_j =
+  // P^-1 V_j (restart columns), the preconditioned vector of the current
+  // step in the column after them
+  if (pc && (rc = m->gm_pc.ensure(sizeof(double) * (size_t)(restart + 1) * n)) != DG_OK) return rc;
+  double* Z = pc ? m->gm_pc.as<double>() : nullptr;
+  double* zt = pc ? Z + (int64_t)restart * n : nullptr;
   const unsigned gb = grid_for(n, 256);
   // k_dmultiaxpy over element pairs when every target allows 16-byte access
   const int pairs = n % 2 == 0 && ((uintptr_t)V & 15) == 0 && ((uintptr_t)wk.w & 15) == 0 &&
-                    ((uintptr_t)x & 15) == 0;
+                    ((uintptr_t)x & 15) == 0 && (!pc || ((uintptr_t)Z & 15) == 0);
   const unsigned gma = grid_for(pairs ? n / 2 : n, 256);
   const dim3 dgrid(RED_BLOCKS, (restart + 2 + 7) / 8);   // k_ddots: up to restart + 1 vectors and w
   if ((rc = dot_self(m, wk, b, &gs->dot[0], s[0])) != DG_OK) return rc;
@@ -447,7 +461,13 @@ int capture_gmres(dg_mesh* m, const Work& wk, GmState* gs, const Vmult& A, const
     if ((rc = while_open(s[1], s[2], ha)) != DG_OK) return rc;
     {
       cudaStream_t sa = s[2];
-      if ((rc = A(wk.xin, wk.w, sa)) != DG_OK) return rc;
+      if (pc) {
+        if ((rc = vline_apply(m, wk.xin, zt, sa)) != DG_OK) return rc;
+        k_store_col<<<gb, 256, 0, sa>>>(zt, Z, &gs->j, n);
+        if ((rc = A(zt, wk.w, sa)) != DG_OK) return rc;
+      } else if ((rc = A(wk.xin, wk.w, sa)) != DG_OK) {
+        return rc;
+      }
       k_ddots<<<dgrid, 256, 0, sa>>>(V, &gs->j, 1, n, wk.w, wk.partial, nullptr);
       k_dreduce<<<MAX_RESTART + 2, 256, 0, sa>>>(wk.partial, &gs->j, 1, gs->dot, nullptr);
       k_orth1<<<1, 1, 0, sa>>>(gs);
@@ -462,7 +482,7 @@ int capture_gmres(dg_mesh* m, const Work& wk, GmState* gs, const Vmult& A, const
     }
     if ((rc = while_close(s[2])) != DG_OK) return rc;
     k_solve_y<<<1, 1, 0, s[1]>>>(gs);
-    k_dmultiaxpy<<<gma, 256, 0, s[1]>>>(V, &gs->jused, 0, n, gs->y, x, nullptr, pairs);
+    k_dmultiaxpy<<<gma, 256, 0, s[1]>>>(pc ? Z : V, &gs->jused, 0, n, gs->y, x, nullptr, pairs);
     if ((rc = A(x, wk.tmp, s[1])) != DG_OK) return rc;
     k_axpby<<<gb, 256, 0, s[1]>>>(n, 1.0, b, -1.0, wk.tmp, V);
     if ((rc = dot_self(m, wk, V, &gs->dot[0], s[1])) != DG_OK) return rc;
@@ -475,7 +495,8 @@ int capture_gmres(dg_mesh* m, const Work& wk, GmState* gs, const Vmult& A, const
 // Iterative refinement (FP64 residual, inner GMRES on the FP32 operator).
 // Capture streams: s[0] current, s[1] sweeps, s[2..3] inner GMRES.
 int capture_gmres_ir(dg_mesh* m, const Work& wk, const Vmult& A64, const Vmult& A32, const double* b, double* x,
-                     double rtol, int restart, int maxit, double inner_rtol, const cudaStream_t* s) {
+                     double rtol, int restart, int maxit, double inner_rtol, const cudaStream_t* s,
+                     bool pc = false) {
   const int64_t n = m->N;
   int rc;
   if ((rc = m->irw.ensure(sizeof(double) * 2 * n)) != DG_OK) return rc;
@@ -497,7 +518,7 @@ int capture_gmres_ir(dg_mesh* m, const Work& wk, const Vmult& A64, const Vmult& 
   {
     DG_CUDA(cudaMemsetAsync(d, 0, sizeof(double) * n, s[1]));
     if ((rc = capture_gmres(m, wk, wk.gs32, A32, r, d, true, 0.0, 0, restart, &ir->tol_in, &ir->maxit_in,
-                            s + 1)) != DG_OK)
+                            s + 1, pc)) != DG_OK)
       return rc;
     k_ir_after<<<1, 1, 0, s[1]>>>(ir, wk.gs32);
     k_axpby<<<gb, 256, 0, s[1]>>>(n, 1.0, x, 1.0, d, x);
@@ -537,6 +558,7 @@ int capture_step(dg_mesh* m, const dg_phys* ph, double* q, double dt, const dg_s
   const bool mixed = ph->precision != DG_FP64;
   const bool incr = ph->precision == DG_MIXED_EXPLICIT && !m->bg_set;
   const PhysK pk{ph->gamma, ph->g, ph->f, ph->f_cell, ph->lambda_min};
+  const bool pc = o->gmres.precond == DG_PRECOND_VLINE;
   k_step_begin<<<1, 1, 0, s[0]>>>(wk.ss);
   if ((rc = explicit_rt(m, ph, q, Fns[0], Fs[0], s[0])) != DG_OK) return rc;
   if (incr && (rc = increment_begin(m, ph->gamma, q, s[0])) != DG_OK) return rc;
@@ -557,6 +579,12 @@ int capture_step(dg_mesh* m, const dg_phys* ph, double* q, double dt, const dg_s
     DG_LAUNCH_CHECK("graph stage predictors");
     ImplK k = impl_consts(ph, adt);
     const int kmax = o->picard_fixed > 0 ? o->picard_fixed : o->picard_maxit;
+    // preconditioner factored once per stage from the first Picard iterate's
+    // coefficients, as the host-driven step does
+    if (pc) {
+      if ((rc = prepare_rt(m, k, rho, p, u, ph->penalty, s[0])) != DG_OK) return rc;
+      if ((rc = vline_setup(m, k, p, ph->penalty, s[0])) != DG_OK) return rc;
+    }
     cudaGraphConditionalHandle h;
     if ((rc = make_handle(s[0], &h)) != DG_OK) return rc;
     k_pic_begin<<<1, 1, 0, s[0]>>>(wk.ss, h);
@@ -573,12 +601,12 @@ int capture_step(dg_mesh* m, const dg_phys* ph, double* q, double dt, const dg_s
         if ((rc = prepare32(m, k, rho, p, u, ph->penalty, sp, &sc32)) != DG_OK) return rc;
         Vmult A32 = make_vmult32(&sc32);
         if ((rc = capture_gmres_ir(m, wk, A, A32, rhs, pnew, o->gmres.rtol, o->gmres.restart, o->gmres.maxit,
-                                   o->gmres.inner_rtol, s + 1)) != DG_OK)
+                                   o->gmres.inner_rtol, s + 1, pc)) != DG_OK)
           return rc;
         k_acc_solve<<<1, 1, 0, sp>>>(wk.ss, nullptr, wk.ir);
       } else {
         if ((rc = capture_gmres(m, wk, wk.gs64, A, rhs, pnew, false, o->gmres.rtol, o->gmres.maxit,
-                                o->gmres.restart, nullptr, nullptr, s + 1)) != DG_OK)
+                                o->gmres.restart, nullptr, nullptr, s + 1, pc)) != DG_OK)
           return rc;
         k_acc_solve<<<1, 1, 0, sp>>>(wk.ss, wk.gs64, nullptr);
       }
@@ -627,7 +655,7 @@ size_t make_key(const dg_mesh* m, const dg_phys* ph, const double* q, double dt,
     double picard_rtol;
     int picard_maxit, picard_fixed;
     double rtol, inner_rtol;
-    int restart, maxit;
+    int restart, maxit, precond;
     int tile[K_COUNT], tile32[K_COUNT];
     const void* bp[dg_mesh::kBufs];
     size_t bb[dg_mesh::kBufs];
@@ -653,6 +681,7 @@ size_t make_key(const dg_mesh* m, const dg_phys* ph, const double* q, double dt,
   k.inner_rtol = o->gmres.inner_rtol;
   k.restart = o->gmres.restart;
   k.maxit = o->gmres.maxit;
+  k.precond = o->gmres.precond;
   for (int i = 0; i < K_COUNT; ++i) {
     k.tile[i] = m->tile[i];
     k.tile32[i] = m->tile32[i];
@@ -773,10 +802,6 @@ int step_graph(dg_mesh* m, const dg_phys* ph, double* q, double dt, const dg_ste
     set_error("imex_ark2_step: graph mode does not run under dg_profile_begin");
     return DG_ERR_UNSUPPORTED;
   }
-  if (o->gmres.precond != DG_PRECOND_NONE) {
-    set_error("imex_ark2_step: graph mode runs the unpreconditioned GMRES only");
-    return DG_ERR_UNSUPPORTED;
-  }
   int rc;
   StepGraph* G;
   if ((rc = graph_of(m, &G)) != DG_OK) return rc;
@@ -831,10 +856,6 @@ void multi_graph_release(MultiGraph* M) {
 int multi_step_graph(int ng, dg_mesh* const* meshes, const dg_phys* phs, double* const* qs, const double* dts,
                      const dg_step_opts* o, dg_step_info* infos, MultiGraph** cache, cudaStream_t st) {
   int rc;
-  if (o->gmres.precond != DG_PRECOND_NONE) {
-    set_error("dg_ensemble_step: graph mode runs the unpreconditioned GMRES only");
-    return DG_ERR_UNSUPPORTED;
-  }
   if (!*cache) {
     MultiGraph* M = new MultiGraph();
     *cache = M;

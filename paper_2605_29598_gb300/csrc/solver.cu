@@ -215,7 +215,10 @@ static int gmres(dg_mesh* m, const Vmult& A, const double* b, double* x, double 
   // gains Z y, so the update matches the Arnoldi relation A Z = V H even
   // though P^{-1} (FP32 factors) is only accurate to rounding; residuals
   // are those of A x = b itself
-  if (pc && (rc = m->gm_pc.ensure(sizeof(double) * (size_t)restart * n)) != DG_OK) return rc;
+  // (one column more than restart: the device-driven solver keeps the
+  // current preconditioned vector there, and sizes its workspace by a
+  // host-driven step)
+  if (pc && (rc = m->gm_pc.ensure(sizeof(double) * (size_t)(restart + 1) * n)) != DG_OK) return rc;
   double* Z = pc ? m->gm_pc.as<double>() : nullptr;
   Red red;
   if ((rc = ensure_red(m, &red)) != DG_OK) return rc;
