@@ -11,8 +11,7 @@ vertical velocity and the solver counters.
 
 --lambda-min floors the Rusanov coefficient of the non-stiff fluxes (not in
 the paper; without it a checkerboard of vertical momentum grows at rest);
---precond runs the Schur GMRES with the vertical-line preconditioner
-(host-driven steps).
+--precond runs the Schur GMRES with the vertical-line preconditioner.
 """
 from __future__ import annotations
 
@@ -32,7 +31,7 @@ def main(argv=None):
     ap.add_argument("--lambda-min", type=float, default=0.0,
                     help="floor (m/s) of the non-stiff Rusanov coefficient (0: the paper's |u.n|)")
     ap.add_argument("--precond", action="store_true",
-                    help="vertical-line preconditioner for the Schur GMRES (implies --host-loop)")
+                    help="vertical-line preconditioner for the Schur GMRES")
     args = ap.parse_args(argv)
 
     import torch
@@ -48,7 +47,7 @@ def main(argv=None):
                      device="cuda").contiguous()
     phys = D.make_phys(f=case["f"], variant="R2", precision=args.precision, lambda_min=args.lambda_min)
     opts = dict(picard_rtol=1e-10, picard_maxit=10, gmres_rtol=1e-10, gmres_restart=30,
-                gmres_maxit=1000, graph=not (args.host_loop or args.precond),
+                gmres_maxit=1000, graph=not args.host_loop,
                 gmres_inner_rtol=1e-4 if args.precision == "mixed" else 0.0,
                 gmres_precond=args.precond)
     dt = case["dt"] if args.dt is None else args.dt
