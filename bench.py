@@ -314,6 +314,24 @@ def run_graph_modes(D, I, ctx, case, steps, warmup):
     return out
 
 
+def max_over_ranks(ms, dist, device):
+    """The slowest rank's time (every rank gets it); ms itself without a
+    process group."""
+    if not dist:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def throughput(nodes_per_rank, steps, world, ms_max):
+    """Whole-job GDoF-updates/s: every rank advances its own replica of
+    nodes_per_rank nodes x 5 fields by `steps` steps; the job takes the
+    slowest rank's time."""
+    return 5.0 * nodes_per_rank * steps * world / (ms_max / 1e3) / 1e9
+
+
 def run_variant(D, I, ctx, case, steps, warmup, precond=False, state=None, sponge=None):
     """FP64 and mixed steps of another workload (timed with CUDA events);
     precond=True runs the Schur GMRES with the vertical-line preconditioner;
@@ -462,12 +480,8 @@ def gpu_main(args):
         dist.barrier()
     clk = clocks.stop()
     ms = e0.elapsed_time(e1)
-    ms_max = ms
-    if dist:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_max = float(t.item())
-    value = 5.0 * N * args.steps * world / (ms_max / 1e3) / 1e9
+    ms_max = max_over_ranks(ms, dist, "cuda")
+    value = throughput(N, args.steps, world, ms_max)
 
     # end to end: host state copied in and out around every step
     qh = torch.empty_like(q, device="cpu").pin_memory()
@@ -485,12 +499,8 @@ def gpu_main(args):
         qh.copy_(qd, non_blocking=True)
     e3.record(stream)
     torch.cuda.synchronize()
-    ms_e2e = e2.elapsed_time(e3)
-    if dist:
-        t = torch.tensor([ms_e2e], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
-    e2e_value = 5.0 * N * args.steps * world / (ms_e2e / 1e3) / 1e9
+    ms_e2e = max_over_ranks(e2.elapsed_time(e3), dist, "cuda")
+    e2e_value = throughput(N, args.steps, world, ms_e2e)
     state_bytes = 5 * N * 8
 
     # mixed precision (FP32 Schur vmults under FP64 refinement) from the same
@@ -515,11 +525,7 @@ def gpu_main(args):
             mx_ref += inf.refinements_total
         e5.record(stream)
         torch.cuda.synchronize()
-        ms_mx = e4.elapsed_time(e5)
-        if dist:
-            t = torch.tensor([ms_mx], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms_mx = float(t.item())
+        ms_mx = max_over_ranks(e4.elapsed_time(e5), dist, "cuda")
 
         def pert_fields(s):
             u = s[1:4] / s[0]
@@ -548,7 +554,7 @@ def gpu_main(args):
         D.profile_begin(mesh, timed=D.KERNEL_CLASSES)
         mesh.step(phys_mx, qp, dt, **mx_opts)
         prof_mx = D.profile_end(mesh)
-        mixed = {"value": 5.0 * N * args.steps * world / (ms_mx / 1e3) / 1e9,
+        mixed = {"value": throughput(N, args.steps, world, ms_mx),
                  "kernel_breakdown_one_step": {k: {"launches": v[0], "ms": round(v[2], 3)}
                                                for k, v in prof_mx.items() if v[0]},
                  "rel_l2_err_vs_tight_fp64_gpu": err_tight,
@@ -572,14 +578,14 @@ def gpu_main(args):
             mesh.step(phys_mxe, qe, dt, **mx_opts)
         e7.record(stream)
         torch.cuda.synchronize()
-        ms_mxe = e6.elapsed_time(e7)
+        ms_mxe = max_over_ranks(e6.elapsed_time(e7), dist, "cuda")
         fe = pert_fields(qe)
         errs_e = {}
         for k in f0:
             den = torch.linalg.norm(f64[k] - f0[k]).item()
             errs_e[k] = torch.linalg.norm(fe[k] - f64[k]).item() / den if den > 0 else None
         mixed["explicit_fp32_variant"] = {
-            "value": 5.0 * N * args.steps * world / (ms_mxe / 1e3) / 1e9, "unit": "GDoF-updates/s",
+            "value": throughput(N, args.steps, world, ms_mxe), "unit": "GDoF-updates/s",
             "ms_per_step": ms_mxe / args.steps, "speedup_vs_fp64": ms_max / ms_mxe,
             "rel_l2_err_vs_fp64_gpu_perturbation": errs_e,
             "what_is_fp32": "as above, plus the explicit rates of stages 2 and 3 as FP32 "
