@@ -297,15 +297,26 @@ int dg_recover_velocity(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* phys,
  *     by a 2:1 face or a periodic column are left as the identity.  The
  *     stopping test is still on the unpreconditioned residual b - S x.
  *     Also in graph mode (the factorisation is captured once per stage).
+ *   DG_PRECOND_CELL (2) block Jacobi with the exact diagonal cell blocks of
+ *     S (the cell's own volume and face terms plus, through every
+ *     conforming neighbour, the term the face flux of the gradient brings
+ *     back through the divergence's face flux; 2:1 faces keep only their
+ *     own half), inverted in FP32 per cell; same flexible GMRES, setup and
+ *     graph support as DG_PRECOND_VLINE.  For meshes whose stiff part the
+ *     vertical lines miss (columns cut by 2:1 faces).  Degree <= 3 in 3D
+ *     (blocks of up to 64 x 64), any supported degree in 2D; otherwise
+ *     DG_ERR_UNSUPPORTED.
  *   other values: DG_ERR_ARG. */
-enum { DG_PRECOND_NONE = 0, DG_PRECOND_VLINE = 1 };
+enum { DG_PRECOND_NONE = 0, DG_PRECOND_VLINE = 1, DG_PRECOND_CELL = 2 };
 
-/* z = P^{-1} r for the vertical-line preconditioner P of DG_PRECOND_VLINE
- * built from the frozen coefficients cf (r, z: N, device, not aliased);
- * the phys precision field is ignored (P is always factored in FP32 from
- * the FP64 coefficients).  Exposed to test and inspect the preconditioner. */
+/* z = P^{-1} r for the preconditioner P of kind `precond`
+ * (DG_PRECOND_VLINE or DG_PRECOND_CELL) built from the frozen coefficients
+ * cf (r, z: N, device, not aliased); the phys precision field is ignored
+ * (P is always factored in FP32 from the FP64 coefficients).  Exposed to
+ * test and inspect the preconditioners. */
 int dg_precond_apply(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* phys,
-                     const dg_implicit_coeffs* cf, const double* r, double* z, void* stream);
+                     const dg_implicit_coeffs* cf, int precond, const double* r, double* z,
+                     void* stream);
 typedef struct {
   double rtol;
   int restart, maxit;

@@ -80,7 +80,7 @@ namespace dg {
 enum KernelId {
   K_TRACE = 0, K_FACE_EXPLICIT, K_HANG_GATHER, K_VOL_EXPLICIT, K_FACE_LAMBDA, K_FACE_GRAD,
   K_VOL_GRAD, K_FACE_DIV, K_VOL_DIV, K_USTAR, K_MULTIDOT, K_REDUCE, K_MULTIAXPY, K_VEC,
-  K_STAGE, K_PICARD_NORMS, K_VLINE, K_VLINE_SETUP, K_COUNT
+  K_STAGE, K_PICARD_NORMS, K_VLINE, K_VLINE_SETUP, K_COUNT   // K_VLINE*: preconditioner solve / setup
 };
 extern const char* const kKernelNames[K_COUNT];
 
@@ -142,6 +142,9 @@ struct dg_mesh {
   int* vl_below = nullptr;
   int* vl_heads = nullptr;
   dg::DBuf vl_slots, vl_fac, vl_scr, gm_pc;
+  // cell-block preconditioner: per-slot face data, FP32 inverse cell blocks
+  dg::DBuf cb_slots, cb_inv;
+  int pc_kind = 0;   // DG_PRECOND_* of the factors last set up
   // Rayleigh damping layers: lambda (N) then q_bar (5 x N)
   dg::DBuf sponge;
   bool sponge_set = false;
@@ -161,12 +164,13 @@ struct dg_mesh {
   bool terrain = false;
   int64_t workspace_bytes() const;
   // every workspace buffer, for accounting, release and graph capture checks
-  static constexpr int kBufs = 32;
+  static constexpr int kBufs = 34;
   void bufs(const dg::DBuf** out) const {
     const dg::DBuf* b[kBufs] = {&trc, &slot, &hbuf, &trh, &pcoef, &wv, &gm_V, &gm_work, &red, &st,
                                 &fns, &fs, &trh32, &pcoef32, &c32, &ir32, &irw, &irho, &irho32,
                                 &bg, &bg32, &bgF, &bgtr, &bgjump, &pert32, &gstate, &gwork,
-                                &vl_slots, &vl_fac, &vl_scr, &gm_pc, &sponge};
+                                &vl_slots, &vl_fac, &vl_scr, &gm_pc, &sponge,
+                                &cb_slots, &cb_inv};
     for (int i = 0; i < kBufs; ++i) out[i] = b[i];
   }
 };
@@ -175,6 +179,8 @@ namespace dg {
 
 // releases the cached step graph of a mesh (defined with the graph code)
 void graph_release(dg_mesh* m);
+// outward n dS of every face slot (d x S, own cell), mesh.cu
+int slot_normals(const dg_mesh* m, double* out, cudaStream_t st);
 
 }  // namespace dg
 

@@ -462,7 +462,7 @@ int capture_gmres(dg_mesh* m, const Work& wk, GmState* gs, const Vmult& A, const
     {
       cudaStream_t sa = s[2];
       if (pc) {
-        if ((rc = vline_apply(m, wk.xin, zt, sa)) != DG_OK) return rc;
+        if ((rc = precond_apply(m, wk.xin, zt, sa)) != DG_OK) return rc;
         k_store_col<<<gb, 256, 0, sa>>>(zt, Z, &gs->j, n);
         if ((rc = A(zt, wk.w, sa)) != DG_OK) return rc;
       } else if ((rc = A(wk.xin, wk.w, sa)) != DG_OK) {
@@ -558,7 +558,7 @@ int capture_step(dg_mesh* m, const dg_phys* ph, double* q, double dt, const dg_s
   const bool mixed = ph->precision != DG_FP64;
   const bool incr = ph->precision == DG_MIXED_EXPLICIT && !m->bg_set;
   const PhysK pk{ph->gamma, ph->g, ph->f, ph->f_cell, ph->lambda_min};
-  const bool pc = o->gmres.precond == DG_PRECOND_VLINE;
+  const bool pc = o->gmres.precond != DG_PRECOND_NONE;
   k_step_begin<<<1, 1, 0, s[0]>>>(wk.ss);
   if ((rc = explicit_rt(m, ph, q, Fns[0], Fs[0], s[0])) != DG_OK) return rc;
   if (incr && (rc = increment_begin(m, ph->gamma, q, s[0])) != DG_OK) return rc;
@@ -583,7 +583,7 @@ int capture_step(dg_mesh* m, const dg_phys* ph, double* q, double dt, const dg_s
     // coefficients, as the host-driven step does
     if (pc) {
       if ((rc = prepare_rt(m, k, rho, p, u, ph->penalty, s[0])) != DG_OK) return rc;
-      if ((rc = vline_setup(m, k, p, ph->penalty, s[0])) != DG_OK) return rc;
+      if ((rc = precond_setup(m, o->gmres.precond, k, p, ph->penalty, s[0])) != DG_OK) return rc;
     }
     cudaGraphConditionalHandle h;
     if ((rc = make_handle(s[0], &h)) != DG_OK) return rc;

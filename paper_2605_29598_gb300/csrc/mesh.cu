@@ -45,7 +45,7 @@ void DBuf::release() {
 const char* const kKernelNames[K_COUNT] = {
     "trace", "face_explicit", "hang_gather", "volume_explicit", "face_lambda", "face_grad",
     "volume_grad", "face_div", "volume_div", "ustar", "multidot", "reduce", "multiaxpy", "vector",
-    "stage", "picard_norms", "vline", "vline_setup"};
+    "stage", "picard_norms", "precond", "precond_setup"};
 
 cudaEvent_t Profiler::next_event() {
   if (used == pool.size()) {
@@ -299,6 +299,32 @@ int ensure_fp32_geometry(dg_mesh* m) {
   }
   m->lv32 = lv32;
   return DG_OK;
+}
+
+// outward n dS of every face slot of its own cell (all S slots, including
+// the coarse sides of 2:1 faces, which the face-point list does not hold)
+__global__ void k_slot_normals(GeoArgs g, int64_t S, double* out) {
+  const int64_t slot = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (slot >= S) return;
+  const int nfaces = 2 * g.dim;
+  const int pt = (int)(slot % g.nfp);
+  const int f = (int)((slot / g.nfp) % nfaces);
+  const int64_t e = slot / ((int64_t)g.nfp * nfaces);
+  const int a = f / 2, s = f % 2;
+  double xi[3] = {0, 0, 0};
+  double w = 1.0;
+  xi[a] = (double)s;
+  for (int t = 0, r = pt; t < g.dim; ++t) {
+    if (t == a) continue;
+    xi[t] = g.x[r % g.n];
+    w *= g.w[r % g.n];
+    r /= g.n;
+  }
+  double J[3][3], adj[3][3];
+  jac(g.verts + e * (int64_t)(g.dim << g.dim), g.dim, xi, J);
+  adjugate(g.dim, J, adj);
+  const double sg = s ? 1.0 : -1.0;
+  for (int b = 0; b < g.dim; ++b) out[(int64_t)b * S + slot] = sg * w * adj[a][b];
 }
 
 static GeoArgs geo_args(const dg_mesh* m) {
@@ -704,6 +730,21 @@ int dg_mesh_info(const dg_mesh* m, dg_mesh_stats* o) {
   o->terrain_following = m->terrain ? 1 : 0;
   return DG_OK;
 }
+
+}  // extern "C"
+
+namespace dg {
+
+int slot_normals(const dg_mesh* m, double* out, cudaStream_t st) {
+  GeoArgs g = geo_args(m);
+  if (m->S > 0) k_slot_normals<<<grid_for(m->S, 256), 256, 0, st>>>(g, m->S, out);
+  DG_LAUNCH_CHECK("slot normals");
+  return DG_OK;
+}
+
+}  // namespace dg
+
+extern "C" {
 
 int dg_mesh_node_coords(dg_ctx* ctx, const dg_mesh* m, double* xyz, void* stream) {
   if (!ctx || !m || !xyz) {

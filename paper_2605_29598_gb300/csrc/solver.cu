@@ -278,7 +278,7 @@ static int gmres(dg_mesh* m, const Vmult& A, const double* b, double* x, double 
       double* w = V + (int64_t)(j + 1) * n;
       if (pc) {
         double* zj = Z + (int64_t)j * n;
-        if ((rc = vline_apply(m, vj, zj, st)) != DG_OK) return rc;
+        if ((rc = precond_apply(m, vj, zj, st)) != DG_OK) return rc;
         if ((rc = A(zj, w, st)) != DG_OK) return rc;
       } else if ((rc = A(vj, w, st)) != DG_OK) {
         return rc;
@@ -551,14 +551,14 @@ int dg_gmres_solve(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* ph, const dg
   if (rc) return rc;
   dg_mesh* m = const_cast<dg_mesh*>(mesh);
   cudaStream_t st = (cudaStream_t)stream;
-  if (opts->precond != DG_PRECOND_NONE && opts->precond != DG_PRECOND_VLINE) {
-    set_error("dg_gmres_solve: precond must be DG_PRECOND_NONE or DG_PRECOND_VLINE");
+  if (opts->precond < DG_PRECOND_NONE || opts->precond > DG_PRECOND_CELL) {
+    set_error("dg_gmres_solve: precond must be DG_PRECOND_NONE, DG_PRECOND_VLINE or DG_PRECOND_CELL");
     return DG_ERR_ARG;
   }
-  const bool pc = opts->precond == DG_PRECOND_VLINE;
+  const bool pc = opts->precond != DG_PRECOND_NONE;
   ImplK k = impl_consts(ph, cf->a_dt);
   if ((rc = prepare_rt(m, k, cf->rho, cf->p_lag, cf->u_lag, ph->penalty, st)) != DG_OK) return rc;
-  if (pc && (rc = vline_setup(m, k, cf->p_lag, ph->penalty, st)) != DG_OK) return rc;
+  if (pc && (rc = precond_setup(m, opts->precond, k, cf->p_lag, ph->penalty, st)) != DG_OK) return rc;
   SchurCtx sc{m, k, cf->rho, cf->p_lag, ph->penalty};
   Vmult A = make_vmult(&sc);
   if (!A.fn) return DG_ERR_UNSUPPORTED;
@@ -589,8 +589,8 @@ int imex_ark2_step(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* ph, double* 
     set_error("imex_ark2_step: gmres restart must be in 1..%d, maxit >= 0, rtol >= 0", MAX_RESTART);
     return DG_ERR_ARG;
   }
-  if (opts->gmres.precond != DG_PRECOND_NONE && opts->gmres.precond != DG_PRECOND_VLINE) {
-    set_error("imex_ark2_step: gmres precond must be DG_PRECOND_NONE or DG_PRECOND_VLINE");
+  if (opts->gmres.precond < DG_PRECOND_NONE || opts->gmres.precond > DG_PRECOND_CELL) {
+    set_error("imex_ark2_step: gmres precond must be DG_PRECOND_NONE, DG_PRECOND_VLINE or DG_PRECOND_CELL");
     return DG_ERR_ARG;
   }
   dg_mesh* m = const_cast<dg_mesh*>(mesh);
@@ -611,7 +611,7 @@ int step_host(dg_mesh* m, const dg_phys* ph, double* q, double dt, const dg_step
   const auto& a = tab.a;
   const auto& at = tab.at;
   const auto& bw = tab.b;
-  const bool pc = opts->gmres.precond == DG_PRECOND_VLINE;
+  const bool pc = opts->gmres.precond != DG_PRECOND_NONE;
   // workspace: F_NS x3 (5n), F_S x3 (4n), y (5n), rho, mhat (3n), ehat, u, unew (3n each), p, pnew, rhs
   if ((rc = m->fns.ensure(sizeof(double) * 15 * n)) != DG_OK) return rc;
   if ((rc = m->fs.ensure(sizeof(double) * 12 * n)) != DG_OK) return rc;
@@ -664,7 +664,7 @@ int step_host(dg_mesh* m, const dg_phys* ph, double* q, double dt, const dg_step
       // approximate inverse, and the later iterates move the coefficients
       // too little to change the iteration counts (measured: same counts,
       // 4-12 % faster steps than refactoring every Picard iteration)
-      if (pc && kk == 0 && (rc = vline_setup(m, k, p, ph->penalty, st)) != DG_OK) return rc;
+      if (pc && kk == 0 && (rc = precond_setup(m, opts->gmres.precond, k, p, ph->penalty, st)) != DG_OK) return rc;
       if ((rc = rhs_rt(m, k, rho, p, u, mhat, ehat, rhs, st)) != DG_OK) return rc;
       DG_CUDA(cudaMemcpyAsync(pnew, p, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
       SchurCtx schur{m, k, rho, p, ph->penalty};

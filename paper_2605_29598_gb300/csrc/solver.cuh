@@ -197,6 +197,13 @@ int recover_rt(dg_mesh* m, const ImplK& k, const double* rho, const double* ulag
 // z = P^{-1} r as often as needed
 int vline_setup(dg_mesh* m, const ImplK& k, const double* plag, int penalty, cudaStream_t st);
 int vline_apply(dg_mesh* m, const double* r, double* z, cudaStream_t st);
+// cell-block preconditioner (cellblock.cu): exact diagonal cell blocks of
+// the scaled Schur operator, inverted in FP32
+int cellblock_setup(dg_mesh* m, const ImplK& k, const double* plag, int penalty, cudaStream_t st);
+int cellblock_apply(dg_mesh* m, const double* r, double* z, cudaStream_t st);
+// the preconditioner of kind DG_PRECOND_* (setup records it in m->pc_kind)
+int precond_setup(dg_mesh* m, int kind, const ImplK& k, const double* plag, int penalty, cudaStream_t st);
+int precond_apply(dg_mesh* m, const double* r, double* z, cudaStream_t st);
 
 // host-driven ARK2 step (any options) and the device-driven one (graph.cu)
 int step_host(dg_mesh* m, const dg_phys* ph, double* q, double dt, const dg_step_opts* opts,

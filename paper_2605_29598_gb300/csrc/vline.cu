@@ -423,7 +423,7 @@ int vline_apply(dg_mesh* m, const double* r, double* z, cudaStream_t st) {
 using namespace dg;
 
 extern "C" int dg_precond_apply(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* ph, const dg_implicit_coeffs* cf,
-                                const double* r, double* z, void* stream) {
+                                int precond, const double* r, double* z, void* stream) {
   if (!ctx || !mesh || !ph || !cf || !cf->rho || !cf->p_lag || !cf->u_lag || !r || !z || r == z) {
     set_error("dg_precond_apply: NULL or aliased argument");
     return DG_ERR_ARG;
@@ -437,6 +437,10 @@ extern "C" int dg_precond_apply(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys*
   ImplK k = impl_consts(ph, cf->a_dt);
   int rc;
   if ((rc = prepare_rt(m, k, cf->rho, cf->p_lag, cf->u_lag, ph->penalty, st)) != DG_OK) return rc;
-  if ((rc = vline_setup(m, k, cf->p_lag, ph->penalty, st)) != DG_OK) return rc;
-  return vline_apply(m, r, z, st);
+  if (precond != DG_PRECOND_VLINE && precond != DG_PRECOND_CELL) {
+    set_error("dg_precond_apply: precond must be DG_PRECOND_VLINE or DG_PRECOND_CELL");
+    return DG_ERR_ARG;
+  }
+  if ((rc = precond_setup(m, precond, k, cf->p_lag, ph->penalty, st)) != DG_OK) return rc;
+  return precond_apply(m, r, z, st);
 }

@@ -67,6 +67,18 @@ class ImplicitCoeffs(C.Structure):
 # GMRES preconditioner choice (dg_gmres_opts.precond)
 DG_PRECOND_NONE = 0
 DG_PRECOND_VLINE = 1
+DG_PRECOND_CELL = 2
+
+
+def _precond_kind(p):
+    """False/None: none; True or "vline": vertical lines; "cell": cell blocks."""
+    if not p:
+        return DG_PRECOND_NONE
+    if p is True or p == "vline":
+        return DG_PRECOND_VLINE
+    if p == "cell":
+        return DG_PRECOND_CELL
+    raise ValueError(f"unknown preconditioner {p!r}")
 
 
 class GmresOpts(C.Structure):
@@ -103,7 +115,7 @@ EXPORTS = {
                                     C.POINTER(ImplicitCoeffs), C.c_void_p, C.c_void_p,
                                     C.c_void_p]),
     "dg_precond_apply": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Phys),
-                                   C.POINTER(ImplicitCoeffs), C.c_void_p, C.c_void_p, C.c_void_p]),
+                                   C.POINTER(ImplicitCoeffs), C.c_int, C.c_void_p, C.c_void_p, C.c_void_p]),
     "dg_schur_rhs": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Phys), C.POINTER(ImplicitCoeffs),
                                C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "dg_recover_velocity": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Phys),
@@ -332,12 +344,12 @@ class Mesh:
                                           _ptr(y), _stream(stream)), "dg_apply_implicit")
         return y
 
-    def precond_apply(self, phys, cf, r, z=None, stream=None):
-        """z = P^{-1} r, P the vertical-line preconditioner of the Schur GMRES."""
+    def precond_apply(self, phys, cf, r, z=None, stream=None, kind="vline"):
+        """z = P^{-1} r, P the Schur GMRES preconditioner of `kind` ("vline" or "cell")."""
         import torch
         z = torch.empty_like(r) if z is None else z
-        _check(self.lib.dg_precond_apply(self.ctx.h, self.h, C.byref(phys), C.byref(cf), _ptr(r),
-                                         _ptr(z), _stream(stream)), "dg_precond_apply")
+        _check(self.lib.dg_precond_apply(self.ctx.h, self.h, C.byref(phys), C.byref(cf), _precond_kind(kind),
+                                         _ptr(r), _ptr(z), _stream(stream)), "dg_precond_apply")
         return z
 
     def schur_rhs(self, phys, cf, m_hat, e_hat, rhs=None, stream=None):
@@ -359,7 +371,7 @@ class Mesh:
                     allow_not_converged=False, inner_rtol=0.0, precond=False):
         """precond=True: right preconditioning by the vertical-line solve."""
         opts = GmresOpts(rtol=rtol, restart=restart, maxit=maxit, inner_rtol=inner_rtol,
-                         precond=DG_PRECOND_VLINE if precond else DG_PRECOND_NONE)
+                         precond=_precond_kind(precond))
         info = GmresInfo()
         st = self.lib.dg_gmres_solve(self.ctx.h, self.h, C.byref(phys), C.byref(cf), _ptr(b),
                                      _ptr(x), C.byref(opts), C.byref(info), _stream(stream))
@@ -373,7 +385,7 @@ class Mesh:
                         picard_fixed=picard_fixed,
                         gmres=GmresOpts(rtol=gmres_rtol, restart=gmres_restart, maxit=gmres_maxit,
                                         inner_rtol=gmres_inner_rtol,
-                                        precond=DG_PRECOND_VLINE if gmres_precond else DG_PRECOND_NONE),
+                                        precond=_precond_kind(gmres_precond)),
                         graph=1 if graph else 0)
         info = StepInfo()
         _check(self.lib.imex_ark2_step(self.ctx.h, self.h, C.byref(phys), _ptr(q), float(dt),
@@ -388,7 +400,7 @@ class Mesh:
 
 KERNEL_CLASSES = ["trace", "face_explicit", "hang_gather", "volume_explicit", "face_lambda",
                   "face_grad", "volume_grad", "face_div", "volume_div", "ustar", "multidot",
-                  "reduce", "multiaxpy", "vector", "stage", "picard_norms", "vline", "vline_setup"]
+                  "reduce", "multiaxpy", "vector", "stage", "picard_norms", "precond", "precond_setup"]
 
 
 def profile_begin(mesh: "Mesh", timed=()):
@@ -463,7 +475,7 @@ class Ensemble:
                         picard_fixed=picard_fixed,
                         gmres=GmresOpts(rtol=gmres_rtol, restart=gmres_restart, maxit=gmres_maxit,
                                         inner_rtol=gmres_inner_rtol,
-                                        precond=DG_PRECOND_VLINE if gmres_precond else DG_PRECOND_NONE),
+                                        precond=_precond_kind(gmres_precond)),
                         graph=1 if graph else 0)
         dts = (C.c_double * self.n)(*[float(x) for x in dt])
         info = StepInfo()

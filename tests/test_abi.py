@@ -49,7 +49,7 @@ def test_null_arguments_rejected_without_gpu(lib):
     assert lib.dg_apply_explicit(None, None, None, None, None, None, None) == -1
     assert lib.dg_gmres_solve(None, None, None, None, None, None, None, None, None) == -1
     assert lib.imex_ark2_step(None, None, None, None, 1.0, None, None, None) == -1
-    assert lib.dg_precond_apply(None, None, None, None, None, None, None) == -1
+    assert lib.dg_precond_apply(None, None, None, None, 1, None, None, None) == -1
     assert lib.dg_mesh_set_sponge(None, None, None, None, None) == -1
 
 
