@@ -18,7 +18,10 @@
 //    point t: c_d / 4 h_k(t) (n.R_k n)(t) sum_m l_m(face)^2 / (rho_k w det J_k)
 //    along k's line through t, lifted into e by the trace weights.
 // 2:1 faces keep only the cell-local half (their return terms need the
-// prolongation and are left out).  Each block (Np x Np, Np = (r+1)^d <= 64)
+// prolongation and are left out).  The return through a neighbour comes back
+// through the same face only when the neighbour touches the cell through one
+// face; a periodic direction of 2 cells (both faces onto one neighbour) also
+// has a return across to the opposite face, which the blocks leave out.  Each block (Np x Np, Np = (r+1)^d <= 64)
 // is assembled and inverted by Gauss-Jordan with partial pivoting in shared
 // memory, one block of threads per cell, in FP32; the solve is one FP32
 // matrix-vector product per cell.
