@@ -393,7 +393,7 @@ int cb_setup_impl(dg_mesh* m, const ImplK& k, const double* plag, int penalty, c
   float* fl = reinterpret_cast<float*>(nS + (size_t)DIM * S);
   float *wg = fl, *wd = fl + S, *pc = fl + 2 * S, *c2 = fl + 3 * S;
   if ((rc = slot_normals(m, nS, st)) != DG_OK) return rc;
-  DG_RUN(m, K_VLINE_SETUP, st, k_cb_prefill<<<grid_for(S, 256), 256, 0, st>>>(S, wg, wd, pc, c2));
+  DG_RUN(m, K_PRECOND_SETUP, st, k_cb_prefill<<<grid_for(S, 256), 256, 0, st>>>(S, wg, wd, pc, c2));
   CbSlotArgs sa;
   sa.fp_minus = m->fp_minus;
   sa.fp_plus = m->fp_plus;
@@ -415,7 +415,7 @@ int cb_setup_impl(dg_mesh* m, const ImplK& k, const double* plag, int penalty, c
   sa.pc = pc;
   sa.c2 = c2;
   if (m->nF > 0)
-    DG_RUN(m, K_VLINE_SETUP, st, (k_cb_slots<DIM, N><<<grid_for(m->nF, 256), 256, 0, st>>>(sa, m->tab.t)));
+    DG_RUN(m, K_PRECOND_SETUP, st, (k_cb_slots<DIM, N><<<grid_for(m->nF, 256), 256, 0, st>>>(sa, m->tab.t)));
   CbAsmArgs g;
   g.E = E;
   g.S = S;
@@ -445,7 +445,7 @@ int cb_setup_impl(dg_mesh* m, const ImplK& k, const double* plag, int penalty, c
     attr_set = true;
   }
   if (E > 0)
-    DG_RUN(m, K_VLINE_SETUP, st,
+    DG_RUN(m, K_PRECOND_SETUP, st,
            (k_cb_assemble<DIM, N><<<(unsigned)E, NP, CB::BYTES, st>>>(g, cast_tables<float>(m->tab.t))));
   DG_LAUNCH_CHECK("cell-block setup");
   m->pc_kind = DG_PRECOND_CELL;
@@ -456,7 +456,7 @@ template <int DIM, int N>
 int cb_apply_impl(dg_mesh* m, const double* r, double* z, cudaStream_t st) {
   constexpr int NP = ipow(N, DIM), EPB = NP >= 256 ? 1 : 256 / NP;
   if (m->E > 0)
-    DG_RUN(m, K_VLINE, st,
+    DG_RUN(m, K_PRECOND, st,
            (k_cb_apply<DIM, N><<<grid_for(m->E, EPB), EPB * NP, 0, st>>>(m->cb_inv.as<float>(), r, z, m->E)));
   DG_LAUNCH_CHECK("cell-block apply");
   return DG_OK;

@@ -80,7 +80,7 @@ namespace dg {
 enum KernelId {
   K_TRACE = 0, K_FACE_EXPLICIT, K_HANG_GATHER, K_VOL_EXPLICIT, K_FACE_LAMBDA, K_FACE_GRAD,
   K_VOL_GRAD, K_FACE_DIV, K_VOL_DIV, K_USTAR, K_MULTIDOT, K_REDUCE, K_MULTIAXPY, K_VEC,
-  K_STAGE, K_PICARD_NORMS, K_VLINE, K_VLINE_SETUP, K_COUNT   // K_VLINE*: preconditioner solve / setup
+  K_STAGE, K_PICARD_NORMS, K_PRECOND, K_PRECOND_SETUP, K_COUNT   // K_PRECOND*: preconditioner solve / setup
 };
 extern const char* const kKernelNames[K_COUNT];
 

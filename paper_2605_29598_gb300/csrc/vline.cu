@@ -373,7 +373,7 @@ int vl_setup_impl(dg_mesh* m, const ImplK& k, const double* plag, int penalty, c
   DG_CUDA(cudaMemsetAsync(sb + 8 * S, 2, (size_t)S, st));
   VlArgs a = vl_args(m);
   if (m->nF > 0)
-    DG_RUN(m, K_VLINE_SETUP, st,
+    DG_RUN(m, K_PRECOND_SETUP, st,
            k_vl_slots<<<grid_for(m->nF, 256), 256, 0, st>>>(topo(m), m->dim,
                                                              penalty ? m->pcoef.as<double>() : nullptr,
                                                              reinterpret_cast<float*>(sb),
@@ -386,7 +386,7 @@ int vl_setup_impl(dg_mesh* m, const ImplK& k, const double* plag, int penalty, c
   constexpr int G = M2 <= 4 ? 4 : (M2 <= 8 ? 8 : 16);
   const int64_t nth = m->n_vchains * m->nfp * G;
   if (nth > 0)
-    DG_RUN(m, K_VLINE_SETUP, st,
+    DG_RUN(m, K_PRECOND_SETUP, st,
            (k_vl_setup<DIM, N><<<grid_for(nth, 256), 256, 0, st>>>(a, cast_tables<float>(m->tab.t))));
   DG_LAUNCH_CHECK("vertical-line setup");
   return DG_OK;
@@ -397,7 +397,7 @@ int vl_apply_impl(dg_mesh* m, const double* r, double* z, cudaStream_t st) {
   VlArgs a = vl_args(m);
   constexpr int M2 = 2 * N, G = M2 <= 4 ? 4 : (M2 <= 8 ? 8 : 16);
   const int64_t nth = m->n_vchains * m->nfp * G;
-  if (nth > 0) DG_RUN(m, K_VLINE, st, (k_vl_apply<DIM, N><<<grid_for(nth, 256), 256, 0, st>>>(a, r, z)));
+  if (nth > 0) DG_RUN(m, K_PRECOND, st, (k_vl_apply<DIM, N><<<grid_for(nth, 256), 256, 0, st>>>(a, r, z)));
   DG_LAUNCH_CHECK("vertical-line apply");
   return DG_OK;
 }
