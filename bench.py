@@ -332,6 +332,59 @@ def throughput(nodes_per_rank, steps, world, ms_max):
     return 5.0 * nodes_per_rank * steps * world / (ms_max / 1e3) / 1e9
 
 
+def run_per_operator(D, mesh, q, f, a_dt, hbm_gbs, reps=10):
+    """Single applies of the boundary's operators on the bench workload, timed
+    with CUDA events (3 warm-ups, `reps` timed): GDoF/s over the DoF each
+    produces (explicit rates: 5 fields, Schur vmult and preconditioner solves:
+    the pressure unknowns), and the fraction of the measured copy bandwidth
+    their algorithmic bytes reach (explicit: 5 fields in, 9 rates out, 112
+    B/node in FP64; vmult: x, y, rho, p_lag and the face lambda, about 38
+    B/node).  Each is a whole entry-point call: the implicit applies also
+    prepare their frozen coefficients (1/rho, h rho traces, face lambda; FP32
+    copies in the mixed form), the preconditioner call also factors.  All of
+    them are bound by the FP64 pipe or by latency, not by HBM."""
+    import torch
+    N = q.shape[1]
+    rho = q[0].contiguous()
+    u = (q[1:4] / q[0]).contiguous()
+    p = (0.4 * (q[4] - 0.5 * (q[1:4] * u).sum(0))).contiguous()
+    cf = D.Mesh.coeffs(rho, p, u, a_dt)
+    x = (p * (1 + 1e-3 * torch.randn_like(p))).contiguous()
+    y = torch.empty_like(x)
+    fns = torch.empty((5, N), dtype=torch.float64, device="cuda")
+    fs = torch.empty((4, N), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    out = {}
+    rows = [
+        ("apply_explicit_fp64", lambda: mesh.apply_explicit(D.make_phys(f=f), q, fns, fs), 5, 112),
+        ("apply_implicit_fp64", lambda: mesh.apply_implicit(D.make_phys(f=f), cf, x, y), 1, 38),
+        ("apply_implicit_mixed", lambda: mesh.apply_implicit(D.make_phys(f=f, precision="mixed"), cf, x, y), 1, 38),
+        ("precond_vline_setup_and_solve", lambda: mesh.precond_apply(D.make_phys(f=f), cf, x, y), 1, None),
+    ]
+    for name, fn, fields, bpn in rows:
+        ms = timed(fn)
+        r = {"ms": ms, "gdof_per_s": fields * N / (ms / 1e3) / 1e9}
+        if bpn:
+            gbs = bpn * N / (ms / 1e3) / 1e9
+            r.update({"algorithmic_bytes_per_node": bpn, "gb_per_s": gbs, "frac_of_measured_hbm": gbs / hbm_gbs})
+        out[name] = r
+    return out
+
+
 def run_variant(D, I, ctx, case, steps, warmup, precond=False, state=None, sponge=None):
     """FP64 and mixed steps of another workload (timed with CUDA events);
     precond=True runs the Schur GMRES with the vertical-line preconditioner;
@@ -623,7 +676,9 @@ def gpu_main(args):
     breakdown = {k: {"launches": v[0], "ms": round(v[2], 3)} for k, v in prof_all.items() if v[0]}
 
     variants = {}
+    per_op = None
     if not args.no_variants and world == 1:
+        per_op = run_per_operator(D, mesh, q, case["f"], 0.29289321881345254 * dt, pk["hbm_gbs"])
         variants["hill3d_nc"] = run_variant(D, I, ctx, I.hill3d_case(refine=True), steps=2, warmup=1)
         variants["hill3d_vline_precond"] = run_variant(D, I, ctx, I.hill3d_case(), steps=2, warmup=1,
                                                        precond=True)
@@ -669,6 +724,7 @@ def gpu_main(args):
         "cpu_baseline": cpu,
         "mixed_precision": mixed,
         "variants": variants,
+        "per_operator": per_op,
         "clocks": clk,
         "gpu_launches": total_launches,
         "iterations": {"picard_per_stage": picard, "gmres_total": gm_its, "gmres_max_relres": relres},
