@@ -208,7 +208,9 @@ def run_oracle_sample(steps, warmup):
 def run_ensemble(D, I, ctx, steps, warmup):
     """32 uneven instances: FP64 one instance at a time (one mesh each) vs
     the batched ensemble (instances sharing (dim, degree) merged) in FP64
-    and mixed precision; whole-ensemble steps timed with CUDA events."""
+    and mixed precision, as host-driven steps and as one graph launch (also
+    with the vertical-line preconditioner); whole-ensemble steps timed with
+    CUDA events."""
     import torch
     cases = I.ensemble_cases()
     stream = torch.cuda.current_stream()
@@ -256,9 +258,11 @@ def run_ensemble(D, I, ctx, steps, warmup):
                      [c["f"] for c in cases])
     out["groups"] = ens.n_groups
     dts = [c["dt"] for c in cases]
-    for prec, graph in (("fp64", False), ("mixed", False), ("mixed", True)):
+    for prec, graph, pc in (("fp64", False, False), ("mixed", False, False), ("mixed", True, False),
+                            ("mixed", True, True)):
         ph = D.make_phys(precision=prec)
-        opts = dict(STEP_OPTS, gmres_inner_rtol=1e-4) if prec == "mixed" else STEP_OPTS
+        opts = dict(STEP_OPTS, gmres_inner_rtol=1e-4) if prec == "mixed" else dict(STEP_OPTS)
+        opts["gmres_precond"] = pc
 
         def ens_steps(n):
             for i, q in enumerate(states):
@@ -270,7 +274,7 @@ def run_ensemble(D, I, ctx, steps, warmup):
 
         ens_steps(warmup)
         ms, its = timed(lambda: ens_steps(steps))
-        out["batched_" + prec + ("_one_graph_launch" if graph else "")] = {
+        out["batched_" + prec + ("_one_graph_launch" if graph else "") + ("_vline_precond" if pc else "")] = {
             "value": 5.0 * nodes * steps / (ms / 1e3) / 1e9, "ms_per_step": ms / steps, "gmres_iters": its}
     ens.close()
     out["unit"] = "GDoF-updates/s"
