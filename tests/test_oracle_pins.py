@@ -364,13 +364,6 @@ def test_balanced_rest_state():
     assert np.abs(q[0] - rho).max() < 1e-11 * rho.max()
 
 
-def test_dof_counts_of_the_paper_meshes():
-    """4800 cells of degree 4 give 6e5 values per scalar field (Section 4.3)."""
-    mesh = I.box_mesh((30, 20, 8), (60e3, 40e3, 16e3))
-    assert mesh.n_elem * 5 ** 3 == 600_000
-    assert 1594 * 5 ** 3 == 199_250
-
-
 # ----------------------------------------------------------------------------
 # convergence orders on a linear rotating acoustic-inertia plane wave
 # ----------------------------------------------------------------------------
