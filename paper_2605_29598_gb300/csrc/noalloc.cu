@@ -59,7 +59,7 @@ static int explicit_with_scratch(dg_mesh* m, const PhysK& ph, const double* q, d
     in.f[k] = q + k * m->N;
     in.scale[k] = 1;
   }
-  DG_RUN(m, K_TRACE, st, k_trace<T, DIM, N, 5><<<grid_for(m->S, 256), 256, 0, st>>>(in, m->E, m->N, trc, m->S, tb));
+  DG_RUN(m, K_TRACE, st, k_trace<T, DIM, N, 5><<<trace_grid<DIM, N>(m->E), TraceShape<DIM, N>::THREADS, 0, st>>>(in, m->E, m->N, trc, m->S, tb));
   DG_RUN(m, K_FACE_EXPLICIT, st,
          k_face_explicit<T, DIM, N><<<grid_for(m->nF, 128), 128, 0, st>>>(ft, trc, slot, hbuf, tb, (T)ph.gamma,
                                                                        (T)ph.lambda_min));

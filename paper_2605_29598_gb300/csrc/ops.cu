@@ -23,7 +23,7 @@ int Engine<T, DIM, N>::explicit_rates(dg_mesh* m, const PhysK& ph, const T* q, T
     in.f[k] = q + k * m->N;
     in.scale[k] = 1;
   }
-  DG_RUN(m, K_TRACE, st, k_trace<T, DIM, N, 5><<<grid_for(m->S, 256), 256, 0, st>>>(in, m->E, m->N, trc, m->S, tb));
+  DG_RUN(m, K_TRACE, st, k_trace<T, DIM, N, 5><<<trace_grid<DIM, N>(m->E), TraceShape<DIM, N>::THREADS, 0, st>>>(in, m->E, m->N, trc, m->S, tb));
   DG_RUN(m, K_FACE_EXPLICIT, st, k_face_explicit<T, DIM, N><<<grid_for(m->nF, 128), 128, 0, st>>>(ft, trc, slot, hbuf, tb, (T)ph.gamma,
                                                                                     (T)ph.lambda_min));
   if (m->nHC > 0)
@@ -57,13 +57,13 @@ int Engine<T, DIM, N>::prepare(dg_mesh* m, const ImplK& ph, const T* rho, const 
   Fields<T> in;
   in.f[0] = plag;
   in.scale[0] = (T)(ph.gamma / (ph.gamma - 1.0));
-  DG_RUN(m, K_TRACE, st, k_trace<T, DIM, N, 1><<<grid_for(m->S, 256), 256, 0, st>>>(in, m->E, m->N, buf_trh<T>(m).template as<T>(), m->S, tb));
+  DG_RUN(m, K_TRACE, st, k_trace<T, DIM, N, 1><<<trace_grid<DIM, N>(m->E), TraceShape<DIM, N>::THREADS, 0, st>>>(in, m->E, m->N, buf_trh<T>(m).template as<T>(), m->S, tb));
   if (penalty) {
     for (int c = 0; c < 3; ++c) {
       in.f[c] = ulag + c * m->N;
       in.scale[c] = 1;
     }
-    DG_RUN(m, K_TRACE, st, k_trace<T, DIM, N, 3><<<grid_for(m->S, 256), 256, 0, st>>>(in, m->E, m->N, m->trc.as<T>(), m->S, tb));
+    DG_RUN(m, K_TRACE, st, k_trace<T, DIM, N, 3><<<trace_grid<DIM, N>(m->E), TraceShape<DIM, N>::THREADS, 0, st>>>(in, m->E, m->N, m->trc.as<T>(), m->S, tb));
     DG_RUN(m, K_FACE_LAMBDA, st, k_face_lambda<T, DIM, N><<<grid_for(m->nF, 128), 128, 0, st>>>(ft, m->trc.as<T>(), (T)(0.5 * ph.a_dt),
                                                                     buf_pcoef<T>(m).template as<T>(), tb));
   }
@@ -85,7 +85,7 @@ int Engine<T, DIM, N>::vmult(dg_mesh* m, const ImplK& ph, const T* rho, const T*
   Fields<T> in;
   in.f[0] = x;
   in.scale[0] = 1;
-  DG_RUN(m, K_TRACE, st, k_trace<T, DIM, N, 1><<<grid_for(m->S, 256), 256, 0, st>>>(in, m->E, m->N, trc, m->S, tb));
+  DG_RUN(m, K_TRACE, st, k_trace<T, DIM, N, 1><<<trace_grid<DIM, N>(m->E), TraceShape<DIM, N>::THREADS, 0, st>>>(in, m->E, m->N, trc, m->S, tb));
   DG_RUN(m, K_FACE_GRAD, st, k_face_grad<T, DIM, N><<<grid_for(m->nF, 128), 128, 0, st>>>(ft, trc, penalty ? buf_pcoef<T>(m).template as<T>() : nullptr,
                                                                 slot, hbuf, tb));
   if (m->nHC > 0)
@@ -100,7 +100,7 @@ int Engine<T, DIM, N>::vmult(dg_mesh* m, const ImplK& ph, const T* rho, const T*
     w.f[b] = wv + b * m->N;
     w.scale[b] = 1;
   }
-  DG_RUN(m, K_TRACE, st, k_trace<T, DIM, N, DIM><<<grid_for(m->S, 256), 256, 0, st>>>(w, m->E, m->N, trc, m->S, tb));
+  DG_RUN(m, K_TRACE, st, k_trace<T, DIM, N, DIM><<<trace_grid<DIM, N>(m->E), TraceShape<DIM, N>::THREADS, 0, st>>>(w, m->E, m->N, trc, m->S, tb));
   DG_RUN(m, K_FACE_DIV, st, k_face_div<T, DIM, N><<<grid_for(m->nF, 128), 128, 0, st>>>(ft, trc, buf_trh<T>(m).template as<T>(), slot, hbuf, tb));
   if (m->nHC > 0)
     DG_RUN(m, K_HANG_GATHER, st, k_hang_gather<T, DIM, N, 1><<<grid_for(m->nHC * CS::NFP, 128), 128, 0, st>>>(ft, hbuf, slot, tb));
@@ -134,7 +134,7 @@ int Engine<T, DIM, N>::schur_rhs(dg_mesh* m, const ImplK& ph, const T* rho, cons
     w.f[b] = ustar + c * m->N;
     w.scale[b] = 1;
   }
-  DG_RUN(m, K_TRACE, st, k_trace<T, DIM, N, DIM><<<grid_for(m->S, 256), 256, 0, st>>>(w, m->E, m->N, trc, m->S, tb));
+  DG_RUN(m, K_TRACE, st, k_trace<T, DIM, N, DIM><<<trace_grid<DIM, N>(m->E), TraceShape<DIM, N>::THREADS, 0, st>>>(w, m->E, m->N, trc, m->S, tb));
   DG_RUN(m, K_FACE_DIV, st, k_face_div<T, DIM, N><<<grid_for(m->nF, 128), 128, 0, st>>>(ft, trc, buf_trh<T>(m).template as<T>(), slot, hbuf, tb));
   if (m->nHC > 0)
     DG_RUN(m, K_HANG_GATHER, st, k_hang_gather<T, DIM, N, 1><<<grid_for(m->nHC * CS::NFP, 128), 128, 0, st>>>(ft, hbuf, slot, tb));
@@ -164,7 +164,7 @@ int Engine<T, DIM, N>::recover(dg_mesh* m, const ImplK& ph, const T* rho, const 
   Fields<T> in;
   in.f[0] = p;
   in.scale[0] = 1;
-  DG_RUN(m, K_TRACE, st, k_trace<T, DIM, N, 1><<<grid_for(m->S, 256), 256, 0, st>>>(in, m->E, m->N, trc, m->S, tb));
+  DG_RUN(m, K_TRACE, st, k_trace<T, DIM, N, 1><<<trace_grid<DIM, N>(m->E), TraceShape<DIM, N>::THREADS, 0, st>>>(in, m->E, m->N, trc, m->S, tb));
   DG_RUN(m, K_FACE_GRAD, st, k_face_grad<T, DIM, N><<<grid_for(m->nF, 128), 128, 0, st>>>(ft, trc, nullptr, slot, hbuf, tb));
   if (m->nHC > 0)
     DG_RUN(m, K_HANG_GATHER, st, k_hang_gather<T, DIM, N, DIM + 1><<<grid_for(m->nHC * CS::NFP, 128), 128, 0, st>>>(ft, hbuf, slot, tb));

@@ -78,34 +78,79 @@ __device__ __forceinline__ T prolong_weight(const Tables<T>& tb, int sub, int fp
 
 // ---------------------------------------------------------------------------
 // traces: slot values of up to 5 nodal fields (times a per-field scale)
+//
+// A block owns TraceShape::CPB consecutive cells.  Their nodal values of all
+// fields are staged in shared memory with coalesced loads (each value is read
+// from HBM once), then every slot of those cells, (e * 2d + f) * NFP + t, is
+// the 1D interpolation along the face normal of one node line, written with
+// coalesced stores (a cell's slots are contiguous).
 // ---------------------------------------------------------------------------
-template <typename T, int DIM, int N, int NFLD>
-__global__ void k_trace(Fields<T> in, int64_t E, int64_t Nn, T* __restrict__ trc, int64_t S,
-                        Tables<T> tb) {
-  constexpr int NP = ipow(N, DIM), NFP = ipow(N, DIM - 1), NF = 2 * DIM;
-  int64_t slot = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (slot >= S) return;
-  int pt = (int)(slot % NFP);
-  int f = (int)((slot / NFP) % NF);
-  int64_t e = slot / (NFP * NF);
-  int a = f >> 1, s = f & 1;
-  int idx[3] = {0, 0, 0};
-  for (int b = 0, r = pt; b < DIM; ++b) {
-    if (b == a) continue;
-    idx[b] = r % N;
-    r /= N;
+template <int DIM, int N>
+struct TraceShape {
+  static constexpr int NP = ipow(N, DIM), NFP = ipow(N, DIM - 1), NS = 2 * DIM * NFP;
+  static constexpr int CPB = NP >= 512 ? 1 : 512 / NP;     // about 512 nodes per block
+  static constexpr int THREADS = 256;
+};
+
+template <int DIM, int N>
+inline unsigned trace_grid(int64_t E) {
+  return grid_for(E, TraceShape<DIM, N>::CPB);
+}
+
+// slots [0, nc * NS) of the block's cells from the staged values; SCALED
+// multiplies each field by its scale (the FP64 pipe bounds this kernel, and
+// the multiply is a fifth of its arithmetic, so unit scales skip it)
+template <typename T, int DIM, int N, int NFLD, bool SCALED>
+__device__ __forceinline__ void trace_slots(const T (*__restrict__ sv)[TraceShape<DIM, N>::CPB * TraceShape<DIM, N>::NP],
+                                            const Fields<T>& in, int nc, int64_t out0, T* __restrict__ trc,
+                                            int64_t S, const Tables<T>& tb) {
+  using TS = TraceShape<DIM, N>;
+  constexpr int NP = TS::NP, NFP = TS::NFP, NS = TS::NS;
+  for (int i = threadIdx.x; i < nc * NS; i += TS::THREADS) {
+    const int c = i / NS;
+    const int r = i - c * NS;
+    const int f = r / NFP, pt = r - f * NFP;
+    const int a = f >> 1, s = f & 1;
+    int idx[3] = {0, 0, 0};
+    for (int b = 0, rr = pt; b < DIM; ++b) {
+      if (b == a) continue;
+      idx[b] = rr % N;
+      rr /= N;
+    }
+    const int stride = a == 0 ? 1 : (a == 1 ? N : N * N);
+    const int base = c * NP + idx[0] + N * idx[1] + N * N * idx[2];
+#pragma unroll
+    for (int q = 0; q < NFLD; ++q) {
+      T acc = 0;
+#pragma unroll
+      for (int k = 0; k < N; ++k) acc += tb.L[s][k] * sv[q][base + k * stride];
+      trc[q * S + out0 + i] = SCALED ? acc * in.scale[q] : acc;
+    }
   }
-  int stride = a == 0 ? 1 : (a == 1 ? N : N * N);
-  int base = idx[0] + N * idx[1] + N * N * idx[2];
-  const int64_t off = e * NP + base;
+}
+
+template <typename T, int DIM, int N, int NFLD>
+__global__ void __launch_bounds__(TraceShape<DIM, N>::THREADS)
+    k_trace(Fields<T> in, int64_t E, int64_t Nn, T* __restrict__ trc, int64_t S, Tables<T> tb) {
+  using TS = TraceShape<DIM, N>;
+  constexpr int NP = TS::NP, NS = TS::NS, CPB = TS::CPB;
+  __shared__ T sv[NFLD][CPB * NP];
+  const int64_t e0 = (int64_t)blockIdx.x * CPB;
+  const int64_t left = E - e0;
+  const int nc = left < CPB ? (int)left : CPB;
+  if (nc <= 0) return;
+  bool unit = true;
 #pragma unroll
   for (int q = 0; q < NFLD; ++q) {
-    const T* __restrict__ src = in.f[q] + off;
-    T acc = 0;
-#pragma unroll
-    for (int k = 0; k < N; ++k) acc += tb.L[s][k] * __ldg(src + k * stride);
-    trc[q * S + slot] = acc * in.scale[q];
+    unit = unit && in.scale[q] == T(1);
+    const T* __restrict__ src = in.f[q] + e0 * NP;
+    for (int i = threadIdx.x; i < nc * NP; i += TS::THREADS) sv[q][i] = __ldg(src + i);
   }
+  __syncthreads();
+  if (unit)
+    trace_slots<T, DIM, N, NFLD, false>(sv, in, nc, e0 * NS, trc, S, tb);
+  else
+    trace_slots<T, DIM, N, NFLD, true>(sv, in, nc, e0 * NS, trc, S, tb);
 }
 
 // plus-side value of a traced field at face point p

@@ -318,9 +318,9 @@ static int bg_faces(dg_mesh* m, const double* qb, double gamma, cudaStream_t st)
     in32.scale[k] = 1;
   }
   DG_RUN(m, K_VEC, st, k_bg_cast<<<grid_for(5 * n, 256), 256, 0, st>>>(qb, m->bg32.as<float>(), 5 * n));
-  DG_RUN(m, K_TRACE, st, k_trace<double, DIM, N, 5><<<grid_for(m->S, 256), 256, 0, st>>>(in, m->E, n, m->trc.as<double>(), m->S, tb));
+  DG_RUN(m, K_TRACE, st, k_trace<double, DIM, N, 5><<<trace_grid<DIM, N>(m->E), TraceShape<DIM, N>::THREADS, 0, st>>>(in, m->E, n, m->trc.as<double>(), m->S, tb));
   DG_RUN(m, K_FACE_EXPLICIT, st, k_bg_jumps<DIM, N><<<grid_for(m->nF, 128), 128, 0, st>>>(ft, m->trc.as<double>(), tb, gamma, m->bgjump.as<float>()));
-  DG_RUN(m, K_TRACE, st, k_trace<float, DIM, N, 5><<<grid_for(m->S, 256), 256, 0, st>>>(in32, m->E, n, m->bgtr.as<float>(), m->S, tb32));
+  DG_RUN(m, K_TRACE, st, k_trace<float, DIM, N, 5><<<trace_grid<DIM, N>(m->E), TraceShape<DIM, N>::THREADS, 0, st>>>(in32, m->E, n, m->bgtr.as<float>(), m->S, tb32));
   DG_LAUNCH_CHECK("background faces");
   return DG_OK;
 }
@@ -381,7 +381,7 @@ static int explicit_pert_impl(dg_mesh* m, const PhysK& ph, const double* q, cons
     in.f[k] = qp + k * n;
     in.scale[k] = 1;
   }
-  DG_RUN(m, K_TRACE, st, k_trace<float, DIM, N, 5><<<grid_for(m->S, 256), 256, 0, st>>>(in, m->E, n, trp, m->S, tb));
+  DG_RUN(m, K_TRACE, st, k_trace<float, DIM, N, 5><<<trace_grid<DIM, N>(m->E), TraceShape<DIM, N>::THREADS, 0, st>>>(in, m->E, n, trp, m->S, tb));
   DG_RUN(m, K_FACE_EXPLICIT, st,
          k_face_explicit_pert<DIM, N><<<grid_for(m->nF, 128), 128, 0, st>>>(
              ft, trp, m->bgtr.as<float>(), m->bgjump.as<float>(), slot, hbuf, tb, (float)ph.gamma,
