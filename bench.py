@@ -540,19 +540,21 @@ def gpu_main(args):
     ms_max = max_over_ranks(ms, dist, "cuda")
     value = throughput(N, args.steps, world, ms_max)
 
-    # end to end: host state copied in and out around every step
+    # end to end: the timed steps again from the same start state (same
+    # iterations), with the host state copied in and out around every step
     qh = torch.empty_like(q, device="cpu").pin_memory()
-    qh.copy_(q)
+    qh.copy_(q_start)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     e2 = torch.cuda.Event(enable_timing=True)
     e3 = torch.cuda.Event(enable_timing=True)
     qd = torch.empty_like(q)
+    e2e_gmres = 0
     e2.record(stream)
     for _ in range(args.steps):
         qd.copy_(qh, non_blocking=True)
-        step(qd)
+        e2e_gmres += step(qd).gmres_iters_total
         qh.copy_(qd, non_blocking=True)
     e3.record(stream)
     torch.cuda.synchronize()
@@ -723,7 +725,7 @@ def gpu_main(args):
                    "parallelism": "replicas" if world > 1 else "single",
                    "tiles_fp64_fp32": tiles},
         "e2e": {"value": e2e_value, "unit": "GDoF-updates/s", "h2d_bytes_per_step": state_bytes,
-                "d2h_bytes_per_step": state_bytes},
+                "d2h_bytes_per_step": state_bytes, "gmres_total": e2e_gmres},
         "roofline": roof,
         "cpu_baseline": cpu,
         "mixed_precision": mixed,
