@@ -196,12 +196,24 @@ def _check(status, where, allow=()):
     return status
 
 
-def _ptr(t):
-    """Device pointer of a contiguous FP64 CUDA tensor."""
+def _validate(numel, device_index, n=None, device=None):
+    """The C ABI takes raw pointers and cannot see a buffer's length or
+    device, so the binding checks both: a short buffer would be read or
+    written out of bounds on the GPU."""
+    if n is not None and numel != n:
+        raise ValueError(f"expected {n} elements, got {numel}")
+    if device is not None and device_index != device:
+        raise ValueError(f"tensor on cuda:{device_index}, context on cuda:{device}")
+
+
+def _ptr(t, n=None, device=None):
+    """Device pointer of a contiguous FP64 CUDA tensor (of n elements on
+    cuda:device when given)."""
     import torch
     if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64
             and t.is_contiguous()):
         raise TypeError("expected a contiguous float64 CUDA tensor")
+    _validate(t.numel(), t.device.index, n, device)
     return C.c_void_p(t.data_ptr())
 
 
@@ -265,16 +277,26 @@ class Mesh:
         self.N = st.n_nodes
         self.Np = st.nodes_per_elem
 
+    def _p(self, t, fields=1):
+        """Pointer of a field-major device array of `fields` x N values."""
+        return _ptr(t, fields * self.N, self.ctx.device)
+
+    def _cf(self, cf):
+        """Coefficients built by `coeffs` for another mesh size or device are
+        rejected before they reach the library."""
+        _validate(getattr(cf, "_n", self.N), getattr(cf, "_dev", self.ctx.device), self.N, self.ctx.device)
+        return C.byref(cf)
+
     def geostrophic_error(self, phys, q, stream=None):
         """E_geo: domain mean of |(1/rho) dp/dx - f v| (scheme's own operators)."""
         out = C.c_double()
-        _check(self.lib.dg_geostrophic_error(self.ctx.h, self.h, C.byref(phys), _ptr(q), C.byref(out),
+        _check(self.lib.dg_geostrophic_error(self.ctx.h, self.h, C.byref(phys), self._p(q, 5), C.byref(out),
                                              _stream(stream)), "dg_geostrophic_error")
         return out.value
 
     def set_background(self, phys, q_bg, stream=None):
         """Background state for the perturbation-form (mixed) explicit operator."""
-        _check(self.lib.dg_mesh_set_background(self.ctx.h, self.h, C.byref(phys), _ptr(q_bg),
+        _check(self.lib.dg_mesh_set_background(self.ctx.h, self.h, C.byref(phys), self._p(q_bg, 5),
                                                _stream(stream)), "dg_mesh_set_background")
 
     def set_sponge(self, q_bar=None, lambda_bar=0.0, z_b=0.0, z_t=1.0, x_layers=None, y_layers=None,
@@ -290,7 +312,7 @@ class Mesh:
             s.x_layers, (s.x_lo, s.x_hi, s.x_width) = 1, x_layers
         if y_layers is not None:
             s.y_layers, (s.y_lo, s.y_hi, s.y_width) = 1, y_layers
-        _check(self.lib.dg_mesh_set_sponge(self.ctx.h, self.h, C.byref(s), _ptr(q_bar), _stream(stream)),
+        _check(self.lib.dg_mesh_set_sponge(self.ctx.h, self.h, C.byref(s), self._p(q_bar, 5), _stream(stream)),
                "dg_mesh_set_sponge")
 
     def autotune(self, precision="mixed", stream=None):
@@ -320,8 +342,8 @@ class Mesh:
     # -- operators -----------------------------------------------------------
     def node_coords(self, stream=None):
         import torch
-        xyz = torch.empty((self.dim, self.N), dtype=torch.float64, device="cuda")
-        _check(self.lib.dg_mesh_node_coords(self.ctx.h, self.h, _ptr(xyz), _stream(stream)),
+        xyz = torch.empty((self.dim, self.N), dtype=torch.float64, device=f"cuda:{self.ctx.device}")
+        _check(self.lib.dg_mesh_node_coords(self.ctx.h, self.h, self._p(xyz, self.dim), _stream(stream)),
                "dg_mesh_node_coords")
         return xyz
 
@@ -329,41 +351,49 @@ class Mesh:
         import torch
         f_ns = torch.empty((5, self.N), dtype=torch.float64, device=q.device) if f_ns is None else f_ns
         f_s = torch.empty((4, self.N), dtype=torch.float64, device=q.device) if f_s is None else f_s
-        _check(self.lib.dg_apply_explicit(self.ctx.h, self.h, C.byref(phys), _ptr(q), _ptr(f_ns),
-                                          _ptr(f_s), _stream(stream)), "dg_apply_explicit")
+        _check(self.lib.dg_apply_explicit(self.ctx.h, self.h, C.byref(phys), self._p(q, 5), self._p(f_ns, 5),
+                                          self._p(f_s, 4), _stream(stream)), "dg_apply_explicit")
         return f_ns, f_s
 
     @staticmethod
     def coeffs(rho, p_lag, u_lag, a_dt):
-        return ImplicitCoeffs(rho=_ptr(rho), p_lag=_ptr(p_lag), u_lag=_ptr(u_lag), a_dt=float(a_dt))
+        """Frozen stage coefficients: rho and p_lag (N values), u_lag (3 x N),
+        all on one device.  The returned struct holds the three tensors, so
+        they live at least as long as it does."""
+        n = rho.numel()
+        dev = rho.device.index
+        cf = ImplicitCoeffs(rho=_ptr(rho), p_lag=_ptr(p_lag, n, dev), u_lag=_ptr(u_lag, 3 * n, dev),
+                            a_dt=float(a_dt))
+        cf._n, cf._dev, cf._keep = n, dev, (rho, p_lag, u_lag)
+        return cf
 
     def apply_implicit(self, phys, cf, x, y=None, stream=None):
         import torch
         y = torch.empty_like(x) if y is None else y
-        _check(self.lib.dg_apply_implicit(self.ctx.h, self.h, C.byref(phys), C.byref(cf), _ptr(x),
-                                          _ptr(y), _stream(stream)), "dg_apply_implicit")
+        _check(self.lib.dg_apply_implicit(self.ctx.h, self.h, C.byref(phys), self._cf(cf), self._p(x),
+                                          self._p(y), _stream(stream)), "dg_apply_implicit")
         return y
 
     def precond_apply(self, phys, cf, r, z=None, stream=None, kind="vline"):
         """z = P^{-1} r, P the Schur GMRES preconditioner of `kind` ("vline" or "cell")."""
         import torch
         z = torch.empty_like(r) if z is None else z
-        _check(self.lib.dg_precond_apply(self.ctx.h, self.h, C.byref(phys), C.byref(cf), _precond_kind(kind),
-                                         _ptr(r), _ptr(z), _stream(stream)), "dg_precond_apply")
+        _check(self.lib.dg_precond_apply(self.ctx.h, self.h, C.byref(phys), self._cf(cf), _precond_kind(kind),
+                                         self._p(r), self._p(z), _stream(stream)), "dg_precond_apply")
         return z
 
     def schur_rhs(self, phys, cf, m_hat, e_hat, rhs=None, stream=None):
         import torch
         rhs = torch.empty_like(e_hat) if rhs is None else rhs
-        _check(self.lib.dg_schur_rhs(self.ctx.h, self.h, C.byref(phys), C.byref(cf), _ptr(m_hat),
-                                     _ptr(e_hat), _ptr(rhs), _stream(stream)), "dg_schur_rhs")
+        _check(self.lib.dg_schur_rhs(self.ctx.h, self.h, C.byref(phys), self._cf(cf), self._p(m_hat, 3),
+                                     self._p(e_hat), self._p(rhs), _stream(stream)), "dg_schur_rhs")
         return rhs
 
     def recover_velocity(self, phys, cf, m_hat, p, u=None, stream=None):
         import torch
         u = torch.empty_like(m_hat) if u is None else u
-        _check(self.lib.dg_recover_velocity(self.ctx.h, self.h, C.byref(phys), C.byref(cf),
-                                            _ptr(m_hat), _ptr(p), _ptr(u), _stream(stream)),
+        _check(self.lib.dg_recover_velocity(self.ctx.h, self.h, C.byref(phys), self._cf(cf),
+                                            self._p(m_hat, 3), self._p(p), self._p(u, 3), _stream(stream)),
                "dg_recover_velocity")
         return u
 
@@ -373,8 +403,8 @@ class Mesh:
         opts = GmresOpts(rtol=rtol, restart=restart, maxit=maxit, inner_rtol=inner_rtol,
                          precond=_precond_kind(precond))
         info = GmresInfo()
-        st = self.lib.dg_gmres_solve(self.ctx.h, self.h, C.byref(phys), C.byref(cf), _ptr(b),
-                                     _ptr(x), C.byref(opts), C.byref(info), _stream(stream))
+        st = self.lib.dg_gmres_solve(self.ctx.h, self.h, C.byref(phys), self._cf(cf), self._p(b),
+                                     self._p(x), C.byref(opts), C.byref(info), _stream(stream))
         _check(st, "dg_gmres_solve", allow=(-4,) if allow_not_converged else ())
         return info
 
@@ -388,7 +418,7 @@ class Mesh:
                                         precond=_precond_kind(gmres_precond)),
                         graph=1 if graph else 0)
         info = StepInfo()
-        _check(self.lib.imex_ark2_step(self.ctx.h, self.h, C.byref(phys), _ptr(q), float(dt),
+        _check(self.lib.imex_ark2_step(self.ctx.h, self.h, C.byref(phys), self._p(q, 5), float(dt),
                                        C.byref(opts), C.byref(info), _stream(stream)),
                "imex_ark2_step")
         return info
@@ -461,11 +491,16 @@ class Ensemble:
         self.n_groups = g.value
         self.total_nodes = t.value
 
+    def _q(self, i, q):
+        if not 0 <= i < self.n:
+            raise IndexError(f"instance {i} of {self.n}")
+        return _ptr(q, 5 * self.nodes[i], self.ctx.device)
+
     def set_state(self, i, q, stream=None):
-        _check(self.lib.dg_ensemble_set_state(self.h, i, _ptr(q), _stream(stream)), "set_state")
+        _check(self.lib.dg_ensemble_set_state(self.h, i, self._q(i, q), _stream(stream)), "set_state")
 
     def get_state(self, i, q, stream=None):
-        _check(self.lib.dg_ensemble_get_state(self.h, i, _ptr(q), _stream(stream)), "get_state")
+        _check(self.lib.dg_ensemble_get_state(self.h, i, self._q(i, q), _stream(stream)), "get_state")
         return q
 
     def step(self, phys, dt, picard_rtol=1e-10, picard_maxit=10, picard_fixed=0, gmres_rtol=1e-10,
@@ -477,6 +512,8 @@ class Ensemble:
                                         inner_rtol=gmres_inner_rtol,
                                         precond=_precond_kind(gmres_precond)),
                         graph=1 if graph else 0)
+        if len(dt) != self.n:
+            raise ValueError(f"{len(dt)} time steps for {self.n} instances")
         dts = (C.c_double * self.n)(*[float(x) for x in dt])
         info = StepInfo()
         _check(self.lib.dg_ensemble_step(self.h, C.byref(phys), dts, C.byref(opts), C.byref(info),

@@ -59,3 +59,22 @@ def test_context_fails_cleanly_without_gpu(lib):
         pytest.skip("a GPU is present")
     h = ctypes.c_void_p()
     assert lib.dg_ctx_create(0, ctypes.byref(h)) in (-1, -3)
+
+
+def test_binding_checks_buffer_sizes_and_devices():
+    """The C ABI receives raw pointers, so the binding checks each buffer's
+    length and device before the call (no GPU needed for the checks)."""
+    torch = pytest.importorskip("torch")
+    from paper_2605_29598_gb300 import dgimex as D
+    D._validate(15, 0, 15, 0)
+    D._validate(15, 1)                     # nothing to check against
+    with pytest.raises(ValueError):
+        D._validate(14, 0, 15, 0)          # short buffer
+    with pytest.raises(ValueError):
+        D._validate(16, 0, 15, 0)          # long buffer: a shape mistake all the same
+    with pytest.raises(ValueError):
+        D._validate(15, 1, 15, 0)          # another GPU than the context's
+    with pytest.raises(TypeError):
+        D._ptr(torch.zeros(4, dtype=torch.float64))          # host tensor
+    with pytest.raises(TypeError):
+        D._ptr(torch.zeros(4, dtype=torch.float32))

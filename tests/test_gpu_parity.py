@@ -328,3 +328,26 @@ def test_mesh_edge_cases_rejected(D, ctx):
         with pytest.raises(D.DGError) as ei:
             D.Mesh(ctx, bad, 2)
         assert ei.value.status == -1
+
+
+def test_binding_rejects_mis_sized_buffers(D, ctx):
+    """Wrong lengths are refused by the binding before any launch: the state,
+    the Schur vector, and coefficients built for another mesh."""
+    import torch
+    gm = D.Mesh(ctx, I.box_mesh((3, 2), (3e3, 2e3)), 2)
+    N = gm.N
+    opt = dict(dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError):
+        gm.apply_explicit(D.make_phys(), torch.ones((5, N - 1), **opt))
+    cf = D.Mesh.coeffs(torch.ones(N, **opt), torch.full((N,), 1e5, **opt), torch.zeros((3, N), **opt), 1.0)
+    with pytest.raises(ValueError):
+        gm.apply_implicit(D.make_phys(), cf, torch.ones(N + 1, **opt))
+    with pytest.raises(ValueError):
+        D.Mesh.coeffs(torch.ones(N, **opt), torch.ones(N, **opt), torch.zeros((2, N), **opt), 1.0)
+    small = D.Mesh.coeffs(torch.ones(N - 9, **opt), torch.ones(N - 9, **opt), torch.zeros((3, N - 9), **opt), 1.0)
+    with pytest.raises(ValueError):
+        gm.apply_implicit(D.make_phys(), small, torch.ones(N, **opt))
+    y = gm.apply_implicit(D.make_phys(), cf, torch.full((N,), 1e5, **opt))
+    torch.cuda.synchronize()
+    assert torch.isfinite(y).all()
+
