@@ -22,13 +22,16 @@ It restates the paper's discretisation in the plainest form available:
   Picard (fixed-point) loop, restarted GMRES with modified Gram-Schmidt and
   Givens rotations, and the three-stage ARK2 step (Butcher tableau);
 * the Rayleigh damping layers of the orography tests (Section 4, eq.
-  damping) as an extra non-stiff rate -lambda (q - q_bar), in weak form.
+  damping) as an extra non-stiff rate -lambda (q - q_bar), in weak form;
+* far-field boundary faces (the upper boundary of the orography tests,
+  Section 4.3), whose outer state is a given background state.
 
 Readings where the paper is silent or garbled (each also used by the CUDA
 path) are marked ``READING`` below.
 
 Parity status: every function here is pinned by tests in
-``tests/test_oracle_pins.py`` (closed forms, invariants, brute force).
+``tests/test_oracle_pins.py`` and ``tests/test_golden.py`` (closed forms, invariants, brute force, values the
+paper prints).
 """
 from __future__ import annotations
 
@@ -38,6 +41,10 @@ from dataclasses import dataclass
 import numpy as np
 
 CHI = 2.0 - math.sqrt(2.0)
+
+# boundary ids of the mesh's boundary face rows [e, f, bc]
+BC_WALL = 1        # slip wall, mirror state (READING c12)
+BC_FARFIELD = 2    # outer state = a given background state (READING R-farfield)
 
 
 # ----------------------------------------------------------------------------
@@ -278,15 +285,17 @@ class Discretisation:
         Vf = [self._basis_at(self._face_ref(f)[0]) for f in range(2 * d)]
         Vh = [[self._basis_at(self._face_ref(f, sub)[0]) for sub in range(1 << (d - 1))]
               for f in range(2 * d)]
-        em, fm, ep, Vm_list, Vp_list = [], [], [], [], []
+        em, fm, ep, Vm_list, Vp_list, bcs = [], [], [], [], [], []
         for eL, fL, eR, fR in m.int_faces:
-            em.append(eL); fm.append(fL); ep.append(eR)
+            em.append(eL); fm.append(fL); ep.append(eR); bcs.append(0)
             Vm_list.append(Vf[fL]); Vp_list.append(Vf[fR])
         for ec, fc, ef, ff, sub in m.hang_faces:
-            em.append(ef); fm.append(ff); ep.append(ec)
+            em.append(ef); fm.append(ff); ep.append(ec); bcs.append(0)
             Vm_list.append(Vf[ff]); Vp_list.append(Vh[fc][sub])
         for e, f, bc in m.bdry_faces:
-            em.append(e); fm.append(f); ep.append(-1)
+            if bc not in (BC_WALL, BC_FARFIELD):
+                raise ValueError(f"unknown boundary condition {bc}")
+            em.append(e); fm.append(f); ep.append(-1); bcs.append(bc)
             Vm_list.append(Vf[f]); Vp_list.append(Vf[f])
         self.f_em = np.array(em, dtype=np.int64)
         self.f_fm = np.array(fm, dtype=np.int64)
@@ -297,8 +306,26 @@ class Discretisation:
         self.f_nS = self._normals(self.f_em, self.f_fm)              # (F, p, d)
         self.f_dS = np.linalg.norm(self.f_nS, axis=-1)              # (F, p)
         self.f_nhat = self.f_nS / self.f_dS[..., None]
-        self.f_wall = self.f_ep < 0
+        self.f_wall = self.f_ep < 0                 # boundary faces: no plus cell
+        self.f_far = np.array(bcs) == BC_FARFIELD   # ... of them, the far-field ones
+        self.f_mirror = self.f_wall & ~self.f_far   # ... and the slip walls
         self.f_epc = np.where(self.f_wall, self.f_em, self.f_ep)
+        self.far_tr = None
+
+    def set_far_state(self, q_far):
+        """Outer state of the far-field faces: traces, at their face points,
+        of the nodal background state q_far (5, E, Np) from the inner cell."""
+        self.far_tr = self.traces(np.asarray(q_far, dtype=np.float64))[0]
+
+    def far_primitives(self, gamma):
+        """(u, p) of the outer state at every face point, (3, F, p) and
+        (F, p), from its conserved traces (meaningful on far-field faces)."""
+        if self.f_far.any() and self.far_tr is None:
+            raise ValueError("far-field faces need set_far_state()")
+        t = self.far_tr
+        u = t[1:4] / t[0]
+        p = (gamma - 1.0) * (t[4] - 0.5 * np.sum(t[1:4] * u, axis=0))
+        return u, p
 
     # -- small helpers --------------------------------------------------------
     def at_quad(self, v):
@@ -418,7 +445,8 @@ def explicit_residuals(disc, q, phys):
       [rho E], duplicates this one and is dropped), gravity -rho g k and
       Coriolis -f rho k x u in momentum, -g rho k.u in energy.
     lambda = max(|u- . n|, |u+ . n|) pointwise at face points (READING c3).
-    Walls use the mirror state (READING c12).
+    Walls use the mirror state (READING c12); far-field faces use the given
+    outer state (READING R-farfield) in the same fluxes as interior faces.
 
     Option not in the paper: phys.lambda_min > 0 floors lambda in the three
     non-stiff Rusanov terms (the stiff rho e term keeps |u.n|, as does its
@@ -460,7 +488,7 @@ def explicit_residuals(disc, q, phys):
     # faces
     tm, tp = disc.traces(q)                               # (5, F, p)
     nS, dS, nh = disc.f_nS, disc.f_dS, disc.f_nhat
-    wall = disc.f_wall
+    wall = disc.f_mirror
     # mirror state on walls: m+ = m- - 2 (m-.n) n
     mS_m = np.stack([tm[1 + c] for c in comp], axis=-1)  # (F, p, d)
     mn = np.sum(mS_m * nh, axis=-1)
@@ -468,6 +496,9 @@ def explicit_residuals(disc, q, phys):
     for b, c in enumerate(comp):
         mirror[1 + c] = tm[1 + c] - 2.0 * mn * nh[..., b]
     tp = np.where(wall[None, :, None], mirror, tp)
+    if disc.f_far.any():
+        disc.far_primitives(gm)                           # checks that the state is set
+        tp = np.where(disc.f_far[None, :, None], disc.far_tr, tp)
 
     def prim(t):
         r_, m_, E_ = t[0], t[1:4], t[4]
@@ -539,7 +570,10 @@ class StageCoeffs:
 
 
 def op_B(disc, cf, x):
-    """B x:  -adt int div(phi_i) x  +  adt int_Gamma {x} [phi_i]  (3, E, Np)."""
+    """B x:  -adt int div(phi_i) x  +  adt int_Gamma {x} [phi_i]  (3, E, Np).
+
+    Walls: {x} = x-.  Far-field faces: {x} = (x- + p_far)/2, of which this
+    linear operator holds x-/2 (the p_far/2 part is in far_affine)."""
     X = disc.at_quad(x)
     out = np.zeros((3,) + x.shape)
     for b, c in enumerate(disc.comp):
@@ -547,7 +581,8 @@ def op_B(disc, cf, x):
         fl[b] = X
         out[c] = -cf.adt * disc.vol_grad(fl)
     tm, tp = disc.traces(x)
-    avg = np.where(disc.f_wall[:, None], tm, 0.5 * (tm + tp))
+    avg = np.where(disc.f_mirror[:, None], tm, 0.5 * (tm + tp))
+    avg = np.where(disc.f_far[:, None], 0.5 * tm, avg)
     flux = np.zeros((3,) + avg.shape)
     for b, c in enumerate(disc.comp):
         # +adt {x} phi.n  enters with the opposite sign of the generic lift
@@ -605,7 +640,9 @@ def op_C(disc, cf, u, gamma):
     """C u:  -adt int h rho phi . grad psi_i + adt int_Gamma {h rho phi}.[psi_i].
 
     h rho = gamma p_lag / (gamma - 1) (h = e + p / rho for the ideal gas).
-    Walls: the mirror velocity makes {h rho u}.n vanish."""
+    Walls: the mirror velocity makes {h rho u}.n vanish.  Far-field faces:
+    the linear part (h rho u)-.n / 2 (the outer state's half is in
+    far_affine)."""
     H = gamma / (gamma - 1.0) * disc.at_quad(cf.p_lag)
     U = disc.at_quad(u)
     fl = np.stack([H * U[c] for c in disc.comp])
@@ -614,7 +651,8 @@ def op_C(disc, cf, u, gamma):
     um, up = disc.traces(u)
     fm = sum(Hm * um[c] * disc.f_nS[..., b] for b, c in enumerate(disc.comp))
     fp = sum(Hp * up[c] * disc.f_nS[..., b] for b, c in enumerate(disc.comp))
-    avg = np.where(disc.f_wall[:, None], 0.0, 0.5 * (fm + fp))
+    avg = np.where(disc.f_mirror[:, None], 0.0, 0.5 * (fm + fp))
+    avg = np.where(disc.f_far[:, None], 0.5 * fm, avg)
     out = out[None]
     disc.lift(out, (-cf.adt * avg)[None])
     return out[0]
@@ -625,21 +663,28 @@ def op_D(disc, p, gamma):
     return disc.vol_weak(disc.at_quad(p)) / (gamma - 1.0)
 
 
-def face_lambda(disc, u_lag):
-    """lambda = max(|u- . n|, |u+ . n|) at face points from nodal u."""
+def face_lambda(disc, u_lag, gamma=1.4):
+    """lambda = max(|u- . n|, |u+ . n|) at face points from nodal u (the
+    outer state's velocity on far-field faces)."""
     um, up = disc.traces(u_lag)
     unm = sum(um[c] * disc.f_nhat[..., b] for b, c in enumerate(disc.comp))
     unp = sum(up[c] * disc.f_nhat[..., b] for b, c in enumerate(disc.comp))
-    unp = np.where(disc.f_wall[:, None], -unm, unp)
+    unp = np.where(disc.f_mirror[:, None], -unm, unp)
+    if disc.f_far.any():
+        uf, _ = disc.far_primitives(gamma)
+        unf = sum(uf[c] * disc.f_nhat[..., b] for b, c in enumerate(disc.comp))
+        unp = np.where(disc.f_far[:, None], unf, unp)
     return np.maximum(np.abs(unm), np.abs(unp))
 
 
 def op_P(disc, cf, p, gamma):
     """Implicit Rusanov term on rho e = p/(gamma-1) at stage l (READING c5):
-    adt/(2(gamma-1)) int_Gamma lambda^(k) [p].[psi_i]; zero on walls."""
-    lam = face_lambda(disc, cf.u_lag)
+    adt/(2(gamma-1)) int_Gamma lambda^(k) [p].[psi_i]; zero on walls; on
+    far-field faces the linear part lambda p- (-lambda p_far in far_affine)."""
+    lam = face_lambda(disc, cf.u_lag, gamma)
     pm, pp = disc.traces(p)
-    jump = np.where(disc.f_wall[:, None], 0.0, pm - pp)
+    jump = np.where(disc.f_mirror[:, None], 0.0, pm - pp)
+    jump = np.where(disc.f_far[:, None], pm, jump)
     flux = cf.adt / (2.0 * (gamma - 1.0)) * lam * disc.f_dS * jump
     out = np.zeros((1,) + p.shape)
     # [p].[psi_i]: minus cell gets +flux psi-, plus cell -flux psi+
@@ -666,6 +711,37 @@ def vec_fg(disc, cf, g):
     out = np.zeros((3,) + cf.rho.shape)
     out[2] = cf.adt * g * disc.vol_weak(disc.at_quad(cf.rho))
     return out
+
+
+def far_affine(disc, cf, phys):
+    """Parts of B p, C u and the implicit Rusanov term P p that the outer
+    state of far-field faces contributes (READING R-farfield): known data,
+    moved to the right-hand sides of the coupled stage system.
+
+    Returns (b_far (3, E, Np), g_far (E, Np)): B p = B_lin p + b_far and
+    C u + P p = C_lin u + P_lin p + g_far, with
+      b_far:  adt int_far (p_far / 2) n . phi_i,
+      g_far:  adt int_far (h rho u)_far . n / 2 psi_i
+              - adt / (2 (gamma - 1)) int_far lambda p_far psi_i."""
+    gm = phys.gamma
+    fb = np.zeros((3,) + cf.rho.shape)
+    gb = np.zeros((1,) + cf.rho.shape)
+    if not disc.f_far.any():
+        return fb, gb[0]
+    far = disc.f_far[:, None]
+    uf, pf = disc.far_primitives(gm)
+    flux = np.zeros((3,) + pf.shape)
+    for b, c in enumerate(disc.comp):
+        flux[c] = np.where(far, -cf.adt * 0.5 * pf * disc.f_nS[..., b], 0.0)
+    disc.lift(fb, flux)
+    unS = sum(uf[c] * disc.f_nS[..., b] for b, c in enumerate(disc.comp))
+    cfl = np.where(far, 0.5 * gm / (gm - 1.0) * pf * unS, 0.0)
+    disc.lift(gb, (-cf.adt * cfl)[None])
+    if phys.penalty:
+        lam = face_lambda(disc, cf.u_lag, gm)
+        pfl = np.where(far, cf.adt / (2.0 * (gm - 1.0)) * lam * disc.f_dS * (-pf), 0.0)
+        disc.lift(gb, -pfl[None])
+    return fb, gb[0]
 
 
 def D_solve(disc, r, gamma):
@@ -811,11 +887,14 @@ def picard_solve(disc, phys, rho, f_w, g_w, u0, p0, adt, opts, info=None):
     kmax = opts.picard_fixed if opts.picard_fixed > 0 else opts.picard_maxit
     for k in range(kmax):
         cf = StageCoeffs(rho=rho, p_lag=p, u_lag=u, adt=adt)
-        rhs = schur_rhs(disc, cf, phys, f_w, g_w)
+        # far-field faces: their known outer data on the right-hand sides
+        fb, gb = far_affine(disc, cf, phys)
+        fk, gk = f_w - fb, g_w - gb
+        rhs = schur_rhs(disc, cf, phys, fk, gk)
         p_new, its, rr, ok = gmres(lambda x: schur_apply(disc, cf, phys, x), rhs, p,
                                    rtol=opts.gmres_rtol, restart=opts.gmres_restart,
                                    maxit=opts.gmres_maxit)
-        u_new = recover_velocity(disc, cf, phys, f_w, p_new)
+        u_new = recover_velocity(disc, cf, phys, fk, p_new)
         dp = np.linalg.norm(p_new - p) / max(np.linalg.norm(p_new), 1e-300)
         nu = np.linalg.norm(u_new)
         du = np.linalg.norm(u_new - u) / nu if nu > 0 else 0.0

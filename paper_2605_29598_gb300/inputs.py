@@ -19,7 +19,8 @@ Conventions (shared by every consumer of these lists):
   fine cell's face covers one half (2D) or quarter (3D) of the coarse face;
   bit ``t`` of ``subface`` says which half along the ``t``-th tangential
   direction (tangential directions in increasing order).
-* Boundary face row ``[e, f, bc]`` with ``bc = BC_WALL``.
+* Boundary face row ``[e, f, bc]`` with ``bc = BC_WALL`` (or ``BC_FARFIELD``,
+  see ``with_boundary``; the oracle supports it, the CUDA library not yet).
 * Physical coordinates are (x, z) in 2D (vertical x-z slice) and (x, y, z)
   in 3D; the vertical is always the last coordinate.
 
@@ -36,6 +37,7 @@ from dataclasses import dataclass, field
 import numpy as np
 
 BC_WALL = 1
+BC_FARFIELD = 2
 
 # physical constants of the paper's experiments (Section 4: gamma, g, R)
 GAMMA = 1.4
@@ -324,6 +326,17 @@ def isothermal_state(points, T0=250.0, ps=P_REF, bubble=None, g=GRAV, R=R_GAS, g
         rho = rho + np.exp(-0.5 * delta * z) * rho_s * (-tb / T0)
     zeros = np.zeros_like(rho)
     return np.stack([rho, zeros, zeros, zeros, p / (gamma - 1.0)], axis=0)
+
+
+def with_boundary(mesh, faces, bc):
+    """Copy of ``mesh`` whose boundary faces with local face index in
+    ``faces`` (e.g. 2d - 1 for the top) carry boundary id ``bc``."""
+    b = np.array(mesh.bdry_faces, dtype=np.int64, copy=True).reshape(-1, 3)
+    sel = np.isin(b[:, 1], list(faces))
+    b[sel, 2] = bc
+    return Mesh(dim=mesh.dim, vertices=mesh.vertices, int_faces=mesh.int_faces,
+                hang_faces=mesh.hang_faces, bdry_faces=b, level=mesh.level,
+                name=mesh.name + "_bc")
 
 
 def perturb(state, rng, rel=1e-3):

@@ -589,3 +589,116 @@ def test_rusanov_floor_inactive_when_flow_faster():
     b_ns, b_s = O.explicit_rates(disc, q, O.Phys(lambda_min=1.0))
     assert np.array_equal(a_s, b_s)
     assert np.abs(a_ns - b_ns).max() <= 1e-13 * np.abs(a_ns).max()
+
+
+# ----------------------------------------------------------------------------
+# far-field faces (outer state = a given background; READING R-farfield)
+# ----------------------------------------------------------------------------
+
+def _top_bottom_farfield(mesh):
+    d = mesh.dim
+    return I.with_boundary(mesh, (2 * (d - 1), 2 * (d - 1) + 1), I.BC_FARFIELD)
+
+
+@pytest.mark.parametrize("d,r,refine", [(2, 2, False), (2, 3, True), (3, 2, True)])
+def test_polynomial_exactness_through_farfield_faces(d, r, refine):
+    """rho in Q_r, constant u (with a vertical component) and p, and the
+    outer state equal to the same fields: the far-field faces then carry the
+    exact flux, so the non-stiff rates equal -(u.grad rho)(1, u, kappa) on
+    every cell without a wall face, those touching the far-field top and
+    bottom included.  With slip walls in their place those cells are not
+    exact."""
+    cells = (4,) * d
+    base = I.box_mesh(cells, (4.0,) * d, periodic=[False] * d,
+                      refine_level=_refine_corner(d) if refine else None)
+    mesh = _top_bottom_farfield(base)
+    disc = O.Discretisation(mesh, r)
+    u = np.array([0.3, -0.2, 0.5])
+    q, ugr = _poly_state(disc, np.random.default_rng(3), u)
+    disc.set_far_state(q)
+    Fns, Fs = O.explicit_rates(disc, q, O.Phys(f=0.0, g=0.0))
+    exp = np.stack([-ugr] + [-ugr * u[c] for c in range(3)] + [-ugr * 0.5 * (u @ u)])
+    b = mesh.bdry_faces
+    keep = np.setdiff1d(np.arange(disc.E), b[b[:, 2] == I.BC_WALL, 0])
+    at_far = np.intersect1d(keep, b[b[:, 2] == I.BC_FARFIELD, 0])
+    assert len(at_far) > 0
+    assert np.abs(Fns[:, keep] - exp[:, keep]).max() < 1e-11
+    assert np.abs(Fs[:, keep]).max() < 1e-10
+    walls = O.Discretisation(base, r)
+    Fw, _ = O.explicit_rates(walls, q, O.Phys(f=0.0, g=0.0))
+    assert np.abs(Fw[:, at_far] - exp[:, at_far]).max() > 1e-3
+
+
+@pytest.mark.parametrize("variant", ["R1", "R2"])
+@pytest.mark.parametrize("d", [2, 3])
+def test_uniform_flow_through_farfield_boundaries_is_steady(variant, d):
+    """A uniform flow crossing the far-field top and bottom (g = f = 0) with
+    the outer state equal to it is an exact steady solution of the scheme:
+    the explicit rates vanish and whole steps keep it, which pins the outer
+    data moved to the right-hand sides of the implicit stage system.  The
+    state holds to about 1e-11 relative (GMRES at 1e-13 on p ~ 1e5 Pa);
+    dropping or flipping any of the three outer-data terms moves it by 1e-2
+    or more."""
+    cells = (5, 4) if d == 2 else (3, 3, 3)
+    ext = (5e3, 2e3) if d == 2 else (3e3, 3e3, 2e3)
+    mesh = _top_bottom_farfield(I.box_mesh(cells, ext))
+    disc = O.Discretisation(mesh, 2)
+    pts = disc.node_points()
+    u = np.array([8.0, -3.0, 2.5]) if d == 3 else np.array([8.0, 0.0, 2.5])
+    rho, p = 1.1, 9.0e4
+    q = np.zeros((5,) + pts.shape[:-1])
+    q[0] = rho
+    q[1:4] = rho * u[:, None, None]
+    q[4] = p / 0.4 + 0.5 * rho * (u @ u)
+    disc.set_far_state(q)
+    ph = O.Phys(f=0.0, g=0.0, variant=variant)
+    Fns, Fs = O.explicit_rates(disc, q, ph)
+    assert np.abs(Fns).max() < 1e-9 and np.abs(Fs).max() < 1e-9
+    opts = O.StepOpts(picard_fixed=2, gmres_rtol=1e-13)
+    qn = q
+    for _ in range(2):
+        qn = O.imex_ark2_step(disc, ph, qn, 5.0, opts)
+    for k in range(5):
+        assert np.abs(qn[k] - q[k]).max() <= 1e-9 * max(np.abs(q[k]).max(), 1.0), k
+
+
+def test_balanced_rest_state_under_a_farfield_top():
+    """The discretely balanced rest state of the wall pin, with the top
+    turned into a far-field face whose outer state is that same state: the
+    pressure traces match there, so it stays at rest as under a wall."""
+    mesh = I.box_mesh((6, 4), (60e3, 8e3))
+    disc = O.Discretisation(mesh, 2)
+    X = disc.node_points()
+    _, pbar, _, _ = I.exner_background(X[..., -1], 300.0, 0.01)
+    gm, g = 1.4, 9.81
+    cf = O.StageCoeffs(rho=np.ones_like(pbar), p_lag=pbar, u_lag=np.zeros((3,) + pbar.shape),
+                       adt=1.0)
+    rho = -disc.mass_solve(O.op_B(disc, cf, pbar))[2] / g
+    q = np.zeros((5,) + pbar.shape)
+    q[0] = rho
+    q[4] = pbar / (gm - 1)
+    far = O.Discretisation(I.with_boundary(mesh, (3,), I.BC_FARFIELD), 2)
+    assert far.f_far.sum() == 6
+    far.set_far_state(q)
+    ph = O.Phys(f=1e-4, g=g)
+    Fw = O.explicit_rates(disc, q, ph)
+    Ff = O.explicit_rates(far, q, ph)
+    for a, b in zip(Fw, Ff):
+        assert np.abs(a - b).max() <= 1e-12 * np.abs(a).max()
+    opts = O.StepOpts(picard_fixed=2, gmres_rtol=1e-12)
+    for _ in range(3):
+        q = O.imex_ark2_step(far, ph, q, 10.0, opts)
+    u = q[1:4] / q[0]
+    assert np.abs(u).max() < 2e-9
+    assert np.abs(q[0] - rho).max() < 1e-11 * rho.max()
+
+
+def test_farfield_faces_need_an_outer_state():
+    mesh = _top_bottom_farfield(I.box_mesh((3, 2), (3e3, 2e3)))
+    disc = O.Discretisation(mesh, 1)
+    q = I.stratified_state(disc.node_points())
+    with pytest.raises(ValueError):
+        O.explicit_rates(disc, q, O.Phys())
+    bad = I.with_boundary(I.box_mesh((3, 2), (3e3, 2e3)), (3,), 7)
+    with pytest.raises(ValueError):
+        O.Discretisation(bad, 1)
