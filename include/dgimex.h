@@ -98,6 +98,13 @@ typedef struct {
 int dg_mesh_create(dg_ctx* ctx, const dg_mesh_desc* desc, dg_mesh** out);
 void dg_mesh_destroy(dg_mesh* mesh);
 
+/* Host-only check of a mesh description: every rule dg_mesh_create applies
+ * before it touches the GPU (dim, degree, node set, list ranges, face
+ * coverage, finite vertices), with the same status and message, and no
+ * context or device needed.  Not checked here: det(J) > 0 at the nodes,
+ * which dg_mesh_create tests with its geometry kernels. */
+int dg_mesh_validate(const dg_mesh_desc* desc);
+
 typedef struct {
   int dim, degree, n1d, nodes_per_elem;
   int64_t n_elem, n_nodes, n_face_points, n_hang_points;

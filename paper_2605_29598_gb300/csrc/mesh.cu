@@ -419,45 +419,50 @@ void dg_mesh_destroy(dg_mesh* m) {
   delete m;
 }
 
-int dg_mesh_create(dg_ctx* ctx, const dg_mesh_desc* d, dg_mesh** out) {
-  if (!ctx || !d || !out) {
-    set_error("dg_mesh_create: NULL argument");
-    return DG_ERR_ARG;
-  }
-  *out = nullptr;
+namespace {
+
+// Hanging rows grouped by coarse face, in the order validation meets them.
+struct HangGroups {
+  std::vector<int64_t> list;   // coarse face keys e * 2d + f
+  std::vector<int64_t> rows;   // 2^(dim-1) hang_faces rows per coarse face, by subface
+};
+
+// Every rule dg_mesh_create checks before its first CUDA call; `who` names
+// the entry point in the error message.
+int check_desc(const dg_mesh_desc* d, const char* who, HangGroups* hg) {
   if (d->dim != 2 && d->dim != 3) {
-    set_error("dg_mesh_create: dim %d not in {2, 3}", d->dim);
+    set_error("%s: dim %d not in {2, 3}", who, d->dim);
     return DG_ERR_ARG;
   }
   if (d->degree < 1 || d->degree > 4) {
-    set_error("dg_mesh_create: degree %d not in 1..4", d->degree);
+    set_error("%s: degree %d not in 1..4", who, d->degree);
     return d->degree > 4 ? DG_ERR_UNSUPPORTED : DG_ERR_ARG;
   }
   if (d->node_set == DG_NODES_GLL) {
-    set_error("dg_mesh_create: Gauss-Lobatto nodes are not implemented");
+    set_error("%s: Gauss-Lobatto nodes are not implemented", who);
     return DG_ERR_UNSUPPORTED;
   }
   if (d->node_set != DG_NODES_GL) {
-    set_error("dg_mesh_create: unknown node_set %d", d->node_set);
+    set_error("%s: unknown node_set %d", who, d->node_set);
     return DG_ERR_ARG;
   }
   if (d->n_elem <= 0 || !d->vertices || d->n_int < 0 || d->n_hang < 0 || d->n_bdry < 0 ||
       (d->n_int && !d->int_faces) || (d->n_hang && !d->hang_faces) ||
       (d->n_bdry && !d->bdry_faces)) {
-    set_error("dg_mesh_create: empty mesh or NULL list");
+    set_error("%s: empty mesh or NULL list", who);
     return DG_ERR_ARG;
   }
   const int dim = d->dim, n = d->degree + 1, nfaces = 2 * dim;
   const int nfp = ipow(n, dim - 1), nsub = 1 << (dim - 1);
   const int64_t E = d->n_elem;
   if (E * nfaces * (int64_t)nfp >= (int64_t)1 << 31 || E * ipow(n, dim) >= (int64_t)1 << 31) {
-    set_error("dg_mesh_create: mesh too large for 32-bit slot indices");
+    set_error("%s: mesh too large for 32-bit slot indices", who);
     return DG_ERR_UNSUPPORTED;
   }
   // ---- validation: every cell face covered exactly once
   std::vector<uint8_t> cover((size_t)E * nfaces, 0);
   auto bad = [&](const char* what, int64_t row) {
-    set_error("dg_mesh_create: %s (row %lld)", what, (long long)row);
+    set_error("%s: %s (row %lld)", who, what, (long long)row);
     return DG_ERR_ARG;
   };
   for (int64_t k = 0; k < d->n_int; ++k) {
@@ -477,8 +482,8 @@ int dg_mesh_create(dg_ctx* ctx, const dg_mesh_desc* d, dg_mesh** out) {
   }
   // group hanging rows by coarse face
   std::vector<int64_t> hc_first((size_t)E * nfaces, -1);
-  std::vector<int64_t> hc_list;                 // coarse face keys in order of appearance
-  std::vector<int64_t> hc_rows;                 // nsub rows per coarse face
+  std::vector<int64_t>& hc_list = hg->list;
+  std::vector<int64_t>& hc_rows = hg->rows;
   for (int64_t k = 0; k < d->n_hang; ++k) {
     const int64_t* r = d->hang_faces + 5 * k;
     if (r[0] < 0 || r[0] >= E || r[2] < 0 || r[2] >= E) return bad("hanging face cell out of range", k);
@@ -500,17 +505,38 @@ int dg_mesh_create(dg_ctx* ctx, const dg_mesh_desc* d, dg_mesh** out) {
   }
   for (size_t k = 0; k < hc_rows.size(); ++k)
     if (hc_rows[k] < 0) {
-      set_error("dg_mesh_create: coarse face %lld misses a subface", (long long)(k / nsub));
+      set_error("%s: coarse face %lld misses a subface", who, (long long)(k / nsub));
       return DG_ERR_ARG;
     }
   for (int64_t k = 0; k < E * nfaces; ++k)
     if (cover[k] != 1) {
-      set_error("dg_mesh_create: face %d of cell %lld covered %d times", (int)(k % nfaces),
+      set_error("%s: face %d of cell %lld covered %d times", who, (int)(k % nfaces),
                 (long long)(k / nfaces), (int)cover[k]);
       return DG_ERR_ARG;
     }
   for (int64_t k = 0; k < E * (dim << dim); ++k)
     if (!std::isfinite(d->vertices[k])) return bad("non-finite vertex coordinate", k / (dim << dim));
+  return DG_OK;
+}
+
+}  // namespace
+
+int dg_mesh_create(dg_ctx* ctx, const dg_mesh_desc* d, dg_mesh** out) {
+  if (!ctx || !d || !out) {
+    set_error("dg_mesh_create: NULL argument");
+    return DG_ERR_ARG;
+  }
+  *out = nullptr;
+  HangGroups hg;
+  {
+    const int rc = check_desc(d, "dg_mesh_create", &hg);
+    if (rc != DG_OK) return rc;
+  }
+  const int dim = d->dim, n = d->degree + 1, nfaces = 2 * dim;
+  const int nfp = ipow(n, dim - 1), nsub = 1 << (dim - 1);
+  const int64_t E = d->n_elem;
+  const std::vector<int64_t>& hc_list = hg.list;
+  const std::vector<int64_t>& hc_rows = hg.rows;
 
   // ---- unified face-point list
   const int64_t nHC = (int64_t)hc_list.size();
@@ -666,6 +692,15 @@ int dg_mesh_create(dg_ctx* ctx, const dg_mesh_desc* d, dg_mesh** out) {
   }
   *out = m;
   return DG_OK;
+}
+
+int dg_mesh_validate(const dg_mesh_desc* d) {
+  if (!d) {
+    set_error("dg_mesh_validate: NULL argument");
+    return DG_ERR_ARG;
+  }
+  HangGroups hg;
+  return check_desc(d, "dg_mesh_validate", &hg);
 }
 
 int dg_profile_begin(dg_mesh* m, uint32_t time_mask) {

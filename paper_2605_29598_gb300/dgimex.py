@@ -107,6 +107,7 @@ EXPORTS = {
     "dg_ctx_destroy": (None, [C.c_void_p]),
     "dg_mesh_create": (C.c_int, [C.c_void_p, C.POINTER(MeshDesc), C.POINTER(C.c_void_p)]),
     "dg_mesh_destroy": (None, [C.c_void_p]),
+    "dg_mesh_validate": (C.c_int, [C.POINTER(MeshDesc)]),
     "dg_mesh_info": (C.c_int, [C.c_void_p, C.POINTER(MeshStats)]),
     "dg_mesh_node_coords": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "dg_apply_explicit": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Phys), C.c_void_p,
@@ -229,6 +230,22 @@ def make_phys(gamma=1.4, g=9.81, f=1e-4, variant="R2", penalty=True, precision="
     return Phys(gamma=gamma, g=g, f=f, variant=DG_R2 if variant == "R2" else DG_R1,
                 penalty=1 if penalty else 0,
                 precision=PRECISIONS[precision], lambda_min=lambda_min)
+
+
+def validate_mesh(mesh, degree, node_set=DG_NODES_GL):
+    """Run dg_mesh_create's host-side checks on a host mesh (see
+    ``inputs.Mesh``) without a context or GPU; raises DGError on failure."""
+    lib = load()
+    v = np.ascontiguousarray(mesh.vertices, dtype=np.float64)
+    a = np.ascontiguousarray(mesh.int_faces, dtype=np.int64).reshape(-1, 4)
+    h = np.ascontiguousarray(mesh.hang_faces, dtype=np.int64).reshape(-1, 5)
+    b = np.ascontiguousarray(mesh.bdry_faces, dtype=np.int64).reshape(-1, 3)
+    d = MeshDesc(dim=int(mesh.dim), degree=int(degree), node_set=int(node_set), n_elem=v.shape[0],
+                 vertices=v.ctypes.data_as(_DP),
+                 n_int=a.shape[0], int_faces=a.ctypes.data_as(_I64P),
+                 n_hang=h.shape[0], hang_faces=h.ctypes.data_as(_I64P),
+                 n_bdry=b.shape[0], bdry_faces=b.ctypes.data_as(_I64P))
+    return _check(lib.dg_mesh_validate(C.byref(d)), "dg_mesh_validate")
 
 
 class Context:

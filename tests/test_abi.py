@@ -78,3 +78,49 @@ def test_binding_checks_buffer_sizes_and_devices():
         D._ptr(torch.zeros(4, dtype=torch.float64))          # host tensor
     with pytest.raises(TypeError):
         D._ptr(torch.zeros(4, dtype=torch.float32))
+
+
+def test_mesh_validation_on_the_host():
+    """dg_mesh_validate runs every host-side rule of dg_mesh_create with no
+    GPU: the generator's meshes pass, and each kind of broken list or
+    unsupported option gets dg_mesh_create's status and message."""
+    import numpy as np
+    from paper_2605_29598_gb300 import dgimex as D, inputs as I
+    good = [I.box_mesh((3, 2), (3.0, 2.0)),
+            I.box_mesh((4, 3), (4.0, 3.0), refine_level=lambda c: 1 if c[0] < 1 else 0),
+            I.box_mesh((3, 3, 2), (3e3, 3e3, 2e3), hill=dict(h0=200.0, a_c=1e3, xc=1.5e3, yc=1.5e3),
+                       refine_level=lambda c: 1 if c[0] < 1e3 and c[2] < 1e3 else 0)]
+    for m in good:
+        for r in (1, 4):
+            assert D.validate_mesh(m, r) == 0
+
+    def status(m, r=2, node_set=D.DG_NODES_GL):
+        with pytest.raises(D.DGError) as ei:
+            D.validate_mesh(m, r, node_set)
+        return ei.value.status, str(ei.value)
+
+    m = good[1]
+    assert len(m.hang_faces) >= 2
+    mk = lambda **kw: I.Mesh(dim=kw.get("dim", m.dim), vertices=kw.get("v", m.vertices),
+                             int_faces=kw.get("i", m.int_faces), hang_faces=kw.get("h", m.hang_faces),
+                             bdry_faces=kw.get("b", m.bdry_faces))
+    assert status(m, r=5)[0] == -2                                   # degree > 4: unsupported
+    assert status(m, r=0)[0] == -1
+    assert status(m, node_set=D.DG_NODES_GLL)[0] == -2
+    assert status(mk(i=m.int_faces[1:]))[0] == -1                     # an uncovered face
+    assert "covered 0 times" in status(mk(i=m.int_faces[1:]))[1]
+    assert "covered 2 times" in status(mk(i=np.vstack([m.int_faces, m.int_faces[:1]])))[1]
+    assert "misses a subface" in status(mk(h=m.hang_faces[1:]))[1]
+    bad_cell = m.int_faces.copy()
+    bad_cell[0, 2] = m.n_elem
+    assert "out of range" in status(mk(i=bad_cell))[1]
+    b = m.bdry_faces.copy()
+    b[0, 2] = I.BC_FARFIELD                                            # oracle-only id
+    assert "unknown boundary condition" in status(mk(b=b))[1]
+    v = m.vertices.copy()
+    v[2, 1, 0] = np.nan
+    assert "non-finite" in status(mk(v=v))[1]
+    empty = I.Mesh(dim=2, vertices=np.zeros((0, 4, 2)), int_faces=np.zeros((0, 4), np.int64),
+                   hang_faces=np.zeros((0, 5), np.int64), bdry_faces=np.zeros((0, 3), np.int64))
+    assert status(empty)[0] == -1
+    assert D.load().dg_mesh_validate(None) == -1
