@@ -629,9 +629,19 @@ def test_polynomial_exactness_through_farfield_faces(d, r, refine):
     assert np.abs(Fw[:, at_far] - exp[:, at_far]).max() > 1e-3
 
 
+FAR_FLOW_MESHES = {
+    "2d": lambda: I.box_mesh((5, 4), (5e3, 2e3)),
+    "3d": lambda: I.box_mesh((3, 3, 3), (3e3, 3e3, 2e3)),
+    # far-field bottom on the terrain surface: curved faces, and 2:1 faces
+    "3d_hill_nc": lambda: I.box_mesh((3, 3, 3), (3e3, 3e3, 2e3),
+                                     hill=dict(h0=300.0, a_c=0.8e3, xc=1.5e3, yc=1.5e3),
+                                     refine_level=lambda c: 1 if c[0] < 1e3 and c[2] < 700 else 0),
+}
+
+
 @pytest.mark.parametrize("variant", ["R1", "R2"])
-@pytest.mark.parametrize("d", [2, 3])
-def test_uniform_flow_through_farfield_boundaries_is_steady(variant, d):
+@pytest.mark.parametrize("name", list(FAR_FLOW_MESHES))
+def test_uniform_flow_through_farfield_boundaries_is_steady(variant, name):
     """A uniform flow crossing the far-field top and bottom (g = f = 0) with
     the outer state equal to it is an exact steady solution of the scheme:
     the explicit rates vanish and whole steps keep it, which pins the outer
@@ -639,9 +649,8 @@ def test_uniform_flow_through_farfield_boundaries_is_steady(variant, d):
     state holds to about 1e-11 relative (GMRES at 1e-13 on p ~ 1e5 Pa);
     dropping or flipping any of the three outer-data terms moves it by 1e-2
     or more."""
-    cells = (5, 4) if d == 2 else (3, 3, 3)
-    ext = (5e3, 2e3) if d == 2 else (3e3, 3e3, 2e3)
-    mesh = _top_bottom_farfield(I.box_mesh(cells, ext))
+    mesh = _top_bottom_farfield(FAR_FLOW_MESHES[name]())
+    d = mesh.dim
     disc = O.Discretisation(mesh, 2)
     pts = disc.node_points()
     u = np.array([8.0, -3.0, 2.5]) if d == 3 else np.array([8.0, 0.0, 2.5])
