@@ -403,6 +403,51 @@ def hill3d_case(nx=60, ny=60, nz=20, r=3, refine=False, refine_box=None):
     return dict(mesh=mesh, degree=r, f=1e-4, dt=4.0, state_params=params)
 
 
+def paper_igw_case(nx=300, nz=20, r=4):
+    """Inertia-gravity wave, reference run of Section 4.1: 6000 km x 10 km
+    x-z channel, periodic in x, walls in z, 300 x 20 cells, degree 4;
+    isothermal background at rest (T0 = 250 K), Bretherton perturbation at
+    x_c = 3000 km with half-width a = 100 km, f = 1.03126e-4 1/s, dt = 0.5 s,
+    8 h."""
+    mesh = box_mesh((nx, nz), (6000e3, 10e3), name="paper_igw")
+    params = dict(T0=250.0, ps=P_REF, bubble=dict(dT=0.01, xc=3000e3, a=100e3, H=10e3))
+    return dict(mesh=mesh, degree=r, f=1.03126e-4, dt=0.5, hours=8.0, state_params=params)
+
+
+def paper_hill_benchmark_case(f=1e-4):
+    """Medium-steep bell hill, benchmark test of Section 4.3: 60 x 40 x 16 km,
+    hill at (30, 20) km with h0 = 400 m and a_c = 1 km, 30 x 20 x 8 cells of
+    degree 4, dt = 8 s, 8 h; N = 0.01 1/s, theta_ref = 293.15 K, inflow
+    10 m/s along x; f = 0 or 1e-4 1/s.  Damping layers (for
+    ``Mesh.set_sponge``): 20 km at both ends of x, 10 km at both ends of y,
+    the top 6 km, lambda_bar dt = 1.2.  The geostrophic pressure correction
+    of a rotating run is left out (it is not periodic)."""
+    dt = 8.0
+    mesh = box_mesh((30, 20, 8), (60e3, 40e3, 16e3), hill=dict(h0=400.0, a_c=1e3, xc=30e3, yc=20e3),
+                    name="paper_hill")
+    sponge = dict(lambda_bar=1.2 / dt, z_b=10e3, z_t=16e3, x_layers=(0.0, 60e3, 20e3),
+                  y_layers=(0.0, 40e3, 10e3))
+    params = dict(theta_ref=293.15, n_bv=0.01, wind=(10.0, 0.0, 0.0), bubble=None)
+    return dict(mesh=mesh, degree=4, f=f, dt=dt, hours=8.0, state_params=params, sponge=sponge)
+
+
+def paper_hill_large_case(f=1e-4):
+    """Larger-scale hill test of Section 4.3: 240 x 240 x 30 km, hill at
+    (120, 120) km with h0 = 100 m and a_c = 10 km, 50 x 50 x 50 cells of
+    degree 4, dt = 4 s, 8 h; isothermal background at 250 K (its buoyancy
+    frequency g / sqrt(c_p T) = 0.0196 1/s, printed as 0.02), inflow 10 m/s
+    along x.  Damping layers: 60 km at both ends of x and y, the top 14 km,
+    lambda_bar dt = 1.2."""
+    dt = 4.0
+    T = 250.0
+    mesh = box_mesh((50, 50, 50), (240e3, 240e3, 30e3), hill=dict(h0=100.0, a_c=10e3, xc=120e3, yc=120e3),
+                    name="paper_hill_large")
+    sponge = dict(lambda_bar=1.2 / dt, z_b=16e3, z_t=30e3, x_layers=(0.0, 240e3, 60e3),
+                  y_layers=(0.0, 240e3, 60e3))
+    params = dict(theta_ref=T, n_bv=GRAV / math.sqrt(CP * T), wind=(10.0, 0.0, 0.0), bubble=None)
+    return dict(mesh=mesh, degree=4, f=f, dt=dt, hours=8.0, state_params=params, sponge=sponge)
+
+
 def ensemble_cases(n=32, seed0=1000):
     """Ensemble of independent instances of uneven sizes and degrees.
 

@@ -181,3 +181,66 @@ def test_r1_and_r2_reach_the_same_state():
         for k in range(5):
             d = np.abs(out["R1"][k] - out["R2"][k]).max() / np.abs(out["R2"][k]).max()
             assert d < bound, (fixed, k, d)
+
+
+# ----------------------------------------------------------------------------
+# Section 4: the experiments' configurations
+# ----------------------------------------------------------------------------
+
+def _workloads():
+    out = {}
+    for row in _lines("paper_workloads.txt"):
+        rec = {}
+        for kv in row[1:]:
+            k, v = kv.split("=")
+            rec[k] = [float(x) for x in v.split("x")] if k in ("extent", "cells", "hill") else float(v)
+        out[row[0]] = rec
+    return out
+
+
+GENERATORS = {
+    "igw_reference": lambda: I.paper_igw_case(),
+    "planetary_igw": lambda: I.planetary_igw_case(),
+    "hill_benchmark": lambda: I.paper_hill_benchmark_case(),
+    "hill_large": lambda: I.paper_hill_large_case(),
+}
+
+
+@pytest.mark.parametrize("name", list(GENERATORS))
+def test_workload_generators_follow_the_printed_configurations(name):
+    rec = _workloads()[name]
+    case = GENERATORS[name]()
+    mesh = case["mesh"]
+    cells = [int(c) for c in rec["cells"]]
+    ext = np.array(rec["extent"]) * 1e3
+    d = len(cells)
+    assert mesh.dim == d and mesh.n_elem == int(np.prod(cells))
+    assert case["degree"] == int(rec["degree"])
+    assert case["dt"] == rec["dt"] and case.get("hours", rec["hours"]) == rec["hours"]
+    if "f" in rec:
+        assert case["f"] == rec["f"]
+    v = np.asarray(mesh.vertices).reshape(-1, d)
+    for a in range(d - 1):
+        assert v[:, a].min() == 0.0 and abs(v[:, a].max() - ext[a]) < 1e-6 * ext[a]
+    assert abs(v[:, -1].max() - ext[-1]) < 1e-6 * ext[-1]
+    sp = case["state_params"]
+    if "xc" in rec:
+        assert sp["bubble"]["xc"] == rec["xc"] * 1e3
+    if "a" in rec:
+        assert sp["bubble"]["a"] == rec["a"] * 1e3
+    if "hill" in rec:
+        # bottom vertices follow the bell: h0 at the centre, h0 / (1 + r^2 / a_c^2) around it
+        xc, yc = np.array(rec["hill"]) * 1e3
+        bottom = v[v[:, 2] < 0.5 * ext[2] / cells[2]]
+        r2 = (bottom[:, 0] - xc) ** 2 + (bottom[:, 1] - yc) ** 2
+        h = rec["h0_m"] / (1.0 + r2 / (rec["ac"] * 1e3) ** 2)
+        assert np.abs(bottom[:, 2] - h).max() < 1e-9 * rec["h0_m"]
+        assert abs(bottom[:, 2].max() - rec["h0_m"]) < 1e-9 * rec["h0_m"]
+        s = case["sponge"]
+        assert abs(s["lambda_bar"] * case["dt"] - rec["lam_dt"]) < 1e-12
+        assert s["z_t"] == ext[2] and abs(s["z_t"] - s["z_b"] - rec["damp_top"] * 1e3) < 1e-6
+        assert s["x_layers"] == (0.0, ext[0], rec["damp_x"] * 1e3)
+        assert s["y_layers"] == (0.0, ext[1], rec["damp_y"] * 1e3)
+        assert sp["theta_ref"] == rec["theta_ref"] and sp["wind"][0] == rec["U0"]
+        # N as printed (the isothermal case's g / sqrt(c_p T) = 0.0196 is printed as 0.02)
+        assert abs(sp["n_bv"] - rec["N"]) < 0.025 * rec["N"]
