@@ -49,7 +49,7 @@ typedef enum {
 } dg_status;
 
 enum { DG_NODES_GL = 0, DG_NODES_GLL = 1 };
-enum { DG_BC_WALL = 1 };
+enum { DG_BC_WALL = 1, DG_BC_FARFIELD = 2 };
 enum { DG_R1 = 1, DG_R2 = 2 };
 enum { DG_FP64 = 0, DG_MIXED = 1, DG_MIXED_EXPLICIT = 2 };
 
@@ -78,7 +78,9 @@ void dg_ctx_destroy(dg_ctx* ctx);
  *  hang_faces n_hang x 5: [e_coarse, f_coarse, e_fine, f_fine, subface];
  *             2:1 only; f_fine = f_coarse ^ 1; bit t of subface selects the
  *             half along the t-th tangential axis.
- *  bdry_faces n_bdry x 3: [e, f, DG_BC_WALL] (slip wall, mirror state).
+ *  bdry_faces n_bdry x 3: [e, f, DG_BC_WALL] (slip wall, mirror state);
+ *             DG_BC_FARFIELD (outer state = a background, the non-reflecting
+ *             top of Section 4.3) is not implemented: DG_ERR_UNSUPPORTED.
  * Every face of every cell must be covered exactly once (interior side,
  * fine hanging side, one of the 2^(dim-1) coarse subfaces, or boundary);
  * otherwise DG_ERR_ARG.

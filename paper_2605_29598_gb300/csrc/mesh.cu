@@ -477,6 +477,10 @@ int check_desc(const dg_mesh_desc* d, const char* who, HangGroups* hg) {
   for (int64_t k = 0; k < d->n_bdry; ++k) {
     const int64_t* r = d->bdry_faces + 3 * k;
     if (r[0] < 0 || r[0] >= E || r[1] < 0 || r[1] >= nfaces) return bad("boundary face out of range", k);
+    if (r[2] == DG_BC_FARFIELD) {
+      set_error("%s: far-field boundary faces are not implemented (row %lld)", who, (long long)k);
+      return DG_ERR_UNSUPPORTED;
+    }
     if (r[2] != DG_BC_WALL) return bad("unknown boundary condition", k);
     cover[r[0] * nfaces + r[1]]++;
   }

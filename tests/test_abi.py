@@ -115,7 +115,9 @@ def test_mesh_validation_on_the_host():
     bad_cell[0, 2] = m.n_elem
     assert "out of range" in status(mk(i=bad_cell))[1]
     b = m.bdry_faces.copy()
-    b[0, 2] = I.BC_FARFIELD                                            # oracle-only id
+    b[0, 2] = I.BC_FARFIELD                                            # oracle only so far
+    assert status(mk(b=b))[0] == -2
+    b[0, 2] = 7
     assert "unknown boundary condition" in status(mk(b=b))[1]
     v = m.vertices.copy()
     v[2, 1, 0] = np.nan
