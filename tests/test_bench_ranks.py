@@ -56,3 +56,21 @@ def test_single_rank_needs_no_process_group():
     import bench
     assert bench.max_over_ranks(123.0, None, "cpu") == 123.0
     assert abs(bench.throughput(1000, 2, 1, 10.0) - 5 * 1000 * 2 / 0.01 / 1e9) < 1e-15
+
+
+def test_reference_arm_prints_the_contract_line():
+    """`bench.py --impl reference` (the FP64 oracle on host cores) needs no
+    GPU: one JSON line with the contract's keys, its e2e copying nothing."""
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference",
+                          "--steps", "1", "--warmup", "0"], cwd=ROOT, capture_output=True, text=True,
+                         timeout=300)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["value"] > 0 and line["steps"] == 1
+    assert line["config"]["workload"] == "hill3d_60x60x20_r3_fp64_R2"
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
