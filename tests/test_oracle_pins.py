@@ -711,3 +711,182 @@ def test_farfield_faces_need_an_outer_state():
     bad = I.with_boundary(I.box_mesh((3, 2), (3e3, 2e3)), (3,), 7)
     with pytest.raises(ValueError):
         O.Discretisation(bad, 1)
+
+
+# ----------------------------------------------------------------------------
+# the stiff rho e Rusanov term (explicit, g vector) and its implicit
+# counterpart P (READING c5), pinned in absolute terms
+# ----------------------------------------------------------------------------
+
+def _piecewise_constant_state(disc, rng, u, gm=1.4):
+    """rho and p constant in each cell (random per cell), uniform velocity u."""
+    rho_c = 1.0 + 0.2 * rng.uniform(size=disc.E)
+    p_c = 1e5 * (1.0 + 0.1 * rng.uniform(size=disc.E))
+    u = np.asarray(u, dtype=np.float64)
+    q = np.zeros((5, disc.E, disc.Np))
+    q[0] = rho_c[:, None]
+    for c in range(3):
+        q[1 + c] = rho_c[:, None] * u[c]
+    q[4] = (p_c / (gm - 1.0) + 0.5 * rho_c * (u @ u))[:, None]
+    return q, p_c
+
+
+@pytest.mark.parametrize("d,u", [(2, (12.0, 0.0, 0.0)), (2, (-7.0, 3.0, 0.0)), (3, (9.0, -5.0, 0.0))])
+def test_flux_balance_of_piecewise_constant_state_is_upwind(d, u):
+    """Cell-wise constant rho and p, uniform horizontal u, g = f = 0, axis-
+    aligned box (periodic sides, walls top and bottom).  Summing the test
+    functions of a cell removes the volume terms, so each cell mean of the
+    rates is a finite-volume balance of the face fluxes.  With u uniform the
+    Rusanov flux with lambda = |u.n| is the upwind flux, and the split of the
+    energy flux into kappa rho u (non-stiff, Rusanov on rho kappa) and
+    h rho u (stiff, Rusanov on rho e) adds up to the upwind flux of the total
+    energy plus the centred pressure work {p} u.n.  Expected means:
+      mass      -1/|K| sum_F rho_up (u.n) |F|
+      momentum  -1/|K| sum_F (m_up (u.n) + {p} n) |F|   (walls: p n)
+      energy    -1/|K| sum_F ((rho E)_up + {p}) (u.n) |F|
+    A sign slip or a lost factor 1/2 in any Rusanov term (the stiff rho e
+    term included), or in a centred pressure / enthalpy flux, moves a mean
+    by O(jump)."""
+    rng = np.random.default_rng(3 + d)
+    cells, ext = ((5, 3), (5e3, 3e3)) if d == 2 else ((3, 3, 2), (3e3, 3e3, 2e3))
+    mesh = I.box_mesh(cells, ext)
+    disc = O.Discretisation(mesh, 2)
+    q, p_c = _piecewise_constant_state(disc, rng, u)
+    u = np.asarray(u, dtype=np.float64)
+    Fns, Fs = O.explicit_rates(disc, q, O.Phys(f=0.0, g=0.0))
+    vol = disc.wJ.sum(axis=1)
+    mean = (disc.at_quad(Fns + Fs) * disc.wJ[None]).sum(axis=-1) / vol[None]
+    h = np.array(ext) / np.array(cells)                   # cell sizes
+
+    def area(a):
+        return np.prod([h[t] for t in range(d) if t != a])
+
+    exp = np.zeros((5, disc.E))
+    for eL, fL, eR, _ in mesh.int_faces:
+        a = fL // 2
+        n = np.zeros(d)
+        n[a] = 1.0                                        # outward of eL
+        un = sum(u[c] * n[b] for b, c in enumerate(disc.comp))
+        up = eL if un >= 0 else eR
+        pav = 0.5 * (p_c[eL] + p_c[eR])
+        flux = np.array([q[k, up, 0] * un for k in range(5)])
+        for b, c in enumerate(disc.comp):
+            flux[1 + c] += pav * n[b]
+        flux[4] += pav * un
+        exp[:, eL] -= flux * area(a)
+        exp[:, eR] += flux * area(a)
+    for e, f, _ in mesh.bdry_faces:                       # walls: u.n = 0
+        a, s = f // 2, f % 2
+        for b, c in enumerate(disc.comp):
+            if b == a:
+                exp[1 + c, e] -= p_c[e] * (1.0 if s else -1.0) * area(a)
+    exp /= vol[None]
+    for k in range(5):
+        scale = np.abs(exp[k]).max()
+        if scale == 0.0:
+            assert np.abs(mean[k]).max() < 1e-9
+            continue
+        assert np.abs(mean[k] - exp[k]).max() < 1e-12 * scale, k
+
+
+def _two_cell_and_nc_meshes():
+    return {
+        "2cells_2d": I.box_mesh((2, 1), (2e3, 1e3), periodic=[False, False]),
+        "2cells_3d": I.box_mesh((2, 1, 1), (2e3, 1e3, 1e3), periodic=[False, False, False]),
+        "nc_2d": I.box_mesh((3, 2), (3e3, 2e3), periodic=[False, False],
+                            refine_level=lambda c: 1 if c[0] < 1e3 else 0),
+        "nc_3d_far": _top_bottom_farfield(
+            I.box_mesh((2, 2, 2), (2e3, 2e3, 2e3), refine_level=lambda c: 1 if c[0] < 1e3 else 0)),
+    }
+
+
+@pytest.mark.parametrize("name", ["2cells_2d", "2cells_3d", "nc_2d", "nc_3d_far"])
+def test_implicit_rusanov_term_is_the_linearised_explicit_one(name):
+    """P (op_P) by brute force on two-cell and 2:1 meshes (one with
+    far-field top and bottom):
+      * P is symmetric positive semidefinite and nonzero, and P p = 0 for a
+        pressure polynomial continuous across every face (no jumps);
+      * P is the implicit form of the explicit stiff rho e Rusanov term:
+        with rho and m held fixed, u and so lambda are fixed, p is affine in
+        rho E, and the stiff energy residual of the explicit operator
+        changes by -(C(u; h rho from dp) + P dp) / a_dt when rho E changes
+        by dp / (gamma - 1).  This ties P's sign, its factor 1/2, its
+        1/(gamma - 1) and its lambda to the explicit term, whose own sign
+        and factor the upwind flux balance above fixes."""
+    mesh = _two_cell_and_nc_meshes()[name]
+    d = mesh.dim
+    disc = O.Discretisation(mesh, 2 if d == 2 else 1)
+    rng = np.random.default_rng(17)
+    gm, adt = 1.4, 2.5
+    X = disc.node_points()
+    # uniform velocity, so that the explicit operator's u = m / rho at the
+    # face points (from traces of m and rho) and P's lambda (from traces of
+    # nodal u) see the same velocity; rho and p vary from node to node
+    uw = np.array([15.0, -6.0, 4.0])
+    q = I.stratified_state(X, wind=tuple(uw))
+    rho = q[0] * (1.0 + 2e-2 * rng.standard_normal(q[0].shape))
+    pn = 0.4 * (q[4] - 0.5 * q[0] * (uw @ uw)) * (1.0 + 2e-2 * rng.standard_normal(q[0].shape))
+    q = np.concatenate([rho[None], rho[None] * uw[:, None, None],
+                        (pn / 0.4 + 0.5 * rho * (uw @ uw))[None]])
+    if disc.f_far.any():
+        disc.set_far_state(I.stratified_state(X, wind=(12.0, 3.0, -2.0)))
+    u, p = O.nodal_primitives(q, gm)
+    cf = O.StageCoeffs(rho=q[0], p_lag=p, u_lag=u, adt=adt)
+    n_p = disc.E * disc.Np
+    P = _dense(lambda x: O.op_P(disc, cf, x, gm), n_p, (disc.E, disc.Np))
+    scale = np.abs(P).max()
+    assert scale > 0
+    assert np.abs(P - P.T).max() < 1e-13 * scale
+    assert np.linalg.eigvalsh(0.5 * (P + P.T)).min() > -1e-12 * scale
+    # continuous pressure: a global polynomial of degree <= r at the nodes
+    pc = 1.0 + sum(rng.uniform(-1, 1) * (X[..., a] / 1e3) ** k for a in range(d)
+                   for k in range(1, disc.r + 1))
+    pc = pc + 0.3 * (X[..., 0] / 1e3) * (X[..., -1] / 1e3)
+    if not disc.f_far.any():
+        assert np.abs(P @ pc.reshape(-1)).max() < 1e-12 * scale * np.abs(pc).max()
+    # the linearisation of the explicit stiff energy residual
+    ph = O.Phys(f=0.0, g=0.0)
+    dp = rng.standard_normal((disc.E, disc.Np)) * 1e3
+    q2 = q.copy()
+    q2[4] += dp / (gm - 1.0)
+    dr = O.explicit_residuals(disc, q2, ph)[1][4] - O.explicit_residuals(disc, q, ph)[1][4]
+    cfd = O.StageCoeffs(rho=q[0], p_lag=dp, u_lag=u, adt=adt)
+    got = -adt * dr - O.op_C(disc, cfd, u, gm)
+    want = O.op_P(disc, cf, dp, gm)
+    assert np.abs(want).max() > 1e-3 * np.abs(got).max()
+    assert np.abs(got - want).max() < 1e-9 * np.abs(want).max()
+
+
+def test_linearised_step_about_uniform_flow_is_stable():
+    """Linearised ARK2 step about a uniform moving state on a doubly
+    periodic mesh (g = f = 0): every spatial term of the base state
+    vanishes, the perturbations are advected and carried by sound waves,
+    and the Rusanov terms (explicit and implicit) are their only damping.
+    Spectral radius <= 1 (to the finite-difference accuracy): with the sign
+    of the stiff rho e Rusanov term flipped the radius is 1.17 per step,
+    and an inconsistent factor between the explicit term and P leaves a
+    slowly growing mode (1 + 6e-10 to 1 + 2e-9)."""
+    mesh = I.box_mesh((3, 3), (3e3, 3e3), periodic=[True, True])
+    disc = O.Discretisation(mesh, 1)
+    gm, rho0, p0 = 1.4, 1.1, 1e5
+    u = np.array([20.0, 0.0, 8.0])
+    q0 = np.zeros((5, disc.E, disc.Np))
+    q0[0] = rho0
+    for c in range(3):
+        q0[1 + c] = rho0 * u[c]
+    q0[4] = p0 / (gm - 1.0) + 0.5 * rho0 * (u @ u)
+    ph = O.Phys(f=0.0, g=0.0)
+    opts = O.StepOpts(picard_fixed=3, gmres_rtol=1e-14, gmres_restart=80, gmres_maxit=2000)
+    field_scale = np.array([rho0, 10 * rho0, 10 * rho0, 10 * rho0, p0 / (gm - 1.0)]) * 1e-6
+    sc = np.repeat(field_scale, disc.E * disc.Np)
+    flat = q0.reshape(-1)
+    J = np.zeros((flat.size, flat.size))
+    for j in range(flat.size):
+        dq = np.zeros(flat.size)
+        dq[j] = sc[j]
+        a = O.imex_ark2_step(disc, ph, (flat + dq).reshape(q0.shape), 1.0, opts).reshape(-1)
+        b = O.imex_ark2_step(disc, ph, (flat - dq).reshape(q0.shape), 1.0, opts).reshape(-1)
+        J[:, j] = (a - b) / (2.0 * sc) # scaled Jacobian diag(sc)^-1 J diag(sc)
+    radius = np.abs(np.linalg.eigvals(J)).max()
+    assert radius < 1.0 + 1e-11, radius
+    assert radius > 1.0 - 1e-11                     # conserved quantities: neutral
