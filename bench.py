@@ -179,16 +179,45 @@ def oracle_sample_main(steps, warmup, out_path):
         json.dump({"times": times, "nodes": nodes, "cells": disc.E}, f)
 
 
-def run_oracle_sample(steps, warmup):
+def host_description():
+    """CPU model and logical core count of this host."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith("model name"):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return {"nproc": os.cpu_count(), "cpu_model": model}
+
+
+def _oracle_child_cmd(path, steps, warmup):
+    return [sys.executable, os.path.abspath(__file__), "--oracle-child", path,
+            "--steps", str(steps), "--warmup", str(warmup)]
+
+
+def run_oracle_sample(steps, warmup, all_cores=False):
+    """The oracle on the column sample with one thread.  all_cores=True also
+    runs one copy of the same sample per host core at once (independent
+    processes, one thread each) and reports their aggregate throughput."""
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = "1"
     env["CUDA_VISIBLE_DEVICES"] = ""
     fd, path = tempfile.mkstemp(suffix=".json")
     os.close(fd)
-    cmd = [sys.executable, os.path.abspath(__file__), "--oracle-child", path,
-           "--steps", str(steps), "--warmup", str(warmup)]
-    subprocess.run(cmd, check=True, env=env, cwd=ROOT)
+    subprocess.run(_oracle_child_cmd(path, steps, warmup), check=True, env=env, cwd=ROOT)
     with open(path) as f:
         r = json.load(f)
     os.unlink(path)
@@ -197,8 +226,32 @@ def run_oracle_sample(steps, warmup):
     sample = (f"ARK2 steps of the FP64 oracle on a {SAMPLE['nx']}x{SAMPLE['ny']}x20-cell "
               f"column of the hill workload ({r['cells']} cells, degree 3, {r['nodes']} nodes, "
               f"same dt/physics/solver), mean of {len(r['times'])} step(s)")
-    return {"value": value, "unit": "GDoF-updates/s", "cores": 1, "kind": "oracle",
-            "sample": sample, "seconds_per_step": t}
+    out = {"value": value, "unit": "GDoF-updates/s", "cores": 1, "kind": "oracle",
+           "sample": sample, "seconds_per_step": t}
+    out.update(host_description())
+    if all_cores:
+        ncores = os.cpu_count() or 1
+        paths, procs = [], []
+        for _ in range(ncores):
+            fd, pth = tempfile.mkstemp(suffix=".json")
+            os.close(fd)
+            paths.append(pth)
+            procs.append(subprocess.Popen(_oracle_child_cmd(pth, 1, 0), env=env, cwd=ROOT))
+        ok = all(pr.wait() == 0 for pr in procs)
+        if ok:
+            ts = []
+            for pth in paths:
+                with open(pth) as f:
+                    ts.append(sum(json.load(f)["times"]))
+            tmax = max(ts)
+            out["all_cores"] = {"value": 5 * r["nodes"] * ncores / tmax / 1e9, "unit": "GDoF-updates/s",
+                                "cores": ncores, "seconds_per_step_slowest": tmax,
+                                "how": "one single-threaded oracle process per core, each stepping "
+                                       "its own copy of the column sample once; aggregate nodes / "
+                                       "slowest process's step time"}
+        for pth in paths:
+            os.unlink(pth)
+    return out
 
 
 # ----------------------------------------------------------------------------
@@ -430,6 +483,142 @@ def run_variant(D, I, ctx, case, steps, warmup, precond=False, state=None, spong
     mesh.close()
     return out
 
+def pert_fields(s, gamma=1.4, R=287.0, p_ref=1e5):
+    """rho, potential temperature theta, u, v, w of a state (5, N)."""
+    u = s[1:4] / s[0]
+    p = (gamma - 1.0) * (s[4] - 0.5 * (s[1:4] * u).sum(0))
+    theta = p / (R * s[0]) * (p_ref / p) ** ((gamma - 1.0) / gamma)
+    return {"rho": s[0], "theta": theta, "u": u[0], "v": u[1], "w": u[2]}
+
+
+def perturbation_errors(test, ref, bg):
+    """Relative L2 error per perturbation field: ||phi(test) - phi(ref)|| /
+    ||phi(ref) - phi(bg)||, phi' = phi - phi(bg) about the background bg
+    (rho', theta', u' = u - U, v, w)."""
+    import torch
+    ft, fr, fb = pert_fields(test), pert_fields(ref), pert_fields(bg)
+    out = {}
+    for k in fr:
+        den = torch.linalg.norm(fr[k] - fb[k]).item()
+        out[k] = torch.linalg.norm(ft[k] - fr[k]).item() / den if den > 0 else None
+    return out
+
+
+def timed_steps(mesh, phys, q, dt, steps, opts):
+    """`steps` ARK2 steps of q in place, bracketed by CUDA events on the
+    current stream: (ms, GMRES iterations, FP64 refinement sweeps)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    its, ref = 0, 0
+    for _ in range(steps):
+        inf = mesh.step(phys, q, dt, **opts)
+        its += inf.gmres_iters_total
+        ref += inf.refinements_total
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), its, ref
+
+
+PRECISION_OPTS = dict(picard_rtol=1e-12, picard_maxit=20, gmres_rtol=1e-12, gmres_restart=30,
+                      gmres_maxit=6000)
+REFERENCE_OPTS = dict(picard_rtol=1e-13, picard_maxit=30, gmres_rtol=1e-13, gmres_restart=30,
+                      gmres_maxit=8000)
+
+
+def run_precision_pattern(D, mesh, q_bg, f, dt, steps):
+    """The precision pattern at tolerances where FP64 itself is accurate to
+    well below 1e-6 in the perturbation fields: FP64 and DG_MIXED steps
+    (Picard and GMRES / refinement to 1e-12) from the background state,
+    timed with CUDA events, and both against an FP64 run at 1e-13 from the
+    same start (the FP64 path is parity-tested against the oracle; the
+    oracle itself cannot run this mesh)."""
+    import torch
+    out = {"steps": steps, "start": "background state (t = 0)",
+           "tolerances": "Picard 1e-12, GMRES / iterative refinement 1e-12 (FP32 inner 1e-4); "
+                         "reference FP64 at 1e-13"}
+    q64 = q_bg.clone()
+    ph64 = D.make_phys(f=f, variant="R2")
+    phmx = D.make_phys(f=f, variant="R2", precision="mixed")
+    mesh.step(phmx, q_bg.clone(), dt, **dict(PRECISION_OPTS, gmres_inner_rtol=1e-4))  # FP32 copies
+    ms64, it64, _ = timed_steps(mesh, ph64, q64, dt, steps, PRECISION_OPTS)
+    qmx = q_bg.clone()
+    msmx, itmx, refmx = timed_steps(mesh, phmx, qmx, dt, steps, dict(PRECISION_OPTS, gmres_inner_rtol=1e-4))
+    qref = q_bg.clone()
+    timed_steps(mesh, ph64, qref, dt, steps, REFERENCE_OPTS)
+    N = q_bg.shape[1]
+    out["fp64"] = {"value": 5.0 * N * steps / (ms64 / 1e3) / 1e9, "ms_per_step": ms64 / steps,
+                   "gmres_iters": it64, "rel_l2_err_vs_reference": perturbation_errors(q64, qref, q_bg)}
+    out["mixed"] = {"value": 5.0 * N * steps / (msmx / 1e3) / 1e9, "ms_per_step": msmx / steps,
+                    "gmres_inner_iters": itmx, "fp64_refinement_sweeps": refmx,
+                    "rel_l2_err_vs_reference": perturbation_errors(qmx, qref, q_bg),
+                    "rel_l2_err_vs_fp64": perturbation_errors(qmx, q64, q_bg)}
+    out["mixed_speedup_vs_fp64"] = ms64 / msmx
+    out["unit"] = "GDoF-updates/s"
+    return out
+
+
+def run_refined_configs(D, I, ctx, steps, warmup, err_steps=3):
+    """The non-conforming hill (2:1 hanging faces around the hill, Section
+    4.3's refinement shape): FP64 with the headline's solver settings
+    (config 3) and the precision pattern with iterative refinement to 1e-8
+    (config 4), `steps` steps each timed with CUDA events; then, from the
+    background state over `err_steps` steps, the per-field error of the
+    config-4 setting and of FP64 at the same 1e-8 tolerance against an FP64
+    run at 1e-12."""
+    import torch
+    case = I.hill3d_case(refine=True)
+    mesh = D.Mesh(ctx, case["mesh"], case["degree"])
+    mesh.autotune("mixed")
+    st = mesh.stats()
+    xyz = mesh.node_coords().cpu().numpy().T
+    q_bg = torch.tensor(I.stratified_state(xyz, **case["state_params"]), dtype=torch.float64,
+                        device="cuda").contiguous()
+    dt, f = case["dt"], case["f"]
+    N = st.n_nodes
+    ph64 = D.make_phys(f=f, variant="R2")
+    phmx = D.make_phys(f=f, variant="R2", precision="mixed")
+    c4_opts = dict(STEP_OPTS, gmres_rtol=1e-8, gmres_inner_rtol=1e-4)
+    geo = {"cells": st.n_elem, "nodes": N, "hanging_points": st.n_hang_points, "degree": case["degree"],
+           "dt": dt}
+    q = q_bg.clone()
+    for _ in range(warmup):
+        mesh.step(ph64, q, dt, **STEP_OPTS)
+    q3 = q.clone()
+    ms3, it3, _ = timed_steps(mesh, ph64, q3, dt, steps, STEP_OPTS)
+    cfg3 = dict(geo, workload="hill3d_nc_60x60x20_r3_fp64_R2", value=5.0 * N * steps / (ms3 / 1e3) / 1e9,
+                unit="GDoF-updates/s", ms_per_step=ms3 / steps, steps=steps, gmres_iters=it3,
+                solver="Picard 1e-10, GMRES(30) 1e-10, unpreconditioned")
+    q4 = q.clone()
+    mesh.step(phmx, q.clone(), dt, **c4_opts)
+    ms4, it4, ref4 = timed_steps(mesh, phmx, q4, dt, steps, c4_opts)
+    qe_ref = q_bg.clone()
+    timed_steps(mesh, ph64, qe_ref, dt, err_steps, dict(PRECISION_OPTS, picard_rtol=1e-12))
+    qe_mx = q_bg.clone()
+    timed_steps(mesh, phmx, qe_mx, dt, err_steps, c4_opts)
+    qe_64 = q_bg.clone()
+    timed_steps(mesh, ph64, qe_64, dt, err_steps, dict(STEP_OPTS, gmres_rtol=1e-8))
+    # the same precision pattern with refinement to 1e-12 (Picard 1e-12)
+    qe_mx12 = q_bg.clone()
+    ms12, _, _ = timed_steps(mesh, phmx, qe_mx12, dt, err_steps,
+                             dict(PRECISION_OPTS, picard_rtol=1e-12, gmres_inner_rtol=1e-4))
+    cfg4 = dict(geo, workload="hill3d_nc_60x60x20_r3_mixed_R2", value=5.0 * N * steps / (ms4 / 1e3) / 1e9,
+                unit="GDoF-updates/s", ms_per_step=ms4 / steps, steps=steps, gmres_inner_iters=it4,
+                fp64_refinement_sweeps=ref4, speedup_vs_config3=ms3 / ms4,
+                solver="Picard 1e-10, iterative refinement to 1e-8 (FP32 GMRES(30) inner 1e-4)",
+                rel_l2_err_vs_fp64_1e12=perturbation_errors(qe_mx, qe_ref, q_bg),
+                fp64_same_tolerance_rel_l2_err_vs_fp64_1e12=perturbation_errors(qe_64, qe_ref, q_bg),
+                mixed_refined_to_1e12={"rel_l2_err_vs_fp64_1e12": perturbation_errors(qe_mx12, qe_ref, q_bg),
+                                       "ms_per_step": ms12 / err_steps},
+                error_run=f"{err_steps} steps from the background state; the reference is FP64 with "
+                          "Picard and GMRES to 1e-12")
+    mesh.close()
+    return cfg3, cfg4
+
+
 def run_balance(D, I, ctx, case, hours):
     """E_geo of the planetary-scale wave after `hours` of simulated time
     (dt = 10 s, FP64, R2) with the non-stiff Rusanov floor of 1 m/s and the
@@ -495,6 +684,13 @@ def gpu_main(args):
     xyz = mesh.node_coords().cpu().numpy().T
     q0 = I.stratified_state(xyz, **case["state_params"])
     q = torch.tensor(q0, dtype=torch.float64, device="cuda").contiguous()
+    q_bg = q.clone()
+    # FP64 / FP32 FMA roofs of this GPU (library probe, before the timed work)
+    fma_peaks = {}
+    for bits in (64, 32):
+        runs = [D.probe_fma(ctx, bits) for _ in range(5)]
+        fma_peaks["fp%d_fma" % bits] = {"tflops_best": max(x[0] for x in runs),
+                                         "tflops_median": statistics.median(x[0] for x in runs)}
     phys = D.make_phys(f=case["f"], variant="R2")
     dt = case["dt"]
     stream = torch.cuda.current_stream()
@@ -562,130 +758,68 @@ def gpu_main(args):
     e2e_value = throughput(N, args.steps, world, ms_e2e)
     state_bytes = 5 * N * 8
 
-    # mixed precision (FP32 Schur vmults under FP64 refinement) from the same
-    # start state as the timed FP64 steps; error of its perturbation fields
-    # against the FP64 result
+    # mixed precision (FP32 Schur vmults under FP64 refinement) at the
+    # headline's solver settings, from the same start state
     mixed = None
     if not args.no_mixed:
-        q_fp64 = q
         phys_mx = D.make_phys(f=case["f"], variant="R2", precision="mixed")
         mx_opts = dict(STEP_OPTS, gmres_inner_rtol=1e-4)
-        qw = q_start.clone()
-        mesh.step(phys_mx, qw, dt, **mx_opts)               # allocates FP32 copies once
+        mesh.step(phys_mx, q_start.clone(), dt, **mx_opts)       # allocates FP32 copies once
         qm = q_start.clone()
-        torch.cuda.synchronize()
-        e4 = torch.cuda.Event(enable_timing=True)
-        e5 = torch.cuda.Event(enable_timing=True)
-        e4.record(stream)
-        mx_its, mx_ref = 0, 0
-        for _ in range(args.steps):
-            inf = mesh.step(phys_mx, qm, dt, **mx_opts)
-            mx_its += inf.gmres_iters_total
-            mx_ref += inf.refinements_total
-        e5.record(stream)
-        torch.cuda.synchronize()
-        ms_mx = max_over_ranks(e4.elapsed_time(e5), dist, "cuda")
-
-        def pert_fields(s):
-            u = s[1:4] / s[0]
-            p = 0.4 * (s[4] - 0.5 * (s[1:4] * u).sum(0))
-            theta = p / (287.0 * s[0]) * (1e5 / p) ** (0.4 / 1.4)
-            return {"rho": s[0], "theta": theta, "u": u[0], "v": u[1], "w": u[2]}
-
-        f0, f64, fmx = pert_fields(q_start), pert_fields(q_fp64), pert_fields(qm)
-        errs = {}
-        for k in f0:
-            den = torch.linalg.norm(f64[k] - f0[k]).item()
-            errs[k] = torch.linalg.norm(fmx[k] - f64[k]).item() / den if den > 0 else None
-        # error budget: both results against an FP64 run with tight solver
-        # tolerances from the same start state
-        qt = q_start.clone()
-        tight = dict(STEP_OPTS, picard_rtol=1e-13, gmres_rtol=1e-13)
-        for _ in range(args.steps):
-            mesh.step(phys, qt, dt, **tight)
-        ft = pert_fields(qt)
-        err_tight = {"fp64": {}, "mixed": {}}
-        for k in f0:
-            den = torch.linalg.norm(ft[k] - f0[k]).item()
-            err_tight["fp64"][k] = torch.linalg.norm(f64[k] - ft[k]).item() / den if den > 0 else None
-            err_tight["mixed"][k] = torch.linalg.norm(fmx[k] - ft[k]).item() / den if den > 0 else None
+        ms_mx, mx_its, mx_ref = timed_steps(mesh, phys_mx, qm, dt, args.steps, mx_opts)
+        ms_mx = max_over_ranks(ms_mx, dist, "cuda")
         qp = q_start.clone()
         D.profile_begin(mesh, timed=D.KERNEL_CLASSES)
         mesh.step(phys_mx, qp, dt, **mx_opts)
         prof_mx = D.profile_end(mesh)
-        mixed = {"value": throughput(N, args.steps, world, ms_mx),
+        mixed = {"value": throughput(N, args.steps, world, ms_mx), "unit": "GDoF-updates/s",
+                 "ms_per_step": ms_mx / args.steps, "speedup_vs_fp64": ms_max / ms_mx,
+                 "gmres_inner_total": mx_its, "fp64_refinement_sweeps": mx_ref, "inner_rtol": 1e-4,
+                 "what_is_fp32": "Schur vmults inside the Krylov solves (FP32 accumulation)",
+                 "accuracy": "see precision_pattern (same mode at 1e-12 tolerances, per-field errors)",
                  "kernel_breakdown_one_step": {k: {"launches": v[0], "ms": round(v[2], 3)}
-                                               for k, v in prof_mx.items() if v[0]},
-                 "rel_l2_err_vs_tight_fp64_gpu": err_tight,
-                 "unit": "GDoF-updates/s", "ms_per_step": ms_mx / args.steps,
-                 "speedup_vs_fp64": ms_max / ms_mx, "gmres_inner_total": mx_its,
-                 "fp64_refinement_sweeps": mx_ref, "inner_rtol": 1e-4,
-                 "rel_l2_err_vs_fp64_gpu_perturbation": errs,
-                 "what_is_fp32": "Schur vmults inside the Krylov solves (FP32 accumulation)"}
+                                               for k, v in prof_mx.items() if v[0]}}
 
-        # DG_MIXED_EXPLICIT: in addition, the explicit rates of the later
-        # stages as FP32 increments about each step's start state
-        phys_mxe = D.make_phys(f=case["f"], variant="R2", precision="mixed_explicit")
-        qw = q_start.clone()
-        mesh.step(phys_mxe, qw, dt, **mx_opts)
-        qe = q_start.clone()
-        torch.cuda.synchronize()
-        e6 = torch.cuda.Event(enable_timing=True)
-        e7 = torch.cuda.Event(enable_timing=True)
-        e6.record(stream)
-        for _ in range(args.steps):
-            mesh.step(phys_mxe, qe, dt, **mx_opts)
-        e7.record(stream)
-        torch.cuda.synchronize()
-        ms_mxe = max_over_ranks(e6.elapsed_time(e7), dist, "cuda")
-        fe = pert_fields(qe)
-        errs_e = {}
-        for k in f0:
-            den = torch.linalg.norm(f64[k] - f0[k]).item()
-            errs_e[k] = torch.linalg.norm(fe[k] - f64[k]).item() / den if den > 0 else None
-        mixed["explicit_fp32_variant"] = {
-            "value": throughput(N, args.steps, world, ms_mxe), "unit": "GDoF-updates/s",
-            "ms_per_step": ms_mxe / args.steps, "speedup_vs_fp64": ms_max / ms_mxe,
-            "rel_l2_err_vs_fp64_gpu_perturbation": errs_e,
-            "what_is_fp32": "as above, plus the explicit rates of stages 2 and 3 as FP32 "
-                            "increments about the step's start state"}
-
-    # roofline of the dominant class
+    # roofline of the dominant class, against the FP64 FMA rate measured by
+    # the library's probe in this run (best of 5 launches)
     pk, src = peaks()
+    fp64_peak = fma_peaks["fp64_fma"]["tflops_best"]
     nnz = (5 if st.dim == 3 else 3) if st.terrain_following else st.dim * st.dim
     work = work_model(st.dim, st.n1d, N, N // st.nodes_per_elem * 2 * st.dim * st.n1d ** (st.dim - 1),
                       st.n_face_points, nnz)
     launches, timed_launches, tms = prof[dominant]
     roof = None
-    if timed_launches and dominant in work:
+    if timed_launches:
         per_launch_ms = tms / timed_launches
-        flops = work[dominant]
-        achieved = flops / (per_launch_ms / 1e3) / 1e12
+        flops = work.get(dominant)
+        achieved = flops / (per_launch_ms / 1e3) / 1e12 if flops else None
         roof = {"bound": "alu", "kernel": dominant, "achieved": achieved,
-                "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP64_NOMINAL_TFLOPS,
+                "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak if achieved else None,
                 "traffic": (NCU_TRAFFIC_B_PER_NODE[dominant] * N
                             if dominant in NCU_TRAFFIC_B_PER_NODE and st.dim == 3 and st.n1d == 4
                             else None),
+                "peak_source": "measured in this run: dg_probe_fma, FP64 FMA chains filling every SM "
+                               "(best of 5); nominal GB300 FP64 1.25 TFLOP/s",
+                "frac_of_nominal_fp64": achieved / FP64_NOMINAL_TFLOPS if achieved else None,
+                "launches": timed_launches, "ms_per_launch": per_launch_ms,
+                "algorithmic_flops_per_launch": flops,
                 "algorithmic_bytes_per_launch": bytes_model(
                     st.dim, st.n1d, N, st.n_elem * 2 * st.dim * st.n1d ** (st.dim - 1),
                     st.n_face_points, nnz).get(dominant),
-                "nonzero_metric_terms_per_node": nnz,
-                "peak_source": "GB300 nominal FP64 (recipe table); probe measured 1.20",
-                "launches": timed_launches, "ms_per_launch": per_launch_ms,
-                "algorithmic_flops_per_launch": flops}
-    elif timed_launches:
-        per_launch_ms = tms / timed_launches
-        roof = {"bound": "alu", "kernel": dominant, "achieved": None, "peak": FP64_NOMINAL_TFLOPS,
-                "unit": "TFLOP/s", "frac": None, "traffic": None, "launches": timed_launches,
-                "ms_per_launch": per_launch_ms}
+                "nonzero_metric_terms_per_node": nnz}
     total_launches = sum(v[0] for v in prof.values())
     breakdown = {k: {"launches": v[0], "ms": round(v[2], 3)} for k, v in prof_all.items() if v[0]}
 
+    precision = None
+    if not args.no_mixed and world == 1:
+        precision = run_precision_pattern(D, mesh, q_bg, case["f"], dt, min(args.steps, 10))
+
     variants = {}
     per_op = None
+    cfg3 = cfg4 = None
     if not args.no_variants and world == 1:
         per_op = run_per_operator(D, mesh, q, case["f"], 0.29289321881345254 * dt, pk["hbm_gbs"])
-        variants["hill3d_nc"] = run_variant(D, I, ctx, I.hill3d_case(refine=True), steps=2, warmup=1)
+        cfg3, cfg4 = run_refined_configs(D, I, ctx, args.steps, 1)
         variants["hill3d_vline_precond"] = run_variant(D, I, ctx, I.hill3d_case(), steps=2, warmup=1,
                                                        precond=True)
         h3 = I.hill3d_case()
@@ -709,9 +843,40 @@ def gpu_main(args):
     cpu = None
     if not args.no_cpu_baseline and world == 1:
         try:
-            cpu = run_oracle_sample(steps=2, warmup=0)
+            cpu = run_oracle_sample(steps=2, warmup=0, all_cores=True)
         except Exception as exc:  # report, do not fail the bench
             cpu = {"error": str(exc)[:200]}
+
+    def r3(x):
+        if isinstance(x, float):
+            return float("%.3g" % x)
+        if isinstance(x, dict):
+            return {k: r3(v) for k, v in x.items()}
+        return x
+
+    # the driver keeps the end of stdout: the compact summary goes last
+    summary = {"fp64": {"gdof_s": r3(value), "ms_step": r3(ms_max / args.steps)}}
+    if mixed:
+        summary["mixed_same_tol"] = {"gdof_s": r3(mixed["value"]), "speedup": r3(mixed["speedup_vs_fp64"])}
+    if precision:
+        summary["precision_1e-12"] = {
+            "fp64_ms": r3(precision["fp64"]["ms_per_step"]), "mixed_ms": r3(precision["mixed"]["ms_per_step"]),
+            "speedup": r3(precision["mixed_speedup_vs_fp64"]),
+            "mixed_err": r3(precision["mixed"]["rel_l2_err_vs_reference"]),
+            "fp64_err": r3(precision["fp64"]["rel_l2_err_vs_reference"])}
+    if cfg3:
+        summary["config3_nc_fp64"] = {"gdof_s": r3(cfg3["value"]), "ms_step": r3(cfg3["ms_per_step"]),
+                                      "gmres": cfg3["gmres_iters"], "steps": cfg3["steps"]}
+        summary["config4_nc_mixed"] = {"gdof_s": r3(cfg4["value"]), "ms_step": r3(cfg4["ms_per_step"]),
+                                       "speedup": r3(cfg4["speedup_vs_config3"]),
+                                       "err_1e-8": r3(max(cfg4["rel_l2_err_vs_fp64_1e12"].values())),
+                                       "fp64_err_1e-8": r3(max(
+                                           cfg4["fp64_same_tolerance_rel_l2_err_vs_fp64_1e12"].values())),
+                                       "err_1e-12": r3(cfg4["mixed_refined_to_1e12"]["rel_l2_err_vs_fp64_1e12"])}
+    if roof:
+        summary["roofline"] = {"kernel": dominant, "frac_of_measured_fp64": r3(roof["frac"]),
+                               "fp64_peak_tflops": r3(fp64_peak),
+                               "fp32_peak_tflops": r3(fma_peaks["fp32_fma"]["tflops_best"])}
     line = {
         "metric": METRIC, "value": value, "unit": "GDoF-updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
@@ -723,19 +888,24 @@ def gpu_main(args):
                    "gmres_restart": STEP_OPTS["gmres_restart"],
                    "l2": "state (%.0f MB) and Krylov basis exceed the 126 MB L2" % (state_bytes / 1e6),
                    "parallelism": "replicas" if world > 1 else "single",
-                   "tiles_fp64_fp32": tiles},
+                   "schedule_tiles_fp64_fp32_fused_stage": tiles},
+        "variants": variants,
+        "per_operator": per_op,
+        "kernel_breakdown_one_step": breakdown,
+        "mixed_precision": mixed,
+        "precision_pattern": precision,
+        "config3": cfg3,
+        "config4": cfg4,
+        "fma_peaks": fma_peaks,
+        "peaks_source": src,
+        "iterations": {"picard_per_stage": picard[:3], "gmres_total": gm_its, "gmres_max_relres": relres},
         "e2e": {"value": e2e_value, "unit": "GDoF-updates/s", "h2d_bytes_per_step": state_bytes,
                 "d2h_bytes_per_step": state_bytes, "gmres_total": e2e_gmres},
         "roofline": roof,
         "cpu_baseline": cpu,
-        "mixed_precision": mixed,
-        "variants": variants,
-        "per_operator": per_op,
         "clocks": clk,
         "gpu_launches": total_launches,
-        "iterations": {"picard_per_stage": picard, "gmres_total": gm_its, "gmres_max_relres": relres},
-        "kernel_breakdown_one_step": breakdown,
-        "peaks_source": src,
+        "summary": summary,
     }
     print(json.dumps(line), flush=True)
     if dist:
@@ -758,7 +928,8 @@ def reference_main(args):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": "hill3d_60x60x20_r3_fp64_R2", "sample": res["sample"]},
         "cpu_baseline": {"value": res["value"], "unit": res["unit"], "cores": res["cores"],
-                         "kind": "oracle", "sample": res["sample"]},
+                         "kind": "oracle", "sample": res["sample"], "nproc": res.get("nproc"),
+                         "cpu_model": res.get("cpu_model")},
         "e2e": {"value": res["value"], "unit": "GDoF-updates/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }

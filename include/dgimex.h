@@ -51,7 +51,7 @@ typedef enum {
 enum { DG_NODES_GL = 0, DG_NODES_GLL = 1 };
 enum { DG_BC_WALL = 1, DG_BC_FARFIELD = 2 };
 enum { DG_R1 = 1, DG_R2 = 2 };
-enum { DG_FP64 = 0, DG_MIXED = 1, DG_MIXED_EXPLICIT = 2 };
+enum { DG_FP64 = 0, DG_MIXED = 1, DG_MIXED_EXPLICIT = 2, DG_PAIRS = 3 };
 
 typedef struct dg_ctx dg_ctx;
 typedef struct dg_mesh dg_mesh;
@@ -68,7 +68,20 @@ void dg_ctx_destroy(dg_ctx* ctx);
  * Mesh description (host arrays, copied by dg_mesh_create).
  *  dim        2 (x-z slice) or 3.
  *  degree     r in 1..4; nodes per cell (r+1)^dim.
- *  node_set   DG_NODES_GL (Section 3: Gauss-Legendre nodes); GLL -> UNSUPPORTED.
+ *  node_set   DG_NODES_GL (Section 3: Gauss-Legendre nodes) or DG_NODES_GLL
+ *             (Gauss-Lobatto nodes, always with (r+1)-point Gauss-Legendre
+ *             quadrature: the mass matrix S^T W S and its inverse
+ *             S^{-1} W^{-1} S^{-T} of Section 3.1).  With GLL every nodal
+ *             array of every call is in the GLL basis (nodes at the GLL
+ *             points, dg_mesh_node_coords gives them); the library runs the
+ *             operators in the GL basis of the same polynomials and changes
+ *             basis per cell on the way in and out.  GLL meshes support the
+ *             explicit and implicit operators, the Schur right-hand side,
+ *             the velocity recovery, unpreconditioned GMRES and the
+ *             host-driven step in DG_FP64 and DG_MIXED; the rest
+ *             (preconditioners, graph mode, DG_MIXED_EXPLICIT, damping
+ *             layers, E_geo, ensembles, the no-alloc call) answers
+ *             DG_ERR_UNSUPPORTED.
  *  vertices   n_elem x 2^dim x dim doubles: corner v of a cell sits at
  *             reference corner (v&1, (v>>1)&1[, (v>>2)&1]); the cell map is
  *             multilinear (curved terrain-following cells included).
@@ -78,9 +91,10 @@ void dg_ctx_destroy(dg_ctx* ctx);
  *  hang_faces n_hang x 5: [e_coarse, f_coarse, e_fine, f_fine, subface];
  *             2:1 only; f_fine = f_coarse ^ 1; bit t of subface selects the
  *             half along the t-th tangential axis.
- *  bdry_faces n_bdry x 3: [e, f, DG_BC_WALL] (slip wall, mirror state);
- *             DG_BC_FARFIELD (outer state = a background, the non-reflecting
- *             top of Section 4.3) is not implemented: DG_ERR_UNSUPPORTED.
+ *  bdry_faces n_bdry x 3: [e, f, bc]: DG_BC_WALL (slip wall, mirror state)
+ *             or DG_BC_FARFIELD (the non-reflecting top of Section 4.3, read
+ *             as a far-field face whose outer state is a given background
+ *             state: dg_mesh_set_far_state).
  * Every face of every cell must be covered exactly once (interior side,
  * fine hanging side, one of the 2^(dim-1) coarse subfaces, or boundary);
  * otherwise DG_ERR_ARG.
@@ -112,20 +126,39 @@ typedef struct {
   int64_t n_elem, n_nodes, n_face_points, n_hang_points;
   int64_t workspace_bytes;   /* library-owned device memory held now */
   int tile_fp64[3];          /* cells-per-block multipliers (1, 2, 4) of the */
-  int tile_fp32[3];          /* explicit, gradient and divergence cell kernels */
+  int tile_fp32[3];          /* explicit, gradient and divergence cell kernels
+                                (the fused gradient and divergence passes of the
+                                Schur vmult run one tile size: entries 1 and 2
+                                are informational) */
   int terrain_following;     /* 1: every cell has x = x(xi_1) (and y = y(xi_2)),
                                 so the cell kernels skip the metric terms that
                                 vanish exactly (not in the paper) */
+  int fused_stage[2];        /* FP64, FP32 Schur vmult: 1 = plus-side face
+                                values from the neighbour cells' nodal values
+                                staged in shared memory, 0 = from a trace array
+                                written by a separate pass (see
+                                dg_mesh_set_fused_stage) */
 } dg_mesh_stats;
 int dg_mesh_info(const dg_mesh* mesh, dg_mesh_stats* out);
 
-/* Tile autotuner (not in the paper): times the cell kernels of the
- * explicit operator and of the Schur vmult with 1, 2 and 4 times the base
- * number of cells per thread block on this mesh (synthetic coefficients,
- * CUDA events) and keeps the fastest per kernel class, for FP64 and, when
- * precision is DG_MIXED or DG_MIXED_EXPLICIT, for the FP32 kernels too.  Allocates temporary
- * device memory; synchronises `stream`.  Results in dg_mesh_stats. */
+/* Schedule autotuner (not in the paper): times the explicit operator's
+ * cell kernel with 1, 2 and 4 times the base number of cells per thread
+ * block, and whole Schur vmults with either fused-kernel schedule (see
+ * dg_mesh_set_fused_stage), on this mesh (synthetic coefficients, CUDA
+ * events), and keeps the fastest, for FP64 and, when precision is DG_MIXED
+ * or DG_MIXED_EXPLICIT, for the FP32 vmult too.  Allocates temporary device
+ * memory; synchronises `stream`.  Results in dg_mesh_stats. */
 int dg_mesh_autotune(dg_ctx* ctx, dg_mesh* mesh, int precision, void* stream);
+
+/* Schedule of the fused face + cell kernels of the Schur vmult, right-hand
+ * side and velocity recovery (not in the paper): per precision (FP64, FP32),
+ * 1 stages each neighbour cell's nodal values in shared memory and
+ * contracts them to the shared face there (no trace pass, more arithmetic),
+ * 0 reads the neighbour's face values from a trace array that a separate
+ * pass writes (less arithmetic, more memory traffic).  Both give the same
+ * results up to rounding.  Defaults: FP64 0, FP32 1; dg_mesh_autotune times
+ * both and keeps the faster.  Host only, no GPU work. */
+int dg_mesh_set_fused_stage(dg_mesh* mesh, int fp64, int fp32);
 
 /* Physical coordinates of all nodes: xyz[dim][cell][node] (device, FP64). */
 int dg_mesh_node_coords(dg_ctx* ctx, const dg_mesh* mesh, double* xyz, void* stream);
@@ -146,7 +179,16 @@ typedef struct {
                                 explicit operator stay FP64;
                                 DG_MIXED_EXPLICIT: DG_MIXED plus the explicit
                                 operator in FP32 on perturbations (see
-                                dg_mesh_set_background and imex_ark2_step) */
+                                dg_mesh_set_background and imex_ark2_step);
+                                DG_PAIRS (not in the paper; an emulation, not
+                                IEEE FP64): the Schur vmults inside the
+                                Krylov solves run on the FP32 pipe in pairs
+                                of FP32 numbers (hi + lo, about 48
+                                significant bits, about 1e-14 relative per
+                                operation), everything else as DG_FP64;
+                                plain FP64 GMRES, no refinement.  Not with
+                                Gauss-Lobatto nodes, far-field faces or
+                                graph mode (DG_ERR_UNSUPPORTED). */
   const double* f_cell;      /* optional device array, one Coriolis parameter
                                 per cell (NULL: f everywhere); lets one mesh
                                 carry several independent instances */
@@ -213,6 +255,26 @@ int dg_mesh_set_background(dg_ctx* ctx, dg_mesh* mesh, const dg_phys* phys,
                            const double* q_bg, void* stream);
 
 /*
+ * Outer state of the far-field faces (DG_BC_FARFIELD; reading of the
+ * non-reflecting upper boundary of Section 4.3).  q_far: device 5 x N nodal
+ * state (e.g. the background atmosphere); its traces at the far-field face
+ * points are stored (the array itself is not kept).  The explicit operator
+ * uses them as the plus state of those faces in the same Rusanov and centred
+ * fluxes as at an interior face (lambda = max(|u-.n|, |u_far.n|)).  In the
+ * implicit stage system the outer state is known data: B, C and the
+ * implicit Rusanov term keep their inner halves ({x} = x-/2, (h rho u)-.n/2,
+ * lambda x-), and the outer halves move to the right-hand sides
+ * (dg_schur_rhs subtracts M^{-1} b_far and M^{-1} g_far from the
+ * predictors, dg_recover_velocity M^{-1} b_far).  Required before any
+ * operator call on a mesh with far-field faces (else DG_ERR_ARG); a no-op
+ * on a mesh without them.  DG_MIXED_EXPLICIT and ensembles are not
+ * available with far-field faces (DG_ERR_UNSUPPORTED); the preconditioners
+ * treat them as walls (they stay approximate inverses; the flexible GMRES
+ * still solves the exact system).
+ */
+int dg_mesh_set_far_state(dg_ctx* ctx, dg_mesh* mesh, const double* q_far, void* stream);
+
+/*
  * Rayleigh damping (sponge) layers of the orography tests (Section 4, eq.
  * damping).  With layers set, every evaluation of the explicit operator on
  * this mesh (dg_apply_explicit, each stage of imex_ark2_step, host-driven or
@@ -226,7 +288,7 @@ int dg_mesh_set_background(dg_ctx* ctx, dg_mesh* mesh, const dg_phys* phys,
  * polynomial R(-lambda dt), |R| < 1 up to lambda dt of about 2.5 (the
  * paper uses lambda_bar dt = 1.2).
  * q_bar: 5 x N device state, copied; s == NULL switches the layers off.
- * Not applied by dg_apply_explicit_noalloc or by ensembles.
+ * Applied by dg_apply_explicit_noalloc too; not applied by ensembles.
  */
 typedef struct {
   double lambda_bar;               /* 1/s */
@@ -421,8 +483,11 @@ int dg_profile_end(dg_mesh* mesh, dg_kernel_stat* out, int max_out, int* n_out);
  * e.g. a service that reserves its memory up front and forbids allocation
  * in its steady state, or a framework that owns every device allocation
  * and rejects raw cudaMalloc, which may also synchronise the device).
- * Same arguments, results and layout as dg_apply_explicit, which instead
- * grows per-mesh workspace with cudaMalloc on its first call on a mesh.
+ * Same arguments, results and layout as dg_apply_explicit (damping layers
+ * set by dg_mesh_set_sponge included), which instead grows per-mesh
+ * workspace with cudaMalloc on its first call on a mesh.  phys->precision
+ * DG_FP64 and DG_MIXED both run the FP64 explicit kernels, as
+ * dg_apply_explicit does; DG_MIXED_EXPLICIT returns DG_ERR_UNSUPPORTED.
  *  - Scratch comes from one fixed array of 2^22 doubles (32 MiB) of device
  *    memory in the library image; every GPU that loads the library holds it
  *    until the process exits.  A mesh needs 14 doubles per face-point slot
@@ -440,6 +505,20 @@ int dg_profile_end(dg_mesh* mesh, dg_kernel_stat* out, int max_out, int* n_out);
  */
 int dg_apply_explicit_noalloc(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* phys,
                               const double* q, double* f_ns, double* f_s, void* stream);
+
+/*
+ * FMA-throughput probe (no counterpart in the paper; it measures the
+ * arithmetic roof that the FP64 and FP32 cell kernels are bound by).
+ * Launches, on the context's device (which must be current), a grid that
+ * fills every SM with threads each running 8 independent chains of
+ * x <- x * a + b for `iters` rounds in FP64 (bits = 64) or FP32
+ * (bits = 32); two untimed launches, then one launch timed with CUDA events
+ * on `stream`.  *tflops = 2 flops x chains x iters x threads / time;
+ * *ms (may be NULL) = that launch's time.  Allocates and frees a small
+ * device buffer; synchronises `stream`.  Suggested iters: 8192 (FP64),
+ * 524288 (FP32), a few tens of ms each on GB300.
+ */
+int dg_probe_fma(dg_ctx* ctx, int bits, int iters, double* tflops, double* ms, void* stream);
 
 #ifdef __cplusplus
 }

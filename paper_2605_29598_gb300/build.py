@@ -19,7 +19,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libdgimex.so")
 INCLUDE = os.path.join(ROOT, "include")
 
-SOURCES = ["mesh.cu", "ops.cu", "solver.cu", "noalloc.cu", "ensemble.cu", "pert.cu", "graph.cu", "diag.cu", "vline.cu", "sponge.cu", "cellblock.cu"]
+SOURCES = ["mesh.cu", "ops.cu", "solver.cu", "noalloc.cu", "ensemble.cu", "pert.cu", "graph.cu", "diag.cu", "vline.cu", "sponge.cu", "cellblock.cu", "probe.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I" + INCLUDE]

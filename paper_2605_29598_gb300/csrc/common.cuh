@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/dgimex.h"
+#include "df64.cuh"
 
 namespace dg {
 
@@ -41,10 +42,22 @@ struct Tables {
   T P[2][MAX_N][MAX_N];      // P[b][q][j] = l_j((xi_q + b)/2)  (2:1 prolongation)
 };
 
+// A 1D matrix of the nodal change of basis between Gauss-Lobatto and
+// Gauss-Legendre nodes (applied along every direction of a cell).
+template <typename T>
+struct Mat1D {
+  T m[MAX_N][MAX_N];
+};
+
 struct HostTables {
   int n;
   double x[MAX_N], w[MAX_N];
   Tables<double> t;
+  // Gauss-Lobatto nodes on [0, 1]; G[q][j] = l_j^GLL(x_q) (values at the
+  // Gauss-Legendre points of the GLL nodal basis) and Gi[q][j] =
+  // l_j^GL(xl_q) (its inverse: values at the GLL nodes of the GL basis)
+  double xl[MAX_N];
+  Mat1D<double> G, Gi;
 };
 void make_tables(int n, HostTables* out);   // Newton on Legendre P_n
 
@@ -120,16 +133,36 @@ struct dg_mesh {
   float* invM32 = nullptr;
   float* fgeo32 = nullptr;
   float* lv32 = nullptr;     // cell corners minus corner 0 (E x 2^d x d)
+  float* tc32 = nullptr;     // terrain-following meshes: per cell 16 coefficients of
+                             // the vertical row of J (see terrain_row in ops.cuh)
   // face-point topology (device, int32)
   int* fp_minus = nullptr;   // nF: minus slot
   int* fp_plus = nullptr;    // nF: plus slot, -1 wall, -2-hp hanging
   int* hp_cslot = nullptr;   // nH: coarse slot base (e_c*2d+f_c)*nfp
   int* hp_code = nullptr;    // nH: sub | (fine point index << 8)
   int* hc_slot = nullptr;    // nHC: coarse slot base
+  int* cface = nullptr;      // E x 2d: neighbour across each cell face, -1 wall, -2 on a 2:1 face,
+                             // -3 far field
+  // far-field boundary (outer state = a given background state): per face
+  // point its far-point index g (or -1; null without far-field faces), the
+  // face points of the far list grouped by face type f = 0..2d-1
+  // (far_fbeg[f] .. far_fbeg[f+1]), and the outer state's conserved traces
+  // at the far points (5 x nFar, FP64 and FP32) once dg_mesh_set_far_state
+  // has run
+  int* fp_far = nullptr;
+  int* far_p = nullptr;
+  int64_t nFar = 0;
+  int64_t far_fbeg[7] = {0, 0, 0, 0, 0, 0, 0};
+  bool far_set = false;
   // workspace
   dg::DBuf trc, slot, hbuf, trh, pcoef, wv, gm_V, gm_work, red, st, fns, fs;
   dg::DBuf trh32, pcoef32, c32, ir32, irw;   // mixed precision: FP32 coefficients, IR vectors
   dg::DBuf irho, irho32;                      // 1/rho of the frozen stage density
+  // fused face + cell kernels: implicit Rusanov coefficient per own face
+  // slot (FP64, FP32) and outward n dS per own face slot (FP64: d x S)
+  dg::DBuf pcs, pcs32, snS;
+  int fused_stage[2] = {0, 1};   // per precision (FP64, FP32): plus-side traces from
+                                 // staged neighbour cells (1) or from a trace array (0)
   // background of the perturbation-form explicit operator (mixed precision)
   dg::DBuf bg, bg32, bgF, bgtr, bgjump, pert32;
   // device-driven step (CUDA graph): solver state and fixed work vectors
@@ -162,15 +195,28 @@ struct dg_mesh {
   // K_ab = w det(J) (J^-1)_ab vanish exactly for (a, b) = (1, y), (1, z),
   // (2, x), (2, z) (3D) or (1, z) (2D) and the cell kernels skip them
   bool terrain = false;
+  // Gauss-Lobatto nodal basis (Section 3.1's S^{-1} W^{-1} S^{-T} inverse
+  // mass): every nodal array at the ABI is in the GLL basis; the operators
+  // run in the Gauss-Legendre basis of the same polynomials and the arrays
+  // are converted per cell on the way in and out
+  bool gll = false;
+  dg::DBuf gl64, gl32;   // GL copies of coefficients (5N) and inputs (5N)
+  dg::DBuf far_q, far_q32, farw;   // outer traces (FP64, FP32); predictors with the outer data (4N)
+  // DG_PAIRS (FP64-class vmults on the FP32 pipe): pair copies of the
+  // geometry (metric, 1/(w det J), face n dS and dS, per-slot normals), of the
+  // frozen coefficients (5N + E) and their face data, and the vmult's x, y
+  dg::DBuf Kdf, invMdf, fgeodf, snSdf, cdf, trhdf, pcoefdf, irhodf, pcsdf, irdf;
   int64_t workspace_bytes() const;
   // every workspace buffer, for accounting, release and graph capture checks
-  static constexpr int kBufs = 34;
+  static constexpr int kBufs = 52;
   void bufs(const dg::DBuf** out) const {
     const dg::DBuf* b[kBufs] = {&trc, &slot, &hbuf, &trh, &pcoef, &wv, &gm_V, &gm_work, &red, &st,
                                 &fns, &fs, &trh32, &pcoef32, &c32, &ir32, &irw, &irho, &irho32,
                                 &bg, &bg32, &bgF, &bgtr, &bgjump, &pert32, &gstate, &gwork,
                                 &vl_slots, &vl_fac, &vl_scr, &gm_pc, &sponge,
-                                &cb_slots, &cb_inv};
+                                &cb_slots, &cb_inv, &pcs, &pcs32, &snS, &gl64, &gl32, &far_q, &far_q32,
+                                &farw, &Kdf, &invMdf, &fgeodf, &snSdf, &cdf, &trhdf, &pcoefdf, &irhodf,
+                                &pcsdf, &irdf};
     for (int i = 0; i < kBufs; ++i) out[i] = b[i];
   }
 };
@@ -202,11 +248,28 @@ struct FaceTopo {
   const int* hp_code;
   const int* hc_slot;
   int64_t nF, nH, nHC, S;
+  int64_t p0;   // first face point a face kernel handles (0: all of them)
+  // far-field points among the boundary ones (code -1): index g into the
+  // outer traces (5 x nFar), or -1 for a wall; fp_far null: walls only
+  const int* fp_far;
+  const double* far_q;
+  const float* far_q32;
+  int64_t nFar;
+  const df64* fgeodf;   // face geometry as FP32 pairs (DG_PAIRS), or null
 };
 
 inline FaceTopo topo(const dg_mesh* m) {
   return FaceTopo{m->fp_minus, m->fp_plus, m->fgeo, m->fgeo32, m->hp_cslot, m->hp_code,
-                  m->hc_slot, m->nF, m->nH, m->nHC, m->S};
+                  m->hc_slot, m->nF, m->nH, m->nHC, m->S, 0,
+                  m->nFar > 0 ? m->fp_far : nullptr, m->far_q.as<double>(), m->far_q32.as<float>(), m->nFar,
+                  m->fgeodf.as<df64>()};
+}
+
+// the face points of the 2:1 faces only (the last nH of the unified list)
+inline FaceTopo topo_hanging(const dg_mesh* m) {
+  FaceTopo ft = topo(m);
+  ft.p0 = m->nF - m->nH;
+  return ft;
 }
 
 // Counts a launch of class `kid` and brackets it with CUDA events when that

@@ -48,6 +48,10 @@ extern "C" int dg_geostrophic_error(dg_ctx* ctx, const dg_mesh* mesh, const dg_p
     set_error("dg_geostrophic_error: gamma must be > 1");
     return DG_ERR_ARG;
   }
+  if (mesh->gll) {
+    set_error("dg_geostrophic_error: not implemented for Gauss-Lobatto nodes");
+    return DG_ERR_UNSUPPORTED;
+  }
   dg_mesh* m = const_cast<dg_mesh*>(mesh);
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t n = m->N;

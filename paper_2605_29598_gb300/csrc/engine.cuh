@@ -25,12 +25,24 @@ ImplK impl_consts(const dg_phys* ph, double a_dt);
 template <typename T> inline const T* met_K(const dg_mesh* m);
 template <> inline const double* met_K<double>(const dg_mesh* m) { return m->K; }
 template <> inline const float* met_K<float>(const dg_mesh* m) { return m->K32; }
+template <> inline const df64* met_K<df64>(const dg_mesh* m) { return m->Kdf.as<df64>(); }
 template <typename T> inline const T* met_invM(const dg_mesh* m);
 template <> inline const double* met_invM<double>(const dg_mesh* m) { return m->invM; }
 template <> inline const float* met_invM<float>(const dg_mesh* m) { return m->invM32; }
-template <typename T> inline DBuf& buf_trh(dg_mesh* m) { return sizeof(T) == 8 ? m->trh : m->trh32; }
-template <typename T> inline DBuf& buf_pcoef(dg_mesh* m) { return sizeof(T) == 8 ? m->pcoef : m->pcoef32; }
-template <typename T> inline DBuf& buf_irho(dg_mesh* m) { return sizeof(T) == 8 ? m->irho : m->irho32; }
+template <> inline const df64* met_invM<df64>(const dg_mesh* m) { return m->invMdf.as<df64>(); }
+// per-precision coefficient buffers: FP64, FP32 and FP32 pairs each own one
+template <typename T> inline DBuf& buf_trh(dg_mesh* m);
+template <> inline DBuf& buf_trh<double>(dg_mesh* m) { return m->trh; }
+template <> inline DBuf& buf_trh<float>(dg_mesh* m) { return m->trh32; }
+template <> inline DBuf& buf_trh<df64>(dg_mesh* m) { return m->trhdf; }
+template <typename T> inline DBuf& buf_pcoef(dg_mesh* m);
+template <> inline DBuf& buf_pcoef<double>(dg_mesh* m) { return m->pcoef; }
+template <> inline DBuf& buf_pcoef<float>(dg_mesh* m) { return m->pcoef32; }
+template <> inline DBuf& buf_pcoef<df64>(dg_mesh* m) { return m->pcoefdf; }
+template <typename T> inline DBuf& buf_irho(dg_mesh* m);
+template <> inline DBuf& buf_irho<double>(dg_mesh* m) { return m->irho; }
+template <> inline DBuf& buf_irho<float>(dg_mesh* m) { return m->irho32; }
+template <> inline DBuf& buf_irho<df64>(dg_mesh* m) { return m->irhodf; }
 int ensure_fp32_geometry(dg_mesh* m);
 
 // Metric source of the implicit cell kernels: FP64 loads the stored
@@ -41,6 +53,7 @@ inline CellGeo<T> cell_geo(const dg_mesh* m) {
   g.K = met_K<T>(m);
   g.invM = met_invM<T>(m);
   g.lv = nullptr;
+  g.tc = nullptr;
   for (int k = 0; k < MAX_N; ++k) {
     g.x[k] = (T)m->tab.x[k];
     g.w[k] = (T)m->tab.w[k];
@@ -54,6 +67,7 @@ inline CellGeo<float> cell_geo<float>(const dg_mesh* m) {
   g.K = m->K32;
   g.invM = m->invM32;
   g.lv = m->lv32;
+  g.tc = m->tc32;
   for (int k = 0; k < MAX_N; ++k) {
     g.x[k] = (float)m->tab.x[k];
     g.w[k] = (float)m->tab.w[k];
@@ -74,6 +88,19 @@ int explicit_increment(dg_mesh* m, const PhysK& ph, const double* q, const doubl
 // were formed as increments about ref from rates that already hold the
 // damping at ref
 int sponge_rt(dg_mesh* m, const double* q, double* fns, cudaStream_t st, const double* ref = nullptr);
+// Gauss-Lobatto meshes: out = G in (to_gl) or G^{-1} in per cell, nfld
+// fields of N doubles (in == out allowed); gl_scratch: 5N doubles of FP64
+// scratch after the GL copies of the frozen coefficients (null when the
+// allocation fails)
+int gl_basis(dg_mesh* m, const double* in, double* out, int nfld, bool to_gl, cudaStream_t st);
+double* gl_scratch(dg_mesh* m);
+// DG_PAIRS: pair copies of the geometry (made once per mesh), and FP64 <->
+// pair conversions of n values
+int ensure_pairs_geometry(dg_mesh* m, cudaStream_t st);
+int to_pairs(dg_mesh* m, const double* a, df64* b, int64_t n, cudaStream_t st);
+int from_pairs(dg_mesh* m, const df64* a, double* b, int64_t n, cudaStream_t st);
+int schur_vmult_pairs(dg_mesh* m, const ImplK& k, const double* rho, const double* plag, const double* ulag,
+                      int penalty, const double* x, double* y, cudaStream_t st);
 // FP32 Schur vmult (coefficients and vectors cast from / to FP64)
 int schur_vmult_mixed(dg_mesh* m, const ImplK& k, const double* rho, const double* plag, const double* ulag,
                       int penalty, const double* x, double* y, cudaStream_t st);
@@ -81,7 +108,7 @@ int schur_vmult_mixed(dg_mesh* m, const ImplK& k, const double* rho, const doubl
 // Run the statement list with the tile multiplier M_ (cells per block =
 // M_ x the base count) chosen for kernel class `kid` of the mesh.
 template <typename T> inline int tile_of(const dg_mesh* m, int kid) {
-  return sizeof(T) == 8 ? m->tile[kid] : m->tile32[kid];
+  return std::is_same<T, float>::value ? m->tile32[kid] : m->tile[kid];
 }
 #define DG_TILE(m, kid, ...)                                         \
   switch (tile_of<T>((m), kid)) {                                    \

@@ -66,6 +66,17 @@ int dg_ensemble_create(dg_ctx* ctx, const dg_mesh_desc* descs, const double* f_i
   std::map<std::pair<int, int>, int> gid;
   for (int i = 0; i < n; ++i) {
     const dg_mesh_desc& d = descs[i];
+    if (d.node_set != DG_NODES_GL) {
+      dg_ensemble_destroy(ens);
+      set_error("dg_ensemble_create: instance %d: ensembles take Gauss-Legendre nodes only", i);
+      return DG_ERR_UNSUPPORTED;
+    }
+    for (int64_t k = 0; k < d.n_bdry && d.bdry_faces; ++k)
+      if (d.bdry_faces[3 * k + 2] == DG_BC_FARFIELD) {
+        dg_ensemble_destroy(ens);
+        set_error("dg_ensemble_create: instance %d: ensembles take slip walls only", i);
+        return DG_ERR_UNSUPPORTED;
+      }
     if ((d.dim != 2 && d.dim != 3) || d.n_elem <= 0) {
       dg_ensemble_destroy(ens);
       set_error("dg_ensemble_create: instance %d has an invalid mesh description", i);

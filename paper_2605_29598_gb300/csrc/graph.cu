@@ -356,7 +356,7 @@ struct StepGraph {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   dg::StepState* host = nullptr;   // pinned read-back of the counters
-  unsigned char key[1024];
+  unsigned char key[2048];
   size_t key_len = 0;
   bool valid = false;
 };

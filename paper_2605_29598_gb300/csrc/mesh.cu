@@ -123,6 +123,27 @@ void make_tables(int n, HostTables* out) {
     out->t.L[0][j] = lag(j, 0.0);
     out->t.L[1][j] = lag(j, 1.0);
   }
+  // Gauss-Lobatto nodes: the ends and the roots of P'_{n-1} on [-1, 1],
+  // in closed form for n <= 5
+  static const double gll_in[MAX_N + 1][MAX_N] = {
+      {0}, {0.0}, {-1.0, 1.0}, {-1.0, 0.0, 1.0},
+      {-1.0, -0.44721359549995793928, 0.44721359549995793928, 1.0},   // +-1/sqrt 5
+      {-1.0, -0.65465367070797714380, 0.0, 0.65465367070797714380, 1.0}};   // +-sqrt(3/7)
+  double* xl = out->xl;
+  for (int k = 0; k < n; ++k) xl[k] = 0.5 * (gll_in[n][k] + 1.0);
+  auto lagl = [&](int j, double s) {
+    double v = 1.0;
+    for (int k = 0; k < n; ++k)
+      if (k != j) v *= (s - xl[k]) / (xl[j] - xl[k]);
+    return v;
+  };
+  std::memset(&out->G, 0, sizeof(out->G));
+  std::memset(&out->Gi, 0, sizeof(out->Gi));
+  for (int q = 0; q < n; ++q)
+    for (int j = 0; j < n; ++j) {
+      out->G.m[q][j] = lagl(j, x[q]);
+      out->Gi.m[q][j] = lag(j, xl[q]);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -298,6 +319,49 @@ int ensure_fp32_geometry(dg_mesh* m) {
     return cuda_fail(e, "fp32 corner offsets");
   }
   m->lv32 = lv32;
+  if (m->terrain) {
+    // per cell: dx, dy, then the bilinear coefficients (a, b, c, d) of
+    // dz/dxi_0 in (xi_1, xi_2), dz/dxi_1 in (xi_0, xi_2) and dz/dxi_2 in
+    // (xi_0, xi_1) (3D; in 2D dz/dxi_0 = a0 + b0 xi_1, dz/dxi_1 = a1 + b1 xi_0),
+    // all from the corner offsets in FP64
+    const int d = m->dim;
+    std::vector<float> tc((size_t)m->E * 16, 0.0f);
+    for (int64_t c = 0; c < m->E; ++c) {
+      const double* V = hv.data() + c * nv;
+      auto z = [&](int v) { return V[v * d + d - 1] - V[d - 1]; };
+      float* o = tc.data() + c * 16;
+      o[0] = (float)(V[1 * d + 0] - V[0]);
+      if (d == 3) {
+        o[1] = (float)(V[2 * d + 1] - V[1]);
+        double D[3][4];
+        for (int j = 0; j < 4; ++j) {
+          D[0][j] = z(2 * j + 1) - z(2 * j);                                   // bit 0 pairs, j = (b1, b2)
+          const int v1 = (j & 1) | 2 | ((j >> 1) << 2);
+          D[1][j] = z(v1) - z(v1 - 2);                                         // bit 1 pairs, j = (b0, b2)
+          D[2][j] = z(j + 4) - z(j);                                           // bit 2 pairs, j = (b0, b1)
+        }
+        for (int r = 0; r < 3; ++r) {
+          o[2 + 4 * r] = (float)D[r][0];
+          o[3 + 4 * r] = (float)(D[r][1] - D[r][0]);
+          o[4 + 4 * r] = (float)(D[r][2] - D[r][0]);
+          o[5 + 4 * r] = (float)(D[r][3] - D[r][2] - D[r][1] + D[r][0]);
+        }
+      } else {
+        o[2] = (float)(z(1) - z(0));
+        o[3] = (float)((z(3) - z(2)) - (z(1) - z(0)));
+        o[6] = (float)(z(2) - z(0));
+        o[7] = (float)((z(3) - z(1)) - (z(2) - z(0)));
+      }
+    }
+    float* tc32 = nullptr;
+    e = cudaMalloc(&tc32, sizeof(float) * tc.size());
+    if (e == cudaSuccess) e = cudaMemcpy(tc32, tc.data(), sizeof(float) * tc.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaFree(tc32);
+      return cuda_fail(e, "fp32 terrain coefficients");
+    }
+    m->tc32 = tc32;
+  }
   return DG_OK;
 }
 
@@ -408,9 +472,13 @@ void dg_mesh_destroy(dg_mesh* m) {
   cudaFree(m->invM32);
   cudaFree(m->fgeo32);
   cudaFree(m->lv32);
+  cudaFree(m->tc32);
   cudaFree(m->vl_above);
   cudaFree(m->vl_below);
   cudaFree(m->vl_heads);
+  cudaFree(m->cface);
+  cudaFree(m->fp_far);
+  cudaFree(m->far_p);
   graph_release(m);
   const DBuf* b[dg_mesh::kBufs];
   m->bufs(b);
@@ -438,11 +506,7 @@ int check_desc(const dg_mesh_desc* d, const char* who, HangGroups* hg) {
     set_error("%s: degree %d not in 1..4", who, d->degree);
     return d->degree > 4 ? DG_ERR_UNSUPPORTED : DG_ERR_ARG;
   }
-  if (d->node_set == DG_NODES_GLL) {
-    set_error("%s: Gauss-Lobatto nodes are not implemented", who);
-    return DG_ERR_UNSUPPORTED;
-  }
-  if (d->node_set != DG_NODES_GL) {
+  if (d->node_set != DG_NODES_GL && d->node_set != DG_NODES_GLL) {
     set_error("%s: unknown node_set %d", who, d->node_set);
     return DG_ERR_ARG;
   }
@@ -477,11 +541,7 @@ int check_desc(const dg_mesh_desc* d, const char* who, HangGroups* hg) {
   for (int64_t k = 0; k < d->n_bdry; ++k) {
     const int64_t* r = d->bdry_faces + 3 * k;
     if (r[0] < 0 || r[0] >= E || r[1] < 0 || r[1] >= nfaces) return bad("boundary face out of range", k);
-    if (r[2] == DG_BC_FARFIELD) {
-      set_error("%s: far-field boundary faces are not implemented (row %lld)", who, (long long)k);
-      return DG_ERR_UNSUPPORTED;
-    }
-    if (r[2] != DG_BC_WALL) return bad("unknown boundary condition", k);
+    if (r[2] != DG_BC_WALL && r[2] != DG_BC_FARFIELD) return bad("unknown boundary condition", k);
     cover[r[0] * nfaces + r[1]]++;
   }
   // group hanging rows by coarse face
@@ -620,6 +680,7 @@ int dg_mesh_create(dg_ctx* ctx, const dg_mesh_desc* d, dg_mesh** out) {
   m->nF = nF;
   m->nH = nH;
   m->nHC = nHC;
+  m->gll = d->node_set == DG_NODES_GLL;
   make_tables(n, &m->tab);
   auto fail = [&](int st) {
     dg_mesh_destroy(m);
@@ -666,6 +727,50 @@ int dg_mesh_create(dg_ctx* ctx, const dg_mesh_desc* d, dg_mesh** out) {
   UPLOAD(m->hp_cslot, hpc.data(), nH);
   UPLOAD(m->hp_code, hpcode.data(), nH);
   UPLOAD(m->hc_slot, hcs.data(), nHC);
+  {
+    // per-cell face codes of the fused face + cell kernels: the neighbour
+    // cell across a conforming (or periodic) face, -1 on a wall, -2 on
+    // either side of a 2:1 face
+    std::vector<int> cf((size_t)E * nfaces, -1);
+    for (int64_t k = 0; k < d->n_int; ++k) {
+      const int64_t* r = d->int_faces + 4 * k;
+      cf[r[0] * nfaces + r[1]] = (int)r[2];
+      cf[r[2] * nfaces + r[3]] = (int)r[0];
+    }
+    for (int64_t k = 0; k < d->n_hang; ++k) {
+      const int64_t* r = d->hang_faces + 5 * k;
+      cf[r[0] * nfaces + r[1]] = -2;
+      cf[r[2] * nfaces + r[3]] = -2;
+    }
+    // far-field faces: code -3, and the far-point list grouped by face type
+    // (the boundary rows' face points follow the interior ones in the
+    // unified list)
+    std::vector<int> fpf((size_t)nF, -1), farp;
+    const int64_t pb = d->n_int * nfp;
+    for (int f = 0; f < nfaces; ++f) {
+      m->far_fbeg[f] = (int64_t)farp.size();
+      for (int64_t k = 0; k < d->n_bdry; ++k) {
+        const int64_t* r = d->bdry_faces + 3 * k;
+        if (r[2] != DG_BC_FARFIELD || r[1] != f) continue;
+        cf[r[0] * nfaces + r[1]] = -3;
+        for (int t = 0; t < nfp; ++t) {
+          const int64_t p = pb + k * nfp + t;
+          fpf[p] = (int)farp.size();
+          farp.push_back((int)p);
+        }
+      }
+    }
+    m->far_fbeg[nfaces] = (int64_t)farp.size();
+    m->nFar = (int64_t)farp.size();
+    ALLOC(m->cface, E * nfaces);
+    UPLOAD(m->cface, cf.data(), E * nfaces);
+    if (m->nFar > 0) {
+      ALLOC(m->fp_far, nF);
+      ALLOC(m->far_p, m->nFar);
+      UPLOAD(m->fp_far, fpf.data(), nF);
+      UPLOAD(m->far_p, farp.data(), m->nFar);
+    }
+  }
   m->n_vchains = (int64_t)heads.size();
   ALLOC(m->vl_above, E);
   ALLOC(m->vl_below, E);
@@ -767,6 +872,18 @@ int dg_mesh_info(const dg_mesh* m, dg_mesh_stats* o) {
     o->tile_fp32[k] = m->tile32[kinds[k]];
   }
   o->terrain_following = m->terrain ? 1 : 0;
+  o->fused_stage[0] = m->fused_stage[0];
+  o->fused_stage[1] = m->fused_stage[1];
+  return DG_OK;
+}
+
+int dg_mesh_set_fused_stage(dg_mesh* m, int fp64, int fp32) {
+  if (!m || (fp64 != 0 && fp64 != 1) || (fp32 != 0 && fp32 != 1)) {
+    set_error("dg_mesh_set_fused_stage: mesh and 0 / 1 per precision required");
+    return DG_ERR_ARG;
+  }
+  m->fused_stage[0] = fp64;
+  m->fused_stage[1] = fp32;
   return DG_OK;
 }
 
@@ -791,6 +908,8 @@ int dg_mesh_node_coords(dg_ctx* ctx, const dg_mesh* m, double* xyz, void* stream
     return DG_ERR_ARG;
   }
   GeoArgs g = geo_args(m);
+  if (m->gll)   // the nodes of a Gauss-Lobatto mesh
+    for (int k = 0; k < MAX_N; ++k) g.x[k] = k < m->n ? m->tab.xl[k] : 0.0;
   k_node_coords<<<grid_for(m->N, 256), 256, 0, (cudaStream_t)stream>>>(g, xyz);
   DG_LAUNCH_CHECK("k_node_coords");
   return DG_OK;

@@ -66,11 +66,14 @@ static int explicit_with_scratch(dg_mesh* m, const PhysK& ph, const double* q, d
   if (m->nHC > 0)
     DG_RUN(m, K_HANG_GATHER, st,
            k_hang_gather<T, DIM, N, 9><<<grid_for(m->nHC * CS::NFP, 128), 128, 0, st>>>(ft, hbuf, slot, tb));
-  DG_RUN(m, K_VOL_EXPLICIT, st,
-         k_volume_explicit<T, DIM, N><<<grid_for(m->E, CS::EPB), CS::THREADS, 0, st>>>(
-             q, m->K, m->invM, slot, m->E, m->S, tb, ph, fns, fs, 0));
+  DG_TILE(m, K_VOL_EXPLICIT,
+          DG_RUN(m, K_VOL_EXPLICIT, st,
+                 k_volume_explicit<T, DIM, N, M_><<<grid_for(m->E, CellShape<DIM, N, M_>::EPB),
+                                                    CellShape<DIM, N, M_>::THREADS, 0, st>>>(
+                     q, m->K, m->invM, slot, m->E, m->S, tb, ph, fns, fs, m->terrain ? 1 : 0)));
   DG_LAUNCH_CHECK("explicit operator (no-alloc)");
-  return DG_OK;
+  // damping layers: one pointwise pass over stored coefficients, no scratch
+  return sponge_rt(m, q, fns, st);
 }
 
 }  // namespace dg
@@ -87,9 +90,32 @@ extern "C" int dg_apply_explicit_noalloc(dg_ctx* ctx, const dg_mesh* mesh, const
     set_error("dg_apply_explicit_noalloc: gamma must be > 1");
     return DG_ERR_ARG;
   }
-  if (ph->precision != DG_FP64) {
-    set_error("dg_apply_explicit_noalloc: only DG_FP64 is implemented");
+  if (!(ph->lambda_min >= 0.0)) {
+    set_error("dg_apply_explicit_noalloc: lambda_min must be >= 0");
+    return DG_ERR_ARG;
+  }
+  if (mesh->gll) {
+    set_error("dg_apply_explicit_noalloc: not implemented for Gauss-Lobatto nodes");
     return DG_ERR_UNSUPPORTED;
+  }
+  if (mesh->nFar > 0 && !mesh->far_set) {
+    set_error("dg_apply_explicit_noalloc: set the far-field outer state with dg_mesh_set_far_state first");
+    return DG_ERR_ARG;
+  }
+  if (ph->variant != DG_R1 && ph->variant != DG_R2) {
+    set_error("dg_apply_explicit_noalloc: variant must be DG_R1 or DG_R2");
+    return DG_ERR_ARG;
+  }
+  // DG_FP64 and DG_MIXED both evaluate the explicit operator in FP64 (as
+  // dg_apply_explicit does); the FP32 perturbation form needs per-mesh
+  // background buffers and is not offered here
+  if (ph->precision == DG_MIXED_EXPLICIT) {
+    set_error("dg_apply_explicit_noalloc: DG_MIXED_EXPLICIT is not implemented (use DG_FP64 or DG_MIXED)");
+    return DG_ERR_UNSUPPORTED;
+  }
+  if (ph->precision != DG_FP64 && ph->precision != DG_MIXED) {
+    set_error("dg_apply_explicit_noalloc: precision must be DG_FP64 or DG_MIXED");
+    return DG_ERR_ARG;
   }
   const int64_t need = 14 * mesh->S + 9 * mesh->nH;
   if (need > NOALLOC_SCRATCH_DOUBLES) {

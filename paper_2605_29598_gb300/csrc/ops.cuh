@@ -23,6 +23,20 @@ template <typename T> __device__ __forceinline__ const T* geo_ptr(const FaceTopo
 template <> __device__ __forceinline__ const double* geo_ptr<double>(const FaceTopo& ft) { return ft.fgeo; }
 template <> __device__ __forceinline__ const float* geo_ptr<float>(const FaceTopo& ft) { return ft.fgeo32; }
 
+template <> __device__ __forceinline__ const df64* geo_ptr<df64>(const FaceTopo& ft) { return ft.fgeodf; }
+
+// outer state's traces at the far-field points, in the kernel's precision
+// (DG_PAIRS does not run on meshes with far-field faces)
+template <typename T> __device__ __forceinline__ const T* far_ptr(const FaceTopo& ft);
+template <> __device__ __forceinline__ const double* far_ptr<double>(const FaceTopo& ft) { return ft.far_q; }
+template <> __device__ __forceinline__ const float* far_ptr<float>(const FaceTopo& ft) { return ft.far_q32; }
+template <> __device__ __forceinline__ const df64* far_ptr<df64>(const FaceTopo&) { return nullptr; }
+
+// far-point index of boundary face point p (-1: slip wall)
+__device__ __forceinline__ int far_index(const FaceTopo& ft, int64_t p) {
+  return ft.fp_far ? __ldg(ft.fp_far + p) : -1;
+}
+
 template <typename T> struct Fields {
   const T* f[5];
   T scale[5];
@@ -204,7 +218,7 @@ template <int DIM> __device__ __forceinline__ int comp_of(int b) { return DIM ==
 template <typename T, int DIM, int N>
 __global__ void k_face_explicit(FaceTopo ft, const T* __restrict__ trc, T* __restrict__ slot,
                                 T* __restrict__ hbuf, Tables<T> tb, T gamma, T lambda_min) {
-  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t p = ft.p0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= ft.nF) return;
   const int64_t S = ft.S;
   int sm = __ldg(ft.fp_minus + p), code = __ldg(ft.fp_plus + p);
@@ -218,7 +232,12 @@ __global__ void k_face_explicit(FaceTopo ft, const T* __restrict__ trc, T* __res
   T qm[5], qp[5];
 #pragma unroll
   for (int q = 0; q < 5; ++q) qm[q] = __ldg(trc + q * S + sm);
-  if (code == -1) {
+  const int g = code == -1 ? far_index(ft, p) : -1;
+  if (g >= 0) {
+    // far field: the given outer state, in the same fluxes as an interior face
+#pragma unroll
+    for (int q = 0; q < 5; ++q) qp[q] = __ldg(far_ptr<T>(ft) + q * ft.nFar + g);
+  } else if (code == -1) {
     // slip wall: mirror momentum, m+ = m- - 2 (m-.n) n
     T mn = 0;
 #pragma unroll
@@ -275,6 +294,46 @@ template <int DIM, int N, int M = 1> struct CellShape {
   static constexpr int NFP = ipow(N, DIM - 1);
   static constexpr int NF = 2 * DIM;
 };
+
+// ---------------------------------------------------------------------------
+// nodal change of basis per cell (Gauss-Lobatto <-> Gauss-Legendre nodes):
+// out = (B x B [x B]) in for nfld fields (field stride Nn); in == out is
+// allowed (a block reads a cell's values before it writes them)
+// ---------------------------------------------------------------------------
+template <typename T, int DIM, int N>
+__global__ void __launch_bounds__(CellShape<DIM, N>::THREADS)
+    k_basis(const T* in, T* out, int nfld, int64_t E, Mat1D<T> B) {
+  using CS = CellShape<DIM, N>;
+  constexpr int NP = CS::NP, EPB = CS::EPB;
+  __shared__ T sv[2][EPB][NP];
+  const int le = threadIdx.x / NP, i = threadIdx.x % NP;
+  const int64_t e = (int64_t)blockIdx.x * EPB + le;
+  const bool active = e < E;
+  const int64_t Nn = E * NP;
+  const int64_t node = active ? e * NP + i : 0;
+  int idx[3];
+  node_index<DIM, N>(i, idx);
+  for (int q = 0; q < nfld; ++q) {
+    T v = active ? in[q * Nn + node] : (T)0;
+    int cur = 0;
+    sv[cur][le][i] = v;
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < DIM; ++a) {
+      const int stride = a == 0 ? 1 : (a == 1 ? N : N * N);
+      const int i0 = i - idx[a] * stride;
+      T acc = 0;
+#pragma unroll
+      for (int k = 0; k < N; ++k) acc += B.m[idx[a]][k] * sv[cur][le][i0 + k * stride];
+      cur ^= 1;
+      sv[cur][le][i] = acc;
+      v = acc;
+      __syncthreads();
+    }
+    if (active) out[q * Nn + node] = v;
+    __syncthreads();
+  }
+}
 
 // metric terms that vanish on terrain-following cells (x = x(xi_1), y =
 // y(xi_2)): reference direction a, physical component b
@@ -430,7 +489,7 @@ k_volume_explicit(const T* __restrict__ q, const T* __restrict__ Kg, const T* __
 template <typename T, int DIM, int N>
 __global__ void k_face_grad(FaceTopo ft, const T* __restrict__ trc, const T* __restrict__ pcoef,
                             T* __restrict__ slot, T* __restrict__ hbuf, Tables<T> tb) {
-  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t p = ft.p0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= ft.nF) return;
   int sm = __ldg(ft.fp_minus + p), code = __ldg(ft.fp_plus + p);
   T xm = __ldg(trc + sm);
@@ -447,7 +506,7 @@ __global__ void k_face_grad(FaceTopo ft, const T* __restrict__ trc, const T* __r
 template <typename T, int DIM, int N>
 __global__ void k_face_div(FaceTopo ft, const T* __restrict__ trc, const T* __restrict__ trh,
                            T* __restrict__ slot, T* __restrict__ hbuf, Tables<T> tb) {
-  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t p = ft.p0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= ft.nF) return;
   int sm = __ldg(ft.fp_minus + p), code = __ldg(ft.fp_plus + p);
   T avg = 0;
@@ -471,15 +530,19 @@ __global__ void k_face_div(FaceTopo ft, const T* __restrict__ trc, const T* __re
 template <typename T, int DIM, int N>
 __global__ void k_face_lambda(FaceTopo ft, const T* __restrict__ tru, T a_dt_half, T* __restrict__ pcoef,
                               Tables<T> tb) {
-  int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  int64_t p = ft.p0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (p >= ft.nF) return;
   int sm = __ldg(ft.fp_minus + p), code = __ldg(ft.fp_plus + p);
+  const int g = code == -1 ? far_index(ft, p) : -1;
+  const T* fq = far_ptr<T>(ft);
   T unm = 0, unp = 0;
 #pragma unroll
   for (int b = 0; b < DIM; ++b) {
     T n = __ldg(geo_ptr<T>(ft) + b * ft.nF + p);
     T um = __ldg(tru + comp_of<DIM>(b) * ft.S + sm);
-    T up = plus_value<T, DIM, N>(ft, tb, tru + comp_of<DIM>(b) * ft.S, code, um);
+    // far field: the outer state's velocity
+    T up = g >= 0 ? __ldg(fq + (1 + comp_of<DIM>(b)) * ft.nFar + g) / __ldg(fq + g)
+                  : plus_value<T, DIM, N>(ft, tb, tru + comp_of<DIM>(b) * ft.S, code, um);
     unm += um * n;
     unp += up * n;
   }
@@ -500,6 +563,7 @@ struct ImplK {
   // host-folded constants: 1/(1 + beta^2) for a uniform f, (gamma-1) a_dt^2 g
   double dbeta, cgrav;
   float dbeta_f, cgrav_f;
+  int penalty;           // implicit Rusanov term on (far-field outer data included)
 };
 
 // 1/rho of the frozen stage density (read by the gradient cell kernel)
@@ -513,6 +577,7 @@ __global__ void k_recip(const T* __restrict__ a, T* __restrict__ b, int64_t n) {
 template <typename T> __device__ __forceinline__ T kp(double d, float f);
 template <> __device__ __forceinline__ double kp<double>(double d, float) { return d; }
 template <> __device__ __forceinline__ float kp<float>(double, float f) { return f; }
+template <> __device__ __forceinline__ df64 kp<df64>(double d, float) { return df64(d); }
 
 // beta = a_dt f of cell e (Section 3.1)
 template <typename T> __device__ __forceinline__ T beta_of(const ImplK& ph, int64_t e);
@@ -521,6 +586,9 @@ template <> __device__ __forceinline__ double beta_of<double>(const ImplK& ph, i
 }
 template <> __device__ __forceinline__ float beta_of<float>(const ImplK& ph, int64_t e) {
   return ph.adt_f * (ph.fcell32 ? __ldg(ph.fcell32 + e) : ph.f_f);
+}
+template <> __device__ __forceinline__ df64 beta_of<df64>(const ImplK& ph, int64_t e) {
+  return df64(ph.a_dt * coriolis(ph.fcell, ph.f, e));
 }
 
 // Per-node metric K_ab = w det(J) (J^{-1})_ab and 1/(w det J) of the
@@ -533,6 +601,7 @@ struct CellGeo {
   const T* K;
   const T* invM;
   const T* lv;          // n_elem x 2^d x d corner offsets, or null
+  const T* tc;          // terrain-following: 16 coefficients per cell, or null
   T x[MAX_N], w[MAX_N]; // Gauss-Legendre nodes and weights on [0, 1]
   int terrain;          // every cell terrain-following: K_ab = 0 where kzero(a, b)
 };
@@ -551,32 +620,16 @@ __device__ __forceinline__ void stage_nodes(const CellGeo<T>& g, T* sxw) {
   }
 }
 
-template <typename T, int DIM, int N>
-__device__ __forceinline__ void node_metric(const CellGeo<T>& g, int64_t e, int64_t node, int64_t Nn,
-                                            const int idx[3], T K[DIM][DIM], T& iM, const T* sxw = nullptr) {
-  // FP64 always loads the stored metric (the FP64 geometry has no corner
-  // offsets); only FP32 recomputes it
-  if (!std::is_same<T, float>::value || g.lv == nullptr) {
-#pragma unroll
-    for (int a = 0; a < DIM; ++a)
-#pragma unroll
-      for (int b = 0; b < DIM; ++b)
-        K[a][b] = (g.terrain && kzero<DIM>(a, b)) ? (T)0 : __ldg(g.K + (a * DIM + b) * Nn + node);
-    iM = __ldg(g.invM + node);
-    return;
-  }
-  const T* V = g.lv + e * (DIM << DIM);
-  T xi[3], wq = 1;
-#pragma unroll
-  for (int a = 0; a < DIM; ++a) {
-    // nodes and weights from the block's shared copy (sxw[0..N), sxw[N..2N)):
-    // indexing the parameter arrays per thread would copy them to local memory
-    xi[a] = sxw[idx[a]];
-    wq *= sxw[N + idx[a]];
-  }
-  if (g.terrain) {
-    // x = x0 + dx xi_1 (and y = y0 + dy xi_2): only the vertical row of J
-    // varies; dx, dy are the offsets of corners 1 and 2
+// Cofactors C_ab = det(J) (J^{-1})_ab of the cell map at reference point xi
+// and det J, from the cell's corner offsets V relative to its first corner
+// (the FP32 recomputation path).  On terrain-following cells only the
+// vertical row of J varies (x = x0 + dx xi_1, y = y0 + dy xi_2; dx, dy are
+// the offsets of corners 1 and 2), and the entries that vanish exactly are
+// set to zero.
+template <typename T, int DIM>
+__device__ __forceinline__ void corner_cofactors(const T* __restrict__ V, int terrain, const T xi[3],
+                                                 T K[DIM][DIM], T& det) {
+  if (terrain) {
     T Jz[DIM];
 #pragma unroll
     for (int c = 0; c < DIM; ++c) Jz[c] = 0;
@@ -595,7 +648,6 @@ __device__ __forceinline__ void node_metric(const CellGeo<T>& g, int64_t e, int6
       }
     }
     const T dx = __ldg(V + 1 * DIM + 0);
-    T det;
     if (DIM == 2) {
       K[0][0] = Jz[1];
       K[0][1] = 0;
@@ -612,11 +664,6 @@ __device__ __forceinline__ void node_metric(const CellGeo<T>& g, int64_t e, int6
       K[0][1] = K[0][2] = K[1][0] = K[1][2] = 0;
       det = dx * K[0][0];
     }
-#pragma unroll
-    for (int a = 0; a < DIM; ++a)
-#pragma unroll
-      for (int b = 0; b < DIM; ++b) K[a][b] *= wq;
-    iM = 1 / (wq * det);
     return;
   }
   T J[DIM][DIM];   // J[b][c] = d x_b / d xi_c
@@ -639,7 +686,6 @@ __device__ __forceinline__ void node_metric(const CellGeo<T>& g, int64_t e, int6
       for (int b = 0; b < DIM; ++b) J[b][c] += wgt * __ldg(V + v * DIM + b);
     }
   }
-  T det;
   if (DIM == 2) {
     K[0][0] = J[1][1];
     K[0][1] = -J[0][1];
@@ -656,6 +702,65 @@ __device__ __forceinline__ void node_metric(const CellGeo<T>& g, int64_t e, int6
     }
     det = J[0][0] * K[0][0] + J[1][0] * K[0][1] + J[2][0] * K[0][2];
   }
+}
+
+// Cofactors and det J of a terrain-following cell at xi from its 16
+// coefficients t (dx, dy, then bilinear coefficients of the vertical row of
+// J): the same formulas as the terrain branch of corner_cofactors with the
+// corner sums folded per cell.
+template <typename T, int DIM>
+__device__ __forceinline__ void terrain_row(const T* t, const T xi[3], T K[DIM][DIM], T& det) {
+  const T Jz0 = (t[2] + t[3] * xi[1]) + xi[2] * (t[4] + t[5] * xi[1]);
+  const T Jz1 = (t[6] + t[7] * xi[0]) + xi[2] * (t[8] + t[9] * xi[0]);
+  const T dx = t[0];
+  if (DIM == 2) {
+    K[0][0] = Jz1;
+    K[0][1] = 0;
+    K[1][0] = -Jz0;
+    K[1][1] = dx;
+    det = dx * Jz1;
+  } else {
+    const T Jz2 = (t[10] + t[11] * xi[0]) + xi[1] * (t[12] + t[13] * xi[0]);
+    const T dy = t[1];
+    K[0][0] = dy * Jz2;
+    K[1][1] = Jz2 * dx;
+    K[2][0] = -(Jz0 * dy);
+    K[2][1] = -(dx * Jz1);
+    K[2][2] = dx * dy;
+    K[0][1] = K[0][2] = K[1][0] = K[1][2] = 0;
+    det = dx * K[0][0];
+  }
+}
+
+// tcs: the cell's terrain coefficients (shared memory), FP32 only
+template <typename T, int DIM, int N>
+__device__ __forceinline__ void node_metric(const CellGeo<T>& g, int64_t e, int64_t node, int64_t Nn,
+                                            const int idx[3], T K[DIM][DIM], T& iM, const T* sxw = nullptr,
+                                            const T* tcs = nullptr) {
+  // FP64 always loads the stored metric (the FP64 geometry has no corner
+  // offsets); only FP32 recomputes it
+  if (!std::is_same<T, float>::value || g.lv == nullptr) {
+#pragma unroll
+    for (int a = 0; a < DIM; ++a)
+#pragma unroll
+      for (int b = 0; b < DIM; ++b)
+        K[a][b] = (g.terrain && kzero<DIM>(a, b)) ? (T)0 : __ldg(g.K + (a * DIM + b) * Nn + node);
+    iM = __ldg(g.invM + node);
+    return;
+  }
+  T xi[3] = {0, 0, 0}, wq = 1;
+#pragma unroll
+  for (int a = 0; a < DIM; ++a) {
+    // nodes and weights from the block's shared copy (sxw[0..N), sxw[N..2N)):
+    // indexing the parameter arrays per thread would copy them to local memory
+    xi[a] = sxw[idx[a]];
+    wq *= sxw[N + idx[a]];
+  }
+  T det;
+  if (tcs)
+    terrain_row<T, DIM>(tcs, xi, K, det);
+  else
+    corner_cofactors<T, DIM>(g.lv + e * (DIM << DIM), g.terrain, xi, K, det);
 #pragma unroll
   for (int a = 0; a < DIM; ++a)
 #pragma unroll
@@ -663,144 +768,7 @@ __device__ __forceinline__ void node_metric(const CellGeo<T>& g, int64_t e, int6
   iM = 1 / (wq * det);
 }
 
-// weak gradient G = M^{-1}[-int x grad(phi) + faces]; then
-//  VMULT  : w = rho^{-1} (I + beta J)^{-1} G (R2) or G / rho (R1) -> wv (DIM
-//           spatial comps); y = x + pen - (gamma-1) a_dt^2 g G_z (R2)
-//  RECOVER: u = ustar - a_dt * w  (3 comps)
-template <typename T, int DIM, int N, int MODE, int M = 1>
-__global__ void __launch_bounds__(CellShape<DIM, N, M>::THREADS)
-k_volume_grad(const T* __restrict__ x, const T* __restrict__ irho, CellGeo<T> geo,
-              const T* __restrict__ slot, int64_t E, int64_t S,
-              Tables<T> tb, ImplK ph, T* __restrict__ wv, T* __restrict__ y,
-              const T* __restrict__ ustar, T* __restrict__ uout) {
-  using CS = CellShape<DIM, N, M>;
-  constexpr int NP = CS::NP, EPB = CS::EPB;
-  __shared__ T sm[EPB][DIM][NP];
-  const int le = threadIdx.x / NP, i = threadIdx.x % NP;
-  const int64_t e = (int64_t)blockIdx.x * EPB + le;
-  const bool active = e < E;
-  const int64_t Nn = E * NP;
-  const int64_t node = active ? e * NP + i : 0;
-  int idx[3];
-  node_index<DIM, N>(i, idx);
-  T xv = active ? __ldg(x + node) : (T)0;
-  __shared__ T sxw[2 * N];
-  stage_nodes<T, N>(geo, sxw);
-  if (std::is_same<T, float>::value) __syncthreads();
-  T K[DIM][DIM], iM = 0;
-  if (active) node_metric<T, DIM, N>(geo, e, node, Nn, idx, K, iM, sxw);
-  T r[DIM + 1];
-#pragma unroll
-  for (int b = 0; b < DIM; ++b) {
-    const int msk = amask_of<DIM>(geo.terrain, b);
-#pragma unroll
-    for (int a = 0; a < DIM; ++a)
-      if ((msk >> a) & 1) sm[le][a][i] = active ? -xv * K[a][b] : (T)0;
-    __syncthreads();
-    r[b] = contract<T, DIM, N>(tb, sm[le], i, idx, msk);
-    __syncthreads();
-  }
-  r[DIM] = 0;
-  if (!active) return;
-  lift<T, DIM, N, DIM + 1>(tb, slot, S, e, idx, r);
-  T G[3] = {0, 0, 0};
-#pragma unroll
-  for (int b = 0; b < DIM; ++b) G[comp_of<DIM>(b)] = iM * r[b];
-  const T ir = __ldg(irho + node);
-  T w[3];
-  if (ph.r2) {
-    const T beta = beta_of<T>(ph, e);
-    const T d = (ph.fcell || ph.fcell32) ? (T)1 / (1 + beta * beta) : kp<T>(ph.dbeta, ph.dbeta_f);
-    w[0] = (G[0] + beta * G[1]) * d * ir;
-    w[1] = (G[1] - beta * G[0]) * d * ir;
-    w[2] = G[2] * ir;
-  } else {
-    w[0] = G[0] * ir;
-    w[1] = G[1] * ir;
-    w[2] = G[2] * ir;
-  }
-  if (MODE == GRAD_VMULT) {
-#pragma unroll
-    for (int b = 0; b < DIM; ++b) wv[b * Nn + node] = w[comp_of<DIM>(b)];
-    T yv = xv + iM * r[DIM];
-    if (ph.r2) yv -= kp<T>(ph.cgrav, ph.cgrav_f) * G[2];
-    y[node] = yv;
-  } else {
-    const T adt = kp<T>(ph.a_dt, ph.adt_f);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) uout[c * Nn + node] = __ldg(ustar + c * Nn + node) - adt * w[c];
-  }
-}
-
 enum DivMode { DIV_VMULT = 0, DIV_RHS = 1 };
-
-// weak divergence Div = M^{-1}[-int h rho w . grad(psi) + faces], h rho =
-// gamma p_lag / (gamma - 1);
-//  VMULT: y -= (gamma-1) a_dt^2 Div
-//  RHS  : y = (gamma-1) [e_hat - rho |u_lag|^2 / 2 - a_dt (Div + g rho w3_z)],
-//         w3_z = ustar_z (R2) or u_lag_z (R1)
-template <typename T, int DIM, int N, int MODE, int M = 1>
-__global__ void __launch_bounds__(CellShape<DIM, N, M>::THREADS)
-k_volume_div(Fields<T> wv, const T* __restrict__ plag, CellGeo<T> geo,
-             const T* __restrict__ slot, int64_t E, int64_t S,
-             Tables<T> tb, ImplK ph, T* __restrict__ y, const T* __restrict__ ehat,
-             const T* __restrict__ rho, const T* __restrict__ ulag, const T* __restrict__ ustar) {
-  using CS = CellShape<DIM, N, M>;
-  constexpr int NP = CS::NP, EPB = CS::EPB;
-  __shared__ T sm[EPB][DIM][NP];
-  const int le = threadIdx.x / NP, i = threadIdx.x % NP;
-  const int64_t e = (int64_t)blockIdx.x * EPB + le;
-  const bool active = e < E;
-  const int64_t Nn = E * NP;
-  const int64_t node = active ? e * NP + i : 0;
-  int idx[3];
-  node_index<DIM, N>(i, idx);
-  const T gam = kp<T>(ph.gamma, ph.gamma_f);
-  const T gm1 = gam - 1;
-  __shared__ T sxw[2 * N];
-  stage_nodes<T, N>(geo, sxw);
-  if (std::is_same<T, float>::value) __syncthreads();
-  T iM = 0;
-  if (active) {
-    T K[DIM][DIM];
-    node_metric<T, DIM, N>(geo, e, node, Nn, idx, K, iM, sxw);
-    T hr = gam / gm1 * __ldg(plag + node);
-    T wl[DIM];
-#pragma unroll
-    for (int b = 0; b < DIM; ++b) wl[b] = __ldg(wv.f[b] + node);
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) {
-      T v = 0;
-#pragma unroll
-      for (int b = 0; b < DIM; ++b)
-        if (!(geo.terrain && kzero<DIM>(a, b))) v += K[a][b] * wl[b];
-      sm[le][a][i] = -hr * v;
-    }
-  } else {
-#pragma unroll
-    for (int a = 0; a < DIM; ++a) sm[le][a][i] = 0;
-  }
-  __syncthreads();
-  T r[1];
-  r[0] = contract<T, DIM, N>(tb, sm[le], i, idx);
-  if (!active) return;
-  lift<T, DIM, N, 1>(tb, slot, S, e, idx, r);
-  const T div = iM * r[0];
-  const T adt = kp<T>(ph.a_dt, ph.adt_f);
-  if (MODE == DIV_VMULT) {
-    y[node] -= gm1 * adt * adt * div;
-  } else {
-    const T rh = __ldg(rho + node);
-    T u2 = 0;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      T uc = __ldg(ulag + c * Nn + node);
-      u2 += uc * uc;
-    }
-    const T wz = ph.r2 ? __ldg(ustar + 2 * Nn + node) : __ldg(ulag + 2 * Nn + node);
-    y[node] = gm1 * (__ldg(ehat + node) - (T)0.5 * rh * u2 - adt * (div + kp<T>(ph.g, ph.g_f) * rh * wz));
-  }
-}
 
 // u* = rho^{-1} (I + beta J)^{-1} (m_hat - a_dt g rho k)           (R2)
 // u* = rho^{-1} (m_hat - a_dt f rho k x u_lag - a_dt g rho k)       (R1)

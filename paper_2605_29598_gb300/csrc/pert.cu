@@ -438,6 +438,10 @@ extern "C" int dg_mesh_set_background(dg_ctx* ctx, dg_mesh* mesh, const dg_phys*
     set_error("dg_mesh_set_background: gamma must be > 1");
     return DG_ERR_ARG;
   }
+  if (mesh->gll || mesh->nFar > 0) {
+    set_error("dg_mesh_set_background: not implemented for Gauss-Lobatto nodes or far-field faces");
+    return DG_ERR_UNSUPPORTED;
+  }
   PhysK k{ph->gamma, ph->g, ph->f, ph->f_cell, ph->lambda_min};
   return set_background(mesh, k, q_bg, (cudaStream_t)stream);
 }

@@ -422,6 +422,57 @@ Vmult make_vmult32(Schur32Ctx* s) {
   return v;
 }
 
+template <int D, int NN>
+static int schur_pairs_vmult_fn(void* self, const double* x, double* y, cudaStream_t st) {
+  SchurDfCtx* s = static_cast<SchurDfCtx*>(self);
+  dg_mesh* m = s->m;
+  int rc;
+  if ((rc = to_pairs(m, x, s->xdf, m->N, st)) != DG_OK) return rc;
+  if ((rc = Engine<df64, D, NN>::vmult(m, s->k, s->rho, s->plag, s->penalty, s->xdf, s->ydf, st)) != DG_OK)
+    return rc;
+  return from_pairs(m, s->ydf, y, m->N, st);
+}
+
+// Pair copies of the frozen coefficients and their face data for the
+// DG_PAIRS vmult (the FP64 ones stay for the right-hand side and recovery).
+int prepare_pairs(dg_mesh* m, const ImplK& k, const double* rho, const double* plag, const double* ulag,
+                  int penalty, cudaStream_t st, SchurDfCtx* out) {
+  if (m->gll || m->nFar > 0) {
+    set_error("DG_PAIRS is not implemented with Gauss-Lobatto nodes or far-field faces");
+    return DG_ERR_UNSUPPORTED;
+  }
+  int rc;
+  if ((rc = ensure_pairs_geometry(m, st)) != DG_OK) return rc;
+  const int64_t n = m->N;
+  if ((rc = m->cdf.ensure(sizeof(df64) * 5 * n)) != DG_OK) return rc;
+  if ((rc = m->irdf.ensure(sizeof(df64) * 2 * n)) != DG_OK) return rc;
+  df64* c = m->cdf.as<df64>();
+  if ((rc = to_pairs(m, rho, c, n, st)) != DG_OK) return rc;
+  if ((rc = to_pairs(m, plag, c + n, n, st)) != DG_OK) return rc;
+  if ((rc = to_pairs(m, ulag, c + 2 * n, 3 * n, st)) != DG_OK) return rc;
+  rc = DG_ERR_UNSUPPORTED;
+  DG_DISPATCH(m, rc = (Engine<df64, D_, N_>::prepare(m, k, c, c + n, c + 2 * n, penalty, st)));
+  if (rc != DG_OK) return rc;
+  *out = SchurDfCtx{m, k, c, c + n, penalty, m->irdf.as<df64>(), m->irdf.as<df64>() + n};
+  return DG_OK;
+}
+
+Vmult make_vmult_pairs(SchurDfCtx* s) {
+  Vmult v{nullptr, s};
+  DG_DISPATCH(s->m, v.fn = &schur_pairs_vmult_fn<D_, N_>);
+  return v;
+}
+
+int schur_vmult_pairs(dg_mesh* m, const ImplK& k, const double* rho, const double* plag, const double* ulag,
+                      int penalty, const double* x, double* y, cudaStream_t st) {
+  SchurDfCtx sc;
+  int rc = prepare_pairs(m, k, rho, plag, ulag, penalty, st, &sc);
+  if (rc != DG_OK) return rc;
+  Vmult A = make_vmult_pairs(&sc);
+  if (!A.fn) return DG_ERR_UNSUPPORTED;
+  return A(x, y, st);
+}
+
 int schur_vmult_mixed(dg_mesh* m, const ImplK& k, const double* rho, const double* plag, const double* ulag,
                       int penalty, const double* x, double* y, cudaStream_t st) {
   Schur32Ctx sc;
@@ -528,8 +579,9 @@ static int check_phys(const dg_phys* ph, const char* who) {
     set_error("%s: invalid physics (gamma > 1, variant R1/R2, lambda_min >= 0)", who);
     return DG_ERR_ARG;
   }
-  if (ph->precision != DG_FP64 && ph->precision != DG_MIXED && ph->precision != DG_MIXED_EXPLICIT) {
-    set_error("%s: precision must be DG_FP64, DG_MIXED or DG_MIXED_EXPLICIT", who);
+  if (ph->precision != DG_FP64 && ph->precision != DG_MIXED && ph->precision != DG_MIXED_EXPLICIT &&
+      ph->precision != DG_PAIRS) {
+    set_error("%s: precision must be DG_FP64, DG_MIXED, DG_MIXED_EXPLICIT or DG_PAIRS", who);
     return DG_ERR_ARG;
   }
   return DG_OK;
@@ -556,12 +608,22 @@ int dg_gmres_solve(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* ph, const dg
     return DG_ERR_ARG;
   }
   const bool pc = opts->precond != DG_PRECOND_NONE;
+  if (pc && m->gll) {
+    set_error("dg_gmres_solve: the preconditioners are not implemented for Gauss-Lobatto nodes");
+    return DG_ERR_UNSUPPORTED;
+  }
   ImplK k = impl_consts(ph, cf->a_dt);
   if ((rc = prepare_rt(m, k, cf->rho, cf->p_lag, cf->u_lag, ph->penalty, st)) != DG_OK) return rc;
   if (pc && (rc = precond_setup(m, opts->precond, k, cf->p_lag, ph->penalty, st)) != DG_OK) return rc;
   SchurCtx sc{m, k, cf->rho, cf->p_lag, ph->penalty};
   Vmult A = make_vmult(&sc);
   if (!A.fn) return DG_ERR_UNSUPPORTED;
+  if (ph->precision == DG_PAIRS) {
+    SchurDfCtx sdf;
+    if ((rc = prepare_pairs(m, k, cf->rho, cf->p_lag, cf->u_lag, ph->penalty, st, &sdf)) != DG_OK) return rc;
+    if (info) info->refinements = 0;
+    return gmres(m, make_vmult_pairs(&sdf), b, x, opts->rtol, opts->restart, opts->maxit, info, st, false, pc);
+  }
   if (ph->precision != DG_FP64) {
     Schur32Ctx sc32;
     if ((rc = prepare32(m, k, cf->rho, cf->p_lag, cf->u_lag, ph->penalty, st, &sc32)) != DG_OK) return rc;
@@ -595,6 +657,20 @@ int imex_ark2_step(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* ph, double* 
   }
   dg_mesh* m = const_cast<dg_mesh*>(mesh);
   cudaStream_t st = (cudaStream_t)stream;
+  if (m->nFar > 0 && ph->precision == DG_MIXED_EXPLICIT) {
+    set_error("imex_ark2_step: DG_MIXED_EXPLICIT is not implemented with far-field faces");
+    return DG_ERR_UNSUPPORTED;
+  }
+  if (opts->graph && ph->precision == DG_PAIRS) {
+    set_error("imex_ark2_step: DG_PAIRS runs host-driven steps only (graph = 0)");
+    return DG_ERR_UNSUPPORTED;
+  }
+  if (m->gll && (opts->graph || opts->gmres.precond != DG_PRECOND_NONE || ph->precision == DG_MIXED_EXPLICIT ||
+                 m->sponge_set)) {
+    set_error("imex_ark2_step: Gauss-Lobatto nodes support the host-driven, unpreconditioned step in DG_FP64 "
+              "or DG_MIXED only");
+    return DG_ERR_UNSUPPORTED;
+  }
   if (opts->graph) return step_graph(m, ph, q, dt, opts, info, st);
   return step_host(m, ph, q, dt, opts, info, st);
 }
@@ -602,6 +678,22 @@ int imex_ark2_step(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* ph, double* 
 }  // extern "C"
 
 namespace dg {
+
+// Stage state on a Gauss-Lobatto mesh: rho u = M^{-1} A u and rho E =
+// M^{-1}(D p + k(u)) are pointwise at the Gauss-Legendre points, so (rho, u,
+// p) go to the GL basis, k_stage_state runs there, and y comes back.
+static int stage_state_gll(dg_mesh* m, const double* rho, const double* u, const double* p, double gamma,
+                           double* y, cudaStream_t st) {
+  const int64_t n = m->N;
+  double* g = gl_scratch(m);
+  if (!g) return DG_ERR_OOM;
+  int rc;
+  if ((rc = gl_basis(m, rho, g, 1, true, st)) != DG_OK) return rc;
+  if ((rc = gl_basis(m, u, g + n, 3, true, st)) != DG_OK) return rc;
+  if ((rc = gl_basis(m, p, g + 4 * n, 1, true, st)) != DG_OK) return rc;
+  DG_RUN(m, K_STAGE, st, k_stage_state<<<grid_for(n, 256), 256, 0, st>>>(g, g + n, g + 4 * n, n, gamma, y));
+  return gl_basis(m, y, y, 5, false, st);
+}
 
 int step_host(dg_mesh* m, const dg_phys* ph, double* q, double dt, const dg_step_opts* opts,
               dg_step_info* info, cudaStream_t st) {
@@ -670,7 +762,12 @@ int step_host(dg_mesh* m, const dg_phys* ph, double* q, double dt, const dg_step
       SchurCtx schur{m, k, rho, p, ph->penalty};
       Vmult A = make_vmult(&schur);
       dg_gmres_info gi{};
-      if (ph->precision != DG_FP64) {
+      if (ph->precision == DG_PAIRS) {
+        SchurDfCtx sdf;
+        if ((rc = prepare_pairs(m, k, rho, p, u, ph->penalty, st, &sdf)) != DG_OK) return rc;
+        rc = gmres(m, make_vmult_pairs(&sdf), rhs, pnew, opts->gmres.rtol, opts->gmres.restart, opts->gmres.maxit,
+                   &gi, st, false, pc);
+      } else if (ph->precision != DG_FP64) {
         Schur32Ctx sc32;
         if ((rc = prepare32(m, k, rho, p, u, ph->penalty, st, &sc32)) != DG_OK) return rc;
         Vmult A32 = make_vmult32(&sc32);
@@ -704,7 +801,11 @@ int step_host(dg_mesh* m, const dg_phys* ph, double* q, double dt, const dg_step
       }
     }
     inf.picard_iters[l] = kk;
-    DG_RUN(m, K_STAGE, st, k_stage_state<<<gb, 256, 0, st>>>(rho, u, p, n, ph->gamma, y));
+    if (m->gll) {
+      if ((rc = stage_state_gll(m, rho, u, p, ph->gamma, y, st)) != DG_OK) return rc;
+    } else {
+      DG_RUN(m, K_STAGE, st, k_stage_state<<<gb, 256, 0, st>>>(rho, u, p, n, ph->gamma, y));
+    }
     DG_LAUNCH_CHECK("stage state");
     if (incr) {
       rc = explicit_increment(m, pk, y, q, Fns[0], Fs[0], Fns[l], Fs[l], st);
@@ -737,58 +838,84 @@ __global__ void k_fill(double* __restrict__ a, int64_t n, double v) {
   if (i < n) a[i] = v;
 }
 
-// Time the cell-kernel classes of one precision for each tile multiplier
-// and keep the fastest per class.
+// Time the schedules of one precision and keep the fastest: the tile
+// multiplier (cells per block) of the explicit operator's cell kernel
+// (FP64), and the source of the plus-side traces in the fused Schur vmult
+// (staged neighbour cells or a trace array), timed over whole vmults.
 static int tune_precision(dg_mesh* m, bool fp32, const double* q, const double* rho, const double* p,
                           const double* u, double* x, double* y, double* fns, double* fs, cudaStream_t st) {
-  const int cand[3] = {1, 2, 4};
-  const int kinds[3] = {K_VOL_EXPLICIT, K_VOL_GRAD, K_VOL_DIV};
-  double best[3] = {1e300, 1e300, 1e300};
-  int pick[3] = {1, 1, 1};
   dg_phys ph{1.4, 9.81, 1e-4, DG_R2, 1, fp32 ? DG_MIXED : DG_FP64, nullptr, 0.0};
   ImplK k = impl_consts(&ph, 1.0);
-  int* tiles = fp32 ? m->tile32 : m->tile;
   int rc;
-  for (int c : cand) {
-    for (int kk : kinds) tiles[kk] = c;
+  if (!fp32) {
+    const int cand[3] = {1, 2, 4};
+    double best = 1e300;
+    int pick = 1;
+    for (int c : cand) {
+      m->tile[K_VOL_EXPLICIT] = c;
+      for (int w = 0; w < 2; ++w)
+        if ((rc = explicit_rt(m, &ph, q, fns, fs, st)) != DG_OK) return rc;
+      m->prof.reset();
+      m->prof.time_mask = 1u << K_VOL_EXPLICIT;
+      m->prof.on = true;
+      for (int rep = 0; rep < 4; ++rep)
+        if ((rc = explicit_rt(m, &ph, q, fns, fs, st)) != DG_OK) return rc;
+      dg_kernel_stat stats[K_COUNT];
+      int nst = 0;
+      if ((rc = dg_profile_end(m, stats, K_COUNT, &nst)) != DG_OK) return rc;
+      const dg_kernel_stat& s = stats[K_VOL_EXPLICIT];
+      if (s.timed_launches == 0) continue;
+      const double t = s.total_ms / (double)s.timed_launches;
+      if (t < best) {
+        best = t;
+        pick = c;
+      }
+    }
+    m->tile[K_VOL_EXPLICIT] = pick;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  DG_CUDA(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_fail(cudaGetLastError(), "cudaEventCreate");
+  }
+  double best = 1e300;
+  int pick = m->fused_stage[fp32 ? 1 : 0];
+  rc = DG_OK;
+  for (int sv = 0; sv < 2 && rc == DG_OK; ++sv) {
+    m->fused_stage[fp32 ? 1 : 0] = sv;
     SchurCtx sc{m, k, rho, p, 1};
     Schur32Ctx sc32;
     Vmult A{nullptr, nullptr};
     if (fp32) {
-      if ((rc = prepare32(m, k, rho, p, u, 1, st, &sc32)) != DG_OK) return rc;
+      if ((rc = prepare32(m, k, rho, p, u, 1, st, &sc32)) != DG_OK) break;
       A = make_vmult32(&sc32);
     } else {
-      if ((rc = prepare_rt(m, k, rho, p, u, 1, st)) != DG_OK) return rc;
+      if ((rc = prepare_rt(m, k, rho, p, u, 1, st)) != DG_OK) break;
       A = make_vmult(&sc);
     }
-    for (int w = 0; w < 2; ++w) {   // warm-up
-      if ((rc = A(x, y, st)) != DG_OK) return rc;
-      if (!fp32 && (rc = explicit_rt(m, &ph, q, fns, fs, st)) != DG_OK) return rc;
+    for (int w = 0; w < 2 && rc == DG_OK; ++w) rc = A(x, y, st);
+    if (rc != DG_OK) break;
+    cudaEventRecord(e0, st);
+    for (int rep = 0; rep < 5 && rc == DG_OK; ++rep) rc = A(x, y, st);
+    cudaEventRecord(e1, st);
+    if (rc != DG_OK) break;
+    float ms = 0.f;
+    cudaError_t e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+    if (e != cudaSuccess) {
+      rc = cuda_fail(e, "autotune timing");
+      break;
     }
-    uint32_t mask = 0;
-    for (int kk : kinds) mask |= 1u << kk;
-    m->prof.reset();
-    m->prof.time_mask = mask;
-    m->prof.on = true;
-    for (int rep = 0; rep < 4; ++rep) {
-      if ((rc = A(x, y, st)) != DG_OK) return rc;
-      if (!fp32 && (rc = explicit_rt(m, &ph, q, fns, fs, st)) != DG_OK) return rc;
-    }
-    dg_kernel_stat stats[K_COUNT];
-    int nst = 0;
-    if ((rc = dg_profile_end(m, stats, K_COUNT, &nst)) != DG_OK) return rc;
-    for (int j = 0; j < 3; ++j) {
-      const dg_kernel_stat& s = stats[kinds[j]];
-      if (s.timed_launches == 0) continue;
-      const double t = s.total_ms / (double)s.timed_launches;
-      if (t < best[j]) {
-        best[j] = t;
-        pick[j] = c;
-      }
+    if (ms < best) {
+      best = ms;
+      pick = sv;
     }
   }
-  for (int j = 0; j < 3; ++j) tiles[kinds[j]] = pick[j];
-  return DG_OK;
+  m->fused_stage[fp32 ? 1 : 0] = pick;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return rc;
 }
 
 }  // namespace dg

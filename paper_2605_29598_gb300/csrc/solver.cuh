@@ -55,6 +55,17 @@ struct Schur32Ctx {
   float* y32;
 };
 
+// DG_PAIRS: the vmult in FP32 pairs behind an FP64 interface
+struct SchurDfCtx {
+  dg_mesh* m;
+  ImplK k;
+  const df64* rho;
+  const df64* plag;
+  int penalty;
+  df64* xdf;
+  df64* ydf;
+};
+
 // ARK2 (TR-BDF2) tableaux of Section 3: explicit a, implicit at, weights b
 struct Ark2 {
   double a[3][3], at[3][3], b[3];
@@ -182,6 +193,9 @@ __global__ void k_picard_norms(const double* __restrict__ p0, const double* __re
 int ensure_red(dg_mesh* m, Red* r);
 Vmult make_vmult(SchurCtx* s);
 Vmult make_vmult32(Schur32Ctx* s);
+Vmult make_vmult_pairs(SchurDfCtx* s);
+int prepare_pairs(dg_mesh* m, const ImplK& k, const double* rho, const double* plag, const double* ulag,
+                  int penalty, cudaStream_t st, SchurDfCtx* out);
 int prepare32(dg_mesh* m, const ImplK& k, const double* rho, const double* plag, const double* ulag, int penalty,
               cudaStream_t st, Schur32Ctx* out);
 int prepare_rt(dg_mesh* m, const ImplK& k, const double* rho, const double* plag, const double* ulag, int penalty,

@@ -74,6 +74,10 @@ extern "C" int dg_mesh_set_sponge(dg_ctx* ctx, dg_mesh* m, const dg_sponge* s, c
     m->sponge_set = false;
     return DG_OK;
   }
+  if (m->gll) {
+    set_error("dg_mesh_set_sponge: not implemented for Gauss-Lobatto nodes");
+    return DG_ERR_UNSUPPORTED;
+  }
   if (!q_bar || !(s->lambda_bar >= 0.0) || !(s->z_t > s->z_b) || (s->x_layers && !(s->x_width > 0.0)) ||
       (s->y_layers && !(s->y_width > 0.0))) {
     set_error("dg_mesh_set_sponge: q_bar required, lambda_bar >= 0, z_t > z_b, layer widths > 0");

@@ -432,6 +432,10 @@ extern "C" int dg_precond_apply(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys*
     set_error("dg_precond_apply: invalid physics (gamma > 1, variant R1/R2)");
     return DG_ERR_ARG;
   }
+  if (mesh->gll) {
+    set_error("dg_precond_apply: the preconditioners are not implemented for Gauss-Lobatto nodes");
+    return DG_ERR_UNSUPPORTED;
+  }
   dg_mesh* m = const_cast<dg_mesh*>(mesh);
   cudaStream_t st = (cudaStream_t)stream;
   ImplK k = impl_consts(ph, cf->a_dt);

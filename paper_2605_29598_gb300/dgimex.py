@@ -43,7 +43,8 @@ class MeshStats(C.Structure):
                 ("nodes_per_elem", C.c_int), ("n_elem", C.c_int64), ("n_nodes", C.c_int64),
                 ("n_face_points", C.c_int64), ("n_hang_points", C.c_int64),
                 ("workspace_bytes", C.c_int64), ("tile_fp64", C.c_int * 3),
-                ("tile_fp32", C.c_int * 3), ("terrain_following", C.c_int)]
+                ("tile_fp32", C.c_int * 3), ("terrain_following", C.c_int),
+                ("fused_stage", C.c_int * 2)]
 
 
 class Sponge(C.Structure):
@@ -147,12 +148,16 @@ EXPORTS["dg_ensemble_get_state"] = (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C
 EXPORTS["dg_ensemble_step"] = (C.c_int, [C.c_void_p, C.POINTER(Phys), C.POINTER(C.c_double),
                                          C.POINTER(StepOpts), C.POINTER(StepInfo), C.c_void_p])
 EXPORTS["dg_mesh_autotune"] = (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p])
+EXPORTS["dg_mesh_set_fused_stage"] = (C.c_int, [C.c_void_p, C.c_int, C.c_int])
+EXPORTS["dg_mesh_set_far_state"] = (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p])
 EXPORTS["dg_geostrophic_error"] = (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Phys), C.c_void_p,
                                               C.POINTER(C.c_double), C.c_void_p])
 EXPORTS["dg_mesh_set_background"] = (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Phys), C.c_void_p,
                                                 C.c_void_p])
 EXPORTS["dg_mesh_set_sponge"] = (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Sponge), C.c_void_p,
                                             C.c_void_p])
+EXPORTS["dg_probe_fma"] = (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.POINTER(C.c_double),
+                                     C.POINTER(C.c_double), C.c_void_p])
 EXPORTS["dg_profile_begin"] = (C.c_int, [C.c_void_p, C.c_uint32])
 EXPORTS["dg_profile_end"] = (C.c_int, [C.c_void_p, C.POINTER(KernelStat), C.c_int,
                                        C.POINTER(C.c_int)])
@@ -338,7 +343,17 @@ class Mesh:
         _check(self.lib.dg_mesh_autotune(self.ctx.h, self.h, prec, _stream(stream)),
                "dg_mesh_autotune")
         s = self.stats()
-        return list(s.tile_fp64), list(s.tile_fp32)
+        return list(s.tile_fp64), list(s.tile_fp32), list(s.fused_stage)
+
+    def set_far_state(self, q_far, stream=None):
+        """Outer state (5 x N) of the far-field faces (dg_mesh_set_far_state)."""
+        _check(self.lib.dg_mesh_set_far_state(self.ctx.h, self.h, self._p(q_far, 5), _stream(stream)),
+               "dg_mesh_set_far_state")
+
+    def set_fused_stage(self, fp64, fp32):
+        """Schedule of the fused vmult kernels per precision (1: staged
+        neighbour cells, 0: trace array); see dg_mesh_set_fused_stage."""
+        _check(self.lib.dg_mesh_set_fused_stage(self.h, int(fp64), int(fp32)), "dg_mesh_set_fused_stage")
 
     def stats(self) -> MeshStats:
         s = MeshStats()
@@ -439,6 +454,15 @@ class Mesh:
                                        C.byref(opts), C.byref(info), _stream(stream)),
                "imex_ark2_step")
         return info
+
+
+def probe_fma(ctx: "Context", bits: int, iters: int | None = None, stream=None):
+    """FMA throughput of the device (dg_probe_fma): (TFLOP/s, ms)."""
+    iters = iters or (8192 if bits == 64 else 524288)
+    tf, ms = C.c_double(), C.c_double()
+    _check(ctx.lib.dg_probe_fma(ctx.h, int(bits), int(iters), C.byref(tf), C.byref(ms), _stream(stream)),
+           "dg_probe_fma")
+    return tf.value, ms.value
 
 
 # ----------------------------------------------------------------------------

@@ -106,7 +106,8 @@ def test_mesh_validation_on_the_host():
                              bdry_faces=kw.get("b", m.bdry_faces))
     assert status(m, r=5)[0] == -2                                   # degree > 4: unsupported
     assert status(m, r=0)[0] == -1
-    assert status(m, node_set=D.DG_NODES_GLL)[0] == -2
+    assert D.validate_mesh(m, 2, D.DG_NODES_GLL) == 0                # Gauss-Lobatto nodes accepted
+    assert status(m, node_set=7)[0] == -1                            # unknown node set
     assert status(mk(i=m.int_faces[1:]))[0] == -1                     # an uncovered face
     assert "covered 0 times" in status(mk(i=m.int_faces[1:]))[1]
     assert "covered 2 times" in status(mk(i=np.vstack([m.int_faces, m.int_faces[:1]])))[1]
@@ -115,8 +116,8 @@ def test_mesh_validation_on_the_host():
     bad_cell[0, 2] = m.n_elem
     assert "out of range" in status(mk(i=bad_cell))[1]
     b = m.bdry_faces.copy()
-    b[0, 2] = I.BC_FARFIELD                                            # oracle only so far
-    assert status(mk(b=b))[0] == -2
+    b[0, 2] = I.BC_FARFIELD                                            # far-field faces accepted
+    assert D.validate_mesh(mk(b=b), 2) == 0
     b[0, 2] = 7
     assert "unknown boundary condition" in status(mk(b=b))[1]
     v = m.vertices.copy()

@@ -89,3 +89,39 @@ def test_noalloc_rejects_mesh_beyond_capacity(D):
     fs = torch.empty((4, gm.N), dtype=torch.float64, device="cuda")
     assert _noalloc(D, ctx, gm, phys, q, fns, fs) == -1
     assert b"capacity" in D.load().dg_last_error()
+
+
+def test_noalloc_allocates_no_workspace_and_honours_sponge_and_mixed(D):
+    """On a fresh mesh the call leaves the mesh's workspace empty (every
+    scratch value lives in the library's fixed array); damping layers set on
+    the mesh are applied as by dg_apply_explicit; DG_MIXED runs the same
+    FP64 explicit kernels; DG_MIXED_EXPLICIT and a negative lambda_min are
+    refused."""
+    mesh = I.box_mesh((8, 3, 4), (8e3, 3e3, 4e3), hill=dict(h0=200.0, a_c=1.5e3, xc=4e3, yc=1.5e3))
+    ctx = D.Context(0)
+    gm = D.Mesh(ctx, mesh, 2)
+    q = _state(gm, 3)
+    ws0 = gm.stats().workspace_bytes
+    for prec in ("fp64", "mixed"):
+        phys = D.make_phys(f=1e-4, precision=prec)
+        fns = torch.empty((5, gm.N), dtype=torch.float64, device="cuda")
+        fs = torch.empty((4, gm.N), dtype=torch.float64, device="cuda")
+        assert _noalloc(D, ctx, gm, phys, q, fns, fs) == 0, D.load().dg_last_error()
+        torch.cuda.synchronize()
+        assert gm.stats().workspace_bytes == ws0
+    # damping layers (towards a perturbed copy of the state, so that they act)
+    qbar = _state(gm, 4)
+    gm.set_sponge(qbar, lambda_bar=0.3, z_b=1.5e3, z_t=4e3, x_layers=(0.0, 8e3, 2e3))
+    phys = D.make_phys(f=1e-4, precision="mixed")
+    ref_ns, ref_s = gm.apply_explicit(D.make_phys(f=1e-4), q)
+    fns = torch.empty_like(ref_ns)
+    fs = torch.empty_like(ref_s)
+    assert _noalloc(D, ctx, gm, phys, q, fns, fs) == 0, D.load().dg_last_error()
+    torch.cuda.synchronize()
+    for a, b in ((fns, ref_ns), (fs, ref_s)):
+        assert ((a - b).abs().max() / b.abs().max()).item() < 1e-11
+    gm.set_sponge(None)
+    no_ns, _ = gm.apply_explicit(D.make_phys(f=1e-4), q)
+    assert ((no_ns - ref_ns).abs().max() / ref_ns.abs().max()).item() > 1e-6   # the layers acted
+    assert _noalloc(D, ctx, gm, D.make_phys(precision="mixed_explicit"), q, fns, fs) == -2
+    assert _noalloc(D, ctx, gm, D.make_phys(lambda_min=-1.0), q, fns, fs) == -1
