@@ -82,8 +82,8 @@ __device__ __forceinline__ void slot_normal(const CellGeo<T>& g, const T* __rest
 }
 
 // lift of NFLD fields from the block's shared lift values (field stride NSL)
-template <typename T, int DIM, int N, int NFLD>
-__device__ __forceinline__ void lift_shared(const Tables<T>& tb, const T* sl, const int idx[3], T* r) {
+template <typename T, int DIM, int N, int NFLD, typename TB>
+__device__ __forceinline__ void lift_shared(const TB& tb, const T* sl, const int idx[3], T* r) {
   constexpr int NFP = ipow(N, DIM - 1), NF = 2 * DIM, NSL = NF * NFP;
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
@@ -139,6 +139,7 @@ k_grad_fused(const T* __restrict__ x, const T* __restrict__ tx, const int* __res
   __shared__ int scode[EPB][NF];
   __shared__ T sxw[2 * N];
   __shared__ T stc[std::is_same<T, float>::value ? EPB : 1][16];
+  __shared__ SharedTables<T, N> stb;
   const int le = threadIdx.x / NP, i = threadIdx.x % NP;
   const int64_t e0 = (int64_t)blockIdx.x * EPB;
   const int64_t e = e0 + le;
@@ -147,6 +148,7 @@ k_grad_fused(const T* __restrict__ x, const T* __restrict__ tx, const int* __res
   const int64_t node = active ? e * NP + i : 0;
   const bool tcell = std::is_same<T, float>::value && geo.tc != nullptr;
   stage_terrain<T, EPB>(geo, e0, E, stc);
+  stage_tables<T, N>(tb, stb);
   int idx[3];
   node_index<DIM, N>(i, idx);
   const T xv = active ? __ldg(x + node) : (T)0;
@@ -187,8 +189,8 @@ k_grad_fused(const T* __restrict__ x, const T* __restrict__ tx, const int* __res
       xp = 0;
 #pragma unroll
       for (int j = 0; j < N; ++j) {
-        xm += tb.L[s][j] * sx[c][base + j * stride];
-        xp += tb.L[s ^ 1][j] * snb[c][f][base + j * stride];
+        xm += stb.L[s][j] * sx[c][base + j * stride];
+        xp += stb.L[s ^ 1][j] * snb[c][f][base + j * stride];
       }
     } else {
       xm = __ldg(tx + sl);
@@ -215,12 +217,12 @@ k_grad_fused(const T* __restrict__ x, const T* __restrict__ tx, const int* __res
     for (int a = 0; a < DIM; ++a)
       if ((msk >> a) & 1) sm[le][a][i] = active ? -xv * K[a][b] : (T)0;
     __syncthreads();
-    r[b] = contract<T, DIM, N>(tb, sm[le], i, idx, msk);
+    r[b] = contract<T, DIM, N>(stb, sm[le], i, idx, msk);
     __syncthreads();
   }
   r[DIM] = 0;
   if (!active) return;
-  lift_shared<T, DIM, N, DIM + 1>(tb, &slf[le][0][0], idx, r);
+  lift_shared<T, DIM, N, DIM + 1>(stb, &slf[le][0][0], idx, r);
   T G[3] = {0, 0, 0};
 #pragma unroll
   for (int b = 0; b < DIM; ++b) G[comp_of<DIM>(b)] = iM * r[b];
@@ -271,6 +273,7 @@ k_div_fused(Fields<T> wv, const T* __restrict__ tw, const T* __restrict__ trh, c
   __shared__ int scode[EPB][NF];
   __shared__ T sxw[2 * N];
   __shared__ T stc[std::is_same<T, float>::value ? EPB : 1][16];
+  __shared__ SharedTables<T, N> stb;
   const int le = threadIdx.x / NP, i = threadIdx.x % NP;
   const int64_t e0 = (int64_t)blockIdx.x * EPB;
   const int64_t e = e0 + le;
@@ -279,6 +282,7 @@ k_div_fused(Fields<T> wv, const T* __restrict__ tw, const T* __restrict__ trh, c
   const int64_t node = active ? e * NP + i : 0;
   const bool tcell = std::is_same<T, float>::value && geo.tc != nullptr;
   stage_terrain<T, EPB>(geo, e0, E, stc);
+  stage_tables<T, N>(tb, stb);
   int idx[3];
   node_index<DIM, N>(i, idx);
   const T gam = kp<T>(ph.gamma, ph.gamma_f);
@@ -335,7 +339,7 @@ k_div_fused(Fields<T> wv, const T* __restrict__ tw, const T* __restrict__ trh, c
         T wm = 0;
         if (STAGE) {
 #pragma unroll
-          for (int j = 0; j < N; ++j) wm += tb.L[s][j] * sw[c][b][base + j * stride];
+          for (int j = 0; j < N; ++j) wm += stb.L[s][j] * sw[c][b][base + j * stride];
         } else {
           wm = __ldg(tw + b * S + sl);
         }
@@ -355,8 +359,8 @@ k_div_fused(Fields<T> wv, const T* __restrict__ tw, const T* __restrict__ trh, c
         T wm = 0, wp = 0;
 #pragma unroll
         for (int j = 0; j < N; ++j) {
-          wm += tb.L[s][j] * sw[c][b][base + j * stride];
-          wp += tb.L[s ^ 1][j] * snb[c][f][b][base + j * stride];
+          wm += stb.L[s][j] * sw[c][b][base + j * stride];
+          wp += stb.L[s ^ 1][j] * snb[c][f][b][base + j * stride];
         }
         fm += wm * nS[b];
         fp += wp * nS[b];
@@ -389,9 +393,9 @@ k_div_fused(Fields<T> wv, const T* __restrict__ tw, const T* __restrict__ trh, c
   }
   __syncthreads();
   T r[1];
-  r[0] = contract<T, DIM, N>(tb, sm[le], i, idx);
+  r[0] = contract<T, DIM, N>(stb, sm[le], i, idx);
   if (!active) return;
-  lift_shared<T, DIM, N, 1>(tb, &slf[le][0], idx, r);
+  lift_shared<T, DIM, N, 1>(stb, &slf[le][0], idx, r);
   const T div = iM * r[0];
   const T adt = kp<T>(ph.a_dt, ph.adt_f);
   if (MODE == DIV_VMULT) {

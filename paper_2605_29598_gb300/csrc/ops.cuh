@@ -42,6 +42,25 @@ template <typename T> struct Fields {
   T scale[5];
 };
 
+// The 1D tables of a block in shared memory.  Kernel parameters indexed
+// with a per-thread index are read through the constant cache one address
+// at a time (the ADU pipe bound the first cell kernels); shared memory
+// serves a warp's different indices in one pass.
+template <typename T, int N>
+struct SharedTables {
+  T D[N][N];   // D[k][j] = l_j'(xi_k)
+  T L[2][N];   // L[s][j] = l_j(s)
+};
+
+// one entry per thread (blocks have at least N^2 + 2N threads); a barrier
+// must follow before use
+template <typename T, int N>
+__device__ __forceinline__ void stage_tables(const Tables<T>& tb, SharedTables<T, N>& st) {
+  const int k = threadIdx.x;
+  if (k < N * N) st.D[k / N][k % N] = tb.D[k / N][k % N];
+  else if (k < N * N + 2 * N) st.L[(k - N * N) / N][(k - N * N) % N] = tb.L[(k - N * N) / N][(k - N * N) % N];
+}
+
 // tangential index of node i for faces normal to direction a
 template <int DIM, int N>
 __device__ __forceinline__ int tang_index(const int idx[3], int a) {
@@ -117,7 +136,7 @@ inline unsigned trace_grid(int64_t E) {
 template <typename T, int DIM, int N, int NFLD, bool SCALED>
 __device__ __forceinline__ void trace_slots(const T (*__restrict__ sv)[TraceShape<DIM, N>::CPB * TraceShape<DIM, N>::NP],
                                             const Fields<T>& in, int nc, int64_t out0, T* __restrict__ trc,
-                                            int64_t S, const Tables<T>& tb) {
+                                            int64_t S, const SharedTables<T, N>& tb) {
   using TS = TraceShape<DIM, N>;
   constexpr int NP = TS::NP, NFP = TS::NFP, NS = TS::NS;
   for (int i = threadIdx.x; i < nc * NS; i += TS::THREADS) {
@@ -149,10 +168,12 @@ __global__ void __launch_bounds__(TraceShape<DIM, N>::THREADS)
   using TS = TraceShape<DIM, N>;
   constexpr int NP = TS::NP, NS = TS::NS, CPB = TS::CPB;
   __shared__ T sv[NFLD][CPB * NP];
+  __shared__ SharedTables<T, N> stb;
   const int64_t e0 = (int64_t)blockIdx.x * CPB;
   const int64_t left = E - e0;
   const int nc = left < CPB ? (int)left : CPB;
   if (nc <= 0) return;
+  stage_tables<T, N>(tb, stb);
   bool unit = true;
 #pragma unroll
   for (int q = 0; q < NFLD; ++q) {
@@ -162,9 +183,9 @@ __global__ void __launch_bounds__(TraceShape<DIM, N>::THREADS)
   }
   __syncthreads();
   if (unit)
-    trace_slots<T, DIM, N, NFLD, false>(sv, in, nc, e0 * NS, trc, S, tb);
+    trace_slots<T, DIM, N, NFLD, false>(sv, in, nc, e0 * NS, trc, S, stb);
   else
-    trace_slots<T, DIM, N, NFLD, true>(sv, in, nc, e0 * NS, trc, S, tb);
+    trace_slots<T, DIM, N, NFLD, true>(sv, in, nc, e0 * NS, trc, S, stb);
 }
 
 // plus-side value of a traced field at face point p
@@ -306,6 +327,8 @@ __global__ void __launch_bounds__(CellShape<DIM, N>::THREADS)
   using CS = CellShape<DIM, N>;
   constexpr int NP = CS::NP, EPB = CS::EPB;
   __shared__ T sv[2][EPB][NP];
+  __shared__ T sB[N][N];   // the matrix in shared memory (per-thread row index)
+  if (threadIdx.x < N * N) sB[threadIdx.x / N][threadIdx.x % N] = B.m[threadIdx.x / N][threadIdx.x % N];
   const int le = threadIdx.x / NP, i = threadIdx.x % NP;
   const int64_t e = (int64_t)blockIdx.x * EPB + le;
   const bool active = e < E;
@@ -324,7 +347,7 @@ __global__ void __launch_bounds__(CellShape<DIM, N>::THREADS)
       const int i0 = i - idx[a] * stride;
       T acc = 0;
 #pragma unroll
-      for (int k = 0; k < N; ++k) acc += B.m[idx[a]][k] * sv[cur][le][i0 + k * stride];
+      for (int k = 0; k < N; ++k) acc += sB[idx[a]][k] * sv[cur][le][i0 + k * stride];
       cur ^= 1;
       sv[cur][le][i] = acc;
       v = acc;
@@ -354,8 +377,8 @@ __device__ __forceinline__ int amask_of(int terrain, int b) {
 
 // sum_a sum_k D[k][i_a] * sm[a][line(i, a, k)]  (test-gradient contraction)
 // (directions a outside amask are skipped: their fluxes are zero)
-template <typename T, int DIM, int N>
-__device__ __forceinline__ T contract(const Tables<T>& tb, const T (*sm)[ipow(N, DIM)], int i,
+template <typename T, int DIM, int N, typename TB>
+__device__ __forceinline__ T contract(const TB& tb, const T (*sm)[ipow(N, DIM)], int i,
                                       const int idx[3], int amask = (1 << DIM) - 1) {
   T acc = 0;
 #pragma unroll
@@ -370,8 +393,8 @@ __device__ __forceinline__ T contract(const Tables<T>& tb, const T (*sm)[ipow(N,
 }
 
 // lift of NFLD slot fields into the residuals of node i
-template <typename T, int DIM, int N, int NFLD>
-__device__ __forceinline__ void lift(const Tables<T>& tb, const T* __restrict__ slot, int64_t S,
+template <typename T, int DIM, int N, int NFLD, typename TB>
+__device__ __forceinline__ void lift(const TB& tb, const T* __restrict__ slot, int64_t S,
                                      int64_t e, const int idx[3], T* r) {
   constexpr int NFP = ipow(N, DIM - 1), NF = 2 * DIM;
 #pragma unroll
@@ -403,6 +426,8 @@ k_volume_explicit(const T* __restrict__ q, const T* __restrict__ Kg, const T* __
   using CS = CellShape<DIM, N, M>;
   constexpr int NP = CS::NP, EPB = CS::EPB;
   __shared__ T sm[EPB][DIM][NP];
+  __shared__ SharedTables<T, N> stb;
+  stage_tables<T, N>(tb, stb);
   const int le = threadIdx.x / NP, i = threadIdx.x % NP;
   const int64_t e = (int64_t)blockIdx.x * EPB + le;
   const bool active = e < E;
@@ -466,11 +491,11 @@ k_volume_explicit(const T* __restrict__ q, const T* __restrict__ Kg, const T* __
       sm[le][a][i] = v;
     }
     __syncthreads();
-    r[fld] = contract<T, DIM, N>(tb, sm[le], i, idx, msk);
+    r[fld] = contract<T, DIM, N>(stb, sm[le], i, idx, msk);
     __syncthreads();
   }
   if (!active) return;
-  lift<T, DIM, N, 9>(tb, slot, S, e, idx, r);
+  lift<T, DIM, N, 9>(stb, slot, S, e, idx, r);
 #pragma unroll
   for (int fld = 0; fld < 5; ++fld) fns[fld * Nn + node] = iM * r[fld];
   const T f = (T)coriolis(ph.fcell, ph.f, e), g = (T)ph.g;

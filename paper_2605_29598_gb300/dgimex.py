@@ -20,8 +20,8 @@ from . import build as _build
 DG_OK = 0
 DG_NODES_GL, DG_NODES_GLL = 0, 1
 DG_R1, DG_R2 = 1, 2
-DG_FP64, DG_MIXED, DG_MIXED_EXPLICIT = 0, 1, 2
-PRECISIONS = {"fp64": DG_FP64, "mixed": DG_MIXED, "mixed_explicit": DG_MIXED_EXPLICIT}
+DG_FP64, DG_MIXED, DG_MIXED_EXPLICIT, DG_PAIRS = 0, 1, 2, 3
+PRECISIONS = {"fp64": DG_FP64, "mixed": DG_MIXED, "mixed_explicit": DG_MIXED_EXPLICIT, "pairs": DG_PAIRS}
 STATUS = {0: "DG_OK", -1: "DG_ERR_ARG", -2: "DG_ERR_UNSUPPORTED", -3: "DG_ERR_CUDA",
           -4: "DG_ERR_NOT_CONVERGED", -5: "DG_ERR_TIMEOUT", -6: "DG_ERR_NONFINITE",
           -7: "DG_ERR_OOM"}
