@@ -64,10 +64,15 @@ def work_model(dim, n, N, S, nF, nnz=None):
     d = dim
     nnz = d * d if nnz is None else nnz
     return {
-        # sum_b sum_{a: K_ab != 0} (x K_ab) contraction + lift of d+1 fields + pointwise
-        "volume_grad": N * (nnz + 2 * nnz * n + 2 * 2 * d * (d + 1) + 20),
-        # h rho K w, d contractions, lift of 1 field, update
-        "volume_div": N * (2 * nnz + d + 2 * d * n + 2 * 2 * d + 6),
+        # fused gradient pass: per own face slot the centred value, its n dS
+        # products and the penalty jump (d + 4; the plus value read from the
+        # trace array), then sum_b sum_{a: K_ab != 0} (x K_ab) contraction +
+        # lift of d+1 fields + pointwise
+        "volume_grad": S * (d + 4) + N * (nnz + 2 * nnz * n + 2 * 2 * d * (d + 1) + 20),
+        # fused divergence pass: per own slot both sides' w.n dS and the
+        # centred h rho flux (4d + 4), then h rho K w, d contractions, lift of
+        # 1 field, update
+        "volume_div": S * (4 * d + 4) + N * (2 * nnz + d + 2 * d * n + 2 * 2 * d + 6),
         # K u, 6 flux fields x d contractions + 3 pressure fields x their
         # nonzero directions, lift of 9 fields
         "volume_explicit": N * (2 * nnz + 9 * d + 2 * (6 * d + nnz) * n + 2 * 2 * d * 9 + 30),
@@ -80,15 +85,19 @@ def work_model(dim, n, N, S, nF, nnz=None):
 # DRAM bytes per node of one launch, from an ncu capture of the current
 # kernel on the 30 x 30 x 20 hill (profiles/volume_grad_hill3d_30x30x20_r3_fp64.md:
 # 147.9 MB over 1 152 000 nodes), scaled to a launch by the nodes it processes.
-NCU_TRAFFIC_B_PER_NODE = {"volume_grad": 147.9e6 / 1152000}
+NCU_TRAFFIC_B_PER_NODE = {}
 
 
 def bytes_model(dim, n, N, S, nF, nnz=None):
     d = dim
     nnz = d * d if nnz is None else nnz
     return {
-        "volume_grad": N * 8 * (1 + nnz + 1 + 1 + d + 1) + S * 8 * (d + 1),
-        "volume_div": N * 8 * (d + 1 + nnz + 1 + 1 + 1) + S * 8,
+        # x, metric, 1/(w det J), 1/rho, w out, y out; per slot: own and plus
+        # traces, n dS, penalty coefficient
+        "volume_grad": N * 8 * (1 + nnz + 1 + 1 + d + 1) + S * 8 * (2 + d + 1),
+        # w, p_lag, metric, 1/(w det J), y in and out; per slot: both sides' w
+        # traces and h rho traces, n dS
+        "volume_div": N * 8 * (d + 1 + nnz + 1 + 1 + 1) + S * 8 * (2 * d + 2 + d),
         "volume_explicit": N * 8 * (5 + nnz + 1 + 9) + S * 8 * 9,
     }
 
@@ -430,6 +439,7 @@ def run_per_operator(D, mesh, q, f, a_dt, hbm_gbs, reps=10):
         ("apply_explicit_fp64", lambda: mesh.apply_explicit(D.make_phys(f=f), q, fns, fs), 5, 112),
         ("apply_implicit_fp64", lambda: mesh.apply_implicit(D.make_phys(f=f), cf, x, y), 1, 38),
         ("apply_implicit_mixed", lambda: mesh.apply_implicit(D.make_phys(f=f, precision="mixed"), cf, x, y), 1, 38),
+        ("apply_implicit_pairs", lambda: mesh.apply_implicit(D.make_phys(f=f, precision="pairs"), cf, x, y), 1, 38),
         ("precond_vline_setup_and_solve", lambda: mesh.precond_apply(D.make_phys(f=f), cf, x, y), 1, None),
     ]
     for name, fn, fields, bpn in rows:
@@ -439,6 +449,32 @@ def run_per_operator(D, mesh, q, f, a_dt, hbm_gbs, reps=10):
             gbs = bpn * N / (ms / 1e3) / 1e9
             r.update({"algorithmic_bytes_per_node": bpn, "gb_per_s": gbs, "frac_of_measured_hbm": gbs / hbm_gbs})
         out[name] = r
+    # the vmult kernels alone (the calls above also prepare their
+    # coefficients): the fused gradient and divergence passes of each
+    # precision, CUDA events per launch, and the FP32 pair against the HBM
+    # roof at the two-pass algorithmic bytes (43 B/node in FP32: x, y, rho,
+    # p_lag, face lambda and the intermediate w written and read once)
+    st = mesh.stats()
+    for prec, bpn in (("fp64", 86), ("mixed", 43), ("pairs", 86)):
+        ph = D.make_phys(f=f, precision=prec)
+        for _ in range(3):
+            mesh.apply_implicit(ph, cf, x, y)
+        torch.cuda.synchronize()
+        D.profile_begin(mesh, timed=["volume_grad", "volume_div", "trace"])
+        for _ in range(reps):
+            mesh.apply_implicit(ph, cf, x, y)
+        prof = D.profile_end(mesh)
+        g, dv = prof["volume_grad"], prof["volume_div"]
+        stage = st.fused_stage[0 if prec == "fp64" else 1]
+        ms = (g[2] + dv[2]) / reps
+        r = {"grad_ms": g[2] / max(g[1], 1), "div_ms": dv[2] / max(dv[1], 1), "fused_passes_ms": ms,
+             "schedule": "neighbour node lines" if stage else
+                         "trace array (plus two trace passes per vmult, about trace_ms_per_launch each)",
+             "trace_ms_per_launch": prof["trace"][2] / max(prof["trace"][1], 1)}
+        if prec == "mixed":
+            gbs = bpn * N / (ms / 1e3) / 1e9
+            r.update({"algorithmic_bytes_per_node": bpn, "gb_per_s": gbs, "frac_of_measured_hbm": gbs / hbm_gbs})
+        out["vmult_kernels_" + prec] = r
     return out
 
 
@@ -547,6 +583,10 @@ def run_precision_pattern(D, mesh, q_bg, f, dt, steps):
     ms64, it64, _ = timed_steps(mesh, ph64, q64, dt, steps, PRECISION_OPTS)
     qmx = q_bg.clone()
     msmx, itmx, refmx = timed_steps(mesh, phmx, qmx, dt, steps, dict(PRECISION_OPTS, gmres_inner_rtol=1e-4))
+    phpr = D.make_phys(f=f, variant="R2", precision="pairs")
+    mesh.step(phpr, q_bg.clone(), dt, **PRECISION_OPTS)   # pair geometry once
+    qpr = q_bg.clone()
+    mspr, itpr, _ = timed_steps(mesh, phpr, qpr, dt, steps, PRECISION_OPTS)
     qref = q_bg.clone()
     timed_steps(mesh, ph64, qref, dt, steps, REFERENCE_OPTS)
     N = q_bg.shape[1]
@@ -556,7 +596,11 @@ def run_precision_pattern(D, mesh, q_bg, f, dt, steps):
                     "gmres_inner_iters": itmx, "fp64_refinement_sweeps": refmx,
                     "rel_l2_err_vs_reference": perturbation_errors(qmx, qref, q_bg),
                     "rel_l2_err_vs_fp64": perturbation_errors(qmx, q64, q_bg)}
+    out["pairs"] = {"value": 5.0 * N * steps / (mspr / 1e3) / 1e9, "ms_per_step": mspr / steps,
+                    "gmres_iters": itpr, "rel_l2_err_vs_reference": perturbation_errors(qpr, qref, q_bg),
+                    "what": "Schur vmults in pairs of FP32 numbers (an FP64-class emulation), FP64 GMRES"}
     out["mixed_speedup_vs_fp64"] = ms64 / msmx
+    out["pairs_speedup_vs_fp64"] = ms64 / mspr
     out["unit"] = "GDoF-updates/s"
     return out
 
@@ -862,8 +906,11 @@ def gpu_main(args):
         summary["precision_1e-12"] = {
             "fp64_ms": r3(precision["fp64"]["ms_per_step"]), "mixed_ms": r3(precision["mixed"]["ms_per_step"]),
             "speedup": r3(precision["mixed_speedup_vs_fp64"]),
-            "mixed_err": r3(precision["mixed"]["rel_l2_err_vs_reference"]),
-            "fp64_err": r3(precision["fp64"]["rel_l2_err_vs_reference"])}
+            "mixed_err": r3(max(precision["mixed"]["rel_l2_err_vs_reference"].values())),
+            "fp64_err": r3(max(precision["fp64"]["rel_l2_err_vs_reference"].values())),
+            "pairs_ms": r3(precision["pairs"]["ms_per_step"]),
+            "pairs_speedup": r3(precision["pairs_speedup_vs_fp64"]),
+            "pairs_err": r3(max(precision["pairs"]["rel_l2_err_vs_reference"].values()))}
     if cfg3:
         summary["config3_nc_fp64"] = {"gdof_s": r3(cfg3["value"]), "ms_step": r3(cfg3["ms_per_step"]),
                                       "gmres": cfg3["gmres_iters"], "steps": cfg3["steps"]}
@@ -873,6 +920,10 @@ def gpu_main(args):
                                        "fp64_err_1e-8": r3(max(
                                            cfg4["fp64_same_tolerance_rel_l2_err_vs_fp64_1e12"].values())),
                                        "err_1e-12": r3(cfg4["mixed_refined_to_1e12"]["rel_l2_err_vs_fp64_1e12"])}
+    if per_op:
+        vk = {p: per_op["vmult_kernels_" + p] for p in ("fp64", "mixed", "pairs")}
+        summary["vmult_fused_us"] = {p: r3(1e3 * v["fused_passes_ms"]) for p, v in vk.items()}
+        summary["fp32_vmult_frac_hbm"] = r3(vk["mixed"]["frac_of_measured_hbm"])
     if roof:
         summary["roofline"] = {"kernel": dominant, "frac_of_measured_fp64": r3(roof["frac"]),
                                "fp64_peak_tflops": r3(fp64_peak),

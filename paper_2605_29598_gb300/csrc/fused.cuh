@@ -5,12 +5,14 @@
 // A block owns EPB cells.  It evaluates the numerical fluxes at every face
 // point of its own cells itself and keeps the lift values in shared memory,
 // so no face flux goes through global memory and no separate face kernel
-// runs.  The plus-side value at a conforming (or periodic) face point comes
-// either
-//   STAGE = true : from the neighbour cell's nodal values, read once per
-//                  face with coalesced loads (mostly L2 hits: the vectors
-//                  are a few tens of MB) and contracted to the face in
-//                  shared memory, or
+// runs.  The block's threads form N groups of EPB x N^(d-1) threads; group
+// g takes the faces f = g mod N, each thread one point (cell c, point t) of
+// them, so that the face index is a compile-time constant in the unrolled
+// face loop.  The plus-side value at a conforming (or periodic) face point
+// comes either
+//   STAGE = true : from the neighbour cell's node line through that point,
+//                  read by the thread itself (mostly L2 hits: the vectors
+//                  are a few tens of MB) and contracted to the face, or
 //   STAGE = false: from a per-slot trace array written by k_trace, which
 //                  spends no arithmetic on the neighbour's trace (the
 //                  choice where the FP64 pipe binds).
@@ -112,10 +114,11 @@ __device__ __forceinline__ void stage_nodes_all(const CellGeo<T>& g, T* sxw) {
 // in shared memory (the metric and the normals are recomputed from them)
 template <typename T, int EPB>
 __device__ __forceinline__ void stage_terrain(const CellGeo<T>& g, int64_t e0, int64_t E, T (*stc)[16]) {
-  if (!std::is_same<T, float>::value || !g.tc) return;
-  for (int k = threadIdx.x; k < EPB * 16; k += blockDim.x) {
-    const int c = k / 16, j = k % 16;
-    stc[c][j] = e0 + c < E ? __ldg(g.tc + (e0 + c) * 16 + j) : (T)0;
+  if (std::is_same<T, float>::value && g.tc) {
+    for (int k = threadIdx.x; k < EPB * 16; k += blockDim.x) {
+      const int c = k / 16, j = k % 16;
+      stc[c][j] = e0 + c < E ? __ldg(g.tc + (e0 + c) * 16 + j) : (T)0;
+    }
   }
 }
 
@@ -133,7 +136,6 @@ k_grad_fused(const T* __restrict__ x, const T* __restrict__ tx, const int* __res
   using FS = FusedShape<DIM, N>;
   constexpr int NP = FS::NP, EPB = FS::EPB, NF = FS::NF, NFP = FS::NFP, NSL = FS::NSL, TH = FS::THREADS;
   __shared__ T sx[EPB][NP];
-  __shared__ T snb[STAGE ? EPB : 1][STAGE ? NF : 1][NP];
   __shared__ T slf[EPB][DIM + 1][NSL];
   __shared__ T sm[EPB][DIM][NP];
   __shared__ int scode[EPB][NF];
@@ -159,42 +161,34 @@ k_grad_fused(const T* __restrict__ x, const T* __restrict__ tx, const int* __res
   }
   stage_nodes_all<T, N>(geo, sxw);
   __syncthreads();
-  if (STAGE) {
-    for (int k = threadIdx.x; k < EPB * NF * NP; k += TH) {
-      const int c = k / (NF * NP), f = (k / NP) % NF, j = k % NP;
-      const int code = scode[c][f];
-      if (code >= 0) snb[c][f][j] = __ldg(x + (int64_t)code * NP + j);
-    }
-    __syncthreads();
-  }
   // numerical fluxes at the face points of the block's cells
-  for (int k = threadIdx.x; k < EPB * NSL; k += TH) {
-    const int c = k / NSL, r = k % NSL;
-    const int64_t ec = e0 + c;
-    if (ec >= E) continue;
-    const int f = r / NFP, t = r % NFP;
-    const int code = scode[c][f];
+  constexpr int GS = EPB * NFP;
+  const int grp = threadIdx.x / GS, cc = (threadIdx.x % GS) / NFP, tt = threadIdx.x % NFP;
+  const int64_t ec = e0 + cc;
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    if (f % N != grp || ec >= E) continue;
+    const int code = scode[cc][f];
+    const int r = f * NFP + tt;
     const int64_t sl = ec * NSL + r;
     if (code == -2) {
 #pragma unroll
-      for (int q = 0; q <= DIM; ++q) slf[c][q][r] = __ldg(slot + q * S + sl);
+      for (int q = 0; q <= DIM; ++q) slf[cc][q][r] = __ldg(slot + q * S + sl);
       continue;
     }
-    T xm, xp;
+    T xm = 0, xp = 0;
     if (STAGE) {
-      const int s = f & 1;
       int base, stride;
-      face_line<DIM, N>(f, t, base, stride);
-      xm = 0;
-      xp = 0;
+      face_line<DIM, N>(f, tt, base, stride);
+      const T* __restrict__ nb = x + (int64_t)(code >= 0 ? code : 0) * NP + base;
 #pragma unroll
       for (int j = 0; j < N; ++j) {
-        xm += stb.L[s][j] * sx[c][base + j * stride];
-        xp += stb.L[s ^ 1][j] * snb[c][f][base + j * stride];
+        xm += stb.L[f & 1][j] * sx[cc][base + j * stride];
+        if (code >= 0) xp += stb.L[(f & 1) ^ 1][j] * __ldg(nb + j * stride);
       }
     } else {
       xm = __ldg(tx + sl);
-      xp = code >= 0 ? __ldg(tx + ((int64_t)code * NF + (f ^ 1)) * NFP + t) : xm;
+      xp = code >= 0 ? __ldg(tx + ((int64_t)code * NF + (f ^ 1)) * NFP + tt) : xm;
     }
     // wall (-1): {x} = x-, no jump; far field (-3): the linear part, the
     // outer state's value is known data of the right-hand side (zero here)
@@ -202,10 +196,10 @@ k_grad_fused(const T* __restrict__ x, const T* __restrict__ tx, const int* __res
     if (code == -3) xp = 0;
     const T avg = code == -1 ? xm : (T)0.5 * (xm + xp);
     T nS[DIM];
-    slot_normal<T, DIM, N>(geo, snS, S, ec, f, t, sl, sxw, nS, tcell ? stc[c] : nullptr);
+    slot_normal<T, DIM, N>(geo, snS, S, ec, f, tt, sl, sxw, nS, tcell ? stc[cc] : nullptr);
 #pragma unroll
-    for (int b = 0; b < DIM; ++b) slf[c][b][r] = -avg * nS[b];
-    slf[c][DIM][r] = (code == -1 || pcs == nullptr) ? (T)0 : -__ldg(pcs + sl) * (xm - xp);
+    for (int b = 0; b < DIM; ++b) slf[cc][b][r] = -avg * nS[b];
+    slf[cc][DIM][r] = (code == -1 || pcs == nullptr) ? (T)0 : -__ldg(pcs + sl) * (xm - xp);
   }
   T K[DIM][DIM], iM = 0;
   if (active) node_metric<T, DIM, N>(geo, e, node, Nn, idx, K, iM, sxw, tcell ? stc[le] : nullptr);
@@ -267,7 +261,6 @@ k_div_fused(Fields<T> wv, const T* __restrict__ tw, const T* __restrict__ trh, c
   using FS = FusedShape<DIM, N>;
   constexpr int NP = FS::NP, EPB = FS::EPB, NF = FS::NF, NFP = FS::NFP, NSL = FS::NSL, TH = FS::THREADS;
   __shared__ T sw[EPB][DIM][NP];
-  __shared__ T snb[STAGE ? EPB : 1][STAGE ? NF : 1][STAGE ? DIM : 1][NP];
   __shared__ T slf[EPB][NSL];
   __shared__ T sm[EPB][DIM][NP];
   __shared__ int scode[EPB][NF];
@@ -299,80 +292,51 @@ k_div_fused(Fields<T> wv, const T* __restrict__ tw, const T* __restrict__ trh, c
   }
   stage_nodes_all<T, N>(geo, sxw);
   __syncthreads();
-  if (STAGE) {
-    // (the field loop is unrolled: a run-time index into the kernel
-    // parameter wv would copy it to local memory)
-    for (int k = threadIdx.x; k < EPB * NF * NP; k += TH) {
-      const int c = k / (NF * NP), f = (k / NP) % NF, j = k % NP;
-      const int code = scode[c][f];
-      if (code >= 0) {
+  // face points: thread group grp takes the faces f = grp mod N (see above)
+  constexpr int GS = EPB * NFP;
+  const int grp = threadIdx.x / GS, cc = (threadIdx.x % GS) / NFP, tt = threadIdx.x % NFP;
+  const int64_t ec = e0 + cc;
 #pragma unroll
-        for (int b = 0; b < DIM; ++b) snb[c][f][b][j] = __ldg(wv.f[b] + (int64_t)code * NP + j);
-      }
-    }
-    __syncthreads();
-  }
-  for (int k = threadIdx.x; k < EPB * NSL; k += TH) {
-    const int c = k / NSL, r = k % NSL;
-    const int64_t ec = e0 + c;
-    if (ec >= E) continue;
-    const int f = r / NFP, t = r % NFP;
-    const int code = scode[c][f];
+  for (int f = 0; f < NF; ++f) {
+    if (f % N != grp || ec >= E) continue;
+    const int code = scode[cc][f];
+    const int r = f * NFP + tt;
     const int64_t sl = ec * NSL + r;
     if (code == -2) {
-      slf[c][r] = __ldg(slot + sl);
+      slf[cc][r] = __ldg(slot + sl);
       continue;
     }
     if (code == -1) {   // wall: the mirror velocity makes {h rho w}.n vanish
-      slf[c][r] = 0;
+      slf[cc][r] = 0;
       continue;
     }
     T nS[DIM];
-    slot_normal<T, DIM, N>(geo, snS, S, ec, f, t, sl, sxw, nS, tcell ? stc[c] : nullptr);
-    if (code == -3) {   // far field: the linear part (h rho w)-.n / 2
-      const int s = f & 1;
-      int base, stride;
-      face_line<DIM, N>(f, t, base, stride);
-      T fm = 0;
-#pragma unroll
-      for (int b = 0; b < DIM; ++b) {
-        T wm = 0;
-        if (STAGE) {
-#pragma unroll
-          for (int j = 0; j < N; ++j) wm += stb.L[s][j] * sw[c][b][base + j * stride];
-        } else {
-          wm = __ldg(tw + b * S + sl);
-        }
-        fm += wm * nS[b];
-      }
-      slf[c][r] = -(T)0.5 * __ldg(trh + sl) * fm;
-      continue;
-    }
-    const int64_t sp = ((int64_t)code * NF + (f ^ 1)) * NFP + t;
+    slot_normal<T, DIM, N>(geo, snS, S, ec, f, tt, sl, sxw, nS, tcell ? stc[cc] : nullptr);
+    int base, stride;
+    face_line<DIM, N>(f, tt, base, stride);
+    // own normal flux (w-.n dS) and, on a conforming face, the neighbour's
+    // (w+.n dS); far field (-3): the linear part (h rho w)-.n / 2 only
     T fm = 0, fp = 0;
-    if (STAGE) {
-      const int s = f & 1;
-      int base, stride;
-      face_line<DIM, N>(f, t, base, stride);
+    const int64_t sp = code >= 0 ? ((int64_t)code * NF + (f ^ 1)) * NFP + tt : sl;
 #pragma unroll
-      for (int b = 0; b < DIM; ++b) {
-        T wm = 0, wp = 0;
+    for (int b = 0; b < DIM; ++b) {
+      T wm = 0, wp = 0;
+      if (STAGE) {
+        const T* __restrict__ nb = wv.f[b] + (int64_t)(code >= 0 ? code : 0) * NP + base;
 #pragma unroll
         for (int j = 0; j < N; ++j) {
-          wm += stb.L[s][j] * sw[c][b][base + j * stride];
-          wp += stb.L[s ^ 1][j] * snb[c][f][b][base + j * stride];
+          wm += stb.L[f & 1][j] * sw[cc][b][base + j * stride];
+          if (code >= 0) wp += stb.L[(f & 1) ^ 1][j] * __ldg(nb + j * stride);
         }
-        fm += wm * nS[b];
-        fp += wp * nS[b];
+      } else {
+        wm = __ldg(tw + b * S + sl);
+        if (code >= 0) wp = __ldg(tw + b * S + sp);
       }
-    } else {
-#pragma unroll
-      for (int b = 0; b < DIM; ++b) {
-        fm += __ldg(tw + b * S + sl) * nS[b];
-        fp += __ldg(tw + b * S + sp) * nS[b];
-      }
+      fm += wm * nS[b];
+      fp += wp * nS[b];
     }
-    slf[c][r] = -(T)0.5 * (__ldg(trh + sl) * fm + __ldg(trh + sp) * fp);
+    slf[cc][r] = code == -3 ? -(T)0.5 * __ldg(trh + sl) * fm
+                            : -(T)0.5 * (__ldg(trh + sl) * fm + __ldg(trh + sp) * fp);
   }
   T iM = 0;
   if (active) {
