@@ -723,6 +723,7 @@ def gpu_main(args):
     ctx = D.Context(dev)
     mesh = D.Mesh(ctx, mesh_h, r)
     tiles = mesh.autotune("mixed")
+    tiles = [tiles[0], tiles[1], mesh.autotune("pairs")[2]]
     st = mesh.stats()
     N = st.n_nodes
     xyz = mesh.node_coords().cpu().numpy().T

@@ -133,9 +133,9 @@ typedef struct {
   int terrain_following;     /* 1: every cell has x = x(xi_1) (and y = y(xi_2)),
                                 so the cell kernels skip the metric terms that
                                 vanish exactly (not in the paper) */
-  int fused_stage[2];        /* FP64, FP32 Schur vmult: 1 = plus-side face
-                                values from the neighbour cells' nodal values
-                                staged in shared memory, 0 = from a trace array
+  int fused_stage[3];        /* FP64, FP32, FP32-pair Schur vmult: 1 =
+                                plus-side face values from the neighbour
+                                cells' node lines, 0 = from a trace array
                                 written by a separate pass (see
                                 dg_mesh_set_fused_stage) */
 } dg_mesh_stats;
@@ -146,19 +146,21 @@ int dg_mesh_info(const dg_mesh* mesh, dg_mesh_stats* out);
  * block, and whole Schur vmults with either fused-kernel schedule (see
  * dg_mesh_set_fused_stage), on this mesh (synthetic coefficients, CUDA
  * events), and keeps the fastest, for FP64 and, when precision is DG_MIXED
- * or DG_MIXED_EXPLICIT, for the FP32 vmult too.  Allocates temporary device
- * memory; synchronises `stream`.  Results in dg_mesh_stats. */
+ * or DG_MIXED_EXPLICIT, for the FP32 vmult too, when it is DG_PAIRS for the
+ * FP32-pair vmult.  Allocates temporary device memory; synchronises
+ * `stream`.  Results in dg_mesh_stats. */
 int dg_mesh_autotune(dg_ctx* ctx, dg_mesh* mesh, int precision, void* stream);
 
 /* Schedule of the fused face + cell kernels of the Schur vmult, right-hand
- * side and velocity recovery (not in the paper): per precision (FP64, FP32),
- * 1 stages each neighbour cell's nodal values in shared memory and
- * contracts them to the shared face there (no trace pass, more arithmetic),
- * 0 reads the neighbour's face values from a trace array that a separate
- * pass writes (less arithmetic, more memory traffic).  Both give the same
- * results up to rounding.  Defaults: FP64 0, FP32 1; dg_mesh_autotune times
- * both and keeps the faster.  Host only, no GPU work. */
-int dg_mesh_set_fused_stage(dg_mesh* mesh, int fp64, int fp32);
+ * side and velocity recovery (not in the paper): per precision (FP64, FP32,
+ * FP32 pairs of DG_PAIRS), 1 reads the neighbour cell's node line through
+ * each face point and contracts it to the face in the kernel (no trace
+ * pass, more arithmetic), 0 reads the neighbour's face values from a trace
+ * array that a separate pass writes (less arithmetic, more memory
+ * traffic).  Both give the same results up to rounding.  Defaults: FP64 0,
+ * FP32 1, pairs 0; dg_mesh_autotune times both and keeps the faster.  Host
+ * only, no GPU work. */
+int dg_mesh_set_fused_stage(dg_mesh* mesh, int fp64, int fp32, int pairs);
 
 /* Physical coordinates of all nodes: xyz[dim][cell][node] (device, FP64). */
 int dg_mesh_node_coords(dg_ctx* ctx, const dg_mesh* mesh, double* xyz, void* stream);

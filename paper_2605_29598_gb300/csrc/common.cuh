@@ -161,8 +161,9 @@ struct dg_mesh {
   // fused face + cell kernels: implicit Rusanov coefficient per own face
   // slot (FP64, FP32) and outward n dS per own face slot (FP64: d x S)
   dg::DBuf pcs, pcs32, snS;
-  int fused_stage[2] = {0, 1};   // per precision (FP64, FP32): plus-side traces from
-                                 // staged neighbour cells (1) or from a trace array (0)
+  int fused_stage[3] = {0, 1, 0};   // per precision (FP64, FP32, FP32 pairs): plus-side
+                                    // values from the neighbour's node lines (1) or a
+                                    // trace array (0)
   // background of the perturbation-form explicit operator (mixed precision)
   dg::DBuf bg, bg32, bgF, bgtr, bgjump, pert32;
   // device-driven step (CUDA graph): solver state and fixed work vectors

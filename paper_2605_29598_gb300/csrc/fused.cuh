@@ -34,6 +34,15 @@ struct FusedShape {
   static constexpr int THREADS = EPB * NP;
 };
 
+// resident blocks per SM each precision asks the register allocator for:
+// the FP32 kernels wait on barriers and loads, not on a pipe, so more warps
+// hide more latency; the FP64 ones are bound by the FP64 pipe and the pair
+// ones would spill below 64 registers
+template <typename T>
+struct FusedOcc {
+  static constexpr int MIN_BLOCKS = std::is_same<T, float>::value ? 5 : 4;
+};
+
 // node line of face f's point t: first node and stride along the normal
 template <int DIM, int N>
 __device__ __forceinline__ void face_line(int f, int t, int& base, int& stride) {
@@ -128,17 +137,17 @@ __device__ __forceinline__ void stage_terrain(const CellGeo<T>& g, int64_t e0, i
 //           spatial comps); y = x + pen - (gamma-1) a_dt^2 g G_z (R2)
 //  RECOVER: u = ustar - a_dt w (3 comps; no penalty)
 template <typename T, int DIM, int N, int MODE, bool STAGE>
-__global__ void __launch_bounds__(FusedShape<DIM, N>::THREADS)
+__global__ void __launch_bounds__(FusedShape<DIM, N>::THREADS, FusedOcc<T>::MIN_BLOCKS)
 k_grad_fused(const T* __restrict__ x, const T* __restrict__ tx, const int* __restrict__ cface,
              const T* __restrict__ snS, const T* __restrict__ pcs, const T* __restrict__ irho, CellGeo<T> geo,
              const T* __restrict__ slot, int64_t E, int64_t S, Tables<T> tb, ImplK ph, T* __restrict__ wv,
              T* __restrict__ y, const T* __restrict__ ustar, T* __restrict__ uout) {
   using FS = FusedShape<DIM, N>;
-  constexpr int NP = FS::NP, EPB = FS::EPB, NF = FS::NF, NFP = FS::NFP, NSL = FS::NSL, TH = FS::THREADS;
+  constexpr int NP = FS::NP, EPB = FS::EPB, NF = FS::NF, NFP = FS::NFP, NSL = FS::NSL;
   __shared__ T sx[EPB][NP];
+  __shared__ T sxp[EPB][NSL];     // plus-side values at the block's face points
   __shared__ T slf[EPB][DIM + 1][NSL];
-  __shared__ T sm[EPB][DIM][NP];
-  __shared__ int scode[EPB][NF];
+  __shared__ T sm[EPB][DIM][DIM][NP];
   __shared__ T sxw[2 * N];
   __shared__ T stc[std::is_same<T, float>::value ? EPB : 1][16];
   __shared__ SharedTables<T, N> stb;
@@ -155,20 +164,46 @@ k_grad_fused(const T* __restrict__ x, const T* __restrict__ tx, const int* __res
   node_index<DIM, N>(i, idx);
   const T xv = active ? __ldg(x + node) : (T)0;
   sx[le][i] = xv;
-  for (int k = threadIdx.x; k < EPB * NF; k += TH) {
-    const int c = k / NF, f = k % NF;
-    scode[c][f] = e0 + c < E ? __ldg(cface + (e0 + c) * NF + f) : -1;
-  }
-  stage_nodes_all<T, N>(geo, sxw);
-  __syncthreads();
-  // numerical fluxes at the face points of the block's cells
+  // face points: thread group grp takes the faces f = grp mod N; its
+  // global reads (face codes, the neighbour's node line or its trace, the
+  // penalty coefficient) are issued before the block's first barrier
   constexpr int GS = EPB * NFP;
   const int grp = threadIdx.x / GS, cc = (threadIdx.x % GS) / NFP, tt = threadIdx.x % NFP;
   const int64_t ec = e0 + cc;
+  int codes[NF];
+  T pen[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    codes[f] = -1;
+    pen[f] = 0;
+    if (f % N != grp || ec >= E) continue;
+    const int code = __ldg(cface + ec * NF + f);
+    codes[f] = code;
+    const int64_t sl = ec * NSL + f * NFP + tt;
+    T xp = 0;
+    if (code >= 0) {
+      if (STAGE) {
+        int base, stride;
+        face_line<DIM, N>(f, tt, base, stride);
+        const T* __restrict__ nb = x + (int64_t)code * NP + base;
+#pragma unroll
+        for (int j = 0; j < N; ++j) xp += tb.L[(f & 1) ^ 1][j] * __ldg(nb + j * stride);   // compile-time indices
+      } else {
+        xp = __ldg(tx + ((int64_t)code * NF + (f ^ 1)) * NFP + tt);
+      }
+      if (pcs) pen[f] = __ldg(pcs + sl);
+    } else if (code == -3 && pcs) {
+      pen[f] = __ldg(pcs + sl);
+    }
+    sxp[cc][f * NFP + tt] = xp;
+  }
+  stage_nodes_all<T, N>(geo, sxw);
+  __syncthreads();
+  // numerical fluxes at the face points (own traces from the staged cell)
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
     if (f % N != grp || ec >= E) continue;
-    const int code = scode[cc][f];
+    const int code = codes[f];
     const int r = f * NFP + tt;
     const int64_t sl = ec * NSL + r;
     if (code == -2) {
@@ -176,44 +211,39 @@ k_grad_fused(const T* __restrict__ x, const T* __restrict__ tx, const int* __res
       for (int q = 0; q <= DIM; ++q) slf[cc][q][r] = __ldg(slot + q * S + sl);
       continue;
     }
-    T xm = 0, xp = 0;
+    T xm = 0;
     if (STAGE) {
       int base, stride;
       face_line<DIM, N>(f, tt, base, stride);
-      const T* __restrict__ nb = x + (int64_t)(code >= 0 ? code : 0) * NP + base;
 #pragma unroll
-      for (int j = 0; j < N; ++j) {
-        xm += stb.L[f & 1][j] * sx[cc][base + j * stride];
-        if (code >= 0) xp += stb.L[(f & 1) ^ 1][j] * __ldg(nb + j * stride);
-      }
+      for (int j = 0; j < N; ++j) xm += stb.L[f & 1][j] * sx[cc][base + j * stride];
     } else {
       xm = __ldg(tx + sl);
-      xp = code >= 0 ? __ldg(tx + ((int64_t)code * NF + (f ^ 1)) * NFP + tt) : xm;
     }
     // wall (-1): {x} = x-, no jump; far field (-3): the linear part, the
     // outer state's value is known data of the right-hand side (zero here)
-    if (code == -1) xp = xm;
-    if (code == -3) xp = 0;
+    const T xp = code == -1 ? xm : sxp[cc][r];
     const T avg = code == -1 ? xm : (T)0.5 * (xm + xp);
     T nS[DIM];
     slot_normal<T, DIM, N>(geo, snS, S, ec, f, tt, sl, sxw, nS, tcell ? stc[cc] : nullptr);
 #pragma unroll
     for (int b = 0; b < DIM; ++b) slf[cc][b][r] = -avg * nS[b];
-    slf[cc][DIM][r] = (code == -1 || pcs == nullptr) ? (T)0 : -__ldg(pcs + sl) * (xm - xp);
+    slf[cc][DIM][r] = code == -1 ? (T)0 : -pen[f] * (xm - xp);
   }
+  // volume terms: every flux component -x K_ab staged at once, one barrier
   T K[DIM][DIM], iM = 0;
   if (active) node_metric<T, DIM, N>(geo, e, node, Nn, idx, K, iM, sxw, tcell ? stc[le] : nullptr);
-  T r[DIM + 1];
 #pragma unroll
   for (int b = 0; b < DIM; ++b) {
     const int msk = amask_of<DIM>(geo.terrain, b);
 #pragma unroll
     for (int a = 0; a < DIM; ++a)
-      if ((msk >> a) & 1) sm[le][a][i] = active ? -xv * K[a][b] : (T)0;
-    __syncthreads();
-    r[b] = contract<T, DIM, N>(stb, sm[le], i, idx, msk);
-    __syncthreads();
+      if ((msk >> a) & 1) sm[le][b][a][i] = active ? -xv * K[a][b] : (T)0;
   }
+  __syncthreads();
+  T r[DIM + 1];
+#pragma unroll
+  for (int b = 0; b < DIM; ++b) r[b] = contract<T, DIM, N>(stb, sm[le][b], i, idx, amask_of<DIM>(geo.terrain, b));
   r[DIM] = 0;
   if (!active) return;
   lift_shared<T, DIM, N, DIM + 1>(stb, &slf[le][0][0], idx, r);
@@ -224,7 +254,7 @@ k_grad_fused(const T* __restrict__ x, const T* __restrict__ tx, const int* __res
   T w[3];
   if (ph.r2) {
     const T beta = beta_of<T>(ph, e);
-    const T d = (ph.fcell || ph.fcell32) ? (T)1 / (1 + beta * beta) : kp<T>(ph.dbeta, ph.dbeta_f);
+    const T d = (ph.fcell || ph.fcell32) ? (T)1 / (1 + beta * beta) : kp<T>(ph.dbeta, ph.dbeta_f, ph.dbeta_p);
     w[0] = (G[0] + beta * G[1]) * d * ir;
     w[1] = (G[1] - beta * G[0]) * d * ir;
     w[2] = G[2] * ir;
@@ -237,10 +267,10 @@ k_grad_fused(const T* __restrict__ x, const T* __restrict__ tx, const int* __res
 #pragma unroll
     for (int b = 0; b < DIM; ++b) wv[b * Nn + node] = w[comp_of<DIM>(b)];
     T yv = xv + iM * r[DIM];
-    if (ph.r2) yv -= kp<T>(ph.cgrav, ph.cgrav_f) * G[2];
+    if (ph.r2) yv -= kp<T>(ph.cgrav, ph.cgrav_f, ph.cgrav_p) * G[2];
     y[node] = yv;
   } else {
-    const T adt = kp<T>(ph.a_dt, ph.adt_f);
+    const T adt = kp<T>(ph.a_dt, ph.adt_f, ph.adt_p);
 #pragma unroll
     for (int c = 0; c < 3; ++c) uout[c * Nn + node] = __ldg(ustar + c * Nn + node) - adt * w[c];
   }
@@ -253,17 +283,17 @@ k_grad_fused(const T* __restrict__ x, const T* __restrict__ tx, const int* __res
 //  RHS  : y = (gamma-1) [e_hat - rho |u_lag|^2 / 2 - a_dt (Div + g rho w3_z)],
 //         w3_z = ustar_z (R2) or u_lag_z (R1)
 template <typename T, int DIM, int N, int MODE, bool STAGE>
-__global__ void __launch_bounds__(FusedShape<DIM, N>::THREADS)
+__global__ void __launch_bounds__(FusedShape<DIM, N>::THREADS, FusedOcc<T>::MIN_BLOCKS)
 k_div_fused(Fields<T> wv, const T* __restrict__ tw, const T* __restrict__ trh, const int* __restrict__ cface,
             const T* __restrict__ snS, const T* __restrict__ plag, CellGeo<T> geo, const T* __restrict__ slot,
             int64_t E, int64_t S, Tables<T> tb, ImplK ph, T* __restrict__ y, const T* __restrict__ ehat,
             const T* __restrict__ rho, const T* __restrict__ ulag, const T* __restrict__ ustar) {
   using FS = FusedShape<DIM, N>;
-  constexpr int NP = FS::NP, EPB = FS::EPB, NF = FS::NF, NFP = FS::NFP, NSL = FS::NSL, TH = FS::THREADS;
+  constexpr int NP = FS::NP, EPB = FS::EPB, NF = FS::NF, NFP = FS::NFP, NSL = FS::NSL;
   __shared__ T sw[EPB][DIM][NP];
+  __shared__ T swp[EPB][DIM][NSL];   // plus-side w components at the block's face points
   __shared__ T slf[EPB][NSL];
   __shared__ T sm[EPB][DIM][NP];
-  __shared__ int scode[EPB][NF];
   __shared__ T sxw[2 * N];
   __shared__ T stc[std::is_same<T, float>::value ? EPB : 1][16];
   __shared__ SharedTables<T, N> stb;
@@ -278,7 +308,7 @@ k_div_fused(Fields<T> wv, const T* __restrict__ tw, const T* __restrict__ trh, c
   stage_tables<T, N>(tb, stb);
   int idx[3];
   node_index<DIM, N>(i, idx);
-  const T gam = kp<T>(ph.gamma, ph.gamma_f);
+  const T gam = kp<T>(ph.gamma, ph.gamma_f, ph.gamma_p);
   const T gm1 = gam - 1;
   T wl[DIM];
 #pragma unroll
@@ -286,20 +316,46 @@ k_div_fused(Fields<T> wv, const T* __restrict__ tw, const T* __restrict__ trh, c
     wl[b] = active ? __ldg(wv.f[b] + node) : (T)0;
     sw[le][b][i] = wl[b];
   }
-  for (int k = threadIdx.x; k < EPB * NF; k += TH) {
-    const int c = k / NF, f = k % NF;
-    scode[c][f] = e0 + c < E ? __ldg(cface + (e0 + c) * NF + f) : -1;
-  }
-  stage_nodes_all<T, N>(geo, sxw);
-  __syncthreads();
-  // face points: thread group grp takes the faces f = grp mod N (see above)
+  // face points: thread group grp takes the faces f = grp mod N (see above);
+  // the global reads (codes, h rho traces, the neighbour's w) go first
   constexpr int GS = EPB * NFP;
   const int grp = threadIdx.x / GS, cc = (threadIdx.x % GS) / NFP, tt = threadIdx.x % NFP;
   const int64_t ec = e0 + cc;
+  int codes[NF];
+  T hm[NF], hp[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    codes[f] = -1;
+    hm[f] = hp[f] = 0;
+    if (f % N != grp || ec >= E) continue;
+    const int code = __ldg(cface + ec * NF + f);
+    codes[f] = code;
+    const int64_t sl = ec * NSL + f * NFP + tt;
+    if (code >= 0 || code == -3) hm[f] = __ldg(trh + sl);
+    if (code < 0) continue;
+    const int64_t sp = ((int64_t)code * NF + (f ^ 1)) * NFP + tt;
+    hp[f] = __ldg(trh + sp);
+    int base, stride;
+    face_line<DIM, N>(f, tt, base, stride);
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) {
+      T wp = 0;
+      if (STAGE) {
+        const T* __restrict__ nb = wv.f[b] + (int64_t)code * NP + base;
+#pragma unroll
+        for (int j = 0; j < N; ++j) wp += tb.L[(f & 1) ^ 1][j] * __ldg(nb + j * stride);   // compile-time indices
+      } else {
+        wp = __ldg(tw + b * S + sp);
+      }
+      swp[cc][b][f * NFP + tt] = wp;
+    }
+  }
+  stage_nodes_all<T, N>(geo, sxw);
+  __syncthreads();
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
     if (f % N != grp || ec >= E) continue;
-    const int code = scode[cc][f];
+    const int code = codes[f];
     const int r = f * NFP + tt;
     const int64_t sl = ec * NSL + r;
     if (code == -2) {
@@ -317,26 +373,19 @@ k_div_fused(Fields<T> wv, const T* __restrict__ tw, const T* __restrict__ trh, c
     // own normal flux (w-.n dS) and, on a conforming face, the neighbour's
     // (w+.n dS); far field (-3): the linear part (h rho w)-.n / 2 only
     T fm = 0, fp = 0;
-    const int64_t sp = code >= 0 ? ((int64_t)code * NF + (f ^ 1)) * NFP + tt : sl;
 #pragma unroll
     for (int b = 0; b < DIM; ++b) {
-      T wm = 0, wp = 0;
+      T wm = 0;
       if (STAGE) {
-        const T* __restrict__ nb = wv.f[b] + (int64_t)(code >= 0 ? code : 0) * NP + base;
 #pragma unroll
-        for (int j = 0; j < N; ++j) {
-          wm += stb.L[f & 1][j] * sw[cc][b][base + j * stride];
-          if (code >= 0) wp += stb.L[(f & 1) ^ 1][j] * __ldg(nb + j * stride);
-        }
+        for (int j = 0; j < N; ++j) wm += stb.L[f & 1][j] * sw[cc][b][base + j * stride];
       } else {
         wm = __ldg(tw + b * S + sl);
-        if (code >= 0) wp = __ldg(tw + b * S + sp);
       }
       fm += wm * nS[b];
-      fp += wp * nS[b];
+      if (code >= 0) fp += swp[cc][b][r] * nS[b];
     }
-    slf[cc][r] = code == -3 ? -(T)0.5 * __ldg(trh + sl) * fm
-                            : -(T)0.5 * (__ldg(trh + sl) * fm + __ldg(trh + sp) * fp);
+    slf[cc][r] = -(T)0.5 * (hm[f] * fm + hp[f] * fp);
   }
   T iM = 0;
   if (active) {
@@ -361,7 +410,7 @@ k_div_fused(Fields<T> wv, const T* __restrict__ tw, const T* __restrict__ trh, c
   if (!active) return;
   lift_shared<T, DIM, N, 1>(stb, &slf[le][0], idx, r);
   const T div = iM * r[0];
-  const T adt = kp<T>(ph.a_dt, ph.adt_f);
+  const T adt = kp<T>(ph.a_dt, ph.adt_f, ph.adt_p);
   if (MODE == DIV_VMULT) {
     y[node] -= gm1 * adt * adt * div;
   } else {
@@ -373,7 +422,7 @@ k_div_fused(Fields<T> wv, const T* __restrict__ tw, const T* __restrict__ trh, c
       u2 += uc * uc;
     }
     const T wz = ph.r2 ? __ldg(ustar + 2 * Nn + node) : __ldg(ulag + 2 * Nn + node);
-    y[node] = gm1 * (__ldg(ehat + node) - (T)0.5 * rh * u2 - adt * (div + kp<T>(ph.g, ph.g_f) * rh * wz));
+    y[node] = gm1 * (__ldg(ehat + node) - (T)0.5 * rh * u2 - adt * (div + kp<T>(ph.g, ph.g_f, ph.g_p) * rh * wz));
   }
 }
 
@@ -414,7 +463,7 @@ __global__ void k_far_affine(FaceTopo ft, const int* __restrict__ far_p, int64_t
   const int64_t e = sm / NSL;
   const int t = (sm % NSL) % NFP;
   const T* fq = far_ptr<T>(ft);
-  const T gam = kp<T>(ph.gamma, ph.gamma_f), adt = kp<T>(ph.a_dt, ph.adt_f);
+  const T gam = kp<T>(ph.gamma, ph.gamma_f, ph.gamma_p), adt = kp<T>(ph.a_dt, ph.adt_f, ph.adt_p);
   const T rf = __ldg(fq + g);
   T uf[3], mu = 0;
 #pragma unroll

@@ -872,18 +872,18 @@ int dg_mesh_info(const dg_mesh* m, dg_mesh_stats* o) {
     o->tile_fp32[k] = m->tile32[kinds[k]];
   }
   o->terrain_following = m->terrain ? 1 : 0;
-  o->fused_stage[0] = m->fused_stage[0];
-  o->fused_stage[1] = m->fused_stage[1];
+  for (int k = 0; k < 3; ++k) o->fused_stage[k] = m->fused_stage[k];
   return DG_OK;
 }
 
-int dg_mesh_set_fused_stage(dg_mesh* m, int fp64, int fp32) {
-  if (!m || (fp64 != 0 && fp64 != 1) || (fp32 != 0 && fp32 != 1)) {
+int dg_mesh_set_fused_stage(dg_mesh* m, int fp64, int fp32, int pairs) {
+  if (!m || (fp64 != 0 && fp64 != 1) || (fp32 != 0 && fp32 != 1) || (pairs != 0 && pairs != 1)) {
     set_error("dg_mesh_set_fused_stage: mesh and 0 / 1 per precision required");
     return DG_ERR_ARG;
   }
   m->fused_stage[0] = fp64;
   m->fused_stage[1] = fp32;
+  m->fused_stage[2] = pairs;
   return DG_OK;
 }
 

@@ -148,9 +148,8 @@ static int set_far_state(dg_mesh* m, const double* q, cudaStream_t st) {
   m->far_set = true;
   return DG_OK;
 }
-// FP32 pairs run on the FP32 pipe: they take the FP32 schedule
 template <typename T> inline bool fused_stage(const dg_mesh* m) {
-  return m->fused_stage[std::is_same<T, double>::value ? 0 : 1] != 0;
+  return m->fused_stage[std::is_same<T, double>::value ? 0 : (std::is_same<T, float>::value ? 1 : 2)] != 0;
 }
 
 template <typename T, int DIM, int N>
@@ -562,6 +561,12 @@ ImplK dg::impl_consts(const dg_phys* ph, double a_dt) {
   k.cgrav = (ph->gamma - 1.0) * a_dt * a_dt * ph->g;
   k.dbeta_f = (float)k.dbeta;
   k.cgrav_f = (float)k.cgrav;
+  k.gamma_p = df64(ph->gamma);
+  k.g_p = df64(ph->g);
+  k.adt_p = df64(a_dt);
+  k.beta_p = df64(beta);
+  k.dbeta_p = df64(k.dbeta);
+  k.cgrav_p = df64(k.cgrav);
   return k;
 }
 

@@ -589,6 +589,9 @@ struct ImplK {
   double dbeta, cgrav;
   float dbeta_f, cgrav_f;
   int penalty;           // implicit Rusanov term on (far-field outer data included)
+  // FP32-pair copies (DG_PAIRS kernels): converting a double in the kernel
+  // would issue FP64 instructions in every thread
+  df64 gamma_p, g_p, adt_p, dbeta_p, cgrav_p, beta_p;
 };
 
 // 1/rho of the frozen stage density (read by the gradient cell kernel)
@@ -599,10 +602,10 @@ __global__ void k_recip(const T* __restrict__ a, T* __restrict__ b, int64_t n) {
 }
 
 // kernel parameter in the kernel's precision
-template <typename T> __device__ __forceinline__ T kp(double d, float f);
-template <> __device__ __forceinline__ double kp<double>(double d, float) { return d; }
-template <> __device__ __forceinline__ float kp<float>(double, float f) { return f; }
-template <> __device__ __forceinline__ df64 kp<df64>(double d, float) { return df64(d); }
+template <typename T> __device__ __forceinline__ T kp(double d, float f, df64 p);
+template <> __device__ __forceinline__ double kp<double>(double d, float, df64) { return d; }
+template <> __device__ __forceinline__ float kp<float>(double, float f, df64) { return f; }
+template <> __device__ __forceinline__ df64 kp<df64>(double, float, df64 p) { return p; }
 
 // beta = a_dt f of cell e (Section 3.1)
 template <typename T> __device__ __forceinline__ T beta_of(const ImplK& ph, int64_t e);
@@ -613,7 +616,7 @@ template <> __device__ __forceinline__ float beta_of<float>(const ImplK& ph, int
   return ph.adt_f * (ph.fcell32 ? __ldg(ph.fcell32 + e) : ph.f_f);
 }
 template <> __device__ __forceinline__ df64 beta_of<df64>(const ImplK& ph, int64_t e) {
-  return df64(ph.a_dt * coriolis(ph.fcell, ph.f, e));
+  return ph.fcell ? df64(ph.a_dt * __ldg(ph.fcell + e)) : ph.beta_p;
 }
 
 // Per-node metric K_ab = w det(J) (J^{-1})_ab and 1/(w det J) of the

@@ -842,12 +842,13 @@ __global__ void k_fill(double* __restrict__ a, int64_t n, double v) {
 // multiplier (cells per block) of the explicit operator's cell kernel
 // (FP64), and the source of the plus-side traces in the fused Schur vmult
 // (staged neighbour cells or a trace array), timed over whole vmults.
-static int tune_precision(dg_mesh* m, bool fp32, const double* q, const double* rho, const double* p,
+static int tune_precision(dg_mesh* m, int prec, const double* q, const double* rho, const double* p,
                           const double* u, double* x, double* y, double* fns, double* fs, cudaStream_t st) {
-  dg_phys ph{1.4, 9.81, 1e-4, DG_R2, 1, fp32 ? DG_MIXED : DG_FP64, nullptr, 0.0};
+  const bool fp32 = prec != DG_FP64 && prec != DG_PAIRS;
+  dg_phys ph{1.4, 9.81, 1e-4, DG_R2, 1, prec, nullptr, 0.0};
   ImplK k = impl_consts(&ph, 1.0);
   int rc;
-  if (!fp32) {
+  if (prec == DG_FP64) {
     const int cand[3] = {1, 2, 4};
     double best = 1e300;
     int pick = 1;
@@ -880,14 +881,19 @@ static int tune_precision(dg_mesh* m, bool fp32, const double* q, const double* 
     return cuda_fail(cudaGetLastError(), "cudaEventCreate");
   }
   double best = 1e300;
-  int pick = m->fused_stage[fp32 ? 1 : 0];
+  const int slot = prec == DG_FP64 ? 0 : (prec == DG_PAIRS ? 2 : 1);
+  int pick = m->fused_stage[slot];
   rc = DG_OK;
   for (int sv = 0; sv < 2 && rc == DG_OK; ++sv) {
-    m->fused_stage[fp32 ? 1 : 0] = sv;
+    m->fused_stage[slot] = sv;
     SchurCtx sc{m, k, rho, p, 1};
     Schur32Ctx sc32;
+    SchurDfCtx sdf;
     Vmult A{nullptr, nullptr};
-    if (fp32) {
+    if (prec == DG_PAIRS) {
+      if ((rc = prepare_pairs(m, k, rho, p, u, 1, st, &sdf)) != DG_OK) break;
+      A = make_vmult_pairs(&sdf);
+    } else if (fp32) {
       if ((rc = prepare32(m, k, rho, p, u, 1, st, &sc32)) != DG_OK) break;
       A = make_vmult32(&sc32);
     } else {
@@ -912,7 +918,7 @@ static int tune_precision(dg_mesh* m, bool fp32, const double* q, const double* 
       pick = sv;
     }
   }
-  m->fused_stage[fp32 ? 1 : 0] = pick;
+  m->fused_stage[slot] = pick;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return rc;
@@ -925,10 +931,11 @@ extern "C" int dg_mesh_autotune(dg_ctx* ctx, dg_mesh* m, int precision, void* st
     set_error("dg_mesh_autotune: NULL argument");
     return DG_ERR_ARG;
   }
-  if (precision != DG_FP64 && precision != DG_MIXED && precision != DG_MIXED_EXPLICIT) {
-    set_error("dg_mesh_autotune: precision must be DG_FP64, DG_MIXED or DG_MIXED_EXPLICIT");
+  if (precision != DG_FP64 && precision != DG_MIXED && precision != DG_MIXED_EXPLICIT && precision != DG_PAIRS) {
+    set_error("dg_mesh_autotune: precision must be DG_FP64, DG_MIXED, DG_MIXED_EXPLICIT or DG_PAIRS");
     return DG_ERR_ARG;
   }
+  if (precision == DG_PAIRS && (m->gll || m->nFar > 0)) precision = DG_FP64;   // no pair vmult there
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t n = m->N;
   double* buf = nullptr;
@@ -946,8 +953,8 @@ extern "C" int dg_mesh_autotune(dg_ctx* ctx, dg_mesh* m, int precision, void* st
   k_fill<<<gb, 256, 0, st>>>(u, 3 * n, 10.0);
   k_fill<<<gb, 256, 0, st>>>(x, n, 1.0);
   int rc = cudaGetLastError() == cudaSuccess ? DG_OK : DG_ERR_CUDA;
-  if (rc == DG_OK) rc = tune_precision(m, false, q, rho, p, u, x, y, fns, fs, st);
-  if (rc == DG_OK && precision != DG_FP64) rc = tune_precision(m, true, q, rho, p, u, x, y, fns, fs, st);
+  if (rc == DG_OK) rc = tune_precision(m, DG_FP64, q, rho, p, u, x, y, fns, fs, st);
+  if (rc == DG_OK && precision != DG_FP64) rc = tune_precision(m, precision, q, rho, p, u, x, y, fns, fs, st);
   cudaStreamSynchronize(st);
   cudaFree(buf);
   return rc;

@@ -44,7 +44,7 @@ class MeshStats(C.Structure):
                 ("n_face_points", C.c_int64), ("n_hang_points", C.c_int64),
                 ("workspace_bytes", C.c_int64), ("tile_fp64", C.c_int * 3),
                 ("tile_fp32", C.c_int * 3), ("terrain_following", C.c_int),
-                ("fused_stage", C.c_int * 2)]
+                ("fused_stage", C.c_int * 3)]
 
 
 class Sponge(C.Structure):
@@ -148,7 +148,7 @@ EXPORTS["dg_ensemble_get_state"] = (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C
 EXPORTS["dg_ensemble_step"] = (C.c_int, [C.c_void_p, C.POINTER(Phys), C.POINTER(C.c_double),
                                          C.POINTER(StepOpts), C.POINTER(StepInfo), C.c_void_p])
 EXPORTS["dg_mesh_autotune"] = (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p])
-EXPORTS["dg_mesh_set_fused_stage"] = (C.c_int, [C.c_void_p, C.c_int, C.c_int])
+EXPORTS["dg_mesh_set_fused_stage"] = (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int])
 EXPORTS["dg_mesh_set_far_state"] = (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p])
 EXPORTS["dg_geostrophic_error"] = (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Phys), C.c_void_p,
                                               C.POINTER(C.c_double), C.c_void_p])
@@ -350,10 +350,11 @@ class Mesh:
         _check(self.lib.dg_mesh_set_far_state(self.ctx.h, self.h, self._p(q_far, 5), _stream(stream)),
                "dg_mesh_set_far_state")
 
-    def set_fused_stage(self, fp64, fp32):
-        """Schedule of the fused vmult kernels per precision (1: staged
-        neighbour cells, 0: trace array); see dg_mesh_set_fused_stage."""
-        _check(self.lib.dg_mesh_set_fused_stage(self.h, int(fp64), int(fp32)), "dg_mesh_set_fused_stage")
+    def set_fused_stage(self, fp64, fp32, pairs=0):
+        """Schedule of the fused vmult kernels per precision (1: neighbour
+        node lines, 0: trace array); see dg_mesh_set_fused_stage."""
+        _check(self.lib.dg_mesh_set_fused_stage(self.h, int(fp64), int(fp32), int(pairs)),
+               "dg_mesh_set_fused_stage")
 
     def stats(self) -> MeshStats:
         s = MeshStats()

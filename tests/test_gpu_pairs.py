@@ -78,7 +78,7 @@ def test_pairs_vmult_parity(D, ctx, name, variant, penalty):
     ref = O.schur_apply(disc, cf, ph, x)
     t = (to_dev(q[0].reshape(-1)), to_dev(p.reshape(-1)), to_dev(u.reshape(3, -1)))
     dcf = D.Mesh.coeffs(*t, cf.adt)
-    for stage in ((0, 0), (0, 1)):
+    for stage in ((0, 1, 0), (0, 1, 1)):   # both schedules of the pair kernels
         gm.set_fused_stage(*stage)
         y = from_dev(gm.apply_implicit(D.make_phys(f=1.3e-4, variant=variant, penalty=penalty, precision="pairs"),
                                        dcf, to_dev(x.reshape(-1))), ref.shape)
