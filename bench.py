@@ -83,9 +83,10 @@ def work_model(dim, n, N, S, nF, nnz=None):
 
 
 # DRAM bytes per node of one launch, from an ncu capture of the current
-# kernel on the 30 x 30 x 20 hill (profiles/volume_grad_hill3d_30x30x20_r3_fp64.md:
-# 147.9 MB over 1 152 000 nodes), scaled to a launch by the nodes it processes.
-NCU_TRAFFIC_B_PER_NODE = {}
+# fused FP64 gradient pass (trace-array schedule) on the 30 x 30 x 20 hill
+# (profiles/fused_vmult_hill3d_30x30x20_r3.md: 143.1 MB read + 21.2 MB
+# written over 1 152 000 nodes), scaled to a launch by the nodes it processes.
+NCU_TRAFFIC_B_PER_NODE = {"volume_grad": (143.097856e6 + 21.227776e6) / 1152000}
 
 
 def bytes_model(dim, n, N, S, nF, nnz=None):
@@ -724,6 +725,11 @@ def gpu_main(args):
     mesh = D.Mesh(ctx, mesh_h, r)
     tiles = mesh.autotune("mixed")
     tiles = [tiles[0], tiles[1], mesh.autotune("pairs")[2]]
+    if args.schedule is not None:
+        # fixed fused vmult schedule (a profiler slows launches unevenly, so
+        # the timed choice made under it can differ from the plain run's)
+        mesh.set_fused_stage(*args.schedule)
+        tiles[2] = list(args.schedule)
     st = mesh.stats()
     N = st.n_nodes
     xyz = mesh.node_coords().cpu().numpy().T
@@ -840,9 +846,10 @@ def gpu_main(args):
         achieved = flops / (per_launch_ms / 1e3) / 1e12 if flops else None
         roof = {"bound": "alu", "kernel": dominant, "achieved": achieved,
                 "peak": fp64_peak, "unit": "TFLOP/s", "frac": achieved / fp64_peak if achieved else None,
+                # the capture is of the trace-array FP64 schedule only
                 "traffic": (NCU_TRAFFIC_B_PER_NODE[dominant] * N
                             if dominant in NCU_TRAFFIC_B_PER_NODE and st.dim == 3 and st.n1d == 4
-                            else None),
+                            and tiles[2][0] == 0 else None),
                 "peak_source": "measured in this run: dg_probe_fma, FP64 FMA chains filling every SM "
                                "(best of 5); nominal GB300 FP64 1.25 TFLOP/s",
                 "frac_of_nominal_fp64": achieved / FP64_NOMINAL_TFLOPS if achieved else None,
@@ -997,6 +1004,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--schedule", type=int, nargs=3, default=None,
+                    help="fused vmult schedule of FP64, FP32, pairs (1: node lines, 0: trace array) "
+                         "instead of the timed choice")
     ap.add_argument("--oracle-child", default=None)
     args = ap.parse_args()
     if args.oracle_child:

@@ -3,10 +3,15 @@
     python -m paper_2605_29598_gb300.profile_case --op vmult --reps 3
     python -m paper_2605_29598_gb300.profile_case --op explicit --cells 30 30 20
     python -m paper_2605_29598_gb300.profile_case --op precond --cells 30 30 20
+    python -m paper_2605_29598_gb300.profile_case --op vmult --cells 30 30 20 \
+        --precision fp64 mixed pairs --schedule 0 1 0
 
 Builds the mesh and state of the hill workload (optionally with fewer
 cells), prepares one set of implicit coefficients from the state and runs
-`reps` applies of the chosen operator (no timing; pair it with ncu -k).
+`reps` applies of the chosen operator per precision named (no timing; pair
+it with ncu -k).  --schedule sets the fused vmult schedule of FP64, FP32 and
+FP32 pairs (1: neighbour node lines, 0: trace array) instead of the mesh
+default.
 """
 from __future__ import annotations
 
@@ -22,7 +27,8 @@ def main():
     ap.add_argument("--cells", type=int, nargs=3, default=[60, 60, 20])
     ap.add_argument("--degree", type=int, default=3)
     ap.add_argument("--refine", action="store_true")
-    ap.add_argument("--precision", choices=["fp64", "mixed"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "mixed", "pairs"], nargs="+", default=["fp64"])
+    ap.add_argument("--schedule", type=int, nargs=3, default=None)
     args = ap.parse_args()
 
     import torch
@@ -40,13 +46,23 @@ def main():
     xyz = mesh.node_coords().cpu().numpy().T
     q = torch.tensor(I.stratified_state(xyz, **case["state_params"]), dtype=torch.float64,
                      device="cuda").contiguous()
-    phys = D.make_phys(f=case["f"], precision=args.precision)
     rho = q[0].contiguous()
     u = (q[1:4] / q[0]).contiguous()
     p = (0.4 * (q[4] - 0.5 * (q[1:4] * u).sum(0))).contiguous()
     cf = D.Mesh.coeffs(rho, p, u, 0.29289321881345254 * case["dt"])
     x = (p * (1 + 1e-3 * torch.randn_like(p))).contiguous()
     y = torch.empty_like(x)
+    if args.schedule is not None:
+        mesh.set_fused_stage(*args.schedule)
+    for prec in args.precision:
+        phys = D.make_phys(f=case["f"], precision=prec)
+        run(args, mesh, phys, q, cf, x, y)
+    torch.cuda.synchronize()
+    print(f"{args.op}: {args.reps} applies per precision ({' '.join(args.precision)}) on {mesh.n_elem} cells, "
+          f"{mesh.N} nodes")
+
+
+def run(args, mesh, phys, q, cf, x, y):
     for _ in range(args.reps):
         if args.op == "vmult":
             mesh.apply_implicit(phys, cf, x, y)
@@ -58,8 +74,6 @@ def main():
             mesh.schur_rhs(phys, cf, q[1:4].contiguous(), q[4].contiguous(), y)
         else:
             mesh.recover_velocity(phys, cf, q[1:4].contiguous(), x)
-    torch.cuda.synchronize()
-    print(f"{args.op}: {args.reps} applies on {mesh.n_elem} cells, {mesh.N} nodes")
 
 
 if __name__ == "__main__":
