@@ -466,12 +466,16 @@ def run_per_operator(D, mesh, q, f, a_dt, hbm_gbs, reps=10):
             mesh.apply_implicit(ph, cf, x, y)
         prof = D.profile_end(mesh)
         g, dv = prof["volume_grad"], prof["volume_div"]
-        stage = st.fused_stage[0 if prec == "fp64" else 1]
+        slot = {"fp64": 0, "mixed": 1, "pairs": 2}[prec]
+        sched = st.fused_stage[slot]
         ms = (g[2] + dv[2]) / reps
+        names = {0: "trace array (plus two trace passes per vmult, about trace_ms_per_launch each)",
+                 1: "neighbour node lines", 2: "one thread per x-line"}
         r = {"grad_ms": g[2] / max(g[1], 1), "div_ms": dv[2] / max(dv[1], 1), "fused_passes_ms": ms,
-             "schedule": "neighbour node lines" if stage else
-                         "trace array (plus two trace passes per vmult, about trace_ms_per_launch each)",
+             "schedule": names.get(sched, str(sched)),
              "trace_ms_per_launch": prof["trace"][2] / max(prof["trace"][1], 1)}
+        if sched == 2 and prec != "pairs":
+            r["cells_per_block_multiplier"] = (st.tile_fp64 if prec == "fp64" else st.tile_fp32)[1]
         if prec == "mixed":
             gbs = bpn * N / (ms / 1e3) / 1e9
             r.update({"algorithmic_bytes_per_node": bpn, "gb_per_s": gbs, "frac_of_measured_hbm": gbs / hbm_gbs})
@@ -1005,7 +1009,8 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--schedule", type=int, nargs=3, default=None,
-                    help="fused vmult schedule of FP64, FP32, pairs (1: node lines, 0: trace array) "
+                    help="fused vmult schedule of FP64, FP32, pairs (1: node lines, 0: trace array, "
+                         "2: one thread per x-line) "
                          "instead of the timed choice")
     ap.add_argument("--oracle-child", default=None)
     args = ap.parse_args()

@@ -127,24 +127,24 @@ typedef struct {
   int64_t workspace_bytes;   /* library-owned device memory held now */
   int tile_fp64[3];          /* cells-per-block multipliers (1, 2, 4) of the */
   int tile_fp32[3];          /* explicit, gradient and divergence cell kernels
-                                (the fused gradient and divergence passes of the
-                                Schur vmult run one tile size: entries 1 and 2
-                                are informational) */
+                                (entries 1 and 2: the schedule-2 vmult passes;
+                                the other fused schedules run one tile size) */
   int terrain_following;     /* 1: every cell has x = x(xi_1) (and y = y(xi_2)),
                                 so the cell kernels skip the metric terms that
                                 vanish exactly (not in the paper) */
   int fused_stage[3];        /* FP64, FP32, FP32-pair Schur vmult: 1 =
                                 plus-side face values from the neighbour
                                 cells' node lines, 0 = from a trace array
-                                written by a separate pass (see
-                                dg_mesh_set_fused_stage) */
+                                written by a separate pass, 2 = one thread
+                                per x-line (see dg_mesh_set_fused_stage) */
 } dg_mesh_stats;
 int dg_mesh_info(const dg_mesh* mesh, dg_mesh_stats* out);
 
 /* Schedule autotuner (not in the paper): times the explicit operator's
  * cell kernel with 1, 2 and 4 times the base number of cells per thread
- * block, and whole Schur vmults with either fused-kernel schedule (see
- * dg_mesh_set_fused_stage), on this mesh (synthetic coefficients, CUDA
+ * block, and whole Schur vmults with every fused-kernel schedule (see
+ * dg_mesh_set_fused_stage; schedule 2 with 1, 2 and 4 times its base cells
+ * per block), on this mesh (synthetic coefficients, CUDA
  * events), and keeps the fastest, for FP64 and, when precision is DG_MIXED
  * or DG_MIXED_EXPLICIT, for the FP32 vmult too, when it is DG_PAIRS for the
  * FP32-pair vmult.  Allocates temporary device memory; synchronises
@@ -157,10 +157,21 @@ int dg_mesh_autotune(dg_ctx* ctx, dg_mesh* mesh, int precision, void* stream);
  * each face point and contracts it to the face in the kernel (no trace
  * pass, more arithmetic), 0 reads the neighbour's face values from a trace
  * array that a separate pass writes (less arithmetic, more memory
- * traffic).  Both give the same results up to rounding.  Defaults: FP64 0,
- * FP32 1, pairs 0; dg_mesh_autotune times both and keeps the faster.  Host
- * only, no GPU work. */
+ * traffic), 2 runs the two vmult passes with one thread per x-line of a
+ * cell (three dimensions, degree 3, vectors 16-byte aligned: 128-bit loads,
+ * the x-direction work in registers; elsewhere, and for the right-hand
+ * side and the recovery, 2 acts as 1).  All give the same results up to
+ * rounding.  Defaults: FP64 0, FP32 1, pairs 0; dg_mesh_autotune times them
+ * and keeps the fastest.  DG_ERR_ARG for values outside 0..2.  Host only,
+ * no GPU work. */
 int dg_mesh_set_fused_stage(dg_mesh* mesh, int fp64, int fp32, int pairs);
+
+/* Cells per block of the schedule-2 vmult passes, as a multiplier tile
+ * (1, 2 or 4) of the base count, for one precision (DG_FP64, DG_MIXED or
+ * DG_MIXED_EXPLICIT for the FP32 vmult, DG_PAIRS); dg_mesh_autotune sets it
+ * together with the schedule.  DG_ERR_ARG for other values.  Host only, no
+ * GPU work. */
+int dg_mesh_set_vmult_tile(dg_mesh* mesh, int precision, int tile);
 
 /* Physical coordinates of all nodes: xyz[dim][cell][node] (device, FP64). */
 int dg_mesh_node_coords(dg_ctx* ctx, const dg_mesh* mesh, double* xyz, void* stream);

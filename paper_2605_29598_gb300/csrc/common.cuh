@@ -163,7 +163,8 @@ struct dg_mesh {
   dg::DBuf pcs, pcs32, snS;
   int fused_stage[3] = {0, 1, 0};   // per precision (FP64, FP32, FP32 pairs): plus-side
                                     // values from the neighbour's node lines (1) or a
-                                    // trace array (0)
+                                    // trace array (0); 2: one thread per x-line of a cell
+                                    // (3D, degree 3; elsewhere as 1)
   // background of the perturbation-form explicit operator (mixed precision)
   dg::DBuf bg, bg32, bgF, bgtr, bgjump, pert32;
   // device-driven step (CUDA graph): solver state and fixed work vectors
@@ -191,6 +192,7 @@ struct dg_mesh {
   // cells-per-block multiplier of the cell kernels, per class (FP64, FP32)
   int tile[dg::K_COUNT] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};
   int tile32[dg::K_COUNT] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};
+  int tilep[dg::K_COUNT] = {1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1, 1};   // FP32 pairs
   // every cell terrain-following: x depends on xi_1 only and y on xi_2 only
   // (rectangular footprints, any vertical map), so the metric terms
   // K_ab = w det(J) (J^-1)_ab vanish exactly for (a, b) = (1, y), (1, z),

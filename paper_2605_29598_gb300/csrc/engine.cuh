@@ -108,7 +108,8 @@ int schur_vmult_mixed(dg_mesh* m, const ImplK& k, const double* rho, const doubl
 // Run the statement list with the tile multiplier M_ (cells per block =
 // M_ x the base count) chosen for kernel class `kid` of the mesh.
 template <typename T> inline int tile_of(const dg_mesh* m, int kid) {
-  return std::is_same<T, float>::value ? m->tile32[kid] : m->tile[kid];
+  return std::is_same<T, float>::value ? m->tile32[kid]
+                                       : (std::is_same<T, double>::value ? m->tile[kid] : m->tilep[kid]);
 }
 #define DG_TILE(m, kid, ...)                                         \
   switch (tile_of<T>((m), kid)) {                                    \

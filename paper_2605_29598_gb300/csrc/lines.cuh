@@ -1,0 +1,497 @@
+// Line-per-thread form of the two fused Schur-vmult passes (3D, n = 4 nodes
+// per direction, degree 3): the same operators as k_grad_fused /
+// k_div_fused in VMULT mode (Section 3: the weak gradient with centred face
+// values and the implicit Rusanov jump, then the weak divergence of h rho w
+// with the centred face flux), with fewer issued instructions per node.
+//
+// A cell is served by n^2 = 16 threads; thread t = jy + n jz owns the x-line
+// of nodes (0..n-1, jy, jz), which is 16 contiguous bytes (FP32) in the
+// element-major layout, so its values, the coefficients on it and the
+// results move with 128-bit loads and stores.  On that line:
+//  - the x-direction contraction and both x-faces' traces and lifts stay in
+//    registers with compile-time table entries;
+//  - the y and z contractions read the staged flux components of the whole
+//    cell with one 128-bit shared load per quadrature point (the four
+//    values along x share the table entry of the thread's own jy or jz);
+//  - the thread evaluates one point of every face: (jy, jz) on the x-faces,
+//    (x = jy, z = jz) on the y-faces, (x = jy, y = jz) on the z-faces, so the
+//    face work is spread evenly; the lift values of the y and z faces pass
+//    through shared memory and are read back 128 bits at a time.
+// Staged cells use a padded z-plane stride (n^2 + 4 values) so that the
+// strided y- and z-line reads of the face traces are free of bank conflicts.
+// The kernels serve terrain-following meshes (five metric terms per node;
+// every mesh of the paper's workloads); the host keeps the other schedules
+// for general cells.
+#pragma once
+
+#include "fused.cuh"
+
+namespace dg {
+
+template <int EPB_>
+struct LineShape {
+  static constexpr int N = 4, NP = 64, NFP = 16, NF = 6, NSL = NF * NFP;
+  static constexpr int EPB = EPB_;
+  static constexpr int PL = N * N + 4;   // padded z-plane stride of a staged cell
+  static constexpr int CSZ = N * PL;     // staged cell
+  static constexpr int THREADS = EPB * NFP;
+};
+
+// 4 consecutive values, 16-byte aligned: global read-only loads, global
+// stores, shared loads and shared stores
+template <typename T> __device__ __forceinline__ void ld4g(const T* __restrict__ p, T v[4]);
+template <> __device__ __forceinline__ void ld4g<float>(const float* __restrict__ p, float v[4]) {
+  const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+  v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+template <> __device__ __forceinline__ void ld4g<double>(const double* __restrict__ p, double v[4]) {
+  const double2 a = __ldg(reinterpret_cast<const double2*>(p));
+  const double2 b = __ldg(reinterpret_cast<const double2*>(p) + 1);
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+template <> __device__ __forceinline__ void ld4g<df64>(const df64* __restrict__ p, df64 v[4]) {
+  const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+  const float4 b = __ldg(reinterpret_cast<const float4*>(p) + 1);
+  v[0] = df64(a.x, a.y); v[1] = df64(a.z, a.w); v[2] = df64(b.x, b.y); v[3] = df64(b.z, b.w);
+}
+template <typename T> __device__ __forceinline__ void st4(T* p, const T v[4]);
+template <> __device__ __forceinline__ void st4<float>(float* p, const float v[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+template <> __device__ __forceinline__ void st4<double>(double* p, const double v[4]) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+}
+template <> __device__ __forceinline__ void st4<df64>(df64* p, const df64 v[4]) {
+  reinterpret_cast<float4*>(p)[0] = make_float4(v[0].hi, v[0].lo, v[1].hi, v[1].lo);
+  reinterpret_cast<float4*>(p)[1] = make_float4(v[2].hi, v[2].lo, v[3].hi, v[3].lo);
+}
+template <typename T> __device__ __forceinline__ void ld4s(const T* p, T v[4]);
+template <> __device__ __forceinline__ void ld4s<float>(const float* p, float v[4]) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+template <> __device__ __forceinline__ void ld4s<double>(const double* p, double v[4]) {
+  const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+template <> __device__ __forceinline__ void ld4s<df64>(const df64* p, df64 v[4]) {
+  const float4 a = reinterpret_cast<const float4*>(p)[0], b = reinterpret_cast<const float4*>(p)[1];
+  v[0] = df64(a.x, a.y); v[1] = df64(a.z, a.w); v[2] = df64(b.x, b.y); v[3] = df64(b.z, b.w);
+}
+
+// Terrain-following cells only (every cell x = x(xi_1), y = y(xi_2)): of
+// the metric K_ab = w det(J) (J^{-1})_ab the five terms that do not vanish,
+// in the order K00, K11, K20, K21, K22 (stored-array index a * 3 + b below),
+// and 1/(w det J), on the thread's own x-line nodes (ix, jy, jz).  FP64 and
+// pairs load the stored metric; FP32 recomputes it from the cell's 16
+// terrain coefficients (tcs, shared).  xj, xk: the nodes at jy and jz; wjk:
+// the product of their weights.  Indices are 32-bit: the host takes this
+// schedule only while every offset fits.
+__host__ __device__ constexpr int line_term(int j) { return j == 0 ? 0 : (j == 1 ? 4 : j + 4); }
+
+template <typename T>
+__device__ __forceinline__ void line_metric(const CellGeo<T>& g, int n0, int Nn, T xj, T xk, T wjk,
+                                            const T* tcs, T Kt[5][4], T iM[4]) {
+  if (!std::is_same<T, float>::value || tcs == nullptr) {
+#pragma unroll
+    for (int j = 0; j < 5; ++j) ld4g<T>(g.K + (int64_t)line_term(j) * Nn + n0, Kt[j]);
+    ld4g<T>(g.invM + n0, iM);
+    return;
+  }
+#pragma unroll
+  for (int ix = 0; ix < 4; ++ix) {
+    const T xi[3] = {g.x[ix], xj, xk};
+    const T wq = g.w[ix] * wjk;
+    T K[3][3], det;
+    terrain_row<T, 3>(tcs, xi, K, det);
+    Kt[0][ix] = K[0][0] * wq;
+    Kt[1][ix] = K[1][1] * wq;
+    Kt[2][ix] = K[2][0] * wq;
+    Kt[3][ix] = K[2][1] * wq;
+    Kt[4][ix] = K[2][2] * wq;
+    iM[ix] = 1 / (wq * det);
+  }
+}
+
+// Outward n dS at the thread's point of face f (tangential nodes xj, xk in
+// increasing direction order): loaded per slot (FP64, pairs) or recomputed
+// from the terrain coefficients (FP32), as slot_normal does.
+template <typename T>
+__device__ __forceinline__ void line_face_normal(const T* __restrict__ snS, int S, int f, int sl, T xj, T xk,
+                                                 T wjk, const T* tcs, T nS[3]) {
+  if (!std::is_same<T, float>::value || snS) {
+#pragma unroll
+    for (int b = 0; b < 3; ++b) nS[b] = __ldg(snS + b * S + sl);
+    return;
+  }
+  const int a = f >> 1, s = f & 1;
+  T xi[3];
+  xi[a] = (T)s;
+  xi[a == 0 ? 1 : 0] = xj;
+  xi[a == 2 ? 1 : 2] = xk;
+  T C[3][3], det;
+  terrain_row<T, 3>(tcs, xi, C, det);
+  const T sw = s ? wjk : -wjk;
+#pragma unroll
+  for (int b = 0; b < 3; ++b) nS[b] = sw * C[a][b];
+}
+
+// The neighbour's line through the thread's point of face f (direction
+// f / 2), contracted to the neighbour's face f ^ 1: x-lines are one vector
+// load, y- and z-lines n strided loads.
+template <typename T>
+__device__ __forceinline__ T plus_trace(const Tables<T>& tb, const T* __restrict__ nb, int f, int t, int jy,
+                                        int jz) {
+  const int a = f >> 1, s = (f & 1) ^ 1;
+  T v[4];
+  if (a == 0) {
+    ld4g<T>(nb + 4 * t, v);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = __ldg(nb + (a == 1 ? jy + 4 * k + 16 * jz : jy + 4 * jz + 16 * k));
+  }
+  T acc = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) acc += tb.L[s][k] * v[k];
+  return acc;
+}
+
+// own trace at the thread's point of face f from the staged cell (stride PL
+// between z-planes) or, on x-faces, from the thread's registers
+template <typename T, int PL>
+__device__ __forceinline__ T own_trace(const Tables<T>& tb, const T* sc, const T xl[4], int f, int jy, int jz) {
+  const int a = f >> 1, s = f & 1;
+  T acc = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const T v = a == 0 ? xl[k] : sc[a == 1 ? jy + 4 * k + PL * jz : jy + 4 * jz + PL * k];
+    acc += tb.L[s][k] * v;
+  }
+  return acc;
+}
+
+// cells per block for the tile multiplier M (1, 2, 4); 8-byte types stop at
+// 4 cells (static shared memory stays below 48 KB)
+template <typename T>
+constexpr int line_epb(int M) {
+  return sizeof(T) == 4 ? 2 * M : (M >= 2 ? 4 : 2);
+}
+
+// resident blocks per SM asked of the register allocator: FP32 at most
+// kLineReg32 registers per thread (more resident warps hide the load
+// latency that binds these kernels), the 8-byte types up to 255
+constexpr int kLineReg32 = 80;
+template <typename T, int EPB>
+struct LineOcc {
+  static constexpr int MIN_BLOCKS = sizeof(T) == 4 ? 65536 / (kLineReg32 * EPB * 16) : 256 / (EPB * 16);
+};
+
+// Gradient pass (VMULT): w = rho^{-1} (I + beta J)^{-1} G (R2) or G / rho
+// (R1); y = x + pen - (gamma-1) a_dt^2 g G_z (R2).  Same arguments and
+// face semantics as k_grad_fused (cell face codes: >= 0 neighbour, -1
+// wall, -2 2:1 face with slot values, -3 far field).
+template <typename T, int EPB>
+__global__ void __launch_bounds__(LineShape<EPB>::THREADS, LineOcc<T, EPB>::MIN_BLOCKS)
+k_grad_lines(const T* __restrict__ x, const int* __restrict__ cface, const T* __restrict__ snS,
+             const T* __restrict__ pcs, const T* __restrict__ irho, CellGeo<T> geo, const T* __restrict__ slot,
+             int E, int S, Tables<T> tb, ImplK ph, T* __restrict__ wv, T* __restrict__ y) {
+  using LS = LineShape<EPB>;
+  constexpr int N = LS::N, NP = LS::NP, NFP = LS::NFP, NF = LS::NF, NSL = LS::NSL, PL = LS::PL, CSZ = LS::CSZ;
+  __shared__ __align__(16) T sx[EPB][CSZ];
+  // -x K_ab staged for the y and z contractions: (a, b) = (2, 0), (1, 1), (2, 1), (2, 2)
+  __shared__ __align__(16) T sF[EPB][4][CSZ];
+  __shared__ __align__(16) T slf[EPB][4][4][NFP];   // lift values of faces 2..5, fields 0..3
+  // per face: the neighbour's trace and the penalty coefficient, kept by
+  // each thread for itself across the barrier
+  __shared__ T sfp[EPB][NF][2][NFP];
+  __shared__ __align__(16) T stc[std::is_same<T, float>::value ? EPB : 1][16];
+  __shared__ SharedTables<T, N> stb;
+  __shared__ T sxw[2 * N];
+  const int c = threadIdx.x / NFP, t = threadIdx.x % NFP, jy = t % N, jz = t / N;
+  const int e0 = blockIdx.x * EPB, e = e0 + c;
+  const bool active = e < E;
+  const int Nn = E * NP;
+  const int n0 = (active ? e : 0) * NP + N * t;
+  const bool tcell = std::is_same<T, float>::value && geo.tc != nullptr;
+  stage_terrain<T, EPB>(geo, e0, E, stc);
+  stage_tables<T, N>(tb, stb);
+  stage_nodes_all<T, N>(geo, sxw);
+  T xl[N] = {0, 0, 0, 0};
+  if (active) ld4g<T>(x + n0, xl);
+  st4<T>(&sx[c][N * jy + PL * jz], xl);
+  // global reads first: face codes, the neighbours' traces, penalties, 1/rho
+  int codes[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    const int code = active ? __ldg(cface + e * NF + f) : -1;
+    codes[f] = code;
+    T xp = 0, pen = 0;
+    const int sl = e * NSL + f * NFP + t;
+    if (code >= 0) {
+      xp = plus_trace<T>(tb, x + code * NP, f, t, jy, jz);
+      if (pcs) pen = __ldg(pcs + sl);
+    } else if (code == -3 && pcs) {
+      pen = __ldg(pcs + sl);
+    }
+    sfp[c][f][0][t] = xp;
+    sfp[c][f][1][t] = pen;
+  }
+  T ir[N] = {0, 0, 0, 0};
+  if (active) ld4g<T>(irho + n0, ir);
+  __syncthreads();
+  const T xj = sxw[jy], xk = sxw[jz], wjk = sxw[N + jy] * sxw[N + jz];
+  const T* tcs = tcell ? stc[c] : nullptr;
+  // volume term: the x-direction in registers, the others staged
+  T r[4][N], iM[N];
+  {
+    T Kt[5][N];
+    line_metric<T>(geo, n0, Nn, xj, xk, wjk, tcs, Kt, iM);
+    T F[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) F[k] = -xl[k] * Kt[0][k];
+#pragma unroll
+    for (int ix = 0; ix < N; ++ix) {
+      r[0][ix] = 0;
+#pragma unroll
+      for (int k = 0; k < N; ++k) r[0][ix] += tb.D[k][ix] * F[k];
+      r[1][ix] = r[2][ix] = r[3][ix] = 0;
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+#pragma unroll
+      for (int k = 0; k < N; ++k) F[k] = -xl[k] * Kt[j == 0 ? 2 : (j == 1 ? 1 : j + 1)][k];
+      st4<T>(&sF[c][j][N * jy + PL * jz], F);
+    }
+  }
+  // the thread's point of every face
+  T lx[2][4];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    const int a = f >> 1, s = f & 1;
+    const int code = codes[f];
+    const int sl = e * NSL + f * NFP + t;
+    T lv[4] = {0, 0, 0, 0};
+    if (active) {
+      if (code == -2) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) lv[q] = __ldg(slot + q * S + sl);
+      } else {
+        const T xm = own_trace<T, PL>(tb, sx[c], xl, f, jy, jz);
+        // wall: {x} = x-, no jump; far field: the linear part (outer value 0)
+        const T xpv = code == -1 ? xm : sfp[c][f][0][t];
+        const T avg = code == -1 ? xm : (T)0.5 * (xm + xpv);
+        T nS[3];
+        line_face_normal<T>(snS, S, f, sl, xj, xk, wjk, tcs, nS);
+#pragma unroll
+        for (int b = 0; b < 3; ++b) lv[b] = -avg * nS[b];
+        lv[3] = code == -1 ? (T)0 : -sfp[c][f][1][t] * (xm - xpv);
+      }
+    }
+    if (a == 0) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) lx[s][q] = lv[q];
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) slf[c][f - 2][q][t] = lv[q];
+    }
+  }
+  __syncthreads();
+  // y contraction of -x K11 (b = 1), z contractions of -x K2b (b = 0, 1, 2)
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const T dy = stb.D[k][jy], dz = stb.D[k][jz];
+    T v1[N], v0[N], v2[N], v3[N];
+    ld4s<T>(&sF[c][1][N * k + PL * jz], v1);
+    ld4s<T>(&sF[c][0][N * jy + PL * k], v0);
+    ld4s<T>(&sF[c][2][N * jy + PL * k], v2);
+    ld4s<T>(&sF[c][3][N * jy + PL * k], v3);
+#pragma unroll
+    for (int ix = 0; ix < N; ++ix) {
+      r[0][ix] += dz * v0[ix];
+      r[1][ix] += dy * v1[ix] + dz * v2[ix];
+      r[2][ix] += dz * v3[ix];
+    }
+  }
+  // lifts: x-faces from registers, y- and z-faces from the shared values
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const T Ly = stb.L[s][jy], Lz = stb.L[s][jz];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      T vy[N], vz[N];
+      ld4s<T>(&slf[c][s][q][N * jz], vy);
+      ld4s<T>(&slf[c][2 + s][q][N * jy], vz);
+#pragma unroll
+      for (int ix = 0; ix < N; ++ix) r[q][ix] -= lx[s][q] * tb.L[s][ix] + vy[ix] * Ly + vz[ix] * Lz;
+    }
+  }
+  if (!active) return;
+  T beta = 0, d = 1;
+  if (ph.r2) {
+    beta = beta_of<T>(ph, e);
+    d = (ph.fcell || ph.fcell32) ? (T)1 / (1 + beta * beta) : kp<T>(ph.dbeta, ph.dbeta_f, ph.dbeta_p);
+  }
+  const T cg = kp<T>(ph.cgrav, ph.cgrav_f, ph.cgrav_p);
+  T wo[3][N], yo[N];
+#pragma unroll
+  for (int ix = 0; ix < N; ++ix) {
+    const T G0 = iM[ix] * r[0][ix], G1 = iM[ix] * r[1][ix], G2 = iM[ix] * r[2][ix];
+    if (ph.r2) {
+      wo[0][ix] = (G0 + beta * G1) * d * ir[ix];
+      wo[1][ix] = (G1 - beta * G0) * d * ir[ix];
+    } else {
+      wo[0][ix] = G0 * ir[ix];
+      wo[1][ix] = G1 * ir[ix];
+    }
+    wo[2][ix] = G2 * ir[ix];
+    yo[ix] = xl[ix] + iM[ix] * r[3][ix];
+    if (ph.r2) yo[ix] -= cg * G2;
+  }
+#pragma unroll
+  for (int b = 0; b < 3; ++b) st4<T>(wv + b * Nn + n0, wo[b]);
+  st4<T>(y + n0, yo);
+}
+
+// Divergence pass (VMULT): y -= (gamma-1) a_dt^2 Div, Div = M^{-1}[-int h
+// rho w . grad(psi) + {h rho w}.n dS (zero on walls)]; h rho face values
+// from the per-slot traces trh (as k_div_fused).
+template <typename T, int EPB>
+__global__ void __launch_bounds__(LineShape<EPB>::THREADS, LineOcc<T, EPB>::MIN_BLOCKS)
+k_div_lines(Fields<T> wv, const T* __restrict__ trh, const int* __restrict__ cface, const T* __restrict__ snS,
+            const T* __restrict__ plag, CellGeo<T> geo, const T* __restrict__ slot, int E, int S, Tables<T> tb,
+            ImplK ph, T* __restrict__ y) {
+  using LS = LineShape<EPB>;
+  constexpr int N = LS::N, NP = LS::NP, NFP = LS::NFP, NF = LS::NF, NSL = LS::NSL, PL = LS::PL, CSZ = LS::CSZ;
+  __shared__ __align__(16) T sw[EPB][3][CSZ];
+  __shared__ __align__(16) T sF[EPB][2][CSZ];    // -h rho (K w)_a of directions a = 1, 2
+  __shared__ __align__(16) T slf[EPB][4][NFP];   // lift values of faces 2..5
+  // per face: h rho traces of both sides and the neighbour's w trace, kept
+  // by each thread for itself between the loads and the face loop (fewer
+  // registers held across the barrier)
+  __shared__ T sfp[EPB][NF][5][NFP];
+  __shared__ __align__(16) T stc[std::is_same<T, float>::value ? EPB : 1][16];
+  __shared__ SharedTables<T, N> stb;
+  __shared__ T sxw[2 * N];
+  const int c = threadIdx.x / NFP, t = threadIdx.x % NFP, jy = t % N, jz = t / N;
+  const int e0 = blockIdx.x * EPB, e = e0 + c;
+  const bool active = e < E;
+  const int Nn = E * NP;
+  const int n0 = (active ? e : 0) * NP + N * t;
+  const bool tcell = std::is_same<T, float>::value && geo.tc != nullptr;
+  stage_terrain<T, EPB>(geo, e0, E, stc);
+  stage_tables<T, N>(tb, stb);
+  stage_nodes_all<T, N>(geo, sxw);
+  T wl[3][N];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+#pragma unroll
+    for (int ix = 0; ix < N; ++ix) wl[b][ix] = 0;
+    if (active) ld4g<T>(wv.f[b] + n0, wl[b]);
+    st4<T>(&sw[c][b][N * jy + PL * jz], wl[b]);
+  }
+  int codes[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    const int code = active ? __ldg(cface + e * NF + f) : -1;
+    codes[f] = code;
+    T v[5] = {0, 0, 0, 0, 0};   // h rho -, h rho +, w+ (3)
+    const int sl = e * NSL + f * NFP + t;
+    if (code >= 0 || code == -3) v[0] = __ldg(trh + sl);
+    if (code >= 0) {
+      v[1] = __ldg(trh + (code * NF + (f ^ 1)) * NFP + t);
+#pragma unroll
+      for (int b = 0; b < 3; ++b) v[2 + b] = plus_trace<T>(tb, wv.f[b] + code * NP, f, t, jy, jz);
+    }
+#pragma unroll
+    for (int j = 0; j < 5; ++j) sfp[c][f][j][t] = v[j];
+  }
+  T pl[N] = {0, 0, 0, 0}, yl[N] = {0, 0, 0, 0};
+  if (active) {
+    ld4g<T>(plag + n0, pl);
+    ld4g<T>(y + n0, yl);
+  }
+  __syncthreads();
+  const T xj = sxw[jy], xk = sxw[jz], wjk = sxw[N + jy] * sxw[N + jz];
+  const T* tcs = tcell ? stc[c] : nullptr;
+  const T gam = kp<T>(ph.gamma, ph.gamma_f, ph.gamma_p);
+  const T gm1 = gam - 1;
+  const T hcoef = gam / gm1;
+  T r[N], iM[N];
+  {
+    T Kt[5][N];
+    line_metric<T>(geo, n0, Nn, xj, xk, wjk, tcs, Kt, iM);
+    T F0[N], F1[N], F2[N];
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+      const T hr = hcoef * pl[k];
+      F0[k] = -hr * (Kt[0][k] * wl[0][k]);
+      F1[k] = -hr * (Kt[1][k] * wl[1][k]);
+      F2[k] = -hr * (Kt[2][k] * wl[0][k] + Kt[3][k] * wl[1][k] + Kt[4][k] * wl[2][k]);
+    }
+#pragma unroll
+    for (int ix = 0; ix < N; ++ix) {
+      r[ix] = 0;
+#pragma unroll
+      for (int k = 0; k < N; ++k) r[ix] += tb.D[k][ix] * F0[k];
+    }
+    st4<T>(&sF[c][0][N * jy + PL * jz], F1);
+    st4<T>(&sF[c][1][N * jy + PL * jz], F2);
+  }
+  T lx[2];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    const int a = f >> 1, s = f & 1;
+    const int code = codes[f];
+    const int sl = e * NSL + f * NFP + t;
+    T lv = 0;
+    if (active && code != -1) {   // wall: the mirror velocity makes {h rho w}.n vanish
+      if (code == -2) {
+        lv = __ldg(slot + sl);
+      } else {
+        T nS[3];
+        line_face_normal<T>(snS, S, f, sl, xj, xk, wjk, tcs, nS);
+        // own normal flux (w-.n dS) and, on a conforming face, the
+        // neighbour's; far field: the linear part (h rho w)-.n / 2 only
+        T fm = 0, fp = 0;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          fm += own_trace<T, PL>(tb, sw[c][b], wl[b], f, jy, jz) * nS[b];
+          fp += sfp[c][f][2 + b][t] * nS[b];
+        }
+        lv = -(T)0.5 * (sfp[c][f][0][t] * fm + sfp[c][f][1][t] * fp);
+      }
+    }
+    if (a == 0)
+      lx[s] = lv;
+    else
+      slf[c][f - 2][t] = lv;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    const T dy = stb.D[k][jy], dz = stb.D[k][jz];
+    T vy[N], vz[N];
+    ld4s<T>(&sF[c][0][N * k + PL * jz], vy);
+    ld4s<T>(&sF[c][1][N * jy + PL * k], vz);
+#pragma unroll
+    for (int ix = 0; ix < N; ++ix) r[ix] += dy * vy[ix] + dz * vz[ix];
+  }
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    const T Ly = stb.L[s][jy], Lz = stb.L[s][jz];
+    T vy[N], vz[N];
+    ld4s<T>(&slf[c][s][N * jz], vy);
+    ld4s<T>(&slf[c][2 + s][N * jy], vz);
+#pragma unroll
+    for (int ix = 0; ix < N; ++ix) r[ix] -= lx[s] * tb.L[s][ix] + vy[ix] * Ly + vz[ix] * Lz;
+  }
+  if (!active) return;
+  const T adt = kp<T>(ph.a_dt, ph.adt_f, ph.adt_p);
+  const T cdiv = gm1 * adt * adt;
+#pragma unroll
+  for (int ix = 0; ix < N; ++ix) yl[ix] -= cdiv * (iM[ix] * r[ix]);
+  st4<T>(y + n0, yl);
+}
+
+}  // namespace dg

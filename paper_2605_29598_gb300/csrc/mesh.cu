@@ -877,13 +877,24 @@ int dg_mesh_info(const dg_mesh* m, dg_mesh_stats* o) {
 }
 
 int dg_mesh_set_fused_stage(dg_mesh* m, int fp64, int fp32, int pairs) {
-  if (!m || (fp64 != 0 && fp64 != 1) || (fp32 != 0 && fp32 != 1) || (pairs != 0 && pairs != 1)) {
-    set_error("dg_mesh_set_fused_stage: mesh and 0 / 1 per precision required");
+  if (!m || fp64 < 0 || fp64 > 2 || fp32 < 0 || fp32 > 2 || pairs < 0 || pairs > 2) {
+    set_error("dg_mesh_set_fused_stage: mesh and 0, 1 or 2 per precision required");
     return DG_ERR_ARG;
   }
   m->fused_stage[0] = fp64;
   m->fused_stage[1] = fp32;
   m->fused_stage[2] = pairs;
+  return DG_OK;
+}
+
+int dg_mesh_set_vmult_tile(dg_mesh* m, int precision, int tile) {
+  if (!m || (tile != 1 && tile != 2 && tile != 4) ||
+      (precision != DG_FP64 && precision != DG_MIXED && precision != DG_MIXED_EXPLICIT && precision != DG_PAIRS)) {
+    set_error("dg_mesh_set_vmult_tile: mesh, a precision and a tile of 1, 2 or 4 required");
+    return DG_ERR_ARG;
+  }
+  int* t = precision == DG_FP64 ? m->tile : (precision == DG_PAIRS ? m->tilep : m->tile32);
+  t[dg::K_VOL_GRAD] = t[dg::K_VOL_DIV] = tile;
   return DG_OK;
 }
 

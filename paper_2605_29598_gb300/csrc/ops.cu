@@ -3,6 +3,7 @@
 // points.
 #include "engine.cuh"
 #include "fused.cuh"
+#include "lines.cuh"
 
 namespace dg {
 
@@ -148,9 +149,11 @@ static int set_far_state(dg_mesh* m, const double* q, cudaStream_t st) {
   m->far_set = true;
   return DG_OK;
 }
-template <typename T> inline bool fused_stage(const dg_mesh* m) {
-  return m->fused_stage[std::is_same<T, double>::value ? 0 : (std::is_same<T, float>::value ? 1 : 2)] != 0;
+template <typename T> inline int fused_sched(const dg_mesh* m) {
+  return m->fused_stage[std::is_same<T, double>::value ? 0 : (std::is_same<T, float>::value ? 1 : 2)];
 }
+template <typename T> inline bool fused_stage(const dg_mesh* m) { return fused_sched<T>(m) != 0; }
+inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 template <typename T, int DIM, int N>
 int Engine<T, DIM, N>::explicit_rates(dg_mesh* m, const PhysK& ph, const T* q, T* fns, T* fs,
@@ -280,7 +283,23 @@ int Engine<T, DIM, N>::vmult(dg_mesh* m, const ImplK& ph, const T* rho, const T*
     DG_RUN(m, K_HANG_GATHER, st, k_hang_gather<T, DIM, N, DIM + 1><<<grid_for(m->nHC * CS::NFP, 128), 128, 0, st>>>(fh, hbuf, slot, tb));
   }
   const unsigned grid = grid_for(m->E, FS::EPB);
-  if (stage)
+  // schedule 2: one thread per x-line (3D, degree 3, terrain-following
+  // cells, 16-byte aligned vectors, 32-bit offsets)
+  const T* irho = buf_irho<T>(m).template as<T>();
+  const bool lines = DIM == 3 && N == 4 && fused_sched<T>(m) == 2 && m->terrain &&
+                     (!std::is_same<T, float>::value || m->tc32 != nullptr) && m->S <= (int64_t(1) << 29) &&
+                     aligned16(x) && aligned16(y) && aligned16(wv) && aligned16(irho) && aligned16(plag);
+  if constexpr (DIM == 3 && N == 4) {
+    if (lines)
+      DG_TILE(m, K_VOL_GRAD, {
+        constexpr int EPB = line_epb<T>(M_);
+        DG_RUN(m, K_VOL_GRAD, st, k_grad_lines<T, EPB><<<grid_for(m->E, EPB), LineShape<EPB>::THREADS, 0, st>>>(
+                   x, m->cface, snS, pcs, irho, cell_geo<T>(m), slot, (int)m->E, (int)m->S, tb, ph, wv, y));
+      })
+  }
+  if (lines)
+    ;
+  else if (stage)
     DG_RUN(m, K_VOL_GRAD, st, k_grad_fused<T, DIM, N, GRAD_VMULT, true><<<grid, FS::THREADS, 0, st>>>(
                x, trc, m->cface, snS, pcs, buf_irho<T>(m).template as<T>(), cell_geo<T>(m), slot, m->E, m->S, tb, ph,
                wv, y, nullptr, nullptr));
@@ -299,7 +318,18 @@ int Engine<T, DIM, N>::vmult(dg_mesh* m, const ImplK& ph, const T* rho, const T*
     DG_RUN(m, K_FACE_DIV, st, k_face_div<T, DIM, N><<<grid_for(m->nH, 128), 128, 0, st>>>(fh, trc, buf_trh<T>(m).template as<T>(), slot, hbuf, tb));
     DG_RUN(m, K_HANG_GATHER, st, k_hang_gather<T, DIM, N, 1><<<grid_for(m->nHC * CS::NFP, 128), 128, 0, st>>>(fh, hbuf, slot, tb));
   }
-  if (stage)
+  if constexpr (DIM == 3 && N == 4) {
+    if (lines)
+      DG_TILE(m, K_VOL_DIV, {
+        constexpr int EPB = line_epb<T>(M_);
+        DG_RUN(m, K_VOL_DIV, st, k_div_lines<T, EPB><<<grid_for(m->E, EPB), LineShape<EPB>::THREADS, 0, st>>>(
+                   w, buf_trh<T>(m).template as<T>(), m->cface, snS, plag, cell_geo<T>(m), slot, (int)m->E,
+                   (int)m->S, tb, ph, y));
+      })
+  }
+  if (lines)
+    ;
+  else if (stage)
     DG_RUN(m, K_VOL_DIV, st, k_div_fused<T, DIM, N, DIV_VMULT, true><<<grid, FS::THREADS, 0, st>>>(
                w, trc, buf_trh<T>(m).template as<T>(), m->cface, snS, plag, cell_geo<T>(m), slot, m->E, m->S, tb, ph,
                y, nullptr, nullptr, nullptr, nullptr));

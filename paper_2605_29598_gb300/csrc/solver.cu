@@ -840,8 +840,9 @@ __global__ void k_fill(double* __restrict__ a, int64_t n, double v) {
 
 // Time the schedules of one precision and keep the fastest: the tile
 // multiplier (cells per block) of the explicit operator's cell kernel
-// (FP64), and the source of the plus-side traces in the fused Schur vmult
-// (staged neighbour cells or a trace array), timed over whole vmults.
+// (FP64), and the schedule of the fused Schur vmult (plus-side traces from
+// a trace array or the neighbours' node lines, or one thread per x-line
+// with its cells per block), timed over whole vmults.
 static int tune_precision(dg_mesh* m, int prec, const double* q, const double* rho, const double* p,
                           const double* u, double* x, double* y, double* fns, double* fs, cudaStream_t st) {
   const bool fp32 = prec != DG_FP64 && prec != DG_PAIRS;
@@ -882,10 +883,18 @@ static int tune_precision(dg_mesh* m, int prec, const double* q, const double* r
   }
   double best = 1e300;
   const int slot = prec == DG_FP64 ? 0 : (prec == DG_PAIRS ? 2 : 1);
-  int pick = m->fused_stage[slot];
+  int* tiles = prec == DG_FP64 ? m->tile : (prec == DG_PAIRS ? m->tilep : m->tile32);
+  int pick = m->fused_stage[slot], pick_tg = tiles[K_VOL_GRAD], pick_td = tiles[K_VOL_DIV];
+  // candidates: trace array, neighbour node lines, and (3D, degree 3) one
+  // thread per x-line with 1, 2 or 4 times the base cells per block
+  struct Cand { int sched, tile; };
+  Cand cand[5] = {{0, 1}, {1, 1}, {2, 1}, {2, 2}, {2, 4}};
+  const int ncand = (m->dim == 3 && m->n == 4) ? 5 : 2;
   rc = DG_OK;
-  for (int sv = 0; sv < 2 && rc == DG_OK; ++sv) {
+  for (int ci = 0; ci < ncand && rc == DG_OK; ++ci) {
+    const int sv = cand[ci].sched;
     m->fused_stage[slot] = sv;
+    tiles[K_VOL_GRAD] = tiles[K_VOL_DIV] = cand[ci].tile;
     SchurCtx sc{m, k, rho, p, 1};
     Schur32Ctx sc32;
     SchurDfCtx sdf;
@@ -916,8 +925,11 @@ static int tune_precision(dg_mesh* m, int prec, const double* q, const double* r
     if (ms < best) {
       best = ms;
       pick = sv;
+      pick_tg = pick_td = cand[ci].tile;
     }
   }
+  tiles[K_VOL_GRAD] = pick_tg;
+  tiles[K_VOL_DIV] = pick_td;
   m->fused_stage[slot] = pick;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

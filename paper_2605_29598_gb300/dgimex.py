@@ -149,6 +149,7 @@ EXPORTS["dg_ensemble_step"] = (C.c_int, [C.c_void_p, C.POINTER(Phys), C.POINTER(
                                          C.POINTER(StepOpts), C.POINTER(StepInfo), C.c_void_p])
 EXPORTS["dg_mesh_autotune"] = (C.c_int, [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p])
 EXPORTS["dg_mesh_set_fused_stage"] = (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int])
+EXPORTS["dg_mesh_set_vmult_tile"] = (C.c_int, [C.c_void_p, C.c_int, C.c_int])
 EXPORTS["dg_mesh_set_far_state"] = (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p])
 EXPORTS["dg_geostrophic_error"] = (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(Phys), C.c_void_p,
                                               C.POINTER(C.c_double), C.c_void_p])
@@ -352,9 +353,16 @@ class Mesh:
 
     def set_fused_stage(self, fp64, fp32, pairs=0):
         """Schedule of the fused vmult kernels per precision (1: neighbour
-        node lines, 0: trace array); see dg_mesh_set_fused_stage."""
+        node lines, 0: trace array, 2: one thread per x-line); see
+        dg_mesh_set_fused_stage."""
         _check(self.lib.dg_mesh_set_fused_stage(self.h, int(fp64), int(fp32), int(pairs)),
                "dg_mesh_set_fused_stage")
+
+    def set_vmult_tile(self, precision, tile):
+        """Cells-per-block multiplier (1, 2, 4) of the schedule-2 vmult
+        passes of one precision; see dg_mesh_set_vmult_tile."""
+        _check(self.lib.dg_mesh_set_vmult_tile(self.h, PRECISIONS[precision], int(tile)),
+               "dg_mesh_set_vmult_tile")
 
     def stats(self) -> MeshStats:
         s = MeshStats()

@@ -10,8 +10,8 @@ Builds the mesh and state of the hill workload (optionally with fewer
 cells), prepares one set of implicit coefficients from the state and runs
 `reps` applies of the chosen operator per precision named (no timing; pair
 it with ncu -k).  --schedule sets the fused vmult schedule of FP64, FP32 and
-FP32 pairs (1: neighbour node lines, 0: trace array) instead of the mesh
-default.
+FP32 pairs (1: neighbour node lines, 0: trace array, 2: one thread per
+x-line) instead of the mesh default, --tile the cells per block of schedule 2.
 """
 from __future__ import annotations
 
@@ -29,6 +29,7 @@ def main():
     ap.add_argument("--refine", action="store_true")
     ap.add_argument("--precision", choices=["fp64", "mixed", "pairs"], nargs="+", default=["fp64"])
     ap.add_argument("--schedule", type=int, nargs=3, default=None)
+    ap.add_argument("--tile", type=int, default=None, help="cells-per-block multiplier of schedule 2")
     args = ap.parse_args()
 
     import torch
@@ -54,6 +55,9 @@ def main():
     y = torch.empty_like(x)
     if args.schedule is not None:
         mesh.set_fused_stage(*args.schedule)
+    if args.tile is not None:
+        for prec in args.precision:
+            mesh.set_vmult_tile(prec, args.tile)
     for prec in args.precision:
         phys = D.make_phys(f=case["f"], precision=prec)
         run(args, mesh, phys, q, cf, x, y)
