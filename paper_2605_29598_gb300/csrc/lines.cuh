@@ -19,6 +19,13 @@
 //    through shared memory and are read back 128 bits at a time.
 // Staged cells use a padded z-plane stride (n^2 + 4 values) so that the
 // strided y- and z-line reads of the face traces are free of bank conflicts.
+// The gradient pass fetches the neighbours' lines with asynchronous copies
+// into shared memory as soon as the face codes arrive and reads them only
+// after its own volume work, so the second of its two dependent global
+// round trips is hidden (the kernels are bound by load latency, not by
+// bandwidth or issue).  The divergence pass would need three such lines per
+// face point, 4.6 KB per cell in FP32; the occupancy that costs outweighed
+// the latency it hid when measured, so it loads them into registers.
 // The kernels serve terrain-following meshes (five metric terms per node;
 // every mesh of the paper's workloads); the host keeps the other schedules
 // for general cells.
@@ -93,25 +100,27 @@ __host__ __device__ constexpr int line_term(int j) { return j == 0 ? 0 : (j == 1
 template <typename T>
 __device__ __forceinline__ void line_metric(const CellGeo<T>& g, int n0, int Nn, T xj, T xk, T wjk,
                                             const T* tcs, T Kt[5][4], T iM[4]) {
-  if (!std::is_same<T, float>::value || tcs == nullptr) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (tcs) {
 #pragma unroll
-    for (int j = 0; j < 5; ++j) ld4g<T>(g.K + (int64_t)line_term(j) * Nn + n0, Kt[j]);
-    ld4g<T>(g.invM + n0, iM);
-    return;
+      for (int ix = 0; ix < 4; ++ix) {
+        const float xi[3] = {g.x[ix], xj, xk};
+        const float wq = g.w[ix] * wjk;
+        float K[3][3], det;
+        terrain_row<float, 3>(tcs, xi, K, det);
+        Kt[0][ix] = K[0][0] * wq;
+        Kt[1][ix] = K[1][1] * wq;
+        Kt[2][ix] = K[2][0] * wq;
+        Kt[3][ix] = K[2][1] * wq;
+        Kt[4][ix] = K[2][2] * wq;
+        iM[ix] = __frcp_rn(wq * det);
+      }
+      return;
+    }
   }
 #pragma unroll
-  for (int ix = 0; ix < 4; ++ix) {
-    const T xi[3] = {g.x[ix], xj, xk};
-    const T wq = g.w[ix] * wjk;
-    T K[3][3], det;
-    terrain_row<T, 3>(tcs, xi, K, det);
-    Kt[0][ix] = K[0][0] * wq;
-    Kt[1][ix] = K[1][1] * wq;
-    Kt[2][ix] = K[2][0] * wq;
-    Kt[3][ix] = K[2][1] * wq;
-    Kt[4][ix] = K[2][2] * wq;
-    iM[ix] = 1 / (wq * det);
-  }
+  for (int j = 0; j < 5; ++j) ld4g<T>(g.K + (int64_t)line_term(j) * Nn + n0, Kt[j]);
+  ld4g<T>(g.invM + n0, iM);
 }
 
 // Outward n dS at the thread's point of face f (tangential nodes xj, xk in
@@ -151,6 +160,48 @@ __device__ __forceinline__ T plus_trace(const Tables<T>& tb, const T* __restrict
 #pragma unroll
     for (int k = 0; k < 4; ++k) v[k] = __ldg(nb + (a == 1 ? jy + 4 * k + 16 * jz : jy + 4 * jz + 16 * k));
   }
+  T acc = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) acc += tb.L[s][k] * v[k];
+  return acc;
+}
+
+// Asynchronous global -> shared copies (cp.async): the neighbours' lines
+// are in flight while the thread does the cell's own volume work, and are
+// waited for (cp.async.wait_all, each thread its own copies) only before
+// the face fluxes.  16-byte copies need 16-byte aligned addresses on both
+// sides; smaller ones the element's alignment.
+template <int B>
+__device__ __forceinline__ void cp_async(void* s, const void* g) {
+  const unsigned sa = static_cast<unsigned>(__cvta_generic_to_shared(s));
+  if constexpr (B == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(g) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(sa), "l"(g), "n"(B) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
+// the neighbour's line through the thread's point of face f, copied raw to
+// dst (4 values, 16-byte aligned): x-lines in 16-byte pieces, y- and
+// z-lines value by value
+template <typename T>
+__device__ __forceinline__ void plus_line_async(const T* __restrict__ nb, int f, int t, int jy, int jz, T* dst) {
+  const int a = f >> 1;
+  if (a == 0) {
+#pragma unroll
+    for (int h = 0; h < (int)(4 * sizeof(T) / 16); ++h)
+      cp_async<16>(reinterpret_cast<char*>(dst) + 16 * h, reinterpret_cast<const char*>(nb + 4 * t) + 16 * h);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      cp_async<(int)sizeof(T)>(dst + k, nb + (a == 1 ? jy + 4 * k + 16 * jz : jy + 4 * jz + 16 * k));
+  }
+}
+
+// the copied line contracted to the neighbour's face f ^ 1
+template <typename T>
+__device__ __forceinline__ T plus_from(const Tables<T>& tb, const T* v, int f) {
+  const int s = (f & 1) ^ 1;
   T acc = 0;
 #pragma unroll
   for (int k = 0; k < 4; ++k) acc += tb.L[s][k] * v[k];
@@ -202,9 +253,10 @@ k_grad_lines(const T* __restrict__ x, const int* __restrict__ cface, const T* __
   // -x K_ab staged for the y and z contractions: (a, b) = (2, 0), (1, 1), (2, 1), (2, 2)
   __shared__ __align__(16) T sF[EPB][4][CSZ];
   __shared__ __align__(16) T slf[EPB][4][4][NFP];   // lift values of faces 2..5, fields 0..3
-  // per face: the neighbour's trace and the penalty coefficient, kept by
-  // each thread for itself across the barrier
-  __shared__ T sfp[EPB][NF][2][NFP];
+  // per face: the penalty coefficient and the neighbour's line through the
+  // thread's point, each thread's own (asynchronous copies)
+  __shared__ T spen[EPB][NF][NFP];
+  __shared__ __align__(16) T snb[EPB][NF][NFP][4];
   __shared__ __align__(16) T stc[std::is_same<T, float>::value ? EPB : 1][16];
   __shared__ SharedTables<T, N> stb;
   __shared__ T sxw[2 * N];
@@ -220,22 +272,19 @@ k_grad_lines(const T* __restrict__ x, const int* __restrict__ cface, const T* __
   T xl[N] = {0, 0, 0, 0};
   if (active) ld4g<T>(x + n0, xl);
   st4<T>(&sx[c][N * jy + PL * jz], xl);
-  // global reads first: face codes, the neighbours' traces, penalties, 1/rho
+  // global reads first: face codes, then the neighbours' lines and the
+  // penalties as asynchronous copies, 1/rho
   int codes[NF];
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
     const int code = active ? __ldg(cface + e * NF + f) : -1;
     codes[f] = code;
-    T xp = 0, pen = 0;
     const int sl = e * NSL + f * NFP + t;
-    if (code >= 0) {
-      xp = plus_trace<T>(tb, x + code * NP, f, t, jy, jz);
-      if (pcs) pen = __ldg(pcs + sl);
-    } else if (code == -3 && pcs) {
-      pen = __ldg(pcs + sl);
-    }
-    sfp[c][f][0][t] = xp;
-    sfp[c][f][1][t] = pen;
+    if (code >= 0) plus_line_async<T>(x + code * NP, f, t, jy, jz, snb[c][f][t]);
+    if ((code >= 0 || code == -3) && pcs)
+      cp_async<(int)sizeof(T)>(&spen[c][f][t], pcs + sl);
+    else
+      spen[c][f][t] = 0;
   }
   T ir[N] = {0, 0, 0, 0};
   if (active) ld4g<T>(irho + n0, ir);
@@ -264,7 +313,8 @@ k_grad_lines(const T* __restrict__ x, const int* __restrict__ cface, const T* __
       st4<T>(&sF[c][j][N * jy + PL * jz], F);
     }
   }
-  // the thread's point of every face
+  // the thread's point of every face (its copies have landed)
+  cp_async_wait_all();
   T lx[2][4];
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
@@ -279,13 +329,13 @@ k_grad_lines(const T* __restrict__ x, const int* __restrict__ cface, const T* __
       } else {
         const T xm = own_trace<T, PL>(tb, sx[c], xl, f, jy, jz);
         // wall: {x} = x-, no jump; far field: the linear part (outer value 0)
-        const T xpv = code == -1 ? xm : sfp[c][f][0][t];
+        const T xpv = code == -1 ? xm : (code >= 0 ? plus_from<T>(tb, snb[c][f][t], f) : (T)0);
         const T avg = code == -1 ? xm : (T)0.5 * (xm + xpv);
         T nS[3];
         line_face_normal<T>(snS, S, f, sl, xj, xk, wjk, tcs, nS);
 #pragma unroll
         for (int b = 0; b < 3; ++b) lv[b] = -avg * nS[b];
-        lv[3] = code == -1 ? (T)0 : -sfp[c][f][1][t] * (xm - xpv);
+        lv[3] = code == -1 ? (T)0 : -spen[c][f][t] * (xm - xpv);
       }
     }
     if (a == 0) {
