@@ -23,9 +23,10 @@
 // into shared memory as soon as the face codes arrive and reads them only
 // after its own volume work, so the second of its two dependent global
 // round trips is hidden (the kernels are bound by load latency, not by
-// bandwidth or issue).  The divergence pass would need three such lines per
-// face point, 4.6 KB per cell in FP32; the occupancy that costs outweighed
-// the latency it hid when measured, so it loads them into registers.
+// bandwidth or issue).  Having w, it also writes g = (h rho)- (w- . n dS)
+// at every own face point; the divergence pass then forms each face flux
+// from its own g and the neighbour's, two values per face point instead of
+// three neighbour lines, the own traces and the normals.
 // The kernels serve terrain-following meshes (five metric terms per node;
 // every mesh of the paper's workloads); the host keeps the other schedules
 // for general cells.
@@ -146,26 +147,6 @@ __device__ __forceinline__ void line_face_normal(const T* __restrict__ snS, int 
   for (int b = 0; b < 3; ++b) nS[b] = sw * C[a][b];
 }
 
-// The neighbour's line through the thread's point of face f (direction
-// f / 2), contracted to the neighbour's face f ^ 1: x-lines are one vector
-// load, y- and z-lines n strided loads.
-template <typename T>
-__device__ __forceinline__ T plus_trace(const Tables<T>& tb, const T* __restrict__ nb, int f, int t, int jy,
-                                        int jz) {
-  const int a = f >> 1, s = (f & 1) ^ 1;
-  T v[4];
-  if (a == 0) {
-    ld4g<T>(nb + 4 * t, v);
-  } else {
-#pragma unroll
-    for (int k = 0; k < 4; ++k) v[k] = __ldg(nb + (a == 1 ? jy + 4 * k + 16 * jz : jy + 4 * jz + 16 * k));
-  }
-  T acc = 0;
-#pragma unroll
-  for (int k = 0; k < 4; ++k) acc += tb.L[s][k] * v[k];
-  return acc;
-}
-
 // Asynchronous global -> shared copies (cp.async): the neighbours' lines
 // are in flight while the thread does the cell's own volume work, and are
 // waited for (cp.async.wait_all, each thread its own copies) only before
@@ -246,7 +227,8 @@ template <typename T, int EPB>
 __global__ void __launch_bounds__(LineShape<EPB>::THREADS, LineOcc<T, EPB>::MIN_BLOCKS)
 k_grad_lines(const T* __restrict__ x, const int* __restrict__ cface, const T* __restrict__ snS,
              const T* __restrict__ pcs, const T* __restrict__ irho, CellGeo<T> geo, const T* __restrict__ slot,
-             int E, int S, Tables<T> tb, ImplK ph, T* __restrict__ wv, T* __restrict__ y) {
+             int E, int S, Tables<T> tb, ImplK ph, T* __restrict__ wv, T* __restrict__ y,
+             const T* __restrict__ trh, T* __restrict__ gout) {
   using LS = LineShape<EPB>;
   constexpr int N = LS::N, NP = LS::NP, NFP = LS::NFP, NF = LS::NF, NSL = LS::NSL, PL = LS::PL, CSZ = LS::CSZ;
   __shared__ __align__(16) T sx[EPB][CSZ];
@@ -257,6 +239,11 @@ k_grad_lines(const T* __restrict__ x, const int* __restrict__ cface, const T* __
   // thread's point, each thread's own (asynchronous copies)
   __shared__ T spen[EPB][NF][NFP];
   __shared__ __align__(16) T snb[EPB][NF][NFP][4];
+  __shared__ T shm[EPB][NF][NFP];                   // own h rho traces (for gout)
+  // w staged for its face traces, in the neighbours' lines' space (free
+  // once every thread has passed the barrier after the face loop)
+  static_assert(3 * CSZ <= NF * NFP * 4, "w staging does not fit the neighbour-line space");
+  T (*sw)[3][CSZ] = reinterpret_cast<T (*)[3][CSZ]>(&snb[0][0][0][0]);
   __shared__ __align__(16) T stc[std::is_same<T, float>::value ? EPB : 1][16];
   __shared__ SharedTables<T, N> stb;
   __shared__ T sxw[2 * N];
@@ -285,6 +272,10 @@ k_grad_lines(const T* __restrict__ x, const int* __restrict__ cface, const T* __
       cp_async<(int)sizeof(T)>(&spen[c][f][t], pcs + sl);
     else
       spen[c][f][t] = 0;
+    if (code >= 0 || code == -3)
+      cp_async<(int)sizeof(T)>(&shm[c][f][t], trh + sl);
+    else
+      shm[c][f][t] = 0;
   }
   T ir[N] = {0, 0, 0, 0};
   if (active) ld4g<T>(irho + n0, ir);
@@ -376,10 +367,9 @@ k_grad_lines(const T* __restrict__ x, const int* __restrict__ cface, const T* __
       for (int ix = 0; ix < N; ++ix) r[q][ix] -= lx[s][q] * tb.L[s][ix] + vy[ix] * Ly + vz[ix] * Lz;
     }
   }
-  if (!active) return;
   T beta = 0, d = 1;
   if (ph.r2) {
-    beta = beta_of<T>(ph, e);
+    beta = beta_of<T>(ph, active ? e : 0);
     d = (ph.fcell || ph.fcell32) ? (T)1 / (1 + beta * beta) : kp<T>(ph.dbeta, ph.dbeta_f, ph.dbeta_p);
   }
   const T cg = kp<T>(ph.cgrav, ph.cgrav_f, ph.cgrav_p);
@@ -397,10 +387,37 @@ k_grad_lines(const T* __restrict__ x, const int* __restrict__ cface, const T* __
     wo[2][ix] = G2 * ir[ix];
     yo[ix] = xl[ix] + iM[ix] * r[3][ix];
     if (ph.r2) yo[ix] -= cg * G2;
+    if (!active) wo[0][ix] = wo[1][ix] = wo[2][ix] = 0;
   }
 #pragma unroll
-  for (int b = 0; b < 3; ++b) st4<T>(wv + b * Nn + n0, wo[b]);
-  st4<T>(y + n0, yo);
+  for (int b = 0; b < 3; ++b) st4<T>(&sw[c][b][N * jy + PL * jz], wo[b]);
+  if (active) {
+#pragma unroll
+    for (int b = 0; b < 3; ++b) st4<T>(wv + b * Nn + n0, wo[b]);
+    st4<T>(y + n0, yo);
+  }
+  __syncthreads();
+  if (!active) return;
+  // for the divergence pass: g = (h rho)- (w- . n dS) at the thread's point
+  // of every conforming, periodic and far-field face (the other side's
+  // normal is the exact negative, so the divergence face flux is
+  // -(g_own - g_neighbour) / 2)
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    const int code = codes[f];
+    if (code < 0 && code != -3) continue;
+    const int sl = e * NSL + f * NFP + t;
+    T nS[3];
+    line_face_normal<T>(snS, S, f, sl, xj, xk, wjk, tcs, nS);
+    // recomputed terrain normals of x- and y-faces have one non-zero
+    // component (the others are exact zeros), so one trace of w suffices
+    const int a = f >> 1;
+    T fm = 0;
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+      if (!tcs || a == 2 || a == b) fm += own_trace<T, PL>(tb, sw[c][b], wo[b], f, jy, jz) * nS[b];
+    gout[sl] = shm[c][f][t] * fm;
+  }
 }
 
 // Divergence pass (VMULT): y -= (gamma-1) a_dt^2 Div, Div = M^{-1}[-int h
@@ -408,18 +425,15 @@ k_grad_lines(const T* __restrict__ x, const int* __restrict__ cface, const T* __
 // from the per-slot traces trh (as k_div_fused).
 template <typename T, int EPB>
 __global__ void __launch_bounds__(LineShape<EPB>::THREADS, LineOcc<T, EPB>::MIN_BLOCKS)
-k_div_lines(Fields<T> wv, const T* __restrict__ trh, const int* __restrict__ cface, const T* __restrict__ snS,
-            const T* __restrict__ plag, CellGeo<T> geo, const T* __restrict__ slot, int E, int S, Tables<T> tb,
-            ImplK ph, T* __restrict__ y) {
+k_div_lines(Fields<T> wv, const T* __restrict__ gin, const int* __restrict__ cface, const T* __restrict__ plag,
+            CellGeo<T> geo, const T* __restrict__ slot, int E, Tables<T> tb, ImplK ph, T* __restrict__ y) {
   using LS = LineShape<EPB>;
   constexpr int N = LS::N, NP = LS::NP, NFP = LS::NFP, NF = LS::NF, NSL = LS::NSL, PL = LS::PL, CSZ = LS::CSZ;
-  __shared__ __align__(16) T sw[EPB][3][CSZ];
   __shared__ __align__(16) T sF[EPB][2][CSZ];    // -h rho (K w)_a of directions a = 1, 2
   __shared__ __align__(16) T slf[EPB][4][NFP];   // lift values of faces 2..5
-  // per face: h rho traces of both sides and the neighbour's w trace, kept
-  // by each thread for itself between the loads and the face loop (fewer
-  // registers held across the barrier)
-  __shared__ T sfp[EPB][NF][5][NFP];
+  // per face point: g = (h rho w . n dS) of this side and of the neighbour,
+  // written by the gradient pass (asynchronous copies, each thread its own)
+  __shared__ T sg[EPB][NF][2][NFP];
   __shared__ __align__(16) T stc[std::is_same<T, float>::value ? EPB : 1][16];
   __shared__ SharedTables<T, N> stb;
   __shared__ T sxw[2 * N];
@@ -432,29 +446,27 @@ k_div_lines(Fields<T> wv, const T* __restrict__ trh, const int* __restrict__ cfa
   stage_terrain<T, EPB>(geo, e0, E, stc);
   stage_tables<T, N>(tb, stb);
   stage_nodes_all<T, N>(geo, sxw);
+  int codes[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    const int code = active ? __ldg(cface + e * NF + f) : -1;
+    codes[f] = code;
+    const int sl = e * NSL + f * NFP + t;
+    if (code >= 0 || code == -3)
+      cp_async<(int)sizeof(T)>(&sg[c][f][0][t], gin + sl);
+    else
+      sg[c][f][0][t] = 0;
+    if (code >= 0)
+      cp_async<(int)sizeof(T)>(&sg[c][f][1][t], gin + (code * NF + (f ^ 1)) * NFP + t);
+    else
+      sg[c][f][1][t] = 0;
+  }
   T wl[3][N];
 #pragma unroll
   for (int b = 0; b < 3; ++b) {
 #pragma unroll
     for (int ix = 0; ix < N; ++ix) wl[b][ix] = 0;
     if (active) ld4g<T>(wv.f[b] + n0, wl[b]);
-    st4<T>(&sw[c][b][N * jy + PL * jz], wl[b]);
-  }
-  int codes[NF];
-#pragma unroll
-  for (int f = 0; f < NF; ++f) {
-    const int code = active ? __ldg(cface + e * NF + f) : -1;
-    codes[f] = code;
-    T v[5] = {0, 0, 0, 0, 0};   // h rho -, h rho +, w+ (3)
-    const int sl = e * NSL + f * NFP + t;
-    if (code >= 0 || code == -3) v[0] = __ldg(trh + sl);
-    if (code >= 0) {
-      v[1] = __ldg(trh + (code * NF + (f ^ 1)) * NFP + t);
-#pragma unroll
-      for (int b = 0; b < 3; ++b) v[2 + b] = plus_trace<T>(tb, wv.f[b] + code * NP, f, t, jy, jz);
-    }
-#pragma unroll
-    for (int j = 0; j < 5; ++j) sfp[c][f][j][t] = v[j];
   }
   T pl[N] = {0, 0, 0, 0}, yl[N] = {0, 0, 0, 0};
   if (active) {
@@ -488,6 +500,11 @@ k_div_lines(Fields<T> wv, const T* __restrict__ trh, const int* __restrict__ cfa
     st4<T>(&sF[c][0][N * jy + PL * jz], F1);
     st4<T>(&sF[c][1][N * jy + PL * jz], F2);
   }
+  // face fluxes -{h rho w}.n dS = -(g_own - g_neighbour) / 2 (the two sides'
+  // normals are negatives of each other); far field: the linear part
+  // -g_own / 2; wall: the mirror velocity makes the flux vanish; 2:1 faces:
+  // the slot values of the face kernels
+  cp_async_wait_all();
   T lx[2];
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
@@ -495,23 +512,8 @@ k_div_lines(Fields<T> wv, const T* __restrict__ trh, const int* __restrict__ cfa
     const int code = codes[f];
     const int sl = e * NSL + f * NFP + t;
     T lv = 0;
-    if (active && code != -1) {   // wall: the mirror velocity makes {h rho w}.n vanish
-      if (code == -2) {
-        lv = __ldg(slot + sl);
-      } else {
-        T nS[3];
-        line_face_normal<T>(snS, S, f, sl, xj, xk, wjk, tcs, nS);
-        // own normal flux (w-.n dS) and, on a conforming face, the
-        // neighbour's; far field: the linear part (h rho w)-.n / 2 only
-        T fm = 0, fp = 0;
-#pragma unroll
-        for (int b = 0; b < 3; ++b) {
-          fm += own_trace<T, PL>(tb, sw[c][b], wl[b], f, jy, jz) * nS[b];
-          fp += sfp[c][f][2 + b][t] * nS[b];
-        }
-        lv = -(T)0.5 * (sfp[c][f][0][t] * fm + sfp[c][f][1][t] * fp);
-      }
-    }
+    if (active && code != -1)
+      lv = code == -2 ? __ldg(slot + sl) : -(T)0.5 * (sg[c][f][0][t] - sg[c][f][1][t]);
     if (a == 0)
       lx[s] = lv;
     else

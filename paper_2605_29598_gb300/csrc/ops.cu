@@ -284,7 +284,10 @@ int Engine<T, DIM, N>::vmult(dg_mesh* m, const ImplK& ph, const T* rho, const T*
   }
   const unsigned grid = grid_for(m->E, FS::EPB);
   // schedule 2: one thread per x-line (3D, degree 3, terrain-following
-  // cells, 16-byte aligned vectors, 32-bit offsets)
+  // cells, 16-byte aligned vectors, 32-bit offsets); the gradient pass
+  // leaves the face points' h rho w.n dS for the divergence pass in the
+  // fifth field of the trace scratch (the traces of x and w use the first
+  // three)
   const T* irho = buf_irho<T>(m).template as<T>();
   const bool lines = DIM == 3 && N == 4 && fused_sched<T>(m) == 2 && m->terrain &&
                      (!std::is_same<T, float>::value || m->tc32 != nullptr) && m->S <= (int64_t(1) << 29) &&
@@ -294,7 +297,8 @@ int Engine<T, DIM, N>::vmult(dg_mesh* m, const ImplK& ph, const T* rho, const T*
       DG_TILE(m, K_VOL_GRAD, {
         constexpr int EPB = line_epb<T>(M_);
         DG_RUN(m, K_VOL_GRAD, st, k_grad_lines<T, EPB><<<grid_for(m->E, EPB), LineShape<EPB>::THREADS, 0, st>>>(
-                   x, m->cface, snS, pcs, irho, cell_geo<T>(m), slot, (int)m->E, (int)m->S, tb, ph, wv, y));
+                   x, m->cface, snS, pcs, irho, cell_geo<T>(m), slot, (int)m->E, (int)m->S, tb, ph, wv, y,
+                   buf_trh<T>(m).template as<T>(), trc + 4 * m->S));
       })
   }
   if (lines)
@@ -323,8 +327,7 @@ int Engine<T, DIM, N>::vmult(dg_mesh* m, const ImplK& ph, const T* rho, const T*
       DG_TILE(m, K_VOL_DIV, {
         constexpr int EPB = line_epb<T>(M_);
         DG_RUN(m, K_VOL_DIV, st, k_div_lines<T, EPB><<<grid_for(m->E, EPB), LineShape<EPB>::THREADS, 0, st>>>(
-                   w, buf_trh<T>(m).template as<T>(), m->cface, snS, plag, cell_geo<T>(m), slot, (int)m->E,
-                   (int)m->S, tb, ph, y));
+                   w, trc + 4 * m->S, m->cface, plag, cell_geo<T>(m), slot, (int)m->E, tb, ph, y));
       })
   }
   if (lines)
