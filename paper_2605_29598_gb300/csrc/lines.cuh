@@ -189,6 +189,25 @@ __device__ __forceinline__ T plus_from(const Tables<T>& tb, const T* v, int f) {
   return acc;
 }
 
+// Butterfly exchange of one value with lane ^ m (pairs: both halves).
+__device__ __forceinline__ float shfl_x(float v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+__device__ __forceinline__ double shfl_x(double v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+__device__ __forceinline__ df64 shfl_x(df64 v, int m) {
+  return df64(__shfl_xor_sync(0xffffffffu, v.hi, m), __shfl_xor_sync(0xffffffffu, v.lo, m));
+}
+
+// Reduce-scatter over the four lanes whose lane numbers differ in the two
+// bits of unit m (m = 1: the lanes of one jz, q = jy; m = 4: the lanes of
+// one jy, q = jz): the lane at position q of its group returns the group's
+// sum of v[q].  Three exchanges; every lane of the warp must take part.
+template <typename T>
+__device__ __forceinline__ T reduce_scatter4(const T v[4], int q, int m) {
+  const bool h = (q >> 1) & 1, l = q & 1;
+  const T a0 = (h ? v[2] : v[0]) + shfl_x(h ? v[0] : v[2], 2 * m);
+  const T a1 = (h ? v[3] : v[1]) + shfl_x(h ? v[1] : v[3], 2 * m);
+  return (l ? a1 : a0) + shfl_x(l ? a0 : a1, m);
+}
+
 // own trace at the thread's point of face f from the staged cell (stride PL
 // between z-planes) or, on x-faces, from the thread's registers
 template <typename T, int PL>
@@ -240,10 +259,7 @@ k_grad_lines(const T* __restrict__ x, const int* __restrict__ cface, const T* __
   __shared__ T spen[EPB][NF][NFP];
   __shared__ __align__(16) T snb[EPB][NF][NFP][4];
   __shared__ T shm[EPB][NF][NFP];                   // own h rho traces (for gout)
-  // w staged for its face traces, in the neighbours' lines' space (free
-  // once every thread has passed the barrier after the face loop)
-  static_assert(3 * CSZ <= NF * NFP * 4, "w staging does not fit the neighbour-line space");
-  T (*sw)[3][CSZ] = reinterpret_cast<T (*)[3][CSZ]>(&snb[0][0][0][0]);
+
   __shared__ __align__(16) T stc[std::is_same<T, float>::value ? EPB : 1][16];
   __shared__ SharedTables<T, N> stb;
   __shared__ T sxw[2 * N];
@@ -389,34 +405,54 @@ k_grad_lines(const T* __restrict__ x, const int* __restrict__ cface, const T* __
     if (ph.r2) yo[ix] -= cg * G2;
     if (!active) wo[0][ix] = wo[1][ix] = wo[2][ix] = 0;
   }
-#pragma unroll
-  for (int b = 0; b < 3; ++b) st4<T>(&sw[c][b][N * jy + PL * jz], wo[b]);
   if (active) {
 #pragma unroll
     for (int b = 0; b < 3; ++b) st4<T>(wv + b * Nn + n0, wo[b]);
     st4<T>(y + n0, yo);
   }
-  __syncthreads();
-  if (!active) return;
-  // for the divergence pass: g = (h rho)- (w- . n dS) at the thread's point
-  // of every conforming, periodic and far-field face (the other side's
-  // normal is the exact negative, so the divergence face flux is
-  // -(g_own - g_neighbour) / 2)
+  // For the divergence pass: g = (h rho)- (w- . n dS) at the face points of
+  // every conforming, periodic and far-field face (the other side's normal
+  // is the negative, so the divergence face flux is -(g_own - g_nb) / 2).
+  // The traces of w: x-faces from the thread's line; y- and z-faces summed
+  // across the four lanes that hold the line's other nodes, which leaves
+  // lane (jy, jz) the y-face point (x = jy, z = jz) and the z-face point
+  // (x = jz, y = jy).  Recomputed terrain normals of x- and y-faces have
+  // one non-zero component (the others are exact zeros), so one trace of w
+  // suffices there.  All lanes run the exchanges (inactive cells with w = 0).
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
-    const int code = codes[f];
-    if (code < 0 && code != -3) continue;
-    const int sl = e * NSL + f * NFP + t;
+    const int a = f >> 1, s = f & 1;
+    const T Lq = a == 1 ? stb.L[s][jy] : stb.L[s][jz];
+    T tr[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      tr[b] = 0;
+      if (tcs && a != 2 && a != b) continue;
+      if (a == 0) {
+#pragma unroll
+        for (int k = 0; k < N; ++k) tr[b] += tb.L[s][k] * wo[b][k];
+      } else {
+        T v[N];
+#pragma unroll
+        for (int ix = 0; ix < N; ++ix) v[ix] = Lq * wo[b][ix];
+        tr[b] = a == 1 ? reduce_scatter4<T>(v, jy, 1) : reduce_scatter4<T>(v, jz, 4);
+      }
+    }
+    // this lane's point of face f and its tangential nodes
+    const int p = a == 2 ? jz + N * jy : t;
+    const int code = codes[f];   // (the same in every thread of the cell)
+    if (!active || (code < 0 && code != -3)) continue;
+    const int sl = e * NSL + f * NFP + p;
     T nS[3];
-    line_face_normal<T>(snS, S, f, sl, xj, xk, wjk, tcs, nS);
-    // recomputed terrain normals of x- and y-faces have one non-zero
-    // component (the others are exact zeros), so one trace of w suffices
-    const int a = f >> 1;
+    if (a == 2)
+      line_face_normal<T>(snS, S, f, sl, sxw[jz], sxw[jy], wjk, tcs, nS);
+    else
+      line_face_normal<T>(snS, S, f, sl, xj, xk, wjk, tcs, nS);
     T fm = 0;
 #pragma unroll
     for (int b = 0; b < 3; ++b)
-      if (!tcs || a == 2 || a == b) fm += own_trace<T, PL>(tb, sw[c][b], wo[b], f, jy, jz) * nS[b];
-    gout[sl] = shm[c][f][t] * fm;
+      if (!tcs || a == 2 || a == b) fm += tr[b] * nS[b];
+    gout[sl] = shm[c][f][p] * fm;
   }
 }
 
