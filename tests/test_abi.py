@@ -51,6 +51,8 @@ def test_null_arguments_rejected_without_gpu(lib):
     assert lib.imex_ark2_step(None, None, None, None, 1.0, None, None, None) == -1
     assert lib.dg_precond_apply(None, None, None, None, 1, None, None, None) == -1
     assert lib.dg_mesh_set_sponge(None, None, None, None, None) == -1
+    assert lib.dg_mesh_set_fused_stage(None, 0, 2, 0) == -1
+    assert lib.dg_mesh_set_vmult_tile(None, 1, 2) == -1
 
 
 def test_context_fails_cleanly_without_gpu(lib):

@@ -224,3 +224,17 @@ def test_lines_misaligned_vector_falls_back(D, ctx):
     assert xv.data_ptr() % 16 == 8
     y = from_dev(gm.apply_implicit(D.make_phys(f=1e-4), dcf, xv), ref.shape)
     check(y, ref, x, "fp64")
+
+
+def test_lines_setters_validate(D, ctx):
+    """Schedules outside 0..2 and tiles other than 1, 2, 4 are rejected;
+    valid ones show in the mesh statistics."""
+    mesh, disc, gm, q = make(D, ctx, "ragged_walls")
+    with pytest.raises(D.DGError):
+        gm.set_fused_stage(0, 3, 0)
+    with pytest.raises(D.DGError):
+        gm.set_vmult_tile("mixed", 3)
+    gm.set_fused_stage(2, 2, 2)
+    gm.set_vmult_tile("mixed", 4)
+    st = gm.stats()
+    assert list(st.fused_stage) == [2, 2, 2] and st.tile_fp32[1] == 4 and st.tile_fp32[2] == 4
