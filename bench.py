@@ -632,7 +632,8 @@ def run_refined_configs(D, I, ctx, steps, warmup, err_steps=3):
     phmx = D.make_phys(f=f, variant="R2", precision="mixed")
     c4_opts = dict(STEP_OPTS, gmres_rtol=1e-8, gmres_inner_rtol=1e-4)
     geo = {"cells": st.n_elem, "nodes": N, "hanging_points": st.n_hang_points, "degree": case["degree"],
-           "dt": dt}
+           "dt": dt, "terrain_following": st.terrain_following,
+           "schedule_tiles_fp64_fp32_fused_stage": [list(st.tile_fp64), list(st.tile_fp32), list(st.fused_stage)]}
     q = q_bg.clone()
     for _ in range(warmup):
         mesh.step(ph64, q, dt, **STEP_OPTS)
