@@ -132,7 +132,10 @@ def box_mesh(cells, extent, periodic=None, hill=None, z_top=None,
               cell with flat-box centre ``center``; levels are then raised
               until face neighbours differ by at most one (2:1 balance).
               Refined children are placed by multilinear interpolation of
-              their parent, which keeps hanging faces watertight.
+              their parent, which keeps hanging faces watertight; a
+              horizontal coordinate that depends on its own reference
+              direction only (every Gal-Chen cell) keeps that property
+              exactly, so refined meshes stay terrain-following.
     """
     d = len(cells)
     cells = tuple(int(c) for c in cells)
@@ -206,7 +209,18 @@ def box_mesh(cells, extent, periodic=None, hill=None, z_top=None,
         lc = np.stack(np.meshgrid(*[np.arange(m)] * d, indexing="ij"), axis=-1).reshape(-1, d)
         lc = lc[np.lexsort([lc[:, a] for a in range(d)])]
         corners = ((lc[:, None, :] + bits[None, :, :]) / m).reshape(-1, d)
-        cv = _multilinear(base_verts[b], corners).reshape(len(lc), 1 << d, d)
+        cv = _multilinear(base_verts[b], corners)
+        # a horizontal coordinate that depends only on its own reference
+        # direction in the base cell keeps that property exactly in the
+        # children: (1 - t) x0 + t x1 is the same number for every corner
+        # with the same t (the sum over all corners is not)
+        for c in range(d - 1):
+            bit = 1 << c
+            x0, x1 = base_verts[b, 0, c], base_verts[b, bit, c]
+            if all(base_verts[b, k, c] == base_verts[b, k & bit, c] for k in range(1 << d)):
+                tt = corners[:, c]
+                cv[:, c] = (1.0 - tt) * x0 + tt * x1
+        cv = cv.reshape(len(lc), 1 << d, d)
         verts[start[b]:start[b + 1]] = cv
         level[start[b]:start[b + 1]] = L
         for row in lc:
