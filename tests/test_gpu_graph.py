@@ -84,6 +84,29 @@ def test_graph_step_matches_host_step(D, ctx, name, precision):
         assert relerr(a[k], b[k]) < 1e-10
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_graph_step_with_line_schedule(D, ctx, precision):
+    """The one-thread-per-x-line vmult passes (schedule 2, with their
+    asynchronous copies) inside the captured step give the host-driven
+    step's result."""
+    mesh, r, disc, q = setup(D, ctx, "3d_hill_nc", seed=6)
+    ph = D.make_phys(f=1e-4, precision=precision)
+    opts = dict(OPTS, gmres_inner_rtol=1e-4)
+    gh, gg = D.Mesh(ctx, mesh, r), D.Mesh(ctx, mesh, r)
+    for gm in (gh, gg):
+        gm.set_fused_stage(2, 2, 2)
+        gm.set_vmult_tile(precision, 2)
+    qh, qg = dev(q.reshape(5, -1)), dev(q.reshape(5, -1))
+    for _ in range(3):
+        ih = gh.step(ph, qh, 3.0, **opts)
+        ig = gg.step(ph, qg, 3.0, graph=True, **opts)
+        assert list(ig.picard_iters) == list(ih.picard_iters)
+        assert ig.max_relres <= 1e-12
+    a, b = host(qg, q.shape), host(qh, q.shape)
+    for k in range(5):
+        assert relerr(a[k] - q[k], b[k] - q[k]) < 1e-8, (k, relerr(a[k] - q[k], b[k] - q[k]))
+
+
 @pytest.mark.parametrize("variant", ["R2", "R1"])
 def test_graph_step_parity_with_oracle(D, ctx, variant):
     """10 steps of the 2D non-conforming case: 1e-9 relative max-norm."""
