@@ -200,8 +200,8 @@ typedef struct {
                                 significant bits, about 1e-14 relative per
                                 operation), everything else as DG_FP64;
                                 plain FP64 GMRES, no refinement.  Not with
-                                Gauss-Lobatto nodes, far-field faces or
-                                graph mode (DG_ERR_UNSUPPORTED). */
+                                Gauss-Lobatto nodes or graph mode
+                                (DG_ERR_UNSUPPORTED). */
   const double* f_cell;      /* optional device array, one Coriolis parameter
                                 per cell (NULL: f everywhere); lets one mesh
                                 carry several independent instances */

@@ -205,13 +205,14 @@ struct dg_mesh {
   bool gll = false;
   dg::DBuf gl64, gl32;   // GL copies of coefficients (5N) and inputs (5N)
   dg::DBuf far_q, far_q32, farw;   // outer traces (FP64, FP32); predictors with the outer data (4N)
+  dg::DBuf far_qdf;                // outer traces as FP32 pairs (DG_PAIRS)
   // DG_PAIRS (FP64-class vmults on the FP32 pipe): pair copies of the
   // geometry (metric, 1/(w det J), face n dS and dS, per-slot normals), of the
   // frozen coefficients (5N + E) and their face data, and the vmult's x, y
   dg::DBuf Kdf, invMdf, fgeodf, snSdf, cdf, trhdf, pcoefdf, irhodf, pcsdf, irdf;
   int64_t workspace_bytes() const;
   // every workspace buffer, for accounting, release and graph capture checks
-  static constexpr int kBufs = 52;
+  static constexpr int kBufs = 53;
   void bufs(const dg::DBuf** out) const {
     const dg::DBuf* b[kBufs] = {&trc, &slot, &hbuf, &trh, &pcoef, &wv, &gm_V, &gm_work, &red, &st,
                                 &fns, &fs, &trh32, &pcoef32, &c32, &ir32, &irw, &irho, &irho32,
@@ -219,7 +220,7 @@ struct dg_mesh {
                                 &vl_slots, &vl_fac, &vl_scr, &gm_pc, &sponge,
                                 &cb_slots, &cb_inv, &pcs, &pcs32, &snS, &gl64, &gl32, &far_q, &far_q32,
                                 &farw, &Kdf, &invMdf, &fgeodf, &snSdf, &cdf, &trhdf, &pcoefdf, &irhodf,
-                                &pcsdf, &irdf};
+                                &pcsdf, &irdf, &far_qdf};
     for (int i = 0; i < kBufs; ++i) out[i] = b[i];
   }
 };
@@ -259,13 +260,14 @@ struct FaceTopo {
   const float* far_q32;
   int64_t nFar;
   const df64* fgeodf;   // face geometry as FP32 pairs (DG_PAIRS), or null
+  const df64* far_qdf;  // outer traces as FP32 pairs (DG_PAIRS), or null
 };
 
 inline FaceTopo topo(const dg_mesh* m) {
   return FaceTopo{m->fp_minus, m->fp_plus, m->fgeo, m->fgeo32, m->hp_cslot, m->hp_code,
                   m->hc_slot, m->nF, m->nH, m->nHC, m->S, 0,
                   m->nFar > 0 ? m->fp_far : nullptr, m->far_q.as<double>(), m->far_q32.as<float>(), m->nFar,
-                  m->fgeodf.as<df64>()};
+                  m->fgeodf.as<df64>(), m->far_qdf.as<df64>()};
 }
 
 // the face points of the 2:1 faces only (the last nH of the unified list)

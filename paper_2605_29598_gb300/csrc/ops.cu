@@ -111,7 +111,7 @@ static int far_predictors(dg_mesh* m, const ImplK& ph, const T*& mhat, const T*&
 // outer conserved traces at the far points from the trace array
 __global__ void k_far_gather(const int* __restrict__ far_p, const int* __restrict__ fp_minus,
                              const double* __restrict__ trc, int64_t S, int64_t nFar, double* __restrict__ fq,
-                             float* __restrict__ fq32) {
+                             float* __restrict__ fq32, df64* __restrict__ fqdf) {
   const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (g >= nFar) return;
   const int sm = fp_minus[far_p[g]];
@@ -120,6 +120,7 @@ __global__ void k_far_gather(const int* __restrict__ far_p, const int* __restric
     const double v = trc[k * S + sm];
     fq[k * nFar + g] = v;
     fq32[k * nFar + g] = (float)v;
+    fqdf[k * nFar + g] = df64(v);
   }
 }
 
@@ -129,6 +130,7 @@ static int set_far_state(dg_mesh* m, const double* q, cudaStream_t st) {
   if ((rc = m->trc.ensure(sizeof(double) * 5 * m->S)) != DG_OK) return rc;
   if ((rc = m->far_q.ensure(sizeof(double) * 5 * m->nFar)) != DG_OK) return rc;
   if ((rc = m->far_q32.ensure(sizeof(float) * 5 * m->nFar)) != DG_OK) return rc;
+  if ((rc = m->far_qdf.ensure(sizeof(df64) * 5 * m->nFar)) != DG_OK) return rc;
   if (m->gll) {
     if ((rc = gl_buffers<double>(m)) != DG_OK) return rc;
     double* qg = m->gl64.as<double>() + 5 * m->N;
@@ -144,7 +146,8 @@ static int set_far_state(dg_mesh* m, const double* q, cudaStream_t st) {
   k_trace<double, DIM, N, 5><<<trace_grid<DIM, N>(m->E), TraceShape<DIM, N>::THREADS, 0, st>>>(
       in, m->E, m->N, m->trc.as<double>(), m->S, tb);
   k_far_gather<<<grid_for(m->nFar, 128), 128, 0, st>>>(m->far_p, m->fp_minus, m->trc.as<double>(), m->S, m->nFar,
-                                                         m->far_q.as<double>(), m->far_q32.as<float>());
+                                                         m->far_q.as<double>(), m->far_q32.as<float>(),
+                                                         m->far_qdf.as<df64>());
   DG_LAUNCH_CHECK("far-field outer state");
   m->far_set = true;
   return DG_OK;

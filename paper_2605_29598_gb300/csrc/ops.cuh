@@ -30,7 +30,7 @@ template <> __device__ __forceinline__ const df64* geo_ptr<df64>(const FaceTopo&
 template <typename T> __device__ __forceinline__ const T* far_ptr(const FaceTopo& ft);
 template <> __device__ __forceinline__ const double* far_ptr<double>(const FaceTopo& ft) { return ft.far_q; }
 template <> __device__ __forceinline__ const float* far_ptr<float>(const FaceTopo& ft) { return ft.far_q32; }
-template <> __device__ __forceinline__ const df64* far_ptr<df64>(const FaceTopo&) { return nullptr; }
+template <> __device__ __forceinline__ const df64* far_ptr<df64>(const FaceTopo& ft) { return ft.far_qdf; }
 
 // far-point index of boundary face point p (-1: slip wall)
 __device__ __forceinline__ int far_index(const FaceTopo& ft, int64_t p) {

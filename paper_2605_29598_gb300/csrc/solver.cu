@@ -437,8 +437,8 @@ static int schur_pairs_vmult_fn(void* self, const double* x, double* y, cudaStre
 // DG_PAIRS vmult (the FP64 ones stay for the right-hand side and recovery).
 int prepare_pairs(dg_mesh* m, const ImplK& k, const double* rho, const double* plag, const double* ulag,
                   int penalty, cudaStream_t st, SchurDfCtx* out) {
-  if (m->gll || m->nFar > 0) {
-    set_error("DG_PAIRS is not implemented with Gauss-Lobatto nodes or far-field faces");
+  if (m->gll) {
+    set_error("DG_PAIRS is not implemented with Gauss-Lobatto nodes");
     return DG_ERR_UNSUPPORTED;
   }
   int rc;
@@ -947,7 +947,7 @@ extern "C" int dg_mesh_autotune(dg_ctx* ctx, dg_mesh* m, int precision, void* st
     set_error("dg_mesh_autotune: precision must be DG_FP64, DG_MIXED, DG_MIXED_EXPLICIT or DG_PAIRS");
     return DG_ERR_ARG;
   }
-  if (precision == DG_PAIRS && (m->gll || m->nFar > 0)) precision = DG_FP64;   // no pair vmult there
+  if (precision == DG_PAIRS && m->gll) precision = DG_FP64;   // no pair vmult there
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t n = m->N;
   double* buf = nullptr;

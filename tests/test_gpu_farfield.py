@@ -153,6 +153,37 @@ def test_far_steps_match_oracle(D, ctx, name, variant):
     for k in range(5):
         assert relerr(from_dev(qd2, qo.shape)[k], qo[k]) < 1e-9
         assert relerr(from_dev(qd3, qo.shape)[k], qo[k]) < 1e-7
+    # and with the vmults in pairs of FP32 numbers (FP64 GMRES); momentum
+    # against the momentum vector's scale, as in the pair tests
+    qd4 = to_dev(q.reshape(5, -1)).contiguous()
+    for _ in range(4):
+        gm.step(D.make_phys(f=1e-4, variant=variant, precision="pairs"), qd4, 2.0, picard_fixed=2,
+                gmres_rtol=1e-13, gmres_restart=40, gmres_maxit=2000)
+    q4 = from_dev(qd4, qo.shape)
+    mscale = np.abs(qo[1:4]).max()
+    for k in range(5):
+        scale = mscale if 1 <= k <= 3 else np.abs(qo[k]).max()
+        assert np.abs(q4[k] - qo[k]).max() / scale < 1e-9, k
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_far_pairs_vmult(D, ctx, name):
+    """The pair vmult on meshes with far-field faces (every schedule it
+    takes), at the FP64 bar."""
+    mesh, disc, gm, q, _ = make_case(D, ctx, name, seed=3)
+    rng = np.random.default_rng(5)
+    u, p = O.nodal_primitives(q, 1.4)
+    cf = O.StageCoeffs(rho=q[0], p_lag=p, u_lag=u * (1 + 1e-2 * rng.standard_normal(u.shape)), adt=2.5)
+    keep, dcf = dev_coeffs(D, cf)
+    x = p * (1 + 1e-2 * rng.standard_normal(p.shape))
+    for penalty in (True, False):
+        ref = O.schur_apply(disc, cf, O.Phys(f=1.1e-4, penalty=penalty), x)
+        dph = D.make_phys(f=1.1e-4, penalty=penalty, precision="pairs")
+        for stage in (0, 1, 2):
+            gm.set_fused_stage(1, 1, stage)
+            y = from_dev(gm.apply_implicit(dph, dcf, to_dev(x.reshape(-1))), ref.shape)
+            assert relerr(y, ref) < 1e-11, (penalty, stage, relerr(y, ref))
+            assert relerr(y - x, ref - x) < 1e-9
 
 
 def test_uniform_flow_through_far_boundaries_is_steady(D, ctx):
