@@ -203,7 +203,7 @@ struct dg_mesh {
   // run in the Gauss-Legendre basis of the same polynomials and the arrays
   // are converted per cell on the way in and out
   bool gll = false;
-  dg::DBuf gl64, gl32;   // GL copies of coefficients (5N) and inputs (5N)
+  dg::DBuf gl64, gl32, gldf;   // GL copies of coefficients (5N) and inputs (5N): FP64, FP32, pairs
   dg::DBuf far_q, far_q32, farw;   // outer traces (FP64, FP32); predictors with the outer data (4N)
   dg::DBuf far_qdf;                // outer traces as FP32 pairs (DG_PAIRS)
   // DG_PAIRS (FP64-class vmults on the FP32 pipe): pair copies of the
@@ -212,7 +212,7 @@ struct dg_mesh {
   dg::DBuf Kdf, invMdf, fgeodf, snSdf, cdf, trhdf, pcoefdf, irhodf, pcsdf, irdf;
   int64_t workspace_bytes() const;
   // every workspace buffer, for accounting, release and graph capture checks
-  static constexpr int kBufs = 53;
+  static constexpr int kBufs = 54;
   void bufs(const dg::DBuf** out) const {
     const dg::DBuf* b[kBufs] = {&trc, &slot, &hbuf, &trh, &pcoef, &wv, &gm_V, &gm_work, &red, &st,
                                 &fns, &fs, &trh32, &pcoef32, &c32, &ir32, &irw, &irho, &irho32,
@@ -220,7 +220,7 @@ struct dg_mesh {
                                 &vl_slots, &vl_fac, &vl_scr, &gm_pc, &sponge,
                                 &cb_slots, &cb_inv, &pcs, &pcs32, &snS, &gl64, &gl32, &far_q, &far_q32,
                                 &farw, &Kdf, &invMdf, &fgeodf, &snSdf, &cdf, &trhdf, &pcoefdf, &irhodf,
-                                &pcsdf, &irdf, &far_qdf};
+                                &pcsdf, &irdf, &far_qdf, &gldf};
     for (int i = 0; i < kBufs; ++i) out[i] = b[i];
   }
 };

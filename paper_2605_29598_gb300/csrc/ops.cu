@@ -53,7 +53,9 @@ template <> inline DBuf& buf_pcs<df64>(dg_mesh* m) { return m->pcsdf; }
 // becomes G^{-1} (GL inverse mass) on the way out.  Buffer layout per
 // precision: [0, 5N) GL copies of rho, p_lag, u_lag (from prepare), [5N,
 // 10N) GL copies of the other inputs of one call.
-template <typename T> inline DBuf& buf_gl(dg_mesh* m) { return std::is_same<T, float>::value ? m->gl32 : m->gl64; }
+template <typename T> inline DBuf& buf_gl(dg_mesh* m) {
+  return std::is_same<T, float>::value ? m->gl32 : (std::is_same<T, double>::value ? m->gl64 : m->gldf);
+}
 template <typename T>
 inline Mat1D<T> cast_mat(const Mat1D<double>& a) {
   Mat1D<T> o;

@@ -437,10 +437,6 @@ static int schur_pairs_vmult_fn(void* self, const double* x, double* y, cudaStre
 // DG_PAIRS vmult (the FP64 ones stay for the right-hand side and recovery).
 int prepare_pairs(dg_mesh* m, const ImplK& k, const double* rho, const double* plag, const double* ulag,
                   int penalty, cudaStream_t st, SchurDfCtx* out) {
-  if (m->gll) {
-    set_error("DG_PAIRS is not implemented with Gauss-Lobatto nodes");
-    return DG_ERR_UNSUPPORTED;
-  }
   int rc;
   if ((rc = ensure_pairs_geometry(m, st)) != DG_OK) return rc;
   const int64_t n = m->N;
@@ -667,8 +663,8 @@ int imex_ark2_step(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* ph, double* 
   }
   if (m->gll && (opts->graph || opts->gmres.precond != DG_PRECOND_NONE || ph->precision == DG_MIXED_EXPLICIT ||
                  m->sponge_set)) {
-    set_error("imex_ark2_step: Gauss-Lobatto nodes support the host-driven, unpreconditioned step in DG_FP64 "
-              "or DG_MIXED only");
+    set_error("imex_ark2_step: Gauss-Lobatto nodes support the host-driven, unpreconditioned step in DG_FP64, "
+              "DG_MIXED or DG_PAIRS only");
     return DG_ERR_UNSUPPORTED;
   }
   if (opts->graph) return step_graph(m, ph, q, dt, opts, info, st);
@@ -947,7 +943,6 @@ extern "C" int dg_mesh_autotune(dg_ctx* ctx, dg_mesh* m, int precision, void* st
     set_error("dg_mesh_autotune: precision must be DG_FP64, DG_MIXED, DG_MIXED_EXPLICIT or DG_PAIRS");
     return DG_ERR_ARG;
   }
-  if (precision == DG_PAIRS && m->gll) precision = DG_FP64;   // no pair vmult there
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t n = m->N;
   double* buf = nullptr;

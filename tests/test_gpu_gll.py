@@ -102,6 +102,11 @@ def test_gll_schur_operators(D, ctx, name, variant):
     y32 = from_dev(gm.apply_implicit(D.make_phys(f=1.1e-4, variant=variant, precision="mixed"), dcf,
                                      to_dev(x.reshape(-1))), ref.shape)
     assert relerr(y32 - x, ref - x) < 1e-4
+    # in pairs of FP32 numbers: the FP64 bar
+    ydf = from_dev(gm.apply_implicit(D.make_phys(f=1.1e-4, variant=variant, precision="pairs"), dcf,
+                                     to_dev(x.reshape(-1))), ref.shape)
+    assert relerr(ydf, ref) < 1e-11, relerr(ydf, ref)
+    assert relerr(ydf - x, ref - x) < 1e-9
     mhat = q[1:4] * (1 + 1e-3 * rng.standard_normal(q[1:4].shape))
     ehat = q[4] * (1 + 1e-4 * rng.standard_normal(q[4].shape))
     f_w = disc.vol_weak(disc.at_quad(mhat))
@@ -116,7 +121,7 @@ def test_gll_schur_operators(D, ctx, name, variant):
             assert relerr(ug[c], uref[c]) < 1e-10, (c, relerr(ug[c], uref[c]))
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "pairs"])
 @pytest.mark.parametrize("nx", [20, 100])
 def test_gll_steps_match_oracle(D, ctx, precision, nx):
     """Ten ARK2 steps of the 2D inertia-gravity wave (periodic 300 km x 10
@@ -135,7 +140,8 @@ def test_gll_steps_match_oracle(D, ctx, precision, nx):
     qd = to_dev(q.reshape(5, -1)).contiguous()
     dph = D.make_phys(f=case["f"], precision=precision)
     # mixed: FP64 refinement to 1e-12 around FP32 inner solves
-    extra = dict(gmres_inner_rtol=1e-4, gmres_rtol=1e-12) if precision == "mixed" else dict(gmres_rtol=1e-13)
+    extra = {"mixed": dict(gmres_inner_rtol=1e-4, gmres_rtol=1e-12),
+             "pairs": dict(gmres_rtol=1e-12)}.get(precision, dict(gmres_rtol=1e-13))
     qo = q
     for _ in range(10):
         qo = O.imex_ark2_step(disc, ph, qo, case["dt"], opts)
@@ -143,11 +149,16 @@ def test_gll_steps_match_oracle(D, ctx, precision, nx):
     qg = from_dev(qd, qo.shape)
     # FP64: the step parity bar; mixed: FP32 inner solves under FP64
     # refinement to 1e-12 leave relative errors of a few 1e-9 in the small
-    # vertical momentum (itself a perturbation field, so far below 1e-6)
-    bar = 1e-9 if precision == "fp64" else 1e-7
+    # vertical momentum (itself a perturbation field, so far below 1e-6);
+    # pairs: the FP64 bar with the momentum components against the momentum
+    # vector's scale, as in the other pair tests
+    bar = 1e-7 if precision == "mixed" else 1e-9
+    mscale = np.abs(qo[1:4]).max()
     for k in range(5):
         if np.abs(qo[k]).max() > 0:
-            assert relerr(qg[k], qo[k]) < bar, (k, relerr(qg[k], qo[k]))
+            scale = mscale if precision == "pairs" and 1 <= k <= 3 else np.abs(qo[k]).max()
+            err = np.abs(qg[k] - qo[k]).max() / scale
+            assert err < bar, (k, err)
 
 
 def test_gll_unsupported_paths_say_so(D, ctx):

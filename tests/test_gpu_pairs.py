@@ -119,11 +119,11 @@ def test_pairs_steps_match_oracle(D, ctx, precond):
 
 
 def test_pairs_unsupported_paths_say_so(D, ctx):
+    """Graph-mode steps do not take DG_PAIRS."""
     mesh = I.box_mesh((3, 2), (3e3, 2e3))
-    gm = D.Mesh(ctx, mesh, 2, node_set=D.DG_NODES_GLL)
-    n = gm.N
-    t = (torch.ones(n, dtype=torch.float64, device="cuda"), torch.full((n,), 1e5, dtype=torch.float64, device="cuda"),
-         torch.zeros(3 * n, dtype=torch.float64, device="cuda"))
+    disc = O.Discretisation(mesh, 2)
+    gm = D.Mesh(ctx, mesh, 2)
+    q = to_dev(I.stratified_state(disc.node_points()).reshape(5, -1)).contiguous()
     with pytest.raises(D.DGError) as ei:
-        gm.apply_implicit(D.make_phys(precision="pairs"), D.Mesh.coeffs(*t, 1.0), t[0])
+        gm.step(D.make_phys(precision="pairs"), q, 1.0, graph=True)
     assert ei.value.status == -2
