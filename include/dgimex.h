@@ -199,8 +199,7 @@ typedef struct {
                                 of FP32 numbers (hi + lo, about 48
                                 significant bits, about 1e-14 relative per
                                 operation), everything else as DG_FP64;
-                                plain FP64 GMRES, no refinement.  Not in
-                                graph mode (DG_ERR_UNSUPPORTED). */
+                                plain FP64 GMRES, no refinement. */
   const double* f_cell;      /* optional device array, one Coriolis parameter
                                 per cell (NULL: f everywhere); lets one mesh
                                 carry several independent instances */

@@ -555,7 +555,8 @@ int capture_step(dg_mesh* m, const dg_phys* ph, double* q, double dt, const dg_s
   double* pnew = ws + 17 * n;
   double* rhs = ws + 18 * n;
   const unsigned gb = grid_for(n, 256);
-  const bool mixed = ph->precision != DG_FP64;
+  const bool pairs = ph->precision == DG_PAIRS;
+  const bool mixed = ph->precision != DG_FP64 && !pairs;
   const bool incr = ph->precision == DG_MIXED_EXPLICIT && !m->bg_set;
   const PhysK pk{ph->gamma, ph->g, ph->f, ph->f_cell, ph->lambda_min};
   const bool pc = o->gmres.precond != DG_PRECOND_NONE;
@@ -605,6 +606,12 @@ int capture_step(dg_mesh* m, const dg_phys* ph, double* q, double dt, const dg_s
           return rc;
         k_acc_solve<<<1, 1, 0, sp>>>(wk.ss, nullptr, wk.ir);
       } else {
+        // DG_PAIRS: the same FP64 GMRES around the pair vmult
+        SchurDfCtx sdf;
+        if (pairs) {
+          if ((rc = prepare_pairs(m, k, rho, p, u, ph->penalty, sp, &sdf)) != DG_OK) return rc;
+          A = make_vmult_pairs(&sdf);
+        }
         if ((rc = capture_gmres(m, wk, wk.gs64, A, rhs, pnew, false, o->gmres.rtol, o->gmres.maxit,
                                 o->gmres.restart, nullptr, nullptr, s + 1, pc)) != DG_OK)
           return rc;
@@ -656,7 +663,7 @@ size_t make_key(const dg_mesh* m, const dg_phys* ph, const double* q, double dt,
     int picard_maxit, picard_fixed;
     double rtol, inner_rtol;
     int restart, maxit, precond;
-    int tile[K_COUNT], tile32[K_COUNT];
+    int tile[K_COUNT], tile32[K_COUNT], tilep[K_COUNT], fused_stage[3];
     const void* bp[dg_mesh::kBufs];
     size_t bb[dg_mesh::kBufs];
   } k;
@@ -685,7 +692,9 @@ size_t make_key(const dg_mesh* m, const dg_phys* ph, const double* q, double dt,
   for (int i = 0; i < K_COUNT; ++i) {
     k.tile[i] = m->tile[i];
     k.tile32[i] = m->tile32[i];
+    k.tilep[i] = m->tilep[i];
   }
+  for (int i = 0; i < 3; ++i) k.fused_stage[i] = m->fused_stage[i];
   const DBuf* b[dg_mesh::kBufs];
   m->bufs(b);
   for (int i = 0; i < dg_mesh::kBufs; ++i) {

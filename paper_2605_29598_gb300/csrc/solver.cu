@@ -657,10 +657,6 @@ int imex_ark2_step(dg_ctx* ctx, const dg_mesh* mesh, const dg_phys* ph, double* 
     set_error("imex_ark2_step: DG_MIXED_EXPLICIT is not implemented with far-field faces");
     return DG_ERR_UNSUPPORTED;
   }
-  if (opts->graph && ph->precision == DG_PAIRS) {
-    set_error("imex_ark2_step: DG_PAIRS runs host-driven steps only (graph = 0)");
-    return DG_ERR_UNSUPPORTED;
-  }
   if (m->gll && (opts->graph || opts->gmres.precond != DG_PRECOND_NONE || ph->precision == DG_MIXED_EXPLICIT ||
                  m->sponge_set)) {
     set_error("imex_ark2_step: Gauss-Lobatto nodes support the host-driven, unpreconditioned step in DG_FP64, "

@@ -60,7 +60,7 @@ def setup(D, ctx, name, seed=5):
 OPTS = dict(picard_fixed=2, gmres_rtol=1e-12, gmres_restart=50, gmres_maxit=400)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "pairs"])
 @pytest.mark.parametrize("name", ["2d_nc", "3d_hill_nc"])
 def test_graph_step_matches_host_step(D, ctx, name, precision):
     mesh, r, disc, q = setup(D, ctx, name)
@@ -84,7 +84,7 @@ def test_graph_step_matches_host_step(D, ctx, name, precision):
         assert relerr(a[k], b[k]) < 1e-10
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", ["fp64", "mixed", "pairs"])
 def test_graph_step_with_line_schedule(D, ctx, precision):
     """The one-thread-per-x-line vmult passes (schedule 2, with their
     asynchronous copies) inside the captured step give the host-driven

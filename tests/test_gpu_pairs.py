@@ -116,14 +116,3 @@ def test_pairs_steps_match_oracle(D, ctx, precond):
         scale = mscale if 1 <= k <= 3 else np.abs(qo[k]).max()
         err = np.abs(qg[k] - qo[k]).max() / scale
         assert err < 1e-9, (k, err)
-
-
-def test_pairs_unsupported_paths_say_so(D, ctx):
-    """Graph-mode steps do not take DG_PAIRS."""
-    mesh = I.box_mesh((3, 2), (3e3, 2e3))
-    disc = O.Discretisation(mesh, 2)
-    gm = D.Mesh(ctx, mesh, 2)
-    q = to_dev(I.stratified_state(disc.node_points()).reshape(5, -1)).contiguous()
-    with pytest.raises(D.DGError) as ei:
-        gm.step(D.make_phys(precision="pairs"), q, 1.0, graph=True)
-    assert ei.value.status == -2
