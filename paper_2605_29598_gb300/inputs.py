@@ -20,7 +20,7 @@ Conventions (shared by every consumer of these lists):
   bit ``t`` of ``subface`` says which half along the ``t``-th tangential
   direction (tangential directions in increasing order).
 * Boundary face row ``[e, f, bc]`` with ``bc = BC_WALL`` (or ``BC_FARFIELD``,
-  see ``with_boundary``; the oracle supports it, the CUDA library not yet).
+  see ``with_boundary``; the oracle and the CUDA library support it).
 * Physical coordinates are (x, z) in 2D (vertical x-z slice) and (x, y, z)
   in 3D; the vertical is always the last coordinate.
 
