@@ -233,10 +233,12 @@ constexpr int line_epb(int M) {
 // kLineReg32 registers per thread (more resident warps hide the load
 // latency that binds these kernels), the 8-byte types up to 255
 constexpr int kLineReg32 = 80;
-template <typename T, int EPB>
+template <typename T, int EPB, int REG32 = kLineReg32>
 struct LineOcc {
-  static constexpr int MIN_BLOCKS = sizeof(T) == 4 ? 65536 / (kLineReg32 * EPB * 16) : 256 / (EPB * 16);
+  static constexpr int MIN_BLOCKS = sizeof(T) == 4 ? 65536 / (REG32 * EPB * 16) : 256 / (EPB * 16);
 };
+// the divergence pass holds fewer values per thread
+constexpr int kLineReg32Div = 72;
 
 // Gradient pass (VMULT): w = rho^{-1} (I + beta J)^{-1} G (R2) or G / rho
 // (R1); y = x + pen - (gamma-1) a_dt^2 g G_z (R2).  Same arguments and
@@ -460,7 +462,7 @@ k_grad_lines(const T* __restrict__ x, const int* __restrict__ cface, const T* __
 // rho w . grad(psi) + {h rho w}.n dS (zero on walls)]; h rho face values
 // from the per-slot traces trh (as k_div_fused).
 template <typename T, int EPB>
-__global__ void __launch_bounds__(LineShape<EPB>::THREADS, LineOcc<T, EPB>::MIN_BLOCKS)
+__global__ void __launch_bounds__(LineShape<EPB>::THREADS, LineOcc<T, EPB, kLineReg32Div>::MIN_BLOCKS)
 k_div_lines(Fields<T> wv, const T* __restrict__ gin, const int* __restrict__ cface, const T* __restrict__ plag,
             CellGeo<T> geo, const T* __restrict__ slot, int E, Tables<T> tb, ImplK ph, T* __restrict__ y) {
   using LS = LineShape<EPB>;
