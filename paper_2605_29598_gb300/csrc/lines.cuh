@@ -42,6 +42,9 @@ struct LineShape {
   static constexpr int EPB = EPB_;
   static constexpr int PL = N * N + 4;   // padded z-plane stride of a staged cell
   static constexpr int CSZ = N * PL;     // staged cell
+  // staged flux components, read as 128-bit rows only (conflict-free
+  // without padding)
+  static constexpr int FPL = N * N, FSZ = N * FPL;
   static constexpr int THREADS = EPB * NFP;
 };
 
@@ -252,9 +255,10 @@ k_grad_lines(const T* __restrict__ x, const int* __restrict__ cface, const T* __
              const T* __restrict__ trh, T* __restrict__ gout) {
   using LS = LineShape<EPB>;
   constexpr int N = LS::N, NP = LS::NP, NFP = LS::NFP, NF = LS::NF, NSL = LS::NSL, PL = LS::PL, CSZ = LS::CSZ;
+  constexpr int FPL = LS::FPL, FSZ = LS::FSZ;
   __shared__ __align__(16) T sx[EPB][CSZ];
   // -x K_ab staged for the y and z contractions: (a, b) = (2, 0), (1, 1), (2, 1), (2, 2)
-  __shared__ __align__(16) T sF[EPB][4][CSZ];
+  __shared__ __align__(16) T sF[EPB][4][FSZ];
   __shared__ __align__(16) T slf[EPB][4][4][NFP];   // lift values of faces 2..5, fields 0..3
   // per face: the penalty coefficient and the neighbour's line through the
   // thread's point, each thread's own (asynchronous copies)
@@ -319,7 +323,7 @@ k_grad_lines(const T* __restrict__ x, const int* __restrict__ cface, const T* __
     for (int j = 0; j < 4; ++j) {
 #pragma unroll
       for (int k = 0; k < N; ++k) F[k] = -xl[k] * Kt[j == 0 ? 2 : (j == 1 ? 1 : j + 1)][k];
-      st4<T>(&sF[c][j][N * jy + PL * jz], F);
+      st4<T>(&sF[c][j][N * jy + FPL * jz], F);
     }
   }
   // the thread's point of every face (its copies have landed)
@@ -361,10 +365,10 @@ k_grad_lines(const T* __restrict__ x, const int* __restrict__ cface, const T* __
   for (int k = 0; k < N; ++k) {
     const T dy = stb.D[k][jy], dz = stb.D[k][jz];
     T v1[N], v0[N], v2[N], v3[N];
-    ld4s<T>(&sF[c][1][N * k + PL * jz], v1);
-    ld4s<T>(&sF[c][0][N * jy + PL * k], v0);
-    ld4s<T>(&sF[c][2][N * jy + PL * k], v2);
-    ld4s<T>(&sF[c][3][N * jy + PL * k], v3);
+    ld4s<T>(&sF[c][1][N * k + FPL * jz], v1);
+    ld4s<T>(&sF[c][0][N * jy + FPL * k], v0);
+    ld4s<T>(&sF[c][2][N * jy + FPL * k], v2);
+    ld4s<T>(&sF[c][3][N * jy + FPL * k], v3);
 #pragma unroll
     for (int ix = 0; ix < N; ++ix) {
       r[0][ix] += dz * v0[ix];
@@ -466,8 +470,8 @@ __global__ void __launch_bounds__(LineShape<EPB>::THREADS, LineOcc<T, EPB, kLine
 k_div_lines(Fields<T> wv, const T* __restrict__ gin, const int* __restrict__ cface, const T* __restrict__ plag,
             CellGeo<T> geo, const T* __restrict__ slot, int E, Tables<T> tb, ImplK ph, T* __restrict__ y) {
   using LS = LineShape<EPB>;
-  constexpr int N = LS::N, NP = LS::NP, NFP = LS::NFP, NF = LS::NF, NSL = LS::NSL, PL = LS::PL, CSZ = LS::CSZ;
-  __shared__ __align__(16) T sF[EPB][2][CSZ];    // -h rho (K w)_a of directions a = 1, 2
+  constexpr int N = LS::N, NP = LS::NP, NFP = LS::NFP, NF = LS::NF, NSL = LS::NSL, FPL = LS::FPL, FSZ = LS::FSZ;
+  __shared__ __align__(16) T sF[EPB][2][FSZ];    // -h rho (K w)_a of directions a = 1, 2
   __shared__ __align__(16) T slf[EPB][4][NFP];   // lift values of faces 2..5
   // per face point: g = (h rho w . n dS) of this side and of the neighbour,
   // written by the gradient pass (asynchronous copies, each thread its own)
@@ -535,8 +539,8 @@ k_div_lines(Fields<T> wv, const T* __restrict__ gin, const int* __restrict__ cfa
 #pragma unroll
       for (int k = 0; k < N; ++k) r[ix] += tb.D[k][ix] * F0[k];
     }
-    st4<T>(&sF[c][0][N * jy + PL * jz], F1);
-    st4<T>(&sF[c][1][N * jy + PL * jz], F2);
+    st4<T>(&sF[c][0][N * jy + FPL * jz], F1);
+    st4<T>(&sF[c][1][N * jy + FPL * jz], F2);
   }
   // face fluxes -{h rho w}.n dS = -(g_own - g_neighbour) / 2 (the two sides'
   // normals are negatives of each other); far field: the linear part
@@ -562,8 +566,8 @@ k_div_lines(Fields<T> wv, const T* __restrict__ gin, const int* __restrict__ cfa
   for (int k = 0; k < N; ++k) {
     const T dy = stb.D[k][jy], dz = stb.D[k][jz];
     T vy[N], vz[N];
-    ld4s<T>(&sF[c][0][N * k + PL * jz], vy);
-    ld4s<T>(&sF[c][1][N * jy + PL * k], vz);
+    ld4s<T>(&sF[c][0][N * k + FPL * jz], vy);
+    ld4s<T>(&sF[c][1][N * jy + FPL * k], vz);
 #pragma unroll
     for (int ix = 0; ix < N; ++ix) r[ix] += dy * vy[ix] + dz * vz[ix];
   }
