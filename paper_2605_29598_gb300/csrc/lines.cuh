@@ -233,14 +233,15 @@ constexpr int line_epb(int M) {
 }
 
 // resident blocks per SM asked of the register allocator: FP32 at most
-// kLineReg32 registers per thread (more resident warps hide the load
-// latency that binds these kernels), the 8-byte types up to 255
+// REG32 registers per thread (more resident warps hide the load latency
+// that binds these kernels; 80 in the gradient pass, 72 in the lighter
+// divergence pass, the most each fits without spilling), the 8-byte types
+// up to 255
 constexpr int kLineReg32 = 80;
 template <typename T, int EPB, int REG32 = kLineReg32>
 struct LineOcc {
   static constexpr int MIN_BLOCKS = sizeof(T) == 4 ? 65536 / (REG32 * EPB * 16) : 256 / (EPB * 16);
 };
-// the divergence pass holds fewer values per thread
 constexpr int kLineReg32Div = 72;
 
 // Gradient pass (VMULT): w = rho^{-1} (I + beta J)^{-1} G (R2) or G / rho
@@ -265,7 +266,6 @@ k_grad_lines(const T* __restrict__ x, const int* __restrict__ cface, const T* __
   __shared__ T spen[EPB][NF][NFP];
   __shared__ __align__(16) T snb[EPB][NF][NFP][4];
   __shared__ T shm[EPB][NF][NFP];                   // own h rho traces (for gout)
-
   __shared__ __align__(16) T stc[std::is_same<T, float>::value ? EPB : 1][16];
   __shared__ SharedTables<T, N> stb;
   __shared__ T sxw[2 * N];
@@ -463,8 +463,9 @@ k_grad_lines(const T* __restrict__ x, const int* __restrict__ cface, const T* __
 }
 
 // Divergence pass (VMULT): y -= (gamma-1) a_dt^2 Div, Div = M^{-1}[-int h
-// rho w . grad(psi) + {h rho w}.n dS (zero on walls)]; h rho face values
-// from the per-slot traces trh (as k_div_fused).
+// rho w . grad(psi) + {h rho w}.n dS (zero on walls)], h rho = gamma p_lag /
+// (gamma - 1); the central face flux from the per-slot g = (h rho)- (w- .
+// n dS) that the gradient pass writes, this side's and the neighbour's.
 template <typename T, int EPB>
 __global__ void __launch_bounds__(LineShape<EPB>::THREADS, LineOcc<T, EPB, kLineReg32Div>::MIN_BLOCKS)
 k_div_lines(Fields<T> wv, const T* __restrict__ gin, const int* __restrict__ cface, const T* __restrict__ plag,
