@@ -143,8 +143,9 @@ int dg_mesh_info(const dg_mesh* mesh, dg_mesh_stats* out);
 /* Schedule autotuner (not in the paper): times the explicit operator's
  * cell kernel with 1, 2 and 4 times the base number of cells per thread
  * block, and whole Schur vmults with every fused-kernel schedule (see
- * dg_mesh_set_fused_stage; schedule 2 with 1, 2 and 4 times its base cells
- * per block), on this mesh (synthetic coefficients, CUDA
+ * dg_mesh_set_fused_stage; schedule 2, on three-dimensional degree-3
+ * terrain-following meshes, with 1, 2 and 4 times its base cells per
+ * block), on this mesh (synthetic coefficients, CUDA
  * events), and keeps the fastest, for FP64 and, when precision is DG_MIXED
  * or DG_MIXED_EXPLICIT, for the FP32 vmult too, when it is DG_PAIRS for the
  * FP32-pair vmult.  Allocates temporary device memory; synchronises

@@ -881,7 +881,7 @@ static int tune_precision(dg_mesh* m, int prec, const double* q, const double* r
   // thread per x-line with 1, 2 or 4 times the base cells per block
   struct Cand { int sched, tile; };
   Cand cand[5] = {{0, 1}, {1, 1}, {2, 1}, {2, 2}, {2, 4}};
-  const int ncand = (m->dim == 3 && m->n == 4) ? 5 : 2;
+  const int ncand = (m->dim == 3 && m->n == 4 && m->terrain) ? 5 : 2;   // where schedule 2 runs
   rc = DG_OK;
   for (int ci = 0; ci < ncand && rc == DG_OK; ++ci) {
     const int sv = cand[ci].sched;
